@@ -1,0 +1,374 @@
+"""Pins of the CPU oracle against mathematics it does not compute itself.
+
+Each test checks the oracle against something fixed outside it: closed forms
+of the Legendre polynomials and of the small Lobatto rules, high-precision
+roots from mpmath, quadrature exactness, brute-force Kronecker products built
+here from numpy's Legendre evaluation, Parseval's identity, exact rational
+arithmetic for the step exponent, and the special cases of the method (tau = 0
+lossless, tau >= 1, zero blocks, single modes, constants).  The method is the
+lossy SEM compression of arXiv 2407.20731, Sec. IV-B.
+"""
+import math
+from fractions import Fraction
+
+import mpmath
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+LX_ALL = list(range(2, 17))
+
+
+# --------------------------------------------------------------- Legendre
+
+@pytest.mark.parametrize("x", [-1.0, -0.73, -0.2, 0.0, 0.31, 0.5, 0.999, 1.0])
+def test_legendre_closed_forms(x):
+    closed = {
+        0: 1.0,
+        1: x,
+        2: (3 * x**2 - 1) / 2,
+        3: (5 * x**3 - 3 * x) / 2,
+        4: (35 * x**4 - 30 * x**2 + 3) / 8,
+        5: (63 * x**5 - 70 * x**3 + 15 * x) / 8,
+    }
+    for k, v in closed.items():
+        assert oracle.legendre(k, x) == pytest.approx(v, abs=1e-15)
+
+
+def test_legendre_end_value_and_parity():
+    for k in range(0, 17):
+        assert oracle.legendre(k, 1.0) == pytest.approx(1.0, abs=1e-14)
+        for x in (0.13, 0.57, 0.91):
+            assert oracle.legendre(k, -x) == pytest.approx((-1) ** k * oracle.legendre(k, x), abs=1e-14)
+
+
+# ------------------------------------------------------------- GLL rule
+
+def test_gll_closed_forms():
+    s5, s37 = math.sqrt(0.2), math.sqrt(3.0 / 7.0)
+    a, b = math.sqrt(1 / 3 - 2 * math.sqrt(7) / 21), math.sqrt(1 / 3 + 2 * math.sqrt(7) / 21)
+    r7 = math.sqrt(7)
+    table = {
+        2: ([-1, 1], [1, 1]),
+        3: ([-1, 0, 1], [1 / 3, 4 / 3, 1 / 3]),
+        4: ([-1, -s5, s5, 1], [1 / 6, 5 / 6, 5 / 6, 1 / 6]),
+        5: ([-1, -s37, 0, s37, 1], [1 / 10, 49 / 90, 32 / 45, 49 / 90, 1 / 10]),
+        6: ([-1, -b, -a, a, b, 1],
+            [1 / 15, (14 - r7) / 30, (14 + r7) / 30, (14 + r7) / 30, (14 - r7) / 30, 1 / 15]),
+    }
+    for lx, (xs, ws) in table.items():
+        x, w = oracle.gll(lx)
+        np.testing.assert_allclose(x, xs, rtol=0, atol=2e-15)
+        np.testing.assert_allclose(w, ws, rtol=0, atol=2e-15)
+
+
+@pytest.mark.parametrize("lx", LX_ALL)
+def test_gll_nodes_match_high_precision_roots(lx):
+    """Interior nodes are the roots of P_N' (mpmath at 40 digits)."""
+    N = lx - 1
+    x, w = oracle.gll(lx)
+    mpmath.mp.dps = 40
+    if N >= 2:
+        # coefficients of P_N' from the Legendre power-series coefficients
+        coeffs = np.polynomial.legendre.leg2poly([0] * N + [1])
+        dcoef = [mpmath.mpf(int(round(c * 2**N))) / 2**N for c in coeffs]
+        deriv = [k * dcoef[k] for k in range(1, N + 1)]
+        roots = sorted(float(mpmath.re(r)) for r in mpmath.polyroots(deriv[::-1], maxsteps=200, extraprec=200))
+        np.testing.assert_allclose(x[1:-1], roots, rtol=0, atol=1e-14)
+    assert x[0] == -1.0 and x[-1] == 1.0
+    # weights: w_j = 2 / (N (N+1) P_N(x_j)^2), P_N evaluated by mpmath
+    for j in range(lx):
+        pn = mpmath.legendre(N, mpmath.mpf(x[j]))
+        assert w[j] == pytest.approx(float(2 / (N * (N + 1) * pn**2)), rel=1e-14)
+
+
+@pytest.mark.parametrize("lx", LX_ALL)
+def test_gll_quadrature_exactness(lx):
+    """Exact for x^d, d <= 2N-1; not exact at d = 2N (that is what makes it the
+    Lobatto rule and not a Gauss rule)."""
+    N = lx - 1
+    x, w = oracle.gll(lx)
+    assert w.sum() == pytest.approx(2.0, abs=1e-14)
+    for d in range(0, 2 * N):
+        exact = 0.0 if d % 2 else 2.0 / (d + 1)
+        assert np.dot(w, x**d) == pytest.approx(exact, abs=2e-14)
+    d = 2 * N
+    assert abs(np.dot(w, x**d) - 2.0 / (d + 1)) > 1e-10
+
+
+# ----------------------------------------------------------- basis tables
+
+def _indep_basis(lx):
+    """Phi and A built here: nodes from mpmath roots, orthonormal Legendre
+    from numpy's legval, gamma_N = 2/N for the top mode."""
+    N = lx - 1
+    x, w = oracle.gll(lx)  # nodes/weights already pinned above
+    phi = np.zeros((lx, lx))
+    for k in range(lx):
+        c = np.zeros(k + 1)
+        c[k] = 1.0
+        gamma = 2.0 / (2 * k + 1) if k < N else 2.0 / N
+        phi[:, k] = np.polynomial.legendre.legval(x, c) / math.sqrt(gamma)
+    return phi, phi.T * w[None, :], w
+
+
+@pytest.mark.parametrize("lx", LX_ALL)
+def test_basis_tables_against_numpy_legval(lx):
+    phi, amat = oracle.tables(lx)
+    phi_i, amat_i, _ = _indep_basis(lx)
+    np.testing.assert_allclose(phi, phi_i, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(amat, amat_i, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("lx", LX_ALL)
+def test_basis_discrete_orthonormality(lx):
+    phi, amat = oracle.tables(lx)
+    _, w = oracle.gll(lx)
+    g = phi.T @ np.diag(w) @ phi
+    assert np.abs(g - np.eye(lx)).max() <= 1e-13
+    assert np.abs(amat @ phi - np.eye(lx)).max() <= 1e-13
+
+
+# -------------------------------------------------------------- transform
+
+@pytest.mark.parametrize("lx", [2, 3, 4, 5])
+def test_forward_matches_bruteforce_kronecker(lx):
+    rng = np.random.default_rng(lx)
+    _, amat_i, _ = _indep_basis(lx)
+    K = np.kron(np.kron(amat_i, amat_i), amat_i)  # K[(r,q,p),(k,j,i)]
+    for _ in range(4):
+        u = rng.normal(size=(lx, lx, lx))
+        a = oracle.forward(lx, u)
+        np.testing.assert_allclose(a.reshape(-1), K @ u.reshape(-1), rtol=0, atol=1e-13)
+        phi_i, _, _ = _indep_basis(lx)
+        Kinv = np.kron(np.kron(phi_i, phi_i), phi_i)
+        np.testing.assert_allclose(oracle.inverse(lx, a).reshape(-1), Kinv @ a.reshape(-1),
+                                   rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("lx", [3, 6, 8, 10])
+def test_single_mode_input(lx):
+    phi_i, _, _ = _indep_basis(lx)
+    rng = np.random.default_rng(100 + lx)
+    for _ in range(6):
+        p, q, r = rng.integers(0, lx, size=3)
+        u = np.einsum("k,j,i->kji", phi_i[:, r], phi_i[:, q], phi_i[:, p])
+        a = oracle.forward(lx, u).reshape(-1)
+        m = p + lx * (q + lx * r)
+        e = np.zeros(lx**3)
+        e[m] = 1.0
+        np.testing.assert_allclose(a, e, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("lx", [2, 5, 8, 10])
+def test_constant_input(lx):
+    c = 1.7
+    a = oracle.forward(lx, np.full((lx, lx, lx), c)).reshape(-1)
+    assert a[0] == pytest.approx(c * 2**1.5, rel=1e-14)
+    assert np.abs(a[1:]).max() <= 1e-14
+
+
+@pytest.mark.parametrize("lx", LX_ALL)
+def test_forward_inverse_identity_and_parseval(lx):
+    rng = np.random.default_rng(7 * lx)
+    _, w = oracle.gll(lx)
+    W3 = np.einsum("k,j,i->kji", w, w, w)
+    for _ in range(3):
+        u = rng.normal(size=(lx, lx, lx)) * rng.uniform(0.1, 10)
+        a = oracle.forward(lx, u)
+        back = oracle.inverse(lx, a)
+        assert np.abs(back - u).max() <= 1e-13 * np.abs(u).max()
+        assert abs((W3 * u * u).sum() - (a * a).sum()) <= 1e-13 * (a * a).sum()
+
+
+# --------------------------------------------------- truncation / quantisation
+
+def _case(ne=64, lx=8, seed=3, nf=1):
+    f, j = synth.snapshot(ne, lx, [seed + i for i in range(nf)])
+    return f.numpy().reshape(nf, ne, -1), j.numpy()
+
+
+def test_lossless_at_tau_zero():
+    f, j = _case(ne=27, lx=6)
+    r = oracle.reduce(f, j, 0.0)
+    s = oracle.sections(r.payload)
+    assert s["header"]["flags"] & oracle.FLAG_LOSSLESS
+    assert s["masks"].all()
+    assert (s["counts"] == 6**3).all()
+    np.testing.assert_array_equal(s["codes"], r.coeffs.reshape(-1))
+    assert np.abs(r.recon - f).max() <= 1e-13 * np.abs(f).max()
+    assert r.n_fragile == 0
+
+
+def test_bruteforce_mask_codes_tiny():
+    """lx = 2 and 3: mask, steps and codes recomputed here from Kronecker
+    coefficients and exact rational step exponents."""
+    for lx in (2, 3):
+        rng = np.random.default_rng(lx)
+        ne = 40
+        f = rng.normal(size=(1, ne, lx**3)) * rng.uniform(0.01, 100, size=(1, ne, 1))
+        j = rng.uniform(0.5, 2.0, size=ne)
+        tau = 0.05
+        r = oracle.reduce(f, j, tau)
+        s = oracle.sections(r.payload)
+        _, amat_i, _ = _indep_basis(lx)
+        K = np.kron(np.kron(amat_i, amat_i), amat_i)
+        pos = 0
+        for e in range(ne):
+            a = K @ f[0, e]
+            S = float(np.sum(a * a))
+            t = tau * S
+            keep = a * a >= t
+            fr = set(map(tuple, r.fragile[:, 1:3].tolist()))
+            if any((e, m) in fr for m in range(lx**3)) or (e, -1) in fr:
+                pos += int(s["counts"][0, e])
+                continue
+            np.testing.assert_array_equal(s["masks"][0, e], keep)
+            # s = floor(log2 sqrt(t)) exactly: 4^s <= t < 4^(s+1)
+            sv = int(s["steps"][0, e])
+            T = Fraction(t)
+            assert Fraction(4) ** sv <= T < Fraction(4) ** (sv + 1)
+            q = 2.0**sv
+            codes = np.rint(a[keep] / q)
+            np.testing.assert_array_equal(s["codes"][pos:pos + keep.sum()], codes)
+            pos += int(keep.sum())
+
+
+def test_step_exponent_exact_rational():
+    f, j = _case(ne=125, lx=8, seed=5)
+    for tau in (1e-2, 1e-3, 3.7e-5):
+        r = oracle.reduce(f, j, tau)
+        s = oracle.sections(r.payload)
+        flagged = {int(e) for e, m, k in r.fragile[:, 1:4] if m == -1}
+        for e in range(125):
+            if e in flagged:
+                continue
+            S = 0.0
+            for v in r.coeffs[0, e]:
+                S += v * v
+            T = Fraction(tau * S)
+            sv = int(s["steps"][0, e])
+            assert Fraction(4) ** sv <= T < Fraction(4) ** (sv + 1)
+
+
+def test_code_magnitude_bounds():
+    f, j = _case(ne=125, lx=8, seed=9)
+    for tau in (1e-1, 1e-3, 1e-6):
+        r = oracle.reduce(f, j, tau)
+        s = oracle.sections(r.payload)
+        c = np.abs(s["codes"].astype(np.int64))
+        assert c.min() >= 1
+        assert c.max() <= 2.0 / math.sqrt(tau)
+
+
+def test_mask_monotone_in_tau():
+    f, j = _case(ne=64, lx=8, seed=11)
+    prev = None
+    for tau in (1e-6, 1e-5, 1e-4, 1e-3, 1e-2, 1e-1):
+        m = oracle.sections(oracle.reduce(f, j, tau).payload)["masks"]
+        if prev is not None:
+            assert not np.any(m & ~prev)
+        prev = m
+
+
+def test_tau_at_or_above_one():
+    lx = 6
+    f, j = _case(ne=27, lx=lx, seed=13)
+    r = oracle.reduce(f, j, 1.5)
+    assert oracle.sections(r.payload)["counts"].sum() == 0
+    phi_i, _, _ = _indep_basis(lx)
+    u = 3.0 * np.einsum("k,j,i->kji", phi_i[:, 2], phi_i[:, 1], phi_i[:, 4]).reshape(1, 1, -1)
+    r = oracle.reduce(u, np.array([1.3]), 0.999)
+    s = oracle.sections(r.payload)
+    assert s["counts"][0, 0] == 1 and s["masks"][0, 0, 4 + lx * (1 + lx * 2)]
+
+
+def test_zero_block():
+    lx = 8
+    f = np.zeros((1, 3, lx**3))
+    f[0, 1] = 1e-3 * np.arange(lx**3)
+    r = oracle.reduce(f, np.ones(3), 1e-3)
+    s = oracle.sections(r.payload)
+    assert s["counts"][0, 0] == 0 and s["steps"][0, 0] == -32768
+    assert s["counts"][0, 2] == 0 and s["steps"][0, 2] == -32768
+    assert np.all(r.recon[0, 0] == 0.0) and np.all(r.elem_report[0, 0] == 0.0)
+
+
+def test_code_width_switch():
+    f, j = _case(ne=8, lx=6, seed=17)
+    assert oracle.parse_header(oracle.reduce(f, j, 1e-8).payload)["flags"] == 0
+    h = oracle.parse_header(oracle.reduce(f, j, 1e-9).payload)
+    assert h["flags"] & oracle.FLAG_CODE32
+
+
+# -------------------------------------------------------------- error norms
+
+def test_nodal_error_equals_modal_parseval():
+    f, j = _case(ne=64, lx=8, seed=19, nf=2)
+    tau = 1e-3
+    r = oracle.reduce(f, j, tau)
+    s = oracle.sections(r.payload)
+    a = r.coeffs
+    # a~ from the payload: codes times 2^s at the kept modes
+    at = np.zeros_like(a)
+    pos = 0
+    for fi in range(2):
+        for e in range(64):
+            m = s["masks"][fi, e]
+            n = int(m.sum())
+            at[fi, e, m] = np.ldexp(s["codes"][pos:pos + n].astype(np.float64), int(s["steps"][fi, e]))
+            pos += n
+    modal = j[None, :] * ((a - at) ** 2).sum(axis=2)
+    np.testing.assert_allclose(r.elem_report[:, :, 0], modal, rtol=1e-12, atol=0)
+    energy = j[None, :] * (a * a).sum(axis=2)
+    np.testing.assert_allclose(r.elem_report[:, :, 1], energy, rtol=1e-12)
+    # and the truncation/quantisation bound
+    S = (a * a).sum(axis=2)
+    q = np.ldexp(1.0, s["steps"].astype(np.int64))
+    kept = s["counts"].astype(np.float64)
+    bound = j[None, :] * ((512 - kept) * tau * S + kept * q * q / 4)
+    assert np.all(r.elem_report[:, :, 0] <= bound * (1 + 1e-12))
+    # Linf is the unweighted nodal max
+    np.testing.assert_array_equal(r.elem_report[:, :, 2], np.abs(f - r.recon).max(axis=2))
+
+
+def test_field_norms_from_element_rows():
+    f, j = _case(ne=64, lx=6, seed=23, nf=3)
+    r = oracle.reduce(f, j, 1e-4)
+    er, fr = r.elem_report, r.field_report
+    se2, sen = er[:, :, 0].sum(axis=1), er[:, :, 1].sum(axis=1)
+    np.testing.assert_allclose(fr[:, 0], np.sqrt(se2), rtol=1e-13)
+    np.testing.assert_allclose(fr[:, 1], np.sqrt(se2 / sen), rtol=1e-13)
+    np.testing.assert_array_equal(fr[:, 2], er[:, :, 2].max(axis=1))
+    np.testing.assert_array_equal(fr[:, 6], np.abs(f).max(axis=(1, 2)))
+    np.testing.assert_allclose(fr[:, 3], fr[:, 2] / fr[:, 6], rtol=1e-15)
+
+
+# ------------------------------------------------------------------ payload
+
+@pytest.mark.parametrize("lx,nf,ne,tau", [(8, 1, 64, 1e-3), (6, 3, 50, 1e-2), (10, 2, 9, 1e-5), (8, 2, 5, 0.0)])
+def test_payload_roundtrip_and_size(lx, nf, ne, tau):
+    f, j = _case(ne=ne, lx=lx, seed=29, nf=nf)
+    r = oracle.reduce(f, j, tau)
+    h = oracle.parse_header(r.payload)
+    assert (h["lx"], h["n_fields"], h["n_elem"], h["tau"]) == (lx, nf, ne, tau)
+    s = oracle.sections(r.payload)
+    assert h["code_total"] == int(s["counts"].astype(np.int64).sum())
+    np.testing.assert_array_equal(h["code_count"], s["counts"].astype(np.int64).sum(axis=1))
+    width = s["width"]
+    mb = (lx**3 + 7) // 8
+    pad = lambda v: (v + 15) // 16 * 16  # noqa: E731
+    expect = pad(48 + 8 * nf) + nf * (pad(ne * mb) + 2 * pad(2 * ne)) + width * h["code_total"]
+    assert r.payload.size == expect
+    assert np.array_equal(oracle.decode(r.payload), r.recon)
+    np.testing.assert_array_equal(s["masks"].sum(axis=2), s["counts"])
+
+
+def test_compression_ratio_eq1():
+    f, j = _case(ne=125, lx=8, seed=31)
+    r = oracle.reduce(f, j, 1e-2)
+    orig = f.size * 8
+    cr = (orig - r.payload.size) / orig
+    assert 0.9 < cr < 1.0
