@@ -1,0 +1,250 @@
+/*
+ * semr.h -- C ABI of libsemr: in-situ reduction of spectral-element (SEM)
+ * field snapshots on one NVIDIA B300 GPU (sm_103a).
+ *
+ * The operation is the GPU lossy compression step of the in-situ workflow in
+ * arXiv 2407.20731 (Sec. IV-B, "Turbulence with data compression"): each
+ * element's lx^3 block of nodal values on Gauss-Lobatto-Legendre (GLL) points
+ * is transformed to a discretely orthonormal Legendre basis, the modes whose
+ * energy is below tau times the element's energy are dropped (the paper keeps
+ * only the most energetic part of the data, with the amount set by a maximal
+ * allowed error), the rest are quantised with a power-of-two step, written
+ * to a compact payload, reconstructed, and the mass-weighted L2 and the Linf
+ * errors are reported per element and per field.  The compression ratio is
+ * the paper's Eq. 1, CR = (original - compressed) / original.
+ *
+ * Conventions of every entry point:
+ *   - Return value: SEMR_OK (0) or one of the SEMR_E* codes below.  No entry
+ *     point aborts, throws or prints.  semr_strerror() names a code.
+ *   - Device pointers are CUDA device addresses on the device that is current
+ *     when the call is made (stream ordered on the stream passed in);
+ *     host pointers are ordinary host memory.
+ *   - The caller owns every buffer it passes in.  Inputs must stay valid and
+ *     unmodified until the work is complete (the stream has passed the
+ *     launch, or semr_query returns SEMR_OK for the ticket).
+ *   - Field layout: one FP64 array per field, n_elem blocks of lx^3 values,
+ *     element block e at offset e*lx^3, value (i, j, k) at i + lx*(j + lx*k)
+ *     (i fastest).  Modal index m = p + lx*(q + lx*r).  Field pointers
+ *     16-byte aligned for even lx, 8-byte aligned for odd lx; every other
+ *     FP64 pointer 8-byte aligned; payload 16-byte, scratch 256-byte aligned.
+ *
+ * Payload format (version 1, little-endian, all section starts 16-aligned):
+ *   header : "SEMR", u16 version, u16 lx, u16 n_fields, u16 flags,
+ *            u32 header_bytes, u64 n_elem, f64 tau, u64 code_base,
+ *            u64 code_total, u64 code_count[n_fields], padded to 16 bytes
+ *   field f: mask  n_elem x ceil(lx^3/8) bytes (mode m of element e is bit
+ *                  (m & 7) of byte e*ceil(lx^3/8) + (m >> 3)), padded
+ *            step  int16[n_elem]  s_e (INT16_MIN: element keeps nothing), padded
+ *            count uint16[n_elem] n_e, number of kept modes, padded
+ *   codes  : code_total entries from byte code_base, ordered by (field,
+ *            element, mode); int16 (flags & SEMR_PAYLOAD_CODE32 == 0),
+ *            int32 (SEMR_PAYLOAD_CODE32), or the raw FP64 coefficient in
+ *            lossless mode (SEMR_PAYLOAD_LOSSLESS, tau == 0).
+ *   Kept mode m of element e is reconstructed as a~_m = code * 2^{s_e}.
+ *   Quantisation: t = tau * S_e with S_e = sum_m a_m^2; mode m kept iff
+ *   a_m^2 >= t; s_e = floor((ex - 1) / 2) for t = mu * 2^ex, mu in [1/2, 1);
+ *   code = rint(a_m * 2^{-s_e}), ties to even.  Codes are int16 when
+ *   tau * 32767^2 > 4 (then |code| <= 2 / sqrt(tau) < 32767), else int32.
+ *   An element with t below the smallest normal double keeps nothing.
+ */
+#ifndef SEMR_H
+#define SEMR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define SEMR_OK 0
+#define SEMR_EINVAL 1         /* bad argument: null pointer, size, alignment, lx, tau */
+#define SEMR_ENOMEM 2         /* a device or pinned-host allocation failed */
+#define SEMR_EBUDGET 3        /* the request does not fit the stream's memory budget now */
+#define SEMR_EAGAIN 4         /* the ticket's work has not finished yet */
+#define SEMR_ETIMEDOUT 5      /* a bounded device-side wait gave up (result invalid) */
+#define SEMR_ECUDA 6          /* a CUDA runtime call failed */
+#define SEMR_ENOSPACE 7       /* an output buffer is smaller than the result */
+#define SEMR_ENONFINITE 8     /* an element held a NaN or an infinity (that element keeps nothing) */
+#define SEMR_EUNSUPPORTED 9   /* lx or precision not built into this library */
+
+/* ------------------------------------------------------------- parameters */
+#define SEMR_MAX_FIELDS 16
+#define SEMR_LX_MIN 2
+#define SEMR_LX_MAX 12
+
+/* precision of the transforms */
+#define SEMR_FP64 0   /* transforms, energy, threshold test, norms in FP64 */
+#define SEMR_FP32 1   /* transforms in FP32 with FP32 accumulation; energy, threshold test and
+                         cross-thread norm reductions in FP64 (the precision form) */
+
+/* fieldset flags */
+#define SEMR_WRITE_RECON 1   /* also write the reconstruction to fieldset.recon[f] */
+
+/* payload header flag bits */
+#define SEMR_PAYLOAD_LOSSLESS 1
+#define SEMR_PAYLOAD_CODE32 2
+#define SEMR_PAYLOAD_FP32 4
+
+/* summary.status bits (device-written) */
+#define SEMR_STATUS_OVERFLOW 1    /* payload_cap too small: codes not written */
+#define SEMR_STATUS_TIMEOUT 2     /* look-back wait gave up */
+#define SEMR_STATUS_NONFINITE 4   /* some element energy was NaN/Inf */
+
+typedef struct {
+    int32_t lx;            /* GLL points per direction, SEMR_LX_MIN..SEMR_LX_MAX */
+    int32_t pad_;
+    int64_t n_elem;        /* number of elements, >= 1, n_elem * lx^3 < 2^40 */
+    const double* jac;     /* device, n_elem element Jacobians (mass scale), finite */
+} semr_mesh;
+
+typedef struct {
+    int32_t n_fields;                 /* 1..SEMR_MAX_FIELDS */
+    int32_t precision;                /* SEMR_FP64 or SEMR_FP32 */
+    double tau;                       /* threshold, finite, >= 0; 0 = lossless mode */
+    int32_t flags;                    /* SEMR_WRITE_RECON or 0 */
+    int32_t pad_;
+    const double* fields[SEMR_MAX_FIELDS];  /* device, n_elem*lx^3 FP64 each */
+    double* recon[SEMR_MAX_FIELDS];         /* device outputs when SEMR_WRITE_RECON, else ignored */
+} semr_fieldset;
+
+/* Per-field error report (Sec. IV-B's "sufficient accuracy" check and Eq. 1). */
+typedef struct {
+    double l2_abs;      /* sqrt(sum_e e2_e), e2_e = J_e sum w_i w_j w_k (u - u~)^2 */
+    double l2_rel;      /* sqrt(sum e2 / sum E), E_e = J_e sum w_i w_j w_k u^2; 0 if sum E == 0 */
+    double linf_abs;    /* max |u - u~| over all GLL points (unweighted) */
+    double linf_rel;    /* linf_abs / max|u|; 0 if max|u| == 0 */
+    double sum_err2;    /* sum_e e2_e */
+    double sum_energy;  /* sum_e E_e */
+    double umax;        /* max |u| */
+    uint64_t kept;      /* number of codes of this field */
+    uint64_t bytes;     /* fixed sections + codes of this field */
+    double cr;          /* Eq. 1 for this field: 1 - bytes / (8 lx^3 n_elem) */
+} semr_field_report;
+
+/* Device-written result summary of one reduction. */
+typedef struct {
+    uint64_t payload_bytes;   /* total payload size */
+    uint64_t code_total;      /* codes over all fields */
+    uint32_t status;          /* SEMR_STATUS_* bits, 0 when everything is valid */
+    uint32_t n_fields;
+    double cr;                /* Eq. 1 over the whole snapshot */
+    semr_field_report field[SEMR_MAX_FIELDS];
+} semr_summary;
+
+/* Buffer sizes of one reduction (host-computed, exact). */
+typedef struct {
+    uint64_t header_bytes;       /* payload header */
+    uint64_t code_base;          /* header + fixed sections: minimum payload capacity */
+    uint64_t payload_worst;      /* code_base + every mode kept: always sufficient */
+    uint64_t scratch_bytes;      /* device scratch for semr_reduce_async */
+    uint64_t elem_report_bytes;  /* n_fields * n_elem * 3 doubles */
+    uint32_t code_width;         /* 2, 4 or 8 bytes */
+    uint32_t tiles;              /* work tiles of the fused kernel */
+} semr_sizes;
+
+/* Device buffers of one reduction (all caller-owned device memory). */
+typedef struct {
+    uint8_t* payload;          /* device, payload_cap bytes; the complete payload */
+    uint64_t payload_cap;      /* >= semr_sizes.code_base; codes beyond it set SEMR_STATUS_OVERFLOW */
+    double* elem_report;       /* device [n_fields][n_elem][3] = (e2_e, E_e, Linf_e), or NULL */
+    semr_summary* summary;     /* device, one semr_summary */
+    void* scratch;             /* device, semr_sizes.scratch_bytes, 256-byte aligned */
+    uint64_t scratch_bytes;
+} semr_outputs;
+
+typedef struct semr_stream semr_stream;
+
+/*
+ * semr_sizes_for: sizes of the buffers one reduction needs.
+ *   lx, n_elem, n_fields, tau as in semr_mesh / semr_fieldset.
+ * Errors: SEMR_EINVAL (out-of-range argument or null out).
+ */
+int semr_sizes_for(int32_t lx, int64_t n_elem, int32_t n_fields, double tau, semr_sizes* out);
+
+/*
+ * semr_reduce_async: the hot path.  Launches the fused reduce kernel (forward
+ * transform, energy, truncation mask, quantisation, one-pass global
+ * compaction of the codes, reconstruction, error norms) and the finalize
+ * kernel on `cuda_stream` (a cudaStream_t; NULL = legacy default stream).
+ * Writes the complete payload, the optional element report and the summary.
+ * Asynchronous: returns after the launches; results are valid once the
+ * stream passes this point and summary->status == 0.  Allocates nothing.
+ * Errors: SEMR_EINVAL (null/misaligned pointer, bad size or tau, scratch or
+ * payload_cap too small), SEMR_EUNSUPPORTED (lx or precision), SEMR_ECUDA
+ * (launch failure).
+ */
+int semr_reduce_async(const semr_fieldset* fs, const semr_mesh* mesh, const semr_outputs* out,
+                      void* cuda_stream);
+
+/*
+ * semr_reduce_async_timed: semr_reduce_async that also records two CUDA
+ * events (cudaEvent_t handles, either may be NULL) on `cuda_stream`
+ * immediately before and immediately after the fused reduce kernel, so that
+ * a caller can time that kernel alone (the scratch clear and the finalize
+ * kernel fall outside the pair).  Same arguments, errors and effects as
+ * semr_reduce_async; SEMR_ECUDA if an event record fails.
+ */
+int semr_reduce_async_timed(const semr_fieldset* fs, const semr_mesh* mesh, const semr_outputs* out,
+                            void* cuda_stream, void* ev_begin, void* ev_end);
+
+/*
+ * semr_open: a reduction stream with library-owned buffers.
+ *   device: CUDA device ordinal.  cuda_stream: cudaStream_t to order work on
+ *   (NULL: the library creates its own non-blocking stream).
+ *   mem_budget_bytes: upper bound on device memory that in-flight tickets may
+ *   hold (payload worst case + scratch + reports); 0 = no bound.
+ * Errors: SEMR_EINVAL, SEMR_ECUDA, SEMR_ENOMEM.
+ */
+int semr_open(semr_stream** s, int device, void* cuda_stream, uint64_t mem_budget_bytes);
+
+/*
+ * semr_submit: queue the reduction of one snapshot; returns at once with a
+ * ticket.  Allocates the ticket's device buffers (stream-ordered) within the
+ * budget.  The field and Jacobian buffers must stay valid until the ticket
+ * completes.  Errors: SEMR_EINVAL, SEMR_EUNSUPPORTED, SEMR_EBUDGET (does
+ * not fit next to the tickets in flight: fetch some first), SEMR_ENOMEM,
+ * SEMR_ECUDA.
+ */
+int semr_submit(semr_stream* s, const semr_fieldset* fs, const semr_mesh* mesh, uint64_t* ticket);
+
+/* semr_query: SEMR_OK when the ticket's work is complete, SEMR_EAGAIN if not,
+ * SEMR_EINVAL for an unknown ticket. */
+int semr_query(semr_stream* s, uint64_t ticket);
+
+/*
+ * semr_fetch: copy a ticket's results to host memory and release the ticket.
+ *   wait: nonzero blocks until complete; zero returns SEMR_EAGAIN if not.
+ *   payload (host, cap bytes) or NULL; *payload_bytes gets the size.
+ *   reports (host, n_fields entries) or NULL; elem_report (host, n_fields *
+ *   n_elem * 3 doubles) or NULL.
+ * Errors: SEMR_EAGAIN, SEMR_EINVAL, SEMR_ENOSPACE (cap too small: nothing
+ * copied, ticket kept), SEMR_ETIMEDOUT / SEMR_ENONFINITE (device status;
+ * results copied, ticket released), SEMR_ECUDA.
+ */
+int semr_fetch(semr_stream* s, uint64_t ticket, int wait, void* payload, uint64_t cap,
+               uint64_t* payload_bytes, semr_field_report* reports, double* elem_report);
+
+/* semr_close: wait for the stream's work, free everything it owns. */
+void semr_close(semr_stream* s);
+
+/*
+ * semr_decode: rebuild the fields from a payload on the host (FP64).
+ *   out: host, n_fields * n_elem * lx^3 doubles (cap_doubles), layout as the input.
+ *   hdr_out (optional): lx, n_fields, n_elem of the payload.
+ * Errors: SEMR_EINVAL (malformed payload), SEMR_ENOSPACE.
+ */
+int semr_decode(const void* payload, uint64_t bytes, double* out, uint64_t cap_doubles,
+                int32_t* lx_out, int32_t* n_fields_out, int64_t* n_elem_out);
+
+/* semr_gll: the library's GLL nodes and weights (host, lx entries each). */
+int semr_gll(int32_t lx, double* nodes, double* weights);
+
+/* semr_strerror: static text for a status code. */
+const char* semr_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEMR_H */

@@ -1,0 +1,292 @@
+"""paper_2407_20731_b300 -- in-situ reduction of spectral-element field
+snapshots on one B300 GPU.
+
+This module is the thin Python binding of ``libsemr.so``, the C ABI declared
+in ``include/semr.h``: the same entry-point names, argument marshalling only.
+Every step of the reduction runs in the library's CUDA kernels; PyTorch is
+used only to hold device memory and to name CUDA streams.  There is no CPU
+fallback: importing this module raises if the library has not been built.
+
+The method is the GPU lossy compression of SEM fields in arXiv 2407.20731,
+Sec. IV-B (spectral transform, energy-relative truncation, quantisation),
+with the error check the paper calls "sufficient accuracy" and the
+compression ratio of Eq. 1.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsemr.so")
+
+# status codes (include/semr.h)
+SEMR_OK, SEMR_EINVAL, SEMR_ENOMEM, SEMR_EBUDGET, SEMR_EAGAIN = 0, 1, 2, 3, 4
+SEMR_ETIMEDOUT, SEMR_ECUDA, SEMR_ENOSPACE, SEMR_ENONFINITE, SEMR_EUNSUPPORTED = 5, 6, 7, 8, 9
+SEMR_MAX_FIELDS, SEMR_LX_MIN, SEMR_LX_MAX = 16, 2, 12
+SEMR_FP64, SEMR_FP32 = 0, 1
+SEMR_WRITE_RECON = 1
+SEMR_PAYLOAD_LOSSLESS, SEMR_PAYLOAD_CODE32, SEMR_PAYLOAD_FP32 = 1, 2, 4
+SEMR_STATUS_OVERFLOW, SEMR_STATUS_TIMEOUT, SEMR_STATUS_NONFINITE = 1, 2, 4
+
+
+class semr_mesh(ctypes.Structure):
+    _fields_ = [("lx", ctypes.c_int32), ("pad_", ctypes.c_int32), ("n_elem", ctypes.c_int64),
+                ("jac", ctypes.c_void_p)]
+
+
+class semr_fieldset(ctypes.Structure):
+    _fields_ = [("n_fields", ctypes.c_int32), ("precision", ctypes.c_int32), ("tau", ctypes.c_double),
+                ("flags", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("fields", ctypes.c_void_p * SEMR_MAX_FIELDS), ("recon", ctypes.c_void_p * SEMR_MAX_FIELDS)]
+
+
+class semr_field_report(ctypes.Structure):
+    _fields_ = [("l2_abs", ctypes.c_double), ("l2_rel", ctypes.c_double), ("linf_abs", ctypes.c_double),
+                ("linf_rel", ctypes.c_double), ("sum_err2", ctypes.c_double), ("sum_energy", ctypes.c_double),
+                ("umax", ctypes.c_double), ("kept", ctypes.c_uint64), ("bytes", ctypes.c_uint64),
+                ("cr", ctypes.c_double)]
+
+
+class semr_summary(ctypes.Structure):
+    _fields_ = [("payload_bytes", ctypes.c_uint64), ("code_total", ctypes.c_uint64), ("status", ctypes.c_uint32),
+                ("n_fields", ctypes.c_uint32), ("cr", ctypes.c_double),
+                ("field", semr_field_report * SEMR_MAX_FIELDS)]
+
+
+class semr_sizes(ctypes.Structure):
+    _fields_ = [("header_bytes", ctypes.c_uint64), ("code_base", ctypes.c_uint64),
+                ("payload_worst", ctypes.c_uint64), ("scratch_bytes", ctypes.c_uint64),
+                ("elem_report_bytes", ctypes.c_uint64), ("code_width", ctypes.c_uint32),
+                ("tiles", ctypes.c_uint32)]
+
+
+class semr_outputs(ctypes.Structure):
+    _fields_ = [("payload", ctypes.c_void_p), ("payload_cap", ctypes.c_uint64), ("elem_report", ctypes.c_void_p),
+                ("summary", ctypes.c_void_p), ("scratch", ctypes.c_void_p), ("scratch_bytes", ctypes.c_uint64)]
+
+
+# (name, restype, argtypes) of every exported entry point
+_P = ctypes.c_void_p
+EXPORTS = [
+    ("semr_sizes_for", ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
+                                      ctypes.POINTER(semr_sizes)]),
+    ("semr_reduce_async", ctypes.c_int, [ctypes.POINTER(semr_fieldset), ctypes.POINTER(semr_mesh),
+                                         ctypes.POINTER(semr_outputs), _P]),
+    ("semr_reduce_async_timed", ctypes.c_int, [ctypes.POINTER(semr_fieldset), ctypes.POINTER(semr_mesh),
+                                               ctypes.POINTER(semr_outputs), _P, _P, _P]),
+    ("semr_open", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.c_uint64]),
+    ("semr_submit", ctypes.c_int, [_P, ctypes.POINTER(semr_fieldset), ctypes.POINTER(semr_mesh),
+                                   ctypes.POINTER(ctypes.c_uint64)]),
+    ("semr_query", ctypes.c_int, [_P, ctypes.c_uint64]),
+    ("semr_fetch", ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int, _P, ctypes.c_uint64,
+                                  ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(semr_field_report), _P]),
+    ("semr_close", None, [_P]),
+    ("semr_decode", ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32),
+                                   ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]),
+    ("semr_gll", ctypes.c_int, [ctypes.c_int32, _P, _P]),
+    ("semr_strerror", ctypes.c_char_p, [ctypes.c_int]),
+]
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libsemr.so is not built ({LIB_PATH}); run __graft_entry__.build() "
+                      "or python paper_2407_20731_b300/build.py")
+_lib = ctypes.CDLL(LIB_PATH)
+for _name, _res, _args in EXPORTS:
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+class SemrError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {semr_strerror(code)} (status {code})")
+        self.code = code
+
+
+def _check(code: int, where: str) -> int:
+    if code != SEMR_OK:
+        raise SemrError(code, where)
+    return code
+
+
+# ---------------------------------------------------------------- raw ABI
+
+def semr_strerror(code: int) -> str:
+    return _lib.semr_strerror(code).decode()
+
+
+def semr_sizes_for(lx: int, n_elem: int, n_fields: int, tau: float) -> semr_sizes:
+    s = semr_sizes()
+    _check(_lib.semr_sizes_for(lx, n_elem, n_fields, tau, ctypes.byref(s)), "semr_sizes_for")
+    return s
+
+
+def semr_reduce_async(fs: semr_fieldset, mesh: semr_mesh, out: semr_outputs, stream: int) -> int:
+    return _lib.semr_reduce_async(ctypes.byref(fs), ctypes.byref(mesh), ctypes.byref(out), stream)
+
+
+def semr_reduce_async_timed(fs: semr_fieldset, mesh: semr_mesh, out: semr_outputs, stream: int,
+                            ev_begin: int | None, ev_end: int | None) -> int:
+    return _lib.semr_reduce_async_timed(ctypes.byref(fs), ctypes.byref(mesh), ctypes.byref(out), stream,
+                                        ev_begin, ev_end)
+
+
+def semr_open(device: int = 0, stream: int = 0, mem_budget_bytes: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.semr_open(ctypes.byref(h), device, stream or None, mem_budget_bytes), "semr_open")
+    return h.value
+
+
+def semr_submit(handle: int, fs: semr_fieldset, mesh: semr_mesh) -> tuple[int, int]:
+    t = ctypes.c_uint64(0)
+    rc = _lib.semr_submit(handle, ctypes.byref(fs), ctypes.byref(mesh), ctypes.byref(t))
+    return rc, t.value
+
+
+def semr_query(handle: int, ticket: int) -> int:
+    return _lib.semr_query(handle, ticket)
+
+
+def semr_fetch(handle: int, ticket: int, wait: bool, payload: np.ndarray | None, n_fields: int,
+               elem_report: np.ndarray | None = None):
+    """Returns (status, payload_bytes, [semr_field_report] * n_fields)."""
+    nbytes = ctypes.c_uint64(0)
+    reps = (semr_field_report * max(n_fields, 1))()
+    rc = _lib.semr_fetch(handle, ticket, 1 if wait else 0,
+                         None if payload is None else payload.ctypes.data_as(_P),
+                         0 if payload is None else payload.nbytes, ctypes.byref(nbytes), reps,
+                         None if elem_report is None else elem_report.ctypes.data_as(_P))
+    return rc, nbytes.value, list(reps)[:n_fields]
+
+
+def semr_close(handle: int) -> None:
+    _lib.semr_close(handle)
+
+
+def semr_decode(payload: np.ndarray) -> np.ndarray:
+    """Host decode of a payload to [n_fields, n_elem, lx^3] FP64."""
+    payload = np.ascontiguousarray(payload, dtype=np.uint8)
+    lx, nf, ne = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(_lib.semr_decode(payload.ctypes.data_as(_P), payload.nbytes, None, 0, ctypes.byref(lx),
+                            ctypes.byref(nf), ctypes.byref(ne)), "semr_decode")
+    out = np.zeros((nf.value, ne.value, lx.value ** 3))
+    _check(_lib.semr_decode(payload.ctypes.data_as(_P), payload.nbytes, out.ctypes.data_as(_P), out.size,
+                            None, None, None), "semr_decode")
+    return out
+
+
+def semr_gll(lx: int) -> tuple[np.ndarray, np.ndarray]:
+    x, w = np.zeros(lx), np.zeros(lx)
+    _check(_lib.semr_gll(lx, x.ctypes.data_as(_P), w.ctypes.data_as(_P)), "semr_gll")
+    return x, w
+
+
+# ----------------------------------------------------- torch marshalling
+
+def make_fieldset(fields, tau: float, precision: int = SEMR_FP64, recon=None) -> semr_fieldset:
+    """fields: sequence of CUDA FP64 tensors (contiguous, n_elem*lx^3 each)."""
+    fs = semr_fieldset()
+    fs.n_fields = len(fields)
+    fs.precision = precision
+    fs.tau = float(tau)
+    fs.flags = SEMR_WRITE_RECON if recon is not None else 0
+    for i, t in enumerate(fields):
+        _require_cuda_f64(t)
+        fs.fields[i] = t.data_ptr()
+        if recon is not None:
+            _require_cuda_f64(recon[i])
+            fs.recon[i] = recon[i].data_ptr()
+    return fs
+
+
+def make_mesh(lx: int, jac) -> semr_mesh:
+    _require_cuda_f64(jac)
+    m = semr_mesh()
+    m.lx = lx
+    m.n_elem = jac.numel()
+    m.jac = jac.data_ptr()
+    return m
+
+
+def _require_cuda_f64(t) -> None:
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA float64 tensor")
+
+
+@dataclass
+class DeviceBuffers:
+    """Caller-owned device buffers of one reduction (torch uint8 tensors)."""
+    sizes: semr_sizes
+    payload: object
+    scratch: object
+    summary: object
+    elem_report: object | None
+    outputs: semr_outputs
+
+
+def alloc_buffers(lx: int, n_elem: int, n_fields: int, tau: float, device="cuda",
+                  payload_cap: int | None = None, elem_report: bool = True) -> DeviceBuffers:
+    import torch
+    sz = semr_sizes_for(lx, n_elem, n_fields, tau)
+    cap = int(sz.payload_worst if payload_cap is None else payload_cap)
+    payload = torch.empty(cap, dtype=torch.uint8, device=device)
+    scratch = torch.empty(int(sz.scratch_bytes) + 256, dtype=torch.uint8, device=device)
+    summary = torch.zeros(ctypes.sizeof(semr_summary), dtype=torch.uint8, device=device)
+    er = torch.empty(n_fields * n_elem * 3, dtype=torch.float64, device=device) if elem_report else None
+    o = semr_outputs()
+    o.payload = payload.data_ptr()
+    o.payload_cap = cap
+    o.elem_report = er.data_ptr() if er is not None else None
+    o.summary = summary.data_ptr()
+    sp = scratch.data_ptr()
+    o.scratch = (sp + 255) // 256 * 256
+    o.scratch_bytes = int(sz.scratch_bytes)
+    return DeviceBuffers(sz, payload, scratch, summary, er, o)
+
+
+def reduce_async(fields, jac, lx: int, tau: float, bufs: DeviceBuffers, precision: int = SEMR_FP64,
+                 recon=None, stream=None, events=None) -> None:
+    """Launch one reduction on ``stream`` (default: torch's current stream).
+    ``events``: optional (begin, end) torch.cuda.Event pair recorded around the
+    fused reduce kernel alone."""
+    import torch
+    fs = make_fieldset(fields, tau, precision, recon)
+    mesh = make_mesh(lx, jac)
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    if events is None:
+        _check(semr_reduce_async(fs, mesh, bufs.outputs, st), "semr_reduce_async")
+    else:
+        _check(semr_reduce_async_timed(fs, mesh, bufs.outputs, st, events[0].cuda_event, events[1].cuda_event),
+               "semr_reduce_async_timed")
+
+
+def summary_from(bufs: DeviceBuffers) -> semr_summary:
+    raw = bufs.summary.cpu().numpy().tobytes()
+    return semr_summary.from_buffer_copy(raw)
+
+
+@dataclass
+class Result:
+    payload: np.ndarray          # uint8
+    summary: semr_summary
+    elem_report: np.ndarray | None  # [F, E, 3]
+
+
+def reduce(fields, jac, lx: int, tau: float, precision: int = SEMR_FP64, recon=None,
+           elem_report: bool = True) -> Result:
+    """Blocking convenience: reduce, then copy payload, summary and element
+    report to the host."""
+    import torch
+    n_elem = jac.numel()
+    bufs = alloc_buffers(lx, n_elem, len(fields), tau, fields[0].device, elem_report=elem_report)
+    reduce_async(fields, jac, lx, tau, bufs, precision, recon)
+    torch.cuda.current_stream().synchronize()
+    sm = summary_from(bufs)
+    payload = bufs.payload[: sm.payload_bytes].cpu().numpy()
+    er = bufs.elem_report.view(len(fields), n_elem, 3).cpu().numpy() if elem_report else None
+    return Result(payload, sm, er)

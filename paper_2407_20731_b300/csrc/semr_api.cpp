@@ -1,0 +1,397 @@
+// C-ABI runtime of libsemr: argument validation, buffer sizing, launches of
+// the fused reduce kernel, the ticketed stream API with a device-memory
+// budget, and the host-side payload decoder.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "semr_internal.h"
+
+using namespace semr;
+
+namespace {
+
+bool lx_supported(int lx) { return lx >= SEMR_LX_MIN && lx <= SEMR_LX_MAX; }
+
+int check_common(int32_t lx, int64_t n_elem, int32_t n_fields, double tau) {
+    if (!lx_supported(lx)) return SEMR_EINVAL;
+    if (n_elem < 1 || n_fields < 1 || n_fields > SEMR_MAX_FIELDS) return SEMR_EINVAL;
+    const uint64_t n3 = uint64_t(lx) * lx * lx;
+    if (uint64_t(n_elem) * n3 >= (1ull << 40)) return SEMR_EINVAL;
+    if (!(tau >= 0.0) || std::isinf(tau)) return SEMR_EINVAL;
+    return SEMR_OK;
+}
+
+uint64_t tiles_per_field(int lx, int64_t n_elem) {
+    const int t = tile_elems(lx);
+    return (uint64_t(n_elem) + t - 1) / t;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+extern "C" int semr_sizes_for(int32_t lx, int64_t n_elem, int32_t n_fields, double tau, semr_sizes* out) {
+    if (!out) return SEMR_EINVAL;
+    int rc = check_common(lx, n_elem, n_fields, tau);
+    if (rc) return rc;
+    const uint64_t n3 = uint64_t(lx) * lx * lx;
+    const int width = code_width(tau);
+    const uint64_t tiles = uint64_t(n_fields) * tiles_per_field(lx, n_elem);
+    out->header_bytes = header_bytes(n_fields);
+    out->code_base = out->header_bytes + uint64_t(n_fields) * field_fixed_bytes(lx, n_elem);
+    out->payload_worst = out->code_base + uint64_t(width) * n3 * uint64_t(n_elem) * n_fields;
+    out->scratch_bytes = scratch_bytes(tiles);
+    out->elem_report_bytes = 24ull * uint64_t(n_elem) * n_fields;
+    out->code_width = (uint32_t)width;
+    out->tiles = (uint32_t)tiles;
+    return SEMR_OK;
+}
+
+extern "C" int semr_reduce_async(const semr_fieldset* fs, const semr_mesh* mesh, const semr_outputs* out,
+                                 void* cuda_stream) {
+    return semr_reduce_async_timed(fs, mesh, out, cuda_stream, nullptr, nullptr);
+}
+
+extern "C" int semr_reduce_async_timed(const semr_fieldset* fs, const semr_mesh* mesh, const semr_outputs* out,
+                                       void* cuda_stream, void* ev_begin, void* ev_end) {
+    if (!fs || !mesh || !out) return SEMR_EINVAL;
+    if (mesh->lx >= 2 && !lx_supported(mesh->lx)) return SEMR_EUNSUPPORTED;
+    int rc = check_common(mesh->lx, mesh->n_elem, fs->n_fields, fs->tau);
+    if (rc) return rc;
+    if (fs->precision != SEMR_FP64 && fs->precision != SEMR_FP32) return SEMR_EUNSUPPORTED;
+    if (!mesh->jac || !out->payload || !out->summary || !out->scratch) return SEMR_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(out->scratch) & 255u) != 0 || !aligned16(out->payload)) return SEMR_EINVAL;
+    // even lx: element blocks are loaded as 16-byte vectors; odd lx: 8-byte scalars
+    const uintptr_t amask = (mesh->lx % 2 == 0) ? 15u : 7u;
+    for (int f = 0; f < fs->n_fields; ++f) {
+        if (!fs->fields[f] || (reinterpret_cast<uintptr_t>(fs->fields[f]) & amask)) return SEMR_EINVAL;
+        if ((fs->flags & SEMR_WRITE_RECON) && fs->recon[f] && (reinterpret_cast<uintptr_t>(fs->recon[f]) & 7u))
+            return SEMR_EINVAL;
+    }
+    if (reinterpret_cast<uintptr_t>(mesh->jac) & 7u) return SEMR_EINVAL;
+    semr_sizes sz;
+    semr_sizes_for(mesh->lx, mesh->n_elem, fs->n_fields, fs->tau, &sz);
+    if (out->scratch_bytes < sz.scratch_bytes || out->payload_cap < sz.code_base) return SEMR_EINVAL;
+
+    LaunchParams p;
+    std::memset(&p, 0, sizeof(p));
+    for (int f = 0; f < fs->n_fields; ++f) {
+        p.fields[f] = fs->fields[f];
+        p.recon[f] = (fs->flags & SEMR_WRITE_RECON) ? fs->recon[f] : nullptr;
+    }
+    p.jac = mesh->jac;
+    p.payload = out->payload;
+    p.payload_cap = out->payload_cap;
+    p.elem_report = out->elem_report;
+    p.summary = out->summary;
+    p.scratch = static_cast<uint8_t*>(out->scratch);
+    p.n_elem = mesh->n_elem;
+    p.n_fields = fs->n_fields;
+    p.tiles_per_field = (int32_t)tiles_per_field(mesh->lx, mesh->n_elem);
+    p.tau = fs->tau;
+    p.lossless = fs->tau == 0.0;
+    p.width = (int32_t)sz.code_width;
+    p.write_recon = (fs->flags & SEMR_WRITE_RECON) ? 1 : 0;
+    p.precision = fs->precision;
+    p.header_bytes = sz.header_bytes;
+    p.fixed_bytes = field_fixed_bytes(mesh->lx, mesh->n_elem);
+    p.code_base = sz.code_base;
+
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaMemsetAsync(out->scratch, 0, scratch_zero_bytes(sz.tiles), st) != cudaSuccess) return SEMR_ECUDA;
+    if (ev_begin && cudaEventRecord(static_cast<cudaEvent_t>(ev_begin), st) != cudaSuccess) return SEMR_ECUDA;
+    if (launch_reduce(p, mesh->lx, st) != cudaSuccess) return SEMR_ECUDA;
+    if (ev_end && cudaEventRecord(static_cast<cudaEvent_t>(ev_end), st) != cudaSuccess) return SEMR_ECUDA;
+    if (launch_finalize(p, mesh->lx, st) != cudaSuccess) return SEMR_ECUDA;
+    return SEMR_OK;
+}
+
+// ------------------------------------------------------------ stream API
+
+struct Ticket {
+    uint8_t* dev = nullptr;       // one allocation: payload | scratch | summary | elem report
+    uint64_t bytes = 0;
+    uint64_t payload_cap = 0;
+    uint64_t off_scratch = 0, off_summary = 0, off_elem = 0;
+    int32_t n_fields = 0;
+    int64_t n_elem = 0;
+    cudaEvent_t done = nullptr;
+};
+
+struct semr_stream {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    uint64_t budget = 0;
+    uint64_t in_flight = 0;
+    uint64_t next_ticket = 1;
+    std::unordered_map<uint64_t, Ticket> tickets;
+    semr_summary* host_summary = nullptr;  // pinned
+    std::mutex mu;
+};
+
+namespace {
+
+uint64_t align256(uint64_t b) { return (b + 255) & ~uint64_t(255); }
+
+void release(semr_stream* s, Ticket& t) {
+    if (t.dev) cudaFreeAsync(t.dev, s->stream);
+    if (t.done) cudaEventDestroy(t.done);
+    s->in_flight -= t.bytes;
+    t.dev = nullptr;
+    t.done = nullptr;
+}
+
+}  // namespace
+
+extern "C" int semr_open(semr_stream** out, int device, void* cuda_stream, uint64_t mem_budget_bytes) {
+    if (!out) return SEMR_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) return SEMR_ECUDA;
+    if (device < 0 || device >= ndev) return SEMR_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return SEMR_ECUDA;
+    semr_stream* s = new (std::nothrow) semr_stream;
+    if (!s) return SEMR_ENOMEM;
+    s->device = device;
+    s->budget = mem_budget_bytes;
+    if (cuda_stream) {
+        s->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete s;
+            return SEMR_ECUDA;
+        }
+        s->own_stream = true;
+    }
+    if (cudaMallocHost(&s->host_summary, sizeof(semr_summary)) != cudaSuccess) {
+        if (s->own_stream) cudaStreamDestroy(s->stream);
+        delete s;
+        return SEMR_ENOMEM;
+    }
+    *out = s;
+    return SEMR_OK;
+}
+
+extern "C" int semr_submit(semr_stream* s, const semr_fieldset* fs, const semr_mesh* mesh, uint64_t* ticket) {
+    if (!s || !fs || !mesh || !ticket) return SEMR_EINVAL;
+    semr_sizes sz;
+    int rc = semr_sizes_for(mesh->lx, mesh->n_elem, fs->n_fields, fs->tau, &sz);
+    if (rc) return rc;
+    Ticket t;
+    t.n_fields = fs->n_fields;
+    t.n_elem = mesh->n_elem;
+    t.payload_cap = sz.payload_worst;
+    t.off_scratch = align256(sz.payload_worst);
+    t.off_summary = align256(t.off_scratch + sz.scratch_bytes);
+    t.off_elem = align256(t.off_summary + sizeof(semr_summary));
+    t.bytes = align256(t.off_elem + sz.elem_report_bytes);
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->budget && s->in_flight + t.bytes > s->budget) return SEMR_EBUDGET;
+    if (cudaSetDevice(s->device) != cudaSuccess) return SEMR_ECUDA;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&t.dev), t.bytes, s->stream) != cudaSuccess) return SEMR_ENOMEM;
+    if (cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaFreeAsync(t.dev, s->stream);
+        return SEMR_ECUDA;
+    }
+    semr_outputs o;
+    o.payload = t.dev;
+    o.payload_cap = t.payload_cap;
+    o.elem_report = reinterpret_cast<double*>(t.dev + t.off_elem);
+    o.summary = reinterpret_cast<semr_summary*>(t.dev + t.off_summary);
+    o.scratch = t.dev + t.off_scratch;
+    o.scratch_bytes = sz.scratch_bytes;
+    rc = semr_reduce_async(fs, mesh, &o, s->stream);
+    if (rc == SEMR_OK && cudaEventRecord(t.done, s->stream) != cudaSuccess) rc = SEMR_ECUDA;
+    if (rc != SEMR_OK) {
+        cudaFreeAsync(t.dev, s->stream);
+        cudaEventDestroy(t.done);
+        return rc;
+    }
+    s->in_flight += t.bytes;
+    *ticket = s->next_ticket++;
+    s->tickets.emplace(*ticket, t);
+    return SEMR_OK;
+}
+
+extern "C" int semr_query(semr_stream* s, uint64_t ticket) {
+    if (!s) return SEMR_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) return SEMR_EINVAL;
+    cudaError_t e = cudaEventQuery(it->second.done);
+    if (e == cudaSuccess) return SEMR_OK;
+    if (e == cudaErrorNotReady) return SEMR_EAGAIN;
+    return SEMR_ECUDA;
+}
+
+extern "C" int semr_fetch(semr_stream* s, uint64_t ticket, int wait, void* payload, uint64_t cap,
+                          uint64_t* payload_bytes, semr_field_report* reports, double* elem_report) {
+    if (!s) return SEMR_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) return SEMR_EINVAL;
+    Ticket& t = it->second;
+    if (!wait) {
+        cudaError_t e = cudaEventQuery(t.done);
+        if (e == cudaErrorNotReady) return SEMR_EAGAIN;
+        if (e != cudaSuccess) return SEMR_ECUDA;
+    } else if (cudaEventSynchronize(t.done) != cudaSuccess) {
+        return SEMR_ECUDA;
+    }
+    if (cudaSetDevice(s->device) != cudaSuccess) return SEMR_ECUDA;
+    if (cudaMemcpy(s->host_summary, t.dev + t.off_summary, sizeof(semr_summary), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+        return SEMR_ECUDA;
+    const semr_summary& sm = *s->host_summary;
+    if (payload_bytes) *payload_bytes = sm.payload_bytes;
+    if (payload && cap < sm.payload_bytes) return SEMR_ENOSPACE;
+    if (payload && cudaMemcpy(payload, t.dev, sm.payload_bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SEMR_ECUDA;
+    if (reports) std::memcpy(reports, sm.field, sizeof(semr_field_report) * t.n_fields);
+    if (elem_report &&
+        cudaMemcpy(elem_report, t.dev + t.off_elem, 24ull * t.n_elem * t.n_fields, cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+        return SEMR_ECUDA;
+    const uint32_t status = sm.status;
+    release(s, t);
+    s->tickets.erase(it);
+    if (status & SEMR_STATUS_TIMEOUT) return SEMR_ETIMEDOUT;
+    if (status & SEMR_STATUS_OVERFLOW) return SEMR_ENOSPACE;
+    if (status & SEMR_STATUS_NONFINITE) return SEMR_ENONFINITE;
+    return SEMR_OK;
+}
+
+extern "C" void semr_close(semr_stream* s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        cudaSetDevice(s->device);
+        cudaStreamSynchronize(s->stream);
+        for (auto& kv : s->tickets) release(s, kv.second);
+        s->tickets.clear();
+        cudaStreamSynchronize(s->stream);
+        if (s->host_summary) cudaFreeHost(s->host_summary);
+        if (s->own_stream) cudaStreamDestroy(s->stream);
+    }
+    delete s;
+}
+
+// ------------------------------------------------------------ host decoder
+
+extern "C" int semr_decode(const void* payload_v, uint64_t bytes, double* out, uint64_t cap_doubles,
+                           int32_t* lx_out, int32_t* nf_out, int64_t* ne_out) {
+    const uint8_t* b = static_cast<const uint8_t*>(payload_v);
+    if (!b || bytes < kHeaderFixed || std::memcmp(b, "SEMR", 4) != 0) return SEMR_EINVAL;
+    uint16_t version, lx, nf, flags;
+    uint32_t hdr;
+    uint64_t ne, code_base, code_total;
+    std::memcpy(&version, b + 4, 2);
+    std::memcpy(&lx, b + 6, 2);
+    std::memcpy(&nf, b + 8, 2);
+    std::memcpy(&flags, b + 10, 2);
+    std::memcpy(&hdr, b + 12, 4);
+    std::memcpy(&ne, b + 16, 8);
+    std::memcpy(&code_base, b + 32, 8);
+    std::memcpy(&code_total, b + 40, 8);
+    if (version != kPayloadVersion || !lx_supported(lx) || nf < 1 || nf > SEMR_MAX_FIELDS) return SEMR_EINVAL;
+    if (hdr != header_bytes(nf) || ne == 0 || ne >= (1ull << 40)) return SEMR_EINVAL;
+    const int n3 = lx * lx * lx;
+    const uint64_t mb = mask_bytes_per_elem(lx);
+    const uint64_t fixed = field_fixed_bytes(lx, (int64_t)ne);
+    const int width = (flags & SEMR_PAYLOAD_LOSSLESS) ? 8 : ((flags & SEMR_PAYLOAD_CODE32) ? 4 : 2);
+    if (code_base != hdr + nf * fixed || code_base + code_total * width > bytes) return SEMR_EINVAL;
+    if (lx_out) *lx_out = lx;
+    if (nf_out) *nf_out = nf;
+    if (ne_out) *ne_out = (int64_t)ne;
+    if (!out) return SEMR_OK;
+    if (cap_doubles < uint64_t(nf) * ne * n3) return SEMR_ENOSPACE;
+
+    double A[SEMR_LX_MAX * SEMR_LX_MAX], Phi[SEMR_LX_MAX * SEMR_LX_MAX];
+    basis_tables(lx, A, Phi, nullptr);
+    std::vector<double> at(n3), t1(n3), t2(n3);
+    uint64_t pos = code_base, seen_total = 0;
+    for (int f = 0; f < nf; ++f) {
+        const uint8_t* sec = b + hdr + f * fixed;
+        const uint8_t* step = sec + pad16(ne * mb);
+        const uint8_t* cnt = step + pad16(2 * ne);
+        for (uint64_t e = 0; e < ne; ++e) {
+            int16_t s;
+            uint16_t c;
+            std::memcpy(&s, step + 2 * e, 2);
+            std::memcpy(&c, cnt + 2 * e, 2);
+            int seen = 0;
+            for (int m = 0; m < n3; ++m) {
+                if (sec[e * mb + (m >> 3)] & (1u << (m & 7))) {
+                    if (++seen_total > code_total) return SEMR_EINVAL;
+                    if (width == 8) {
+                        std::memcpy(&at[m], b + pos, 8);
+                    } else if (width == 4) {
+                        int32_t v;
+                        std::memcpy(&v, b + pos, 4);
+                        at[m] = std::ldexp((double)v, s);
+                    } else {
+                        int16_t v;
+                        std::memcpy(&v, b + pos, 2);
+                        at[m] = std::ldexp((double)v, s);
+                    }
+                    pos += width;
+                    ++seen;
+                } else {
+                    at[m] = 0.0;
+                }
+            }
+            if (seen != c) return SEMR_EINVAL;
+            // u[k][j][i] = sum Phi[k][r] Phi[j][q] Phi[i][p] a[r][q][p]
+            for (int r = 0; r < lx; ++r)
+                for (int q = 0; q < lx; ++q)
+                    for (int i = 0; i < lx; ++i) {
+                        double acc = 0.0;
+                        for (int pp = 0; pp < lx; ++pp) acc += Phi[i * lx + pp] * at[(r * lx + q) * lx + pp];
+                        t1[(r * lx + q) * lx + i] = acc;
+                    }
+            for (int r = 0; r < lx; ++r)
+                for (int j = 0; j < lx; ++j)
+                    for (int i = 0; i < lx; ++i) {
+                        double acc = 0.0;
+                        for (int q = 0; q < lx; ++q) acc += Phi[j * lx + q] * t1[(r * lx + q) * lx + i];
+                        t2[(r * lx + j) * lx + i] = acc;
+                    }
+            double* dst = out + (uint64_t(f) * ne + e) * n3;
+            for (int k = 0; k < lx; ++k)
+                for (int j = 0; j < lx; ++j)
+                    for (int i = 0; i < lx; ++i) {
+                        double acc = 0.0;
+                        for (int r = 0; r < lx; ++r) acc += Phi[k * lx + r] * t2[(r * lx + j) * lx + i];
+                        dst[(k * lx + j) * lx + i] = acc;
+                    }
+        }
+    }
+    return SEMR_OK;
+}
+
+extern "C" int semr_gll(int32_t lx, double* nodes, double* weights) {
+    if (!lx_supported(lx)) return SEMR_EINVAL;
+    return gll_nodes_weights(lx, nodes, weights);
+}
+
+extern "C" const char* semr_strerror(int code) {
+    switch (code) {
+        case SEMR_OK: return "ok";
+        case SEMR_EINVAL: return "invalid argument";
+        case SEMR_ENOMEM: return "out of memory";
+        case SEMR_EBUDGET: return "request exceeds the stream's memory budget";
+        case SEMR_EAGAIN: return "not finished yet";
+        case SEMR_ETIMEDOUT: return "device-side wait timed out";
+        case SEMR_ECUDA: return "CUDA runtime error";
+        case SEMR_ENOSPACE: return "output buffer too small";
+        case SEMR_ENONFINITE: return "input held NaN or infinity";
+        case SEMR_EUNSUPPORTED: return "unsupported lx or precision";
+        default: return "unknown status";
+    }
+}

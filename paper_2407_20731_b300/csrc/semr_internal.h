@@ -1,0 +1,84 @@
+// Internal declarations shared by the CUDA path's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/semr.h"
+
+#if defined(__CUDACC__)
+#define SEMR_HD __host__ __device__
+#else
+#define SEMR_HD
+#endif
+
+namespace semr {
+
+constexpr int kLxMaxTables = 16;
+
+// Payload layout constants (format version 1; see include/semr.h).
+constexpr uint16_t kPayloadVersion = 1;
+constexpr uint64_t kHeaderFixed = 48;  // bytes before code_count[]
+
+SEMR_HD inline uint64_t pad16(uint64_t b) { return (b + 15) & ~uint64_t(15); }
+SEMR_HD inline uint64_t header_bytes(int n_fields) { return pad16(kHeaderFixed + 8ull * n_fields); }
+SEMR_HD inline uint64_t mask_bytes_per_elem(int lx) { return (uint64_t(lx) * lx * lx + 7) / 8; }
+SEMR_HD inline uint64_t field_fixed_bytes(int lx, int64_t n_elem) {
+    return pad16(uint64_t(n_elem) * mask_bytes_per_elem(lx)) + 2 * pad16(2ull * uint64_t(n_elem));
+}
+// tau * 32767^2 > 4  <=>  2/sqrt(tau) < 32767: int16 codes suffice.
+SEMR_HD inline int code_width(double tau) { return tau == 0.0 ? 8 : ((tau * 32767.0 * 32767.0 > 4.0) ? 2 : 4); }
+
+// Host tables (semr_tables.cpp).
+int gll_nodes_weights(int lx, double* x, double* w);
+int basis_tables(int lx, double* A, double* Phi, double* w);
+
+// Look-back tile state word: bits 62..63 flag, bits 0..61 value.
+constexpr uint64_t kFlagAggregate = 1ull << 62;
+constexpr uint64_t kFlagPrefix = 2ull << 62;
+constexpr uint64_t kValueMask = (1ull << 62) - 1;
+
+// Scratch layout: [control 256 B][tile_state u64 x tiles][tile_part 4 x f64 x tiles]
+struct ScratchControl {
+    uint32_t tile_counter;
+    uint32_t status;
+};
+constexpr uint64_t kScratchControlBytes = 256;
+SEMR_HD inline uint64_t scratch_bytes(uint64_t tiles) {
+    return kScratchControlBytes + pad16(8 * tiles) + 32 * tiles;
+}
+// bytes that must be zero before each launch (control + tile states)
+SEMR_HD inline uint64_t scratch_zero_bytes(uint64_t tiles) { return kScratchControlBytes + pad16(8 * tiles); }
+
+// Elements per tile (one CTA per tile) for a given lx.
+SEMR_HD constexpr int tile_elems(int lx) {
+    return lx <= 2 ? 64 : lx <= 3 ? 32 : lx <= 5 ? 16 : lx <= 7 ? 8 : lx <= 10 ? 4 : 2;
+}
+
+struct LaunchParams {
+    const double* fields[SEMR_MAX_FIELDS];
+    double* recon[SEMR_MAX_FIELDS];
+    const double* jac;
+    uint8_t* payload;
+    uint64_t payload_cap;
+    double* elem_report;
+    semr_summary* summary;
+    uint8_t* scratch;
+    int64_t n_elem;
+    int32_t n_fields;
+    int32_t tiles_per_field;
+    double tau;
+    int32_t lossless;
+    int32_t width;
+    int32_t write_recon;
+    int32_t precision;
+    uint64_t header_bytes;
+    uint64_t fixed_bytes;
+    uint64_t code_base;
+};
+
+// Kernel launchers (semr_kernels.cu).  Return a cudaError_t value.
+int launch_reduce(const LaunchParams& p, int lx, void* stream);
+int launch_finalize(const LaunchParams& p, int lx, void* stream);
+
+}  // namespace semr

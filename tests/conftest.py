@@ -29,3 +29,20 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+def _build_native():
+    """Compile the oracle (gcc) and libsemr (nvcc, sm_103a) if stale, so that
+    test modules can import them.  Both builds are plain compiles."""
+    import importlib.util
+
+    import oracle
+    oracle.build()
+    # load the build script by path: importing the package needs the library
+    spec = importlib.util.spec_from_file_location("semr_build", os.path.join(ROOT, "paper_2407_20731_b300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod.build()
+
+
+_build_native()

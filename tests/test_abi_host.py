@@ -1,0 +1,86 @@
+"""Host-side checks of the C ABI: the library loads, exports every entry
+point that include/semr.h declares, validates its arguments without touching
+a GPU, sizes buffers like the payload format says, and its host decoder
+rebuilds oracle payloads."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2407_20731_b300 as semr
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_every_declared_symbol_is_exported():
+    text = open(os.path.join(ROOT, "include", "semr.h")).read()
+    declared = set(re.findall(r"^\s*(?:int|void|const char\*)\s+(semr_\w+)\s*\(", text, re.M))
+    assert declared, "no declarations parsed"
+    lib = ctypes.CDLL(semr.LIB_PATH)
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    assert declared == {n for n, _, _ in semr.EXPORTS}
+
+
+@pytest.mark.parametrize("lx,ne,nf,tau", [(8, 262144, 4, 1e-3), (6, 1001, 3, 0.0), (10, 7, 1, 1e-9), (2, 5, 16, 0.5)])
+def test_sizes_match_payload_format(lx, ne, nf, tau):
+    s = semr.semr_sizes_for(lx, ne, nf, tau)
+    assert s.header_bytes == oracle.header_bytes(nf)
+    assert s.code_base == oracle.header_bytes(nf) + nf * oracle.field_fixed_bytes(lx, ne)
+    width = 8 if tau == 0 else (2 if tau * 32767.0 ** 2 > 4 else 4)
+    assert s.code_width == width
+    assert s.payload_worst == s.code_base + width * lx ** 3 * ne * nf
+
+
+def test_argument_validation_needs_no_gpu():
+    fs, mesh, out = semr.semr_fieldset(), semr.semr_mesh(), semr.semr_outputs()
+    assert semr.semr_reduce_async(fs, mesh, out, 0) == semr.SEMR_EINVAL  # zero sizes, null pointers
+    mesh.lx, mesh.n_elem = 8, 10
+    fs.n_fields, fs.tau = 1, 1e-3
+    assert semr.semr_reduce_async(fs, mesh, out, 0) == semr.SEMR_EINVAL  # null device pointers
+    fs.tau = -1.0
+    assert semr.semr_reduce_async(fs, mesh, out, 0) == semr.SEMR_EINVAL
+    fs.tau, fs.precision = 1e-3, 7
+    mesh.jac = 16
+    assert semr.semr_reduce_async(fs, mesh, out, 0) in (semr.SEMR_EINVAL, semr.SEMR_EUNSUPPORTED)
+    mesh.lx = 13
+    assert semr.semr_reduce_async(fs, mesh, out, 0) == semr.SEMR_EUNSUPPORTED
+    with pytest.raises(semr.SemrError):
+        semr.semr_sizes_for(1, 10, 1, 1e-3)
+    with pytest.raises(semr.SemrError):
+        semr.semr_sizes_for(8, 10, 17, 1e-3)
+    with pytest.raises(semr.SemrError):
+        semr.semr_sizes_for(8, 10, 1, float("inf"))
+    assert "budget" in semr.semr_strerror(semr.SEMR_EBUDGET)
+
+
+@pytest.mark.parametrize("lx", range(2, 13))
+def test_library_gll_matches_oracle(lx):
+    x, w = semr.semr_gll(lx)
+    xo, wo = oracle.gll(lx)
+    np.testing.assert_allclose(x, xo, rtol=0, atol=2e-15)
+    np.testing.assert_allclose(w, wo, rtol=2e-15, atol=0)
+
+
+@pytest.mark.parametrize("lx,tau", [(8, 1e-3), (5, 1e-2), (6, 0.0), (10, 1e-9)])
+def test_host_decoder_rebuilds_oracle_payload(lx, tau):
+    f, j = synth.snapshot(45, lx, [3, 4])
+    f = f.numpy().reshape(2, 45, -1)
+    r = oracle.reduce(f, j.numpy(), tau)
+    dec = semr.semr_decode(r.payload)
+    assert np.abs(dec - r.recon).max() <= 1e-13 * np.abs(f).max()
+
+
+def test_host_decoder_rejects_malformed():
+    f, j = synth.snapshot(8, 6, [1])
+    r = oracle.reduce(f.numpy().reshape(1, 8, -1), j.numpy(), 1e-3)
+    bad = r.payload.copy()
+    bad[0] = ord("X")
+    with pytest.raises(semr.SemrError):
+        semr.semr_decode(bad)
+    with pytest.raises(semr.SemrError):
+        semr.semr_decode(r.payload[:-2])  # truncated code section

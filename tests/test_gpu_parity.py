@@ -1,0 +1,121 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Every case generates one seeded snapshot on the GPU, runs libsemr on it and
+the oracle on a host copy of the same buffer, and compares payloads, masks,
+codes, reconstructions and error reports element by element (see
+tests/parity.py for the tolerances and their derivation).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2407_20731_b300 as semr
+from parity import compare_payloads, compare_reports, make_case, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _full_compare(n_elem, lx, n_fields, tau, seed=1, slope=-5.0 / 3.0):
+    fields, jac = make_case(n_elem, lx, n_fields, seed, slope)
+    res, rec = run_gpu(fields, jac, lx, tau)
+    assert res.summary.status == 0
+    f_np, j_np = fields.cpu().numpy(), jac.cpu().numpy()
+    o = oracle.reduce(f_np, j_np, tau, fragile_cap=100000)
+    compare_payloads(res.payload, o.payload, o.fragile, lossless=(tau == 0.0))
+    compare_reports(f_np, j_np, rec, o, res.elem_report, res.summary, lx)
+    if tau > 0:
+        # the library's host decoder rebuilds the GPU reconstruction
+        dec = semr.semr_decode(res.payload)
+        umax = np.abs(f_np).reshape(n_fields, -1).max(axis=1)
+        assert np.all(np.abs(dec - rec).reshape(n_fields, -1).max(axis=1) <= 1e-12 * umax)
+    return res, o
+
+
+def test_small_case_bit_exact():
+    """512 elements (8^3), lx = 8, one field, tau = 1e-3: identical payload bytes."""
+    res, o = _full_compare(512, 8, 1, 1e-3)
+    assert o.n_fragile == 0
+    assert res.summary.payload_bytes == o.payload.size
+
+
+@pytest.mark.parametrize("lx", [2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12])
+def test_every_lx_ragged(lx):
+    """All supported orders, an element count that leaves a ragged last tile,
+    two fields (the look-back crosses the field boundary)."""
+    _full_compare(203, lx, 2, 1e-3, seed=lx)
+
+
+@pytest.mark.parametrize("tau", [1e-1, 1e-2, 1e-4, 1e-6])
+def test_thresholds_three_fields(tau):
+    _full_compare(1001, 8, 3, tau, seed=7)
+
+
+@pytest.mark.parametrize("lx", [6, 10])
+def test_steep_spectrum(lx):
+    _full_compare(777, lx, 2, 1e-3, seed=3, slope=-3.0)
+
+
+def test_lossless_tau_zero():
+    _full_compare(130, 8, 2, 0.0)
+
+
+def test_int32_codes():
+    res, o = _full_compare(64, 6, 1, 1e-9)
+    assert oracle.parse_header(res.payload)["flags"] & semr.SEMR_PAYLOAD_CODE32
+
+
+def test_tau_above_one_keeps_nothing():
+    res, o = _full_compare(100, 8, 1, 2.0)
+    assert res.summary.code_total == 0
+
+
+def test_single_element():
+    _full_compare(1, 8, 1, 1e-3)
+
+
+def test_many_tiles_lookback():
+    """~10k tiles: the decoupled look-back chains across many CTAs."""
+    _full_compare(20000, 8, 2, 1e-3, seed=5)
+
+
+def test_zero_and_constant_blocks():
+    lx, E = 8, 40
+    fields, jac = make_case(E, lx, 1)
+    fields[0, :10] = 0.0
+    fields[0, 10:20] = 3.25
+    res, rec = run_gpu(fields, jac, lx, 1e-3)
+    o = oracle.reduce(fields.cpu().numpy(), jac.cpu().numpy(), 1e-3)
+    compare_payloads(res.payload, o.payload, o.fragile)
+    compare_reports(fields.cpu().numpy(), jac.cpu().numpy(), rec, o, res.elem_report, res.summary, lx)
+    s = oracle.sections(res.payload)
+    assert np.all(s["counts"][0, :10] == 0) and np.all(s["steps"][0, :10] == -32768)
+
+
+def test_deterministic_repeat():
+    fields, jac = make_case(3000, 8, 2, seed=11)
+    a, ra = run_gpu(fields, jac, 8, 1e-3)
+    b, rb = run_gpu(fields, jac, 8, 1e-3)
+    assert np.array_equal(a.payload, b.payload)
+    assert np.array_equal(ra, rb)
+    assert np.array_equal(a.elem_report, b.elem_report)
+
+
+def test_payload_overflow_reported():
+    lx, E = 8, 64
+    fields, jac = make_case(E, lx, 1)
+    sz = semr.semr_sizes_for(lx, E, 1, 1e-3)
+    bufs = semr.alloc_buffers(lx, E, 1, 1e-3, payload_cap=int(sz.code_base))
+    semr.reduce_async([fields[0]], jac, lx, 1e-3, bufs)
+    torch.cuda.synchronize()
+    sm = semr.summary_from(bufs)
+    assert sm.status & semr.SEMR_STATUS_OVERFLOW
+
+
+def test_nonfinite_input_flagged():
+    lx, E = 6, 30
+    fields, jac = make_case(E, lx, 1)
+    fields[0, 4, 17] = float("nan")
+    res, _ = run_gpu(fields, jac, lx, 1e-3)
+    assert res.summary.status & semr.SEMR_STATUS_NONFINITE
+    assert oracle.sections(res.payload)["counts"][0, 4] == 0
