@@ -1,0 +1,436 @@
+#!/usr/bin/env python3
+"""Benchmark of the in-situ SEM snapshot reduction (arXiv 2407.20731, Sec. IV-B).
+
+One step = one pass of the whole hot path over one snapshot already resident
+in HBM: forward transform, element energy, truncation mask, global
+compaction of the codes, quantisation, reconstruction and error norms (the
+fused reduce kernel), plus the finalize kernel that writes the field reports
+and the payload header.
+
+Default workload: 64^3 = 262,144 hexahedral elements, lx = 8, four FP64
+fields (u, v, w, p) = 4.29 GB per snapshot, tau = 1e-3, synthetic seeded
+spectra standing in for the paper's NEKO Taylor-Green snapshot.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl semr|reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the plain FP64
+CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SIDE, LX, N_FIELDS = 64, 8, 4
+SEEDS = [10, 11, 12, 13]
+METRIC = "snapshot GB/s reduced (FP64 input ingested per second)"
+L2_NOTE = "inputs 4.29 GB per snapshot > 126 MB L2; no flush needed"
+KERNEL_SOURCES = ["paper_2407_20731_b300/csrc/semr_kernels.cu", "paper_2407_20731_b300/csrc/semr_internal.h"]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["semr", "reference"], default="semr")
+    ap.add_argument("--tau", type=float, default=1e-3)
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-extras", action="store_true", help="skip the per-tau and precision-form extras")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--n-side", type=int, default=64, help="elements per side (profiling a smaller case)")
+    return ap.parse_args()
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6400.0, "source": "fallback"}
+
+
+def profiled_traffic(precision: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"reduce_kernel_{precision}_lx8_64cube.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_hash = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    m_traf = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+    if not (m_hash and m_traf) or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_traf.group(1))
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# -------------------------------------------------------------- distributed
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v: float) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------- cpu baseline
+
+def time_oracle(fields_host, jac_host, tau, n_elem, n_threads=0):
+    """One oracle run over the first n_elem elements of every field."""
+    import numpy as np
+
+    import oracle
+    f = np.ascontiguousarray(fields_host[:, :n_elem])
+    j = np.ascontiguousarray(jac_host[:n_elem])
+    t = time.perf_counter()
+    oracle.reduce(f, j, tau, want_recon=False, want_coeffs=False, n_threads=n_threads)
+    return time.perf_counter() - t
+
+
+def calibrated_sample(fields_host, jac_host, tau, target_s):
+    n0 = 2048
+    t0 = time_oracle(fields_host, jac_host, tau, n0)
+    n = int(min(fields_host.shape[1], max(n0, n0 * target_s / max(t0, 1e-6))))
+    return n
+
+
+def cpu_baseline(fields_host, jac_host, tau, target_s):
+    import oracle
+    n = calibrated_sample(fields_host, jac_host, tau, target_s)
+    dt = time_oracle(fields_host, jac_host, tau, n)
+    nbytes = fields_host.shape[0] * n * LX ** 3 * 8
+    return {"value": nbytes / dt / 1e9, "unit": "GB/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"first {n} of {fields_host.shape[1]} elements of each of the {fields_host.shape[0]} fields "
+                      f"({100.0 * n / fields_host.shape[1]:.2f}% of the snapshot), {dt:.1f} s"}
+
+
+# ------------------------------------------------------------------ helpers
+
+def algorithmic_bytes(n_elem, n_fields, code_total, width):
+    """Bytes the fused kernel must move per launch: read every input value
+    once and the Jacobians once; write masks, steps, counts, codes and the
+    element report."""
+    n3 = LX ** 3
+    mb = (n3 + 7) // 8
+    return (n_fields * n_elem * (8 * n3 + mb + 4 + 24) + 8 * n_elem + width * code_total)
+
+
+def make_snapshot(rank, device):
+    import synth
+    seeds = [s + 100 * rank for s in SEEDS]
+    f, j = synth.snapshot(N_SIDE ** 3, LX, seeds, device=device)
+    return f.reshape(N_FIELDS, N_SIDE ** 3, LX ** 3).contiguous(), j.contiguous()
+
+
+def workload_config(args, world):
+    return {"workload": f"SEM snapshot reduction: {N_SIDE}^3 = {N_SIDE ** 3} hex elements, lx={LX}, "
+                        f"{N_FIELDS} FP64 fields (u,v,w,p), tau={args.tau:g}, {args.precision} transforms",
+            "n_elem": N_SIDE ** 3, "lx": LX, "n_fields": N_FIELDS, "tau": args.tau,
+            "precision": args.precision, "snapshot_bytes": N_FIELDS * N_SIDE ** 3 * LX ** 3 * 8,
+            "l2": L2_NOTE, "parallelism": f"replicas x{world} (one independent snapshot per GPU)"}
+
+
+# ---------------------------------------------------------------- semr arm
+
+def run_semr(args):
+    import numpy as np
+    import torch
+
+    import paper_2407_20731_b300 as semr
+
+    world, rank, local = dist_setup(args)
+    dev = torch.device("cuda", local if world > 1 else 0)
+    prec = semr.SEMR_FP64 if args.precision == "fp64" else semr.SEMR_FP32
+    fields, jac = make_snapshot(rank, dev)
+    E = N_SIDE ** 3
+    flist = [fields[i] for i in range(N_FIELDS)]
+    bufs = semr.alloc_buffers(LX, E, N_FIELDS, args.tau, dev)
+    stream = torch.cuda.current_stream()
+    snapshot_bytes = N_FIELDS * E * LX ** 3 * 8
+
+    def step(events=None):
+        semr.reduce_async(flist, jac, LX, args.tau, bufs, prec, events=events)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0.record(stream)
+    for k in range(args.steps):
+        step(kev[k])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms_step = max_over_ranks(world, e0.elapsed_time(e1) / args.steps)
+    kernel_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
+    sm = semr.summary_from(bufs)
+    if sm.status != 0:
+        raise RuntimeError(f"device status {sm.status}")
+
+    value = world * snapshot_bytes / (ms_step * 1e-3) / 1e9
+    algo = algorithmic_bytes(E, N_FIELDS, sm.code_total, int(bufs.sizes.code_width))
+    peaks = measured_peaks()
+    achieved = algo / (kernel_ms * 1e-3) / 1e9
+    traffic = profiled_traffic(args.precision)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+                "peak_source": f"{peaks['source']} (MEASURED_PEAKS hbm_gbs, copy)",
+                "kernel": f"reduce_kernel<{LX},{'double' if prec == semr.SEMR_FP64 else 'float'}>",
+                "kernel_ms": round(kernel_ms, 4), "algorithmic_bytes_per_launch": algo}
+
+    # ---- end to end through the public stream API: pinned host input -> H2D -> submit -> fetch (D2H)
+    e2e = None if args.no_e2e else run_e2e(args, world, dev, fields, jac, bufs, prec, stream, snapshot_bytes)
+    extras = {}
+    if not args.no_extras:
+        extras = run_extras(dev, flist, jac, E, snapshot_bytes, peaks)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(fields.cpu().numpy(), jac.cpu().numpy(), args.tau, args.cpu_seconds)
+    emit(args, rank, world, value, ms_step, prec, roofline, cpu, e2e, clk, sm, extras)
+
+
+def run_e2e(args, world, dev, fields, jac, bufs, prec, stream, snapshot_bytes):
+    import torch
+
+    import paper_2407_20731_b300 as semr
+    E = jac.numel()
+    host_f = torch.empty((N_FIELDS, E, LX ** 3), dtype=torch.float64, pin_memory=True)
+    host_f.copy_(fields)
+    host_j = torch.empty(E, dtype=torch.float64, pin_memory=True)
+    host_j.copy_(jac)
+    dev_f = torch.empty_like(fields)
+    dev_j = torch.empty_like(jac)
+    host_payload = torch.empty(int(bufs.sizes.payload_worst), dtype=torch.uint8, pin_memory=True).numpy()
+    handle = semr.semr_open(dev.index, stream.cuda_stream, 0)
+    fs = semr.make_fieldset([dev_f[i] for i in range(N_FIELDS)], args.tau, prec)
+    mesh = semr.make_mesh(LX, dev_j)
+    pbytes = 0
+
+    def e2e_step():
+        nonlocal pbytes
+        dev_f.copy_(host_f, non_blocking=True)
+        dev_j.copy_(host_j, non_blocking=True)
+        rc, ticket = semr.semr_submit(handle, fs, mesh)
+        if rc:
+            raise semr.SemrError(rc, "semr_submit")
+        rc, pbytes, reps = semr.semr_fetch(handle, ticket, True, host_payload, N_FIELDS)
+        if rc:
+            raise semr.SemrError(rc, "semr_fetch")
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    k_e2e = max(3, min(args.steps, 20))
+    t = time.perf_counter()
+    for _ in range(k_e2e):
+        e2e_step()
+    torch.cuda.synchronize()
+    dt = max_over_ranks(world, (time.perf_counter() - t) / k_e2e)
+    semr.semr_close(handle)
+    e2e = {"value": round(world * snapshot_bytes / dt / 1e9, 2), "unit": "GB/s",
+           "h2d_bytes_per_step": snapshot_bytes + 8 * E,
+           "d2h_bytes_per_step": int(pbytes) + semr.ctypes.sizeof(semr.semr_summary),
+           "ms_per_step": round(dt * 1e3, 3), "api": "semr_open/semr_submit/semr_fetch, pinned host buffers"}
+    del dev_f, dev_j, host_f, host_j
+    return e2e
+
+
+def run_extras(dev, flist, jac, E, snapshot_bytes, peaks):
+    """Other thresholds of the workload, and the FP32 precision form, on the same snapshot."""
+    import torch
+
+    import paper_2407_20731_b300 as semr
+
+    def timed(tau, p, n=10):
+        b = semr.alloc_buffers(LX, E, N_FIELDS, tau, dev)
+        for _ in range(2):
+            semr.reduce_async(flist, jac, LX, tau, b, p)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for a in ev:
+            semr.reduce_async(flist, jac, LX, tau, b, p, events=a)
+        torch.cuda.synchronize()
+        kms = statistics.mean(a.elapsed_time(c) for a, c in ev)
+        s = semr.summary_from(b)
+        res = {"kernel_ms": round(kms, 4), "GB_s": round(snapshot_bytes / kms / 1e6, 1),
+               "hbm_frac": round(algorithmic_bytes(E, N_FIELDS, s.code_total, int(b.sizes.code_width))
+                                 / (kms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+               "cr": round(s.cr, 5), "l2_rel": [round(s.field[i].l2_rel, 6) for i in range(N_FIELDS)],
+               "linf_rel": [round(s.field[i].linf_rel, 6) for i in range(N_FIELDS)], "status": s.status}
+        del b
+        return res
+
+    return {"by_tau_fp64": {f"{t:g}": timed(t, semr.SEMR_FP64) for t in (1e-2, 1e-3, 1e-4)},
+            "precision_form_fp32": {f"{t:g}": timed(t, semr.SEMR_FP32) for t in (1e-3, 1e-5)}}
+
+
+def emit(args, rank, world, value, ms_step, prec, roofline, cpu, e2e, clk, sm, extras):
+    import paper_2407_20731_b300 as semr
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64" if prec == semr.SEMR_FP64 else "f32",
+                "data": "synthetic (seeded 16-mode |k|^-5/3 spectra + N(0,1e-6) noise, J~U[0.5,2])",
+                "config": workload_config(args, world), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": 2 * args.steps, "clocks": clk,
+                "result": {"cr": round(sm.cr, 5), "payload_bytes": int(sm.payload_bytes),
+                           "l2_rel": [round(sm.field[i].l2_rel, 6) for i in range(N_FIELDS)],
+                           "linf_rel": [round(sm.field[i].linf_rel, 6) for i in range(N_FIELDS)]},
+                "extras": extras}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------- reference arm
+
+def run_reference(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    fields, jac = make_snapshot(0, dev)
+    fh, jh = fields.cpu().numpy(), jac.cpu().numpy()
+    del fields, jac
+    # per-step sample sized so that warmup + steps finish in about 3 minutes
+    per_step = max(0.5, min(10.0, 180.0 / (args.steps + args.warmup)))
+    n = calibrated_sample(fh, jh, args.tau, per_step)
+    for _ in range(args.warmup):
+        time_oracle(fh, jh, args.tau, n)
+    times = [time_oracle(fh, jh, args.tau, n) for _ in range(args.steps)]
+    dt = statistics.mean(times)
+    nbytes = N_FIELDS * n * LX ** 3 * 8
+    value = nbytes / dt / 1e9
+    sample = (f"first {n} of {fh.shape[1]} elements of each of the {N_FIELDS} fields per step "
+              f"({100.0 * n / fh.shape[1]:.2f}% of the snapshot)")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (same generator and seeds)",
+            "config": workload_config(args, world),
+            "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": oracle.max_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    global N_SIDE
+    args = parse_args()
+    N_SIDE = args.n_side
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_semr(args)
+
+
+if __name__ == "__main__":
+    main()

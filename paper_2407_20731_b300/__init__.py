@@ -261,6 +261,9 @@ def reduce_async(fields, jac, lx: int, tau: float, bufs: DeviceBuffers, precisio
     if events is None:
         _check(semr_reduce_async(fs, mesh, bufs.outputs, st), "semr_reduce_async")
     else:
+        for ev in events:  # torch creates its events lazily, on the first record
+            if not ev.cuda_event:
+                ev.record(stream or torch.cuda.current_stream())
         _check(semr_reduce_async_timed(fs, mesh, bufs.outputs, st, events[0].cuda_event, events[1].cuda_event),
                "semr_reduce_async_timed")
 
