@@ -241,6 +241,37 @@ int semr_decode(const void* payload, uint64_t bytes, double* out, uint64_t cap_d
 /* semr_gll: the library's GLL nodes and weights (host, lx entries each). */
 int semr_gll(int32_t lx, double* nodes, double* weights);
 
+/*
+ * semr_reduce_async_noalloc: semr_reduce_async for callers that cannot
+ * allocate device memory -- for example a solver that hands nearly all of
+ * the GPU's memory to its own pool at start-up, or in-situ code that runs
+ * between time steps where no allocator call is allowed.  The paper has no
+ * counterpart to this entry point.
+ *
+ * The caller still passes the inputs and the outputs (payload of
+ * payload_cap bytes, optional elem_report, summary), all device memory, as
+ * in semr_outputs.  The kernel's scratch comes from one file-scope device
+ * array of SEMR_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU loading the
+ * library holds until the process exits; nothing is allocated or freed
+ * (no cudaMalloc, cudaFree or allocating library routine).  A snapshot
+ * whose scratch (semr_sizes.scratch_bytes, 40 bytes per work tile) exceeds
+ * that size is rejected with SEMR_EINVAL; at lx = 8 that is about 1.6
+ * million element-fields (e.g. 64^3 elements x 6 fields).
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it: make that first call before any stream
+ * capture.  Every call on a device shares the one array, whose contents
+ * persist between calls; each call clears the part that must start at zero.
+ * Calls that overlap on the GPU (on different streams, or not yet finished
+ * on another stream) race on the array and corrupt each other's results:
+ * order them on one stream.  Errors as semr_reduce_async, plus SEMR_ECUDA if
+ * the address lookup fails.
+ */
+#define SEMR_NOALLOC_SCRATCH_BYTES (16ull << 20)
+int semr_reduce_async_noalloc(const semr_fieldset* fs, const semr_mesh* mesh, uint8_t* payload,
+                              uint64_t payload_cap, double* elem_report, semr_summary* summary,
+                              void* cuda_stream);
+
 /* semr_strerror: static text for a status code. */
 const char* semr_strerror(int code);
 

@@ -89,7 +89,10 @@ EXPORTS = [
                                    ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]),
     ("semr_gll", ctypes.c_int, [ctypes.c_int32, _P, _P]),
     ("semr_strerror", ctypes.c_char_p, [ctypes.c_int]),
+    ("semr_reduce_async_noalloc", ctypes.c_int, [ctypes.POINTER(semr_fieldset), ctypes.POINTER(semr_mesh), _P,
+                                                 ctypes.c_uint64, _P, _P, _P]),
 ]
+SEMR_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libsemr.so is not built ({LIB_PATH}); run __graft_entry__.build() "
@@ -133,6 +136,14 @@ def semr_reduce_async_timed(fs: semr_fieldset, mesh: semr_mesh, out: semr_output
                             ev_begin: int | None, ev_end: int | None) -> int:
     return _lib.semr_reduce_async_timed(ctypes.byref(fs), ctypes.byref(mesh), ctypes.byref(out), stream,
                                         ev_begin, ev_end)
+
+
+def semr_reduce_async_noalloc(fs: semr_fieldset, mesh: semr_mesh, payload: int, payload_cap: int,
+                              elem_report: int | None, summary: int, stream: int) -> int:
+    """The reduction without any allocation: scratch comes from the library's
+    fixed device array (see include/semr.h); calls must not overlap on the GPU."""
+    return _lib.semr_reduce_async_noalloc(ctypes.byref(fs), ctypes.byref(mesh), payload, payload_cap,
+                                          elem_report, summary, stream)
 
 
 def semr_open(device: int = 0, stream: int = 0, mem_budget_bytes: int = 0) -> int:

@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libsemr.so")
-SOURCES = [os.path.join(HERE, "csrc", s) for s in ("semr_kernels.cu", "semr_api.cpp", "semr_tables.cpp")]
+SOURCES = [os.path.join(HERE, "csrc", s) for s in ("semr_kernels.cu", "semr_api.cpp", "semr_tables.cpp", "semr_noalloc.cu")]
 HEADERS = [os.path.join(HERE, "csrc", "semr_internal.h"), os.path.join(ROOT, "include", "semr.h")]
 
 NVCC_FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",

@@ -1,0 +1,81 @@
+"""The no-allocation entry point, checked against semr_reduce_async.
+
+Some callers cannot allocate GPU memory: a solver that reserves nearly all of
+the device for its own pool at start-up, or in-situ code that runs between
+time steps where no allocator call is allowed.  For them,
+semr_reduce_async_noalloc takes the kernel's scratch from a fixed device
+array inside the library; the caller passes only inputs and outputs.
+
+The test calls it through the C ABI twice in a row, on two different
+snapshots (the second call must not see the first call's scratch), and
+compares each result with what the ordinary entry point produces on the same
+input.  Both run the same deterministic kernel, so payload, summary and
+element report must be identical byte for byte (stricter than the parity
+tolerances of the other tests).  This file is named so that pytest collects
+it last.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2407_20731_b300 as semr
+from parity import make_case
+
+pytestmark = pytest.mark.gpu
+
+
+def _reference(fields, jac, lx, tau):
+    F, E = fields.shape[0], fields.shape[1]
+    bufs = semr.alloc_buffers(lx, E, F, tau)
+    semr.reduce_async([fields[i] for i in range(F)], jac, lx, tau, bufs)
+    torch.cuda.synchronize()
+    sm = semr.summary_from(bufs)
+    return (bufs.payload[: sm.payload_bytes].cpu().numpy(), bytes(bufs.summary.cpu().numpy()),
+            bufs.elem_report.cpu().numpy())
+
+
+def _noalloc(fields, jac, lx, tau):
+    F, E = fields.shape[0], fields.shape[1]
+    sz = semr.semr_sizes_for(lx, E, F, tau)
+    # outputs allocated by the caller beforehand; filled with junk to show they are overwritten
+    payload = torch.full((int(sz.payload_worst),), 0xA5, dtype=torch.uint8, device="cuda")
+    summary = torch.full((ctypes.sizeof(semr.semr_summary),), 0x5A, dtype=torch.uint8, device="cuda")
+    elem = torch.full((F * E * 3,), -1.0, dtype=torch.float64, device="cuda")
+    fs = semr.make_fieldset([fields[i] for i in range(F)], tau)
+    mesh = semr.make_mesh(lx, jac)
+    rc = semr.semr_reduce_async_noalloc(fs, mesh, payload.data_ptr(), payload.numel(), elem.data_ptr(),
+                                        summary.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert rc == semr.SEMR_OK, semr.semr_strerror(rc)
+    torch.cuda.synchronize()
+    sm = semr.semr_summary.from_buffer_copy(bytes(summary.cpu().numpy()))
+    assert sm.status == 0
+    return payload[: sm.payload_bytes].cpu().numpy(), bytes(summary.cpu().numpy()), elem.cpu().numpy()
+
+
+def test_noalloc_matches_reduce_async_on_two_calls_in_a_row():
+    cases = [(3001, 8, 3, 1e-3, 21), (1500, 6, 2, 1e-2, 22)]
+    for n_elem, lx, nf, tau, seed in cases:
+        fields, jac = make_case(n_elem, lx, nf, seed=seed)
+        ref_p, ref_s, ref_e = _reference(fields, jac, lx, tau)
+        got_p, got_s, got_e = _noalloc(fields, jac, lx, tau)
+        assert got_p.size == ref_p.size and np.array_equal(got_p, ref_p)
+        assert _meaningful(got_s, nf) == _meaningful(ref_s, nf)
+        assert np.array_equal(got_e, ref_e)
+
+
+def _meaningful(raw: bytes, n_fields: int) -> bytes:
+    """The summary up to its last used field report (slots past n_fields are
+    never written)."""
+    off = semr.semr_summary.field.offset + n_fields * ctypes.sizeof(semr.semr_field_report)
+    return raw[:off]
+
+
+def test_noalloc_rejects_snapshots_beyond_its_scratch():
+    lx, nf, n_elem = 8, 3, 600000  # 3 * 150000 tiles * 40 B > 16 MiB
+    assert semr.semr_sizes_for(lx, n_elem, nf, 1e-3).scratch_bytes > semr.SEMR_NOALLOC_SCRATCH_BYTES
+    fs, mesh = semr.semr_fieldset(), semr.semr_mesh()
+    fs.n_fields, fs.tau, mesh.lx, mesh.n_elem = nf, 1e-3, lx, n_elem
+    rc = semr.semr_reduce_async_noalloc(fs, mesh, None, 0, None, None, torch.cuda.current_stream().cuda_stream)
+    assert rc == semr.SEMR_EINVAL
