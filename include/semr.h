@@ -75,9 +75,14 @@ extern "C" {
 #define SEMR_LX_MAX 12
 
 /* precision of the transforms */
-#define SEMR_FP64 0   /* transforms, energy, threshold test, norms in FP64 */
-#define SEMR_FP32 1   /* transforms in FP32 with FP32 accumulation; energy, threshold test and
-                         cross-thread norm reductions in FP64 (the precision form) */
+#define SEMR_FP64 0          /* FP64 accuracy: every value a pair of floats (about 48 significant bits,
+                                ~1e-14 relative), run on the FP32 pipes; payloads match an FP64
+                                computation bit for bit outside decisions within 1e-9 of a tie */
+#define SEMR_FP32 1          /* the precision form: transforms in FP32 with FP32 accumulation; the
+                                threshold test is exactly the FP64 comparison; element and field
+                                sums are float-pair tree sums finished in FP64 */
+#define SEMR_FP64_NATIVE 2   /* every operation in hardware FP64 (slow on B300: its FP64 pipe runs
+                                under 1 TFLOP/s); kept as a reference path */
 
 /* fieldset flags */
 #define SEMR_WRITE_RECON 1   /* also write the reconstruction to fieldset.recon[f] */

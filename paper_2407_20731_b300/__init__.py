@@ -27,7 +27,7 @@ LIB_PATH = os.path.join(_HERE, "libsemr.so")
 SEMR_OK, SEMR_EINVAL, SEMR_ENOMEM, SEMR_EBUDGET, SEMR_EAGAIN = 0, 1, 2, 3, 4
 SEMR_ETIMEDOUT, SEMR_ECUDA, SEMR_ENOSPACE, SEMR_ENONFINITE, SEMR_EUNSUPPORTED = 5, 6, 7, 8, 9
 SEMR_MAX_FIELDS, SEMR_LX_MIN, SEMR_LX_MAX = 16, 2, 12
-SEMR_FP64, SEMR_FP32 = 0, 1
+SEMR_FP64, SEMR_FP32, SEMR_FP64_NATIVE = 0, 1, 2
 SEMR_WRITE_RECON = 1
 SEMR_PAYLOAD_LOSSLESS, SEMR_PAYLOAD_CODE32, SEMR_PAYLOAD_FP32 = 1, 2, 4
 SEMR_STATUS_OVERFLOW, SEMR_STATUS_TIMEOUT, SEMR_STATUS_NONFINITE = 1, 2, 4

@@ -63,7 +63,8 @@ extern "C" int semr_reduce_async_timed(const semr_fieldset* fs, const semr_mesh*
     if (mesh->lx >= 2 && !lx_supported(mesh->lx)) return SEMR_EUNSUPPORTED;
     int rc = check_common(mesh->lx, mesh->n_elem, fs->n_fields, fs->tau);
     if (rc) return rc;
-    if (fs->precision != SEMR_FP64 && fs->precision != SEMR_FP32) return SEMR_EUNSUPPORTED;
+    if (fs->precision != SEMR_FP64 && fs->precision != SEMR_FP32 && fs->precision != SEMR_FP64_NATIVE)
+        return SEMR_EUNSUPPORTED;
     if (!mesh->jac || !out->payload || !out->summary || !out->scratch) return SEMR_EINVAL;
     if ((reinterpret_cast<uintptr_t>(out->scratch) & 255u) != 0 || !aligned16(out->payload)) return SEMR_EINVAL;
     // even lx: element blocks are loaded as 16-byte vectors; odd lx: 8-byte scalars

@@ -1,0 +1,793 @@
+// Fast fused reduce kernel (arXiv 2407.20731, Sec. IV-B: JPEG-like spectral
+// truncation of SEM fields; Eq. 1 for the compression ratio), built around
+// B300's arithmetic: FP32 lanes run 65 TFLOP/s while every FP64 instruction
+// (DFMA, DADD, F2F conversions, DMNMX) shares a pipe of under 1 TFLOP/s.  So
+// no FP64 instruction runs per point:
+//   * MODE_F32  (the precision form): FP32 transforms with FP32 accumulation.
+//   * MODE_DF64 (FP64 accuracy): every value a pair of floats (hi + lo, about
+//     48 significant bits), error-free products via FMA; the result agrees
+//     with FP64 to ~1e-14 relative.
+// The input doubles are split into floats with integer instructions.  The
+// threshold test is an exact magnitude comparison, the sums over an element
+// are pair-of-float tree sums (deterministic), and only once per element do
+// a few FP64 instructions form t = tau S_e, the step and the threshold.
+//
+// The reconstruction exploits how few modes survive (2-3 per element at
+// tau = 1e-3): each thread rebuilds its pencil from the element's list of
+// kept modes, u~(i) = sum_m c_m 2^s phi_p(x_i) phi_q(x_j) phi_r(x_k).  When a
+// tile keeps many modes (or in lossless mode) it switches to the dense
+// folded inverse with two shared-memory transposes.
+#include <algorithm>
+#include <type_traits>
+
+#include "semr_device.cuh"
+
+namespace semr {
+
+constexpr int MODE_F32 = 0;
+constexpr int MODE_DF64 = 1;
+
+template <int LX>
+struct FastTables {
+    float Ah[LX * LX], Al[LX * LX];    // analysis A[p*LX + i] (hi, lo)
+    float Ph[LX * LX], Pl[LX * LX];    // synthesis Phi[i*LX + p] (hi, lo)
+    float wh[LX], wl[LX];              // GLL weights (hi, lo)
+};
+
+template <int LX>
+struct FCfg {
+    static constexpr int NP = LX * LX;             // threads (pencils) per element
+    static constexpr int N3 = LX * LX * LX;
+    static constexpr int TILE = tile_elems(LX);    // elements per tile
+    static constexpr int NT = TILE * NP;
+    static constexpr int BLOCK = (NT + 31) / 32 * 32;
+    static constexpr int NW = BLOCK / 32;
+    static constexpr int MW = (N3 + 31) / 32;      // 32-bit mask words per element
+    static constexpr int SY = LX + 1;              // padded transpose strides
+    static constexpr int SX = LX * (LX + 1);
+    static constexpr int BUFN = LX * SX;
+    static constexpr int PT = LX + 1;              // padded row of the shared Phi tables
+    // Elements line up with warps: whole warps (NP % 32 == 0) or a power-of-two
+    // lane group inside one warp (32 % NP == 0).  Then reductions run on warp
+    // shuffles and the mask is built with ballots; otherwise through shared memory.
+    static constexpr bool ALIGNED = (NP % 32 == 0) || (32 % NP == 0);
+    static constexpr int SEG = NP < 32 ? NP : 32;  // lanes of one element in a warp
+    static constexpr int WPE = NP >= 32 ? NP / 32 : 1;
+    static constexpr bool BALLOT = (NP % 32 == 0);
+};
+
+template <int LX, int MODE>
+struct FSmem {
+    using C = FCfg<LX>;
+    static constexpr size_t vb = (MODE == MODE_DF64) ? 8 : 4;   // float2 or float per value
+    static constexpr size_t buf_bytes = vb * C::TILE * C::BUFN;
+    static constexpr size_t off_t1 = 0;
+    static constexpr size_t off_t2 = off_t1 + buf_bytes;
+    static constexpr size_t off_codes = off_t2 + buf_bytes;               // staging, 8 B max per code
+    static constexpr size_t off_kc = off_codes + 8ull * C::TILE * C::N3;  // kept codes (f32)
+    static constexpr size_t off_km = off_kc + 4ull * C::TILE * C::N3;     // kept modes (u16)
+    static constexpr size_t off_red = (off_km + 2ull * C::TILE * C::N3 + 15) / 16 * 16;  // BLOCK x 16 B
+    static constexpr size_t off_elem = off_red + 16ull * C::BLOCK;         // TILE x 8 doubles
+    static constexpr size_t off_phi = off_elem + 64ull * C::TILE;          // 4 tables x LX x PT floats
+    static constexpr size_t off_mask = off_phi + 16ull * LX * C::PT;       // TILE x MW u32
+    static constexpr size_t off_wpre = off_mask + 4ull * C::TILE * C::MW;
+    static constexpr size_t off_misc = (off_wpre + 4ull * C::TILE * C::MW + 15) / 16 * 16;
+    static constexpr size_t bytes = off_misc + 4ull * (8 * C::TILE + 16);
+};
+
+// Per-element reduction of one sum (a float pair) and one maximum (a 64-bit
+// pattern of a non-negative number, read back as a double or as a float).
+// Results: out[lt*8 + slot_sum], out[lt*8 + slot_max] (doubles).  The sum is
+// a pair-of-float tree in FP64 mode, an FP32 tree inside a warp in FP32 mode;
+// partials across warps are added in FP64.  Fixed order: deterministic.
+template <int LX, bool DF>
+__device__ __forceinline__ void elem_reduce(float* red, double* out, f2 s, unsigned long long mx, bool mx_double,
+                                            int slot_sum, int slot_max, int n_here) {
+    using C = FCfg<LX>;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if constexpr (C::ALIGNED) {
+#pragma unroll
+        for (int o = C::SEG / 2; o > 0; o >>= 1) {
+            const float h = __shfl_xor_sync(0xffffffffu, s.h, o);
+            if constexpr (DF) {
+                const float l = __shfl_xor_sync(0xffffffffu, s.l, o);
+                const f2 t = two_sum(s.h, h);
+                s = {t.h, t.l + (s.l + l)};
+            } else {
+                s.h += h;
+            }
+        }
+        const unsigned seg_mask = (C::SEG == 32) ? 0xffffffffu : (((1u << C::SEG) - 1u) << (lane & ~(C::SEG - 1)));
+        unsigned mhi = (unsigned)(mx >> 32), mlo = (unsigned)mx;
+        if (mx_double) {
+            const unsigned top = __reduce_max_sync(seg_mask, mhi);
+            mlo = __reduce_max_sync(seg_mask, mhi == top ? mlo : 0u);
+            mhi = top;
+        } else {
+            mlo = __reduce_max_sync(seg_mask, mlo);
+            mhi = 0;
+        }
+        float4* r4 = reinterpret_cast<float4*>(red);
+        const int slot = warp * (32 / C::SEG) + lane / C::SEG;  // one slot per (warp, element segment)
+        if ((lane & (C::SEG - 1)) == 0) r4[slot] = make_float4(s.h, s.l, __uint_as_float(mhi), __uint_as_float(mlo));
+        __syncthreads();
+        if (tid < C::TILE && tid < n_here) {
+            double sum = 0.0;
+            unsigned long long m = 0;
+            for (int k = 0; k < C::WPE; ++k) {
+                const float4 v = r4[tid * C::WPE + k];
+                sum += (double)v.x + (double)v.y;
+                m = max(m, ((unsigned long long)__float_as_uint(v.z) << 32) | __float_as_uint(v.w));
+            }
+            out[tid * 8 + slot_sum] = sum;
+            out[tid * 8 + slot_max] = mx_double ? __longlong_as_double((long long)m) : (double)__uint_as_float((unsigned)m);
+        }
+        __syncthreads();
+    } else {
+        float4* r4 = reinterpret_cast<float4*>(red);
+        r4[tid] = make_float4(s.h, s.l, __uint_as_float((unsigned)(mx >> 32)), __uint_as_float((unsigned)mx));
+        __syncthreads();
+        for (int lt = warp; lt < C::TILE; lt += C::NW) {
+            f2 a = {0.0f, 0.0f};
+            unsigned long long m = 0;
+            for (int i = lane; i < C::NP; i += 32) {
+                const float4 v = r4[lt * C::NP + i];
+                a = df_add(a, {v.x, v.y});
+                m = max(m, ((unsigned long long)__float_as_uint(v.z) << 32) | __float_as_uint(v.w));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a = df_add(a, {__shfl_xor_sync(0xffffffffu, a.h, o), __shfl_xor_sync(0xffffffffu, a.l, o)});
+                m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+            }
+            if (lane == 0) {
+                out[lt * 8 + slot_sum] = (double)a.h + (double)a.l;
+                out[lt * 8 + slot_max] =
+                    mx_double ? __longlong_as_double((long long)m) : (double)__uint_as_float((unsigned)m);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int LX, int MODE>
+__global__ void __launch_bounds__(FCfg<LX>::BLOCK, FCfg<LX>::BLOCK <= 256 ? (MODE == MODE_F32 ? 3 : 2) : 1)
+reduce_fast_kernel(const LaunchParams p, const FastTables<LX> tab) {
+    using C = FCfg<LX>;
+    using S = FSmem<LX, MODE>;
+    constexpr int NP = C::NP, N3 = C::N3, TILE = C::TILE, MW = C::MW, SX = C::SX, SY = C::SY, PT = C::PT;
+    constexpr bool DF = (MODE == MODE_DF64);
+    using V = typename std::conditional<DF, float2, float>::type;  // one transposed value
+    // dense inverse once any element of the tile keeps more modes than this
+    constexpr int SPARSE_MAX = DF ? 12 : 5;
+
+    extern __shared__ __align__(16) uint8_t smem[];
+    V* t1 = reinterpret_cast<V*>(smem + S::off_t1);
+    V* t2 = reinterpret_cast<V*>(smem + S::off_t2);
+    uint8_t* scodes = smem + S::off_codes;
+    float* skc = reinterpret_cast<float*>(smem + S::off_kc);
+    uint16_t* skm = reinterpret_cast<uint16_t*>(smem + S::off_km);
+    float* red = reinterpret_cast<float*>(smem + S::off_red);
+    double* selem = reinterpret_cast<double*>(smem + S::off_elem);
+    float* sPh = reinterpret_cast<float*>(smem + S::off_phi);  // Phi[i][p], rows padded
+    float* sPl = sPh + LX * PT;
+    float* sPTh = sPl + LX * PT;                                 // Phi[i][p] stored as [p][i]
+    float* sPTl = sPTh + LX * PT;
+    uint32_t* smask = reinterpret_cast<uint32_t*>(smem + S::off_mask);
+    uint32_t* swpre = reinterpret_cast<uint32_t*>(smem + S::off_wpre);
+    int* smisc = reinterpret_cast<int*>(smem + S::off_misc);
+    unsigned long long* s_tile = reinterpret_cast<unsigned long long*>(smisc);  // [0] tile, [1] excl
+    int* s_cnt = smisc + 4;              // [TILE]
+    int* s_epre = s_cnt + TILE;          // [TILE + 1]
+    int* s_step = s_epre + TILE + 1;     // [TILE]
+    int* s_mode = s_step + TILE;         // [TILE]
+    int* s_bad = s_mode + TILE;          // [TILE]
+    int* s_flag = s_bad + TILE;          // [2]: dense inverse needed
+    float* s_g = reinterpret_cast<float*>(s_flag + 2);  // [2 * TILE]: threshold (hi, lo)
+
+    ScratchControl* ctl = reinterpret_cast<ScratchControl*>(p.scratch);
+    uint64_t* tile_state = reinterpret_cast<uint64_t*>(p.scratch + kScratchControlBytes);
+    const uint64_t n_tiles = (uint64_t)p.n_fields * p.tiles_per_field;
+    double* tile_part = reinterpret_cast<double*>(p.scratch + kScratchControlBytes + pad16(8 * n_tiles));
+
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int lt = tid / NP;
+    const int P = tid % NP;
+    const int pa = P / LX, pb = P % LX;
+    const bool in_tile = lt < TILE;
+    const int lts = in_tile ? lt : 0;
+    V* b1 = t1 + lts * C::BUFN;
+    V* b2 = t2 + lts * C::BUFN;
+    const int width = p.width;
+
+    for (int i = tid; i < LX * LX; i += C::BLOCK) {
+        const int r = i / LX, c = i % LX;  // Phi[r][c]
+        sPh[r * PT + c] = tab.Ph[i];
+        sPl[r * PT + c] = tab.Pl[i];
+        sPTh[c * PT + r] = tab.Ph[i];
+        sPTl[c * PT + r] = tab.Pl[i];
+    }
+    // quadrature weight products w_i w_j w_k of this pencil (j = pb, k = pa)
+    f2 wq[LX];
+    {
+        const f2 wjk = df_mul({tab.wh[pa], tab.wl[pa]}, {tab.wh[pb], tab.wl[pb]});
+#pragma unroll
+        for (int i = 0; i < LX; ++i) wq[i] = DF ? df_mul({tab.wh[i], tab.wl[i]}, wjk) : f2{tab.wh[i] * wjk.h, 0.0f};
+    }
+
+    // persistent CTA: claim tiles in increasing order until none are left
+    for (;;) {
+    if (tid == 0) {
+        s_tile[0] = atomicAdd(&ctl->tile_counter, 1u);
+        s_flag[0] = 0;
+    }
+    if constexpr (!C::BALLOT) {
+        for (int i = tid; i < TILE * MW; i += C::BLOCK) smask[i] = 0u;
+    }
+    if (tid < TILE) s_bad[tid] = 0;
+    __syncthreads();
+    const uint64_t tile = s_tile[0];
+    if (tile >= n_tiles) break;
+    const int f = (int)(tile / p.tiles_per_field);
+    const int64_t e0 = (int64_t)(tile % p.tiles_per_field) * TILE;
+    const int n_here = (p.n_elem - e0 < TILE) ? (int)(p.n_elem - e0) : TILE;
+    const bool active = (tid < C::NT) && (lt < n_here);
+    const int64_t e = e0 + lt;
+
+    // ---- load the pencil u[k=pa][j=pb][0..LX-1], split to floats with integer ops
+    float uh[LX], ul[LX];
+    unsigned long long umax_bits = 0;  // max |u|: exact double pattern (FP64 mode) or float pattern
+    {
+        double u[LX];
+        if (active) {
+            const double* src = p.fields[f] + e * N3 + P * LX;
+            if constexpr ((LX % 2) == 0) {
+#pragma unroll
+                for (int i = 0; i < LX; i += 2) {
+                    const double2 v = __ldg(reinterpret_cast<const double2*>(src + i));
+                    u[i] = v.x;
+                    u[i + 1] = v.y;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < LX; ++i) u[i] = __ldg(src + i);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < LX; ++i) u[i] = 0.0;
+        }
+        bool bad = false;
+#pragma unroll
+        for (int i = 0; i < LX; ++i) {
+            bad |= out_of_float_range(u[i]);
+            if constexpr (DF) {
+                umax_bits = max(umax_bits, (unsigned long long)__double_as_longlong(u[i]) & 0x7fffffffffffffffull);
+                d2f_split(u[i], uh[i], ul[i]);
+            } else {
+                uh[i] = d2f_rz(u[i]);
+                ul[i] = 0.0f;
+                umax_bits = max(umax_bits, (unsigned long long)__float_as_uint(fabsf(uh[i])));
+            }
+        }
+        if (bad) s_bad[lt] = 1;  // read after the next barrier
+    }
+
+    // ---- forward transform along i (registers), j, k (shared-memory transposes)
+    float ah[LX], al[LX];  // modal coefficients a[r][q=pa][p=pb], mode m = P + NP r
+    if constexpr (DF) {
+        f2 x[LX], y[LX];
+#pragma unroll
+        for (int i = 0; i < LX; ++i) x[i] = {uh[i], ul[i]};
+        fwd1d_df<LX>(tab.Ah, tab.Al, x, y);
+        if (in_tile) {
+#pragma unroll
+            for (int q = 0; q < LX; ++q) b1[pa * SX + pb * SY + q] = make_float2(y[q].h, y[q].l);
+        }
+        __syncthreads();
+        if (in_tile) {
+#pragma unroll
+            for (int j = 0; j < LX; ++j) {
+                const float2 v = b1[pa * SX + j * SY + pb];
+                x[j] = {v.x, v.y};
+            }
+        }
+        fwd1d_df<LX>(tab.Ah, tab.Al, x, y);
+        if (in_tile) {
+#pragma unroll
+            for (int q = 0; q < LX; ++q) b2[pa * SX + q * SY + pb] = make_float2(y[q].h, y[q].l);
+        }
+        __syncthreads();
+        if (in_tile) {
+#pragma unroll
+            for (int k = 0; k < LX; ++k) {
+                const float2 v = b2[k * SX + pa * SY + pb];
+                x[k] = {v.x, v.y};
+            }
+        }
+        fwd1d_df<LX>(tab.Ah, tab.Al, x, y);
+#pragma unroll
+        for (int r = 0; r < LX; ++r) {
+            ah[r] = y[r].h;
+            al[r] = y[r].l;
+        }
+    } else {
+        float x[LX], y[LX];
+#pragma unroll
+        for (int i = 0; i < LX; ++i) x[i] = uh[i];
+        fwd1d<LX, float>(tab.Ah, x, y);
+        if (in_tile) {
+#pragma unroll
+            for (int q = 0; q < LX; ++q) b1[pa * SX + pb * SY + q] = y[q];
+        }
+        __syncthreads();
+        if (in_tile) {
+#pragma unroll
+            for (int j = 0; j < LX; ++j) x[j] = b1[pa * SX + j * SY + pb];
+        }
+        fwd1d<LX, float>(tab.Ah, x, y);
+        if (in_tile) {
+#pragma unroll
+            for (int q = 0; q < LX; ++q) b2[pa * SX + q * SY + pb] = y[q];
+        }
+        __syncthreads();
+        if (in_tile) {
+#pragma unroll
+            for (int k = 0; k < LX; ++k) x[k] = b2[k * SX + pa * SY + pb];
+        }
+        fwd1d<LX, float>(tab.Ah, x, y);
+#pragma unroll
+        for (int r = 0; r < LX; ++r) {
+            ah[r] = y[r];
+            al[r] = 0.0f;
+        }
+    }
+
+    // ---- element energy S_e = sum a^2, and max |u|
+    f2 sp = {0.0f, 0.0f};
+    if (active) {
+        if constexpr (DF) {
+#pragma unroll
+            for (int r = 0; r < LX; ++r) df_fma_acc(sp, {ah[r], al[r]}, {ah[r], al[r]});
+            sp = df_norm(sp);
+        } else {
+#pragma unroll
+            for (int r = 0; r < LX; ++r) sp.h = fmaf(ah[r], ah[r], sp.h);
+        }
+    }
+    elem_reduce<LX, DF>(red, selem, sp, umax_bits, DF, 0, 2, n_here);  // S -> [0], max|u| -> [2]
+
+    // ---- per element (one thread each): t = tau S, step s, magnitude threshold g
+    if (tid < TILE) {
+        const int l = tid;
+        const double Se = selem[l * 8 + 0];
+        int step = INT16_MIN, mode = 0;  // 0: keep none, 1: threshold, 2: keep all (lossless)
+        double g = 0.0;
+        if (l < n_here) {
+            if (!isfinite(Se) || s_bad[l]) {
+                atomicOr(&ctl->status, (unsigned)SEMR_STATUS_NONFINITE);
+            } else if (p.lossless) {
+                mode = 2;
+            } else {
+                const double t = p.tau * Se;
+                if (t >= DBL_MIN && isfinite(t)) {
+                    const long long bits = __double_as_longlong(t);
+                    const int ex = (int)((bits >> 52) & 0x7ff) - 1022;
+                    const int st = (ex - 1) >> 1;
+                    if (st >= -250 && st <= 250) {  // 2^-s as a product of two normal floats
+                        step = st;
+                        mode = 1;
+                        g = DF ? threshold_abs64(t) : (double)threshold_abs32_fast(t);
+                    } else {
+                        atomicOr(&ctl->status, (unsigned)SEMR_STATUS_NONFINITE);
+                    }
+                } else if (!isfinite(t)) {
+                    atomicOr(&ctl->status, (unsigned)SEMR_STATUS_NONFINITE);
+                }
+            }
+        }
+        const f2 gp = df_from_double(g);  // FP32 mode: g is a float, the low word is 0
+        s_g[2 * l] = gp.h;
+        s_g[2 * l + 1] = gp.l;
+        s_step[l] = step;
+        s_mode[l] = mode;
+    }
+    __syncthreads();
+    const int emode = in_tile ? s_mode[lt] : 0;
+    const int step = (in_tile && emode == 1) ? s_step[lt] : 0;
+    const f2 g2 = in_tile ? f2{s_g[2 * lt], s_g[2 * lt + 1]} : f2{0.0f, 0.0f};
+
+    // ---- mask bits: ballots when elements are whole warps, else shared atomics
+    uint32_t keepbits = 0;
+    uint32_t bw[LX];  // ballot word of mode P + NP r (ballot path)
+#pragma unroll
+    for (int r = 0; r < LX; ++r) {
+        bool k;
+        if constexpr (DF) k = df_ge(df_abs({ah[r], al[r]}), g2);
+        else k = fabsf(ah[r]) >= g2.h;
+        k = active && (emode == 2 || (emode == 1 && k));
+        keepbits |= (k ? 1u : 0u) << r;
+        if constexpr (C::BALLOT) {
+            bw[r] = __ballot_sync(0xffffffffu, k);
+            if (lane == 0 && in_tile) smask[lt * MW + (P >> 5) + (NP / 32) * r] = bw[r];
+        } else {
+            bw[r] = 0;
+            if (k) {
+                const int m = P + NP * r;
+                atomicOr(&smask[lt * MW + (m >> 5)], 1u << (m & 31));
+            }
+        }
+    }
+    __syncthreads();
+    {  // word prefix popcounts and counts, one warp per element
+        const int warp = tid >> 5;
+        for (int l = warp; l < TILE; l += C::NW) {
+            uint32_t carry = 0;
+            for (int w0 = 0; w0 < MW; w0 += 32) {
+                const int w = w0 + lane;
+                const uint32_t c = (w < MW && l < n_here) ? __popc(smask[l * MW + w]) : 0u;
+                uint32_t incl = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                if (w < MW) swpre[l * MW + w] = carry + incl - c;
+                carry += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (lane == 0) s_cnt[l] = (int)carry;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0, big = 0;
+        for (int l = 0; l < TILE; ++l) {
+            s_epre[l] = acc;
+            const int c = (l < n_here) ? s_cnt[l] : 0;
+            acc += c;
+            big |= (c > SPARSE_MAX) || (l < n_here && s_mode[l] == 2);
+        }
+        s_epre[TILE] = acc;
+        s_flag[0] = big;
+        st_release_u64(&tile_state[tile], (tile == 0 ? kFlagPrefix : kFlagAggregate) | ((uint64_t)acc & kValueMask));
+    }
+    __syncthreads();
+    const bool dense = s_flag[0] != 0;
+
+    // ---- quantise: y = a 2^-s (exact, two float factors), code = rint(y), ties to even
+    const int sd1 = (-step) >> 1, sd2 = -step - sd1;  // 2^-s = 2^sd1 2^sd2
+    const float qd1 = pow2f(sd1), qd2 = pow2f(sd2);
+    const int su1 = step >> 1, su2 = step - su1;      // 2^s = 2^su1 2^su2
+    const float qu1 = pow2f(su1), qu2 = pow2f(su2);
+    float ch[LX];  // code values (exact floats), 0 when dropped; lossless: the coefficient (hi)
+    if (emode == 2) {
+        // lossless mode: every mode kept, raw FP64 coefficients stored
+#pragma unroll
+        for (int r = 0; r < LX; ++r) {
+            ch[r] = ah[r];
+            if (keepbits & (1u << r)) {
+                const int m = P + NP * r;
+                const int rank = (int)swpre[lt * MW + (m >> 5)] +
+                                 __popc(smask[lt * MW + (m >> 5)] & ((1u << (m & 31)) - 1u));
+                reinterpret_cast<double*>(scodes)[s_epre[lt] + rank] = (double)ah[r] + (double)al[r];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < LX; ++r) {
+            ch[r] = 0.0f;
+            if constexpr (C::BALLOT) {
+                if (bw[r] == 0u) continue;  // warp-uniform: no lane keeps mode r
+            }
+            const bool k = keepbits & (1u << r);
+            if (k) {
+                const float yh = (ah[r] * qd1) * qd2;
+                float c;
+                if (width == 2) {
+                    c = (yh + 12582912.0f) - 12582912.0f;  // round half to even, exact for |y| < 2^22
+                } else {
+                    c = rintf(yh);
+                }
+                if constexpr (DF) {  // correct by the low word: rounds the pair yh + yl
+                    const float diff = (yh - c) + (al[r] * qd1) * qd2;
+                    c += (diff > 0.5f) ? 1.0f : ((diff < -0.5f) ? -1.0f : 0.0f);
+                }
+                ch[r] = c;
+                const int m = P + NP * r;
+                const uint32_t wm = C::BALLOT ? bw[r] : smask[lt * MW + (m >> 5)];
+                const int rank = (int)swpre[lt * MW + (m >> 5)] + __popc(wm & ((1u << (m & 31)) - 1u));
+                const int pos = s_epre[lt] + rank;
+                if (width == 2) reinterpret_cast<int16_t*>(scodes)[pos] = (int16_t)(int)c;
+                else reinterpret_cast<int32_t*>(scodes)[pos] = (int32_t)c;
+                skm[lt * N3 + rank] = (uint16_t)m;
+                skc[lt * N3 + rank] = c;
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- reconstruction u~ of the pencil (k=pa, j=pb), as pairs in FP64 mode
+    float vh[LX], vl[LX];
+#pragma unroll
+    for (int i = 0; i < LX; ++i) {
+        vh[i] = 0.0f;
+        vl[i] = 0.0f;
+    }
+    if (!dense) {
+        if (active) {
+            const int nk = s_cnt[lt];
+            const int rowj = pb * PT, rowk = pa * PT;
+            for (int t = 0; t < nk; ++t) {
+                const int m = skm[lt * N3 + t];
+                const float cs = (skc[lt * N3 + t] * qu1) * qu2;  // c 2^s, exact
+                const int pp = m % LX, qq = (m / LX) % LX, rr = m / NP;
+                const int col = pp * PT;
+                if constexpr (DF) {
+                    const f2 b = df_mulf(df_mul({sPh[rowj + qq], sPl[rowj + qq]}, {sPh[rowk + rr], sPl[rowk + rr]}), cs);
+#pragma unroll
+                    for (int i = 0; i < LX; ++i) {
+                        f2 acc = {vh[i], vl[i]};
+                        df_fma_acc(acc, b, {sPTh[col + i], sPTl[col + i]});
+                        const f2 n = df_norm(acc);
+                        vh[i] = n.h;
+                        vl[i] = n.l;
+                    }
+                } else {
+                    const float b = cs * sPh[rowj + qq] * sPh[rowk + rr];
+#pragma unroll
+                    for (int i = 0; i < LX; ++i) vh[i] = fmaf(b, sPTh[col + i], vh[i]);
+                }
+            }
+        }
+    } else {
+        // dense folded inverse: along r (registers), q, p (shared-memory transposes)
+        if constexpr (DF) {
+            f2 x[LX], y[LX];
+#pragma unroll
+            for (int r = 0; r < LX; ++r) x[r] = (emode == 2) ? f2{ah[r], al[r]} : f2{(ch[r] * qu1) * qu2, 0.0f};
+            inv1d_df<LX>(tab.Ph, tab.Pl, x, y);  // y[k] = v[k][q=pa][p=pb]
+            if (in_tile) {
+#pragma unroll
+                for (int k = 0; k < LX; ++k) b1[k * SX + pa * SY + pb] = make_float2(y[k].h, y[k].l);
+            }
+            __syncthreads();
+            if (in_tile) {
+#pragma unroll
+                for (int q = 0; q < LX; ++q) {
+                    const float2 v = b1[pa * SX + q * SY + pb];
+                    x[q] = {v.x, v.y};
+                }
+            }
+            inv1d_df<LX>(tab.Ph, tab.Pl, x, y);  // y[j] = v2[k=pa][j][p=pb]
+            if (in_tile) {
+#pragma unroll
+                for (int j = 0; j < LX; ++j) b2[pa * SX + j * SY + pb] = make_float2(y[j].h, y[j].l);
+            }
+            __syncthreads();
+            if (in_tile) {
+#pragma unroll
+                for (int q = 0; q < LX; ++q) {
+                    const float2 v = b2[pa * SX + pb * SY + q];
+                    x[q] = {v.x, v.y};
+                }
+            }
+            inv1d_df<LX>(tab.Ph, tab.Pl, x, y);
+#pragma unroll
+            for (int i = 0; i < LX; ++i) {
+                vh[i] = y[i].h;
+                vl[i] = y[i].l;
+            }
+        } else {
+            float x[LX], y[LX];
+#pragma unroll
+            for (int r = 0; r < LX; ++r) x[r] = (emode == 2) ? ch[r] : (ch[r] * qu1) * qu2;
+            inv1d<LX, float>(tab.Ph, x, y);
+            if (in_tile) {
+#pragma unroll
+                for (int k = 0; k < LX; ++k) b1[k * SX + pa * SY + pb] = y[k];
+            }
+            __syncthreads();
+            if (in_tile) {
+#pragma unroll
+                for (int q = 0; q < LX; ++q) x[q] = b1[pa * SX + q * SY + pb];
+            }
+            inv1d<LX, float>(tab.Ph, x, y);
+            if (in_tile) {
+#pragma unroll
+                for (int j = 0; j < LX; ++j) b2[pa * SX + j * SY + pb] = y[j];
+            }
+            __syncthreads();
+            if (in_tile) {
+#pragma unroll
+                for (int q = 0; q < LX; ++q) x[q] = b2[pa * SX + pb * SY + q];
+            }
+            inv1d<LX, float>(tab.Ph, x, y);
+#pragma unroll
+            for (int i = 0; i < LX; ++i) vh[i] = y[i];
+        }
+    }
+
+    // ---- errors of the pencil: e2 = sum w (u - u~)^2 (without J), Linf = max |u - u~|
+    f2 e2p = {0.0f, 0.0f};
+    unsigned long long linf_bits = 0;
+    if (active) {
+        if constexpr (DF) {
+            f2 dmax = {0.0f, 0.0f};
+#pragma unroll
+            for (int i = 0; i < LX; ++i) {
+                const f2 d = df_sub({uh[i], ul[i]}, {vh[i], vl[i]});
+                df_fma_acc(e2p, df_mul(wq[i], d), d);
+                const f2 ad = df_abs(d);
+                if (df_ge(ad, dmax)) dmax = ad;
+            }
+            e2p = df_norm(e2p);
+            linf_bits = pair_to_double_bits(dmax);
+        } else {
+            unsigned dm = 0;
+#pragma unroll
+            for (int i = 0; i < LX; ++i) {
+                const float d = uh[i] - vh[i];
+                e2p.h = fmaf(wq[i].h * d, d, e2p.h);
+                dm = max(dm, __float_as_uint(fabsf(d)));
+            }
+            linf_bits = dm;
+        }
+        if (p.write_recon && p.recon[f]) {
+            double* dst = p.recon[f] + e * N3 + P * LX;
+#pragma unroll
+            for (int i = 0; i < LX; ++i) dst[i] = (double)vh[i] + (double)vl[i];
+        }
+    }
+    elem_reduce<LX, DF>(red, selem, e2p, linf_bits, DF, 1, 3, n_here);  // e2/J -> [1], Linf -> [3]
+
+    // ---- look-back (one warp) and tile partials
+    if (tid < 32) {
+        const uint64_t ex = lookback_warp(tile_state, tile, (uint64_t)s_epre[TILE], &ctl->status);
+        if (tid == 0) s_tile[1] = ex;
+    }
+    if (tid == 32 % C::BLOCK) {  // another warp, when there is one
+        double s0 = 0.0, s1 = 0.0, m2 = 0.0, m3 = 0.0;
+        for (int l = 0; l < n_here; ++l) {
+            const double J = p.jac[e0 + l];
+            s0 += J * selem[l * 8 + 1];
+            s1 += J * selem[l * 8 + 0];
+            m2 = fmax(m2, selem[l * 8 + 3]);
+            m3 = fmax(m3, selem[l * 8 + 2]);
+        }
+        double* tp = tile_part + 4 * tile;
+        tp[0] = s0;
+        tp[1] = s1;
+        tp[2] = m2;
+        tp[3] = m3;
+    }
+    __syncthreads();
+    const uint64_t tile_excl = s_tile[1];
+
+    // ---- writes: codes (contiguous for the tile), masks, steps, counts, element report
+    {
+        const uint64_t ncodes = (uint64_t)s_epre[TILE];
+        const uint64_t gbyte = p.code_base + (uint64_t)width * tile_excl;
+        const uint64_t nbytes = (uint64_t)width * ncodes;
+        if (gbyte + nbytes <= p.payload_cap) {
+            uint8_t* dst = p.payload + gbyte;
+            if (width == 8) {
+                const double* sc = reinterpret_cast<const double*>(scodes);
+                for (uint64_t i = tid; i < ncodes; i += C::BLOCK) reinterpret_cast<double*>(dst)[i] = sc[i];
+            } else if (width == 4) {
+                const int32_t* sc = reinterpret_cast<const int32_t*>(scodes);
+                for (uint64_t i = tid; i < ncodes; i += C::BLOCK) reinterpret_cast<int32_t*>(dst)[i] = sc[i];
+            } else {
+                const int16_t* sc = reinterpret_cast<const int16_t*>(scodes);
+                for (uint64_t i = tid; i < ncodes; i += C::BLOCK) reinterpret_cast<int16_t*>(dst)[i] = sc[i];
+            }
+        } else if (tid == 0 && nbytes > 0) {
+            atomicOr(&ctl->status, (unsigned)SEMR_STATUS_OVERFLOW);
+        }
+    }
+    {
+        constexpr int mb = (N3 + 7) / 8;
+        uint8_t* fsec = p.payload + p.header_bytes + (uint64_t)f * p.fixed_bytes;
+        if constexpr ((mb % 4) == 0) {  // whole words: element masks are word-aligned
+            uint32_t* mdst = reinterpret_cast<uint32_t*>(fsec) + (uint64_t)e0 * (mb / 4);
+            for (int i = tid; i < n_here * (mb / 4); i += C::BLOCK) mdst[i] = smask[(i / (mb / 4)) * MW + i % (mb / 4)];
+        } else {
+            uint8_t* mdst = fsec + (uint64_t)e0 * mb;
+            const uint8_t* msrc = reinterpret_cast<const uint8_t*>(smask);
+            for (int i = tid; i < n_here * mb; i += C::BLOCK) {
+                const int l = i / mb, b = i % mb;
+                mdst[i] = msrc[l * MW * 4 + b];
+            }
+        }
+        int16_t* sdst = reinterpret_cast<int16_t*>(fsec + pad16((uint64_t)p.n_elem * mb));
+        uint16_t* cdst = reinterpret_cast<uint16_t*>(fsec + pad16((uint64_t)p.n_elem * mb) + pad16(2ull * p.n_elem));
+        if (tid < n_here) {
+            sdst[e0 + tid] = (int16_t)s_step[tid];
+            cdst[e0 + tid] = (uint16_t)s_cnt[tid];
+        }
+        if (e0 + n_here == p.n_elem && tid < 16) {
+            const uint64_t me = (uint64_t)p.n_elem * mb;
+            if (me + tid < pad16(me)) fsec[me + tid] = 0;
+            const uint64_t se = 2ull * p.n_elem;
+            uint8_t* sb = reinterpret_cast<uint8_t*>(sdst);
+            uint8_t* cb = reinterpret_cast<uint8_t*>(cdst);
+            if (se + tid < pad16(se)) {
+                sb[se + tid] = 0;
+                cb[se + tid] = 0;
+            }
+        }
+        if (p.elem_report && tid < 3 * n_here) {
+            const int l = tid / 3, c = tid % 3;
+            const double J = p.jac[e0 + l];
+            const double v = (c == 0) ? J * selem[l * 8 + 1] : (c == 1) ? J * selem[l * 8 + 0] : selem[l * 8 + 3];
+            p.elem_report[((uint64_t)f * p.n_elem + e0) * 3 + tid] = v;
+        }
+    }
+    __syncthreads();  // shared state is reused by the next tile
+    }
+}
+
+}  // namespace semr
+
+// ------------------------------------------------------------ launcher
+
+namespace semr {
+namespace {
+
+template <int LX, int MODE>
+int launch_fast_lx(const LaunchParams& p, void* stream) {
+    using C = FCfg<LX>;
+    FastTables<LX> tab;
+    double A[LX * LX], Phi[LX * LX], w[LX];
+    if (basis_tables(LX, A, Phi, w)) return (int)cudaErrorInvalidValue;
+    for (int i = 0; i < LX * LX; ++i) {
+        tab.Ah[i] = (float)A[i];
+        tab.Al[i] = (float)(A[i] - (double)tab.Ah[i]);
+        tab.Ph[i] = (float)Phi[i];
+        tab.Pl[i] = (float)(Phi[i] - (double)tab.Ph[i]);
+    }
+    for (int i = 0; i < LX; ++i) {
+        tab.wh[i] = (float)w[i];
+        tab.wl[i] = (float)(w[i] - (double)tab.wh[i]);
+    }
+    const size_t smem = FSmem<LX, MODE>::bytes;
+    cudaError_t err =
+        cudaFuncSetAttribute(reduce_fast_kernel<LX, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return (int)err;
+    // persistent grid: as many CTAs as fit on the GPU at once (never more than tiles)
+    const uint64_t tiles = (uint64_t)p.n_fields * p.tiles_per_field;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return (int)err;
+    if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return (int)err;
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reduce_fast_kernel<LX, MODE>, C::BLOCK, smem)) !=
+        cudaSuccess)
+        return (int)err;
+    const uint64_t grid = std::min<uint64_t>(tiles, (uint64_t)std::max(1, sms * std::max(per_sm, 1)));
+    reduce_fast_kernel<LX, MODE><<<(unsigned)grid, C::BLOCK, smem, (cudaStream_t)stream>>>(p, tab);
+    return (int)cudaGetLastError();
+}
+
+template <int MODE>
+int launch_fast_mode(const LaunchParams& p, int lx, void* stream) {
+    switch (lx) {
+        case 2: return launch_fast_lx<2, MODE>(p, stream);
+        case 3: return launch_fast_lx<3, MODE>(p, stream);
+        case 4: return launch_fast_lx<4, MODE>(p, stream);
+        case 5: return launch_fast_lx<5, MODE>(p, stream);
+        case 6: return launch_fast_lx<6, MODE>(p, stream);
+        case 7: return launch_fast_lx<7, MODE>(p, stream);
+        case 8: return launch_fast_lx<8, MODE>(p, stream);
+        case 9: return launch_fast_lx<9, MODE>(p, stream);
+        case 10: return launch_fast_lx<10, MODE>(p, stream);
+        case 11: return launch_fast_lx<11, MODE>(p, stream);
+        case 12: return launch_fast_lx<12, MODE>(p, stream);
+        default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+int launch_reduce_fast(const LaunchParams& p, int lx, void* stream) {
+    return p.precision == SEMR_FP32 ? launch_fast_mode<MODE_F32>(p, lx, stream)
+                                    : launch_fast_mode<MODE_DF64>(p, lx, stream);
+}
+
+}  // namespace semr

@@ -80,5 +80,6 @@ struct LaunchParams {
 // Kernel launchers (semr_kernels.cu).  Return a cudaError_t value.
 int launch_reduce(const LaunchParams& p, int lx, void* stream);
 int launch_finalize(const LaunchParams& p, int lx, void* stream);
+int launch_reduce_fast(const LaunchParams& p, int lx, void* stream);  // semr_fast.cu
 
 }  // namespace semr

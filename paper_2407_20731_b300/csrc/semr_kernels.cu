@@ -23,7 +23,7 @@
 #include <cfloat>
 #include <cstdint>
 
-#include "semr_internal.h"
+#include "semr_device.cuh"
 
 namespace semr {
 
@@ -35,114 +35,6 @@ struct Tables {
     T Phi[LX * LX];  // synthesis Phi[i*LX + p] = phi_p(x_i)
     double w[LX];    // GLL weights (norms are always FP64)
 };
-
-// ------------------------------------------------------ small helpers
-
-__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
-    uint64_t v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release_u64(uint64_t* p, uint64_t v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ double pow2d(int e) {  // 2^e, e in [-1022, 1023]
-    return __longlong_as_double((long long)(1023 + e) << 52);
-}
-__device__ __forceinline__ float pow2f(int e) {  // 2^e, e in [-126, 127]
-    return __int_as_float((127 + e) << 23);
-}
-
-// Neighbours of a positive finite float/double by one unit in the last place.
-__device__ __forceinline__ double next_up(double g) { return __longlong_as_double(__double_as_longlong(g) + 1); }
-__device__ __forceinline__ double next_down(double g) { return __longlong_as_double(__double_as_longlong(g) - 1); }
-__device__ __forceinline__ float next_upf(float g) { return __int_as_float(__float_as_int(g) + 1); }
-__device__ __forceinline__ float next_downf(float g) { return __int_as_float(__float_as_int(g) - 1); }
-
-// Smallest double g > 0 with fl(g*g) >= t (t normal, finite, > 0).  fl(g*g)
-// is monotone in g, so |a| >= g  <=>  fl(a*a) >= t for every double a.
-__device__ double threshold_abs64(double t) {
-    double g = sqrt(t);
-    for (int it = 0; it < 4 && g * g < t; ++it) g = next_up(g);
-    for (int it = 0; it < 4 && g > 0.0; ++it) {
-        const double pr = next_down(g);
-        if (pr * pr >= t) g = pr; else break;
-    }
-    return g;
-}
-// Smallest float g > 0 with (double)g * g >= t.  (double)g*g is exact, so
-// |a| >= g  <=>  (double)a*a >= t  exactly, for every float a.
-__device__ float threshold_abs32(double t) {
-    const double g64 = sqrt(t);
-    if (g64 > (double)FLT_MAX) return __int_as_float(0x7f800000);  // +inf: nothing passes
-    float g = (float)g64;
-    if (g == 0.0f) g = __int_as_float(1);  // smallest subnormal
-    for (int it = 0; it < 4 && (double)g * (double)g < t; ++it) g = next_upf(g);
-    for (int it = 0; it < 4 && g > 0.0f; ++it) {
-        const float pr = next_downf(g);
-        if ((double)pr * (double)pr >= t) g = pr; else break;
-    }
-    return g;
-}
-
-// ------------------------------------------------ 1-D folded transforms
-
-// y_p = sum_i A[p][i] x_i using A[p][N-i] = (-1)^p A[p][i].
-template <int LX, typename T>
-__device__ __forceinline__ void fwd1d(const T* __restrict__ A, const T (&x)[LX], T (&y)[LX]) {
-    constexpr int H = LX / 2;
-    T ev[H > 0 ? H : 1], od[H > 0 ? H : 1];
-#pragma unroll
-    for (int i = 0; i < H; ++i) {
-        ev[i] = x[i] + x[LX - 1 - i];
-        od[i] = x[i] - x[LX - 1 - i];
-    }
-#pragma unroll
-    for (int p = 0; p < LX; ++p) {
-        T s;
-        if ((p & 1) == 0) {
-            if constexpr (LX & 1) {
-                s = A[p * LX + H] * x[H];
-#pragma unroll
-                for (int i = 0; i < H; ++i) s = fma(A[p * LX + i], ev[i], s);
-            } else {
-                s = A[p * LX] * ev[0];
-#pragma unroll
-                for (int i = 1; i < H; ++i) s = fma(A[p * LX + i], ev[i], s);
-            }
-        } else {
-            s = A[p * LX] * od[0];
-#pragma unroll
-            for (int i = 1; i < H; ++i) s = fma(A[p * LX + i], od[i], s);
-        }
-        y[p] = s;
-    }
-}
-
-// y_i = sum_p Phi[i][p] x_p using Phi[N-i][p] = (-1)^p Phi[i][p].
-template <int LX, typename T>
-__device__ __forceinline__ void inv1d(const T* __restrict__ Phi, const T (&x)[LX], T (&y)[LX]) {
-    constexpr int H = LX / 2;
-#pragma unroll
-    for (int i = 0; i < H; ++i) {
-        T e = Phi[i * LX] * x[0];
-        T o = Phi[i * LX + 1] * x[1];
-#pragma unroll
-        for (int p = 2; p < LX; ++p) {
-            if ((p & 1) == 0) e = fma(Phi[i * LX + p], x[p], e);
-            else o = fma(Phi[i * LX + p], x[p], o);
-        }
-        y[i] = e + o;
-        y[LX - 1 - i] = e - o;
-    }
-    if constexpr (LX & 1) {
-        T e = Phi[H * LX] * x[0];
-#pragma unroll
-        for (int p = 2; p < LX; p += 2) e = fma(Phi[H * LX + p], x[p], e);
-        y[H] = e;
-    }
-}
 
 // -------------------------------------------------- kernel configuration
 
@@ -700,8 +592,8 @@ int launch_dispatch(const LaunchParams& p, int lx, void* stream) {
 }  // namespace
 
 int launch_reduce(const LaunchParams& p, int lx, void* stream) {
-    return p.precision == SEMR_FP32 ? launch_dispatch<float>(p, lx, stream)
-                                    : launch_dispatch<double>(p, lx, stream);
+    if (p.precision == SEMR_FP64_NATIVE) return launch_dispatch<double>(p, lx, stream);
+    return launch_reduce_fast(p, lx, stream);
 }
 
 int launch_finalize(const LaunchParams& p, int lx, void* stream) {
