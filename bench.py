@@ -22,6 +22,8 @@ import argparse
 import hashlib
 import json
 import math
+
+import numpy as np
 import os
 import re
 import statistics
@@ -287,6 +289,8 @@ def run_semr(args):
     extras = {}
     if not args.no_extras:
         extras = run_extras(dev, flist, jac, E, snapshot_bytes, peaks)
+        del bufs
+        extras["batched"] = run_batched(dev, prec)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(fields.cpu().numpy(), jac.cpu().numpy(), args.tau, args.cpu_seconds)
@@ -366,6 +370,63 @@ def run_extras(dev, flist, jac, E, snapshot_bytes, peaks):
 
     return {"by_tau_fp64": {f"{t:g}": timed(t, semr.SEMR_FP64) for t in (1e-2, 1e-3, 1e-4)},
             "precision_form_fp32": {f"{t:g}": timed(t, semr.SEMR_FP32) for t in (1e-3, 1e-5)}}
+
+
+def run_batched(dev, precision, reps=5, tau=1e-3):
+    """The batched form: 64 uneven snapshots (element counts log-uniform in
+    [4096, 200000], lx from {6, 8, 10}, 1-4 FP64 fields, spectral slopes in
+    [-3, -5/3]) reduced (a) by plain per-snapshot launches back to back and
+    (b) by one replay of the batch's captured CUDA graph (persistent kernel
+    per lx over a shared work queue, autotuned elements per CTA)."""
+    import torch
+
+    import paper_2407_20731_b300 as semr
+    import synth
+    cases = synth.batched_cases()
+    snaps, total_bytes = [], 0
+    for c in cases:
+        f, j = synth.snapshot(c["n_elem"], c["lx"], c["seeds"], slope=c["slope"], device=dev)
+        f = f.reshape(len(c["seeds"]), c["n_elem"], c["lx"] ** 3)
+        snaps.append(([f[k] for k in range(f.shape[0])], j.contiguous(), c["lx"], tau, precision))
+        total_bytes += f.numel() * 8
+    plain_bufs = [semr.alloc_buffers(s[2], s[1].numel(), len(s[0]), tau, dev) for s in snaps]
+    stream = torch.cuda.current_stream()
+
+    def plain():
+        for s, b in zip(snaps, plain_bufs):
+            semr.reduce_async(s[0], s[1], s[2], s[3], b, s[4])
+
+    t0 = time.perf_counter()
+    batch = semr.Batch(snaps, autotune=True)
+    plan_s = time.perf_counter() - t0
+    batch.capture()
+    for _ in range(2):
+        plain()
+        batch.replay()
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record(stream)
+    for _ in range(reps):
+        plain()
+    e[1].record(stream)
+    e[2].record(stream)
+    for _ in range(reps):
+        batch.replay()
+    e[3].record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e[0].elapsed_time(e[1]) / reps
+    graph_ms = e[2].elapsed_time(e[3]) / reps
+    res = batch.results()
+    same = all(np.array_equal(p, b.payload[: sm.payload_bytes].cpu().numpy())
+               for (p, _), b, sm in zip(res, plain_bufs, [semr.summary_from(b) for b in plain_bufs]))
+    out = {"snapshots": len(snaps), "input_bytes": total_bytes, "precision": "fp64" if precision == 0 else "fp32",
+           "plain_launches_ms": round(plain_ms, 3), "plain_GB_s": round(total_bytes / plain_ms / 1e6, 1),
+           "graph_replay_ms": round(graph_ms, 3), "graph_GB_s": round(total_bytes / graph_ms / 1e6, 1),
+           "speedup": round(plain_ms / graph_ms, 3), "plan_s": round(plan_s, 2), "payloads_identical": bool(same),
+           "schedule": [{"lx": g[0], "tile": g[2], "items": g[3], "tuned_ms": {str(k): round(v, 4) for k, v in g[4].items()}}
+                        for g in batch.schedule()]}
+    batch.close()
+    return out
 
 
 def emit(args, rank, world, value, ms_step, prec, roofline, cpu, e2e, clk, sm, extras):

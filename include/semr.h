@@ -277,6 +277,97 @@ int semr_reduce_async_noalloc(const semr_fieldset* fs, const semr_mesh* mesh, ui
                               uint64_t payload_cap, double* elem_report, semr_summary* summary,
                               void* cuda_stream);
 
+/* ------------------------------------------------------ batched launches */
+
+/* One snapshot of a batch: as for semr_reduce_async; out.scratch is ignored
+ * (the batch owns the scratch).  Precision SEMR_FP64 or SEMR_FP32. */
+typedef struct {
+    semr_fieldset fs;
+    semr_mesh mesh;
+    semr_outputs out;
+} semr_batch_item;
+
+#define SEMR_BATCH_AUTOTUNE 1  /* time every tile variant per (lx, precision) group, keep the fastest */
+
+typedef struct semr_batch semr_batch;
+
+/*
+ * semr_batch_create: plan the reduction of n_items snapshots of any sizes and
+ * orders in one launch sequence (many uneven snapshots per launch, the
+ * batched form of the in-situ reduction).  Snapshots are grouped by (lx,
+ * precision); each group runs one persistent kernel over a single work queue
+ * of all its snapshots' tiles, then one finalize kernel.  With
+ * SEMR_BATCH_AUTOTUNE the elements per CTA of each group are chosen by timing
+ * every compiled variant on the group's largest snapshot (this runs kernels
+ * and writes that snapshot's outputs).  Allocates one device workspace and
+ * uploads the descriptors (synchronises `cuda_stream`).  The item buffers
+ * must stay valid for the plan's lifetime.
+ * Errors: SEMR_EINVAL, SEMR_EUNSUPPORTED, SEMR_ENOMEM, SEMR_ECUDA.
+ */
+int semr_batch_create(semr_batch** b, const semr_batch_item* items, int n_items, int flags, void* cuda_stream);
+
+/* semr_batch_launch: enqueue the whole batch on `cuda_stream` (scratch
+ * clears, kernels).  Asynchronous; may itself be captured into a graph. */
+int semr_batch_launch(semr_batch* b, void* cuda_stream);
+
+/* semr_batch_capture: capture the launch sequence into a CUDA graph owned by
+ * the plan; semr_batch_replay launches it on `cuda_stream` (one graph launch
+ * for the whole batch). */
+int semr_batch_capture(semr_batch* b, void* cuda_stream);
+int semr_batch_replay(semr_batch* b, void* cuda_stream);
+
+/* semr_batch_schedule: group < 0 returns the number of groups; else fills the
+ * group's lx, precision, chosen elements per tile, item count, and the tuned
+ * time (ms, -1 if the variant could not run) of each of up to `cap` variants. */
+int semr_batch_schedule(const semr_batch* b, int group, int* lx, int* precision, int* tile, int* n_items,
+                        float* variant_ms, int* variant_tiles, int cap);
+
+/* semr_batch_destroy: wait for the device, free the workspace and graph. */
+void semr_batch_destroy(semr_batch* b);
+
+/* ------------------------------------------------------------ serving */
+
+/*
+ * A continuous-batching server for in-situ reductions (the paper's
+ * asynchronous approach, Sec. III-A, realised with streams in one process).
+ * Producers on any thread submit reductions of snapshots already in device
+ * memory.  A dispatcher thread admits queued requests in arrival order into
+ * `slots` device slots (one CUDA stream each) whenever a slot is free and the
+ * request's device memory (worst-case payload + scratch + reports) fits
+ * `mem_budget_bytes` (0: no bound) next to every admitted, unreleased request.
+ * Admitted requests run concurrently and overlap on the GPU; results stay on
+ * the device until released.  The input buffers must stay valid until the
+ * request completes.
+ */
+typedef struct semr_server semr_server;
+
+typedef struct {
+    double t_submit, t_admit, t_done;  /* host steady-clock seconds (completion from a stream callback) */
+    int32_t slot;                      /* device slot that ran the request */
+    int32_t status;                    /* SEMR_OK, or the error that stopped the launch */
+    uint64_t device_bytes;             /* device memory the request held */
+    semr_summary summary;              /* as written by the reduction */
+} semr_request_info;
+
+/* Errors: SEMR_EINVAL (device, slots outside 1..64), SEMR_ECUDA, SEMR_ENOMEM. */
+int semr_server_create(semr_server** s, int device, uint32_t slots, uint64_t mem_budget_bytes);
+/* Queue one reduction (thread-safe, returns at once).  SEMR_EBUDGET if the
+ * request alone exceeds the budget; SEMR_EINVAL for bad sizes. */
+int semr_server_submit(semr_server* s, const semr_fieldset* fs, const semr_mesh* mesh, uint64_t* id);
+/* State of a request: SEMR_EAGAIN while queued or running (wait = 0), else
+ * its result status; fills `info` when done.  wait != 0 blocks until done. */
+int semr_server_wait(semr_server* s, uint64_t id, int wait, semr_request_info* info);
+/* Wait for the request, copy its payload to `payload` (host, cap bytes; may
+ * be NULL), free its device memory and forget it.  SEMR_ENOSPACE if cap is
+ * too small (the request is released all the same). */
+int semr_server_release(semr_server* s, uint64_t id, void* payload, uint64_t cap, uint64_t* bytes);
+/* Counters: admitted, completed, still queued, device bytes held, seconds
+ * from the first admission to the last completion, input bytes completed. */
+int semr_server_stats(semr_server* s, uint64_t* admitted, uint64_t* completed, uint64_t* queued,
+                      uint64_t* held_bytes, double* busy_seconds, uint64_t* bytes_done);
+/* Stop the dispatcher, wait for running requests, free everything. */
+void semr_server_destroy(semr_server* s);
+
 /* semr_strerror: static text for a status code. */
 const char* semr_strerror(int code);
 

@@ -69,6 +69,18 @@ class semr_outputs(ctypes.Structure):
                 ("summary", ctypes.c_void_p), ("scratch", ctypes.c_void_p), ("scratch_bytes", ctypes.c_uint64)]
 
 
+class semr_batch_item(ctypes.Structure):
+    _fields_ = [("fs", semr_fieldset), ("mesh", semr_mesh), ("out", semr_outputs)]
+
+
+SEMR_BATCH_AUTOTUNE = 1
+
+
+class semr_request_info(ctypes.Structure):
+    _fields_ = [("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("slot", ctypes.c_int32), ("status", ctypes.c_int32), ("device_bytes", ctypes.c_uint64),
+                ("summary", semr_summary)]
+
 # (name, restype, argtypes) of every exported entry point
 _P = ctypes.c_void_p
 EXPORTS = [
@@ -89,6 +101,25 @@ EXPORTS = [
                                    ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]),
     ("semr_gll", ctypes.c_int, [ctypes.c_int32, _P, _P]),
     ("semr_strerror", ctypes.c_char_p, [ctypes.c_int]),
+    ("semr_batch_create", ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(semr_batch_item), ctypes.c_int,
+                                         ctypes.c_int, _P]),
+    ("semr_batch_launch", ctypes.c_int, [_P, _P]),
+    ("semr_batch_capture", ctypes.c_int, [_P, _P]),
+    ("semr_batch_replay", ctypes.c_int, [_P, _P]),
+    ("semr_batch_schedule", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
+                                           ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    ("semr_batch_destroy", None, [_P]),
+    ("semr_server_create", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64]),
+    ("semr_server_submit", ctypes.c_int, [_P, ctypes.POINTER(semr_fieldset), ctypes.POINTER(semr_mesh),
+                                          ctypes.POINTER(ctypes.c_uint64)]),
+    ("semr_server_wait", ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(semr_request_info)]),
+    ("semr_server_release", ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.c_uint64,
+                                           ctypes.POINTER(ctypes.c_uint64)]),
+    ("semr_server_stats", ctypes.c_int, [_P] + [ctypes.POINTER(ctypes.c_uint64)] * 4 +
+     [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]),
+    ("semr_server_destroy", None, [_P]),
     ("semr_reduce_async_noalloc", ctypes.c_int, [ctypes.POINTER(semr_fieldset), ctypes.POINTER(semr_mesh), _P,
                                                  ctypes.c_uint64, _P, _P, _P]),
 ]
@@ -304,3 +335,133 @@ def reduce(fields, jac, lx: int, tau: float, precision: int = SEMR_FP64, recon=N
     payload = bufs.payload[: sm.payload_bytes].cpu().numpy()
     er = bufs.elem_report.view(len(fields), n_elem, 3).cpu().numpy() if elem_report else None
     return Result(payload, sm, er)
+
+
+# ------------------------------------------------------------ batches
+
+class Batch:
+    """A planned batch of snapshot reductions (semr_batch_* entry points).
+
+    ``snapshots``: list of (fields: list of CUDA FP64 tensors, jac, lx, tau,
+    precision).  Output buffers are allocated here (torch) and kept alive."""
+
+    def __init__(self, snapshots, autotune: bool = True, stream=None):
+        import torch
+        self.snapshots = snapshots
+        self.bufs = []
+        items = (semr_batch_item * len(snapshots))()
+        for i, (fields, jac, lx, tau, prec) in enumerate(snapshots):
+            b = alloc_buffers(lx, jac.numel(), len(fields), tau, fields[0].device)
+            self.bufs.append(b)
+            items[i].fs = make_fieldset(fields, tau, prec)
+            items[i].mesh = make_mesh(lx, jac)
+            items[i].out = b.outputs
+        self._items = items
+        st = (stream or torch.cuda.current_stream()).cuda_stream
+        h = ctypes.c_void_p()
+        _check(_lib.semr_batch_create(ctypes.byref(h), items, len(snapshots),
+                                      SEMR_BATCH_AUTOTUNE if autotune else 0, st), "semr_batch_create")
+        self.handle = h.value
+
+    def launch(self, stream=None):
+        import torch
+        _check(_lib.semr_batch_launch(self.handle, (stream or torch.cuda.current_stream()).cuda_stream),
+               "semr_batch_launch")
+
+    def capture(self, stream=None):
+        import torch
+        _check(_lib.semr_batch_capture(self.handle, (stream or torch.cuda.current_stream()).cuda_stream),
+               "semr_batch_capture")
+
+    def replay(self, stream=None):
+        import torch
+        _check(_lib.semr_batch_replay(self.handle, (stream or torch.cuda.current_stream()).cuda_stream),
+               "semr_batch_replay")
+
+    def schedule(self):
+        """[(lx, precision, tile, n_items, {tile: tuned_ms})] per group."""
+        n = _lib.semr_batch_schedule(self.handle, -1, None, None, None, None, None, None, 0)
+        out = []
+        for g in range(n):
+            lx, pr, tile, ni = (ctypes.c_int() for _ in range(4))
+            ms = (ctypes.c_float * 4)()
+            tl = (ctypes.c_int * 4)()
+            _check(_lib.semr_batch_schedule(self.handle, g, ctypes.byref(lx), ctypes.byref(pr), ctypes.byref(tile),
+                                            ctypes.byref(ni), ms, tl, 4), "semr_batch_schedule")
+            out.append((lx.value, pr.value, tile.value, ni.value,
+                        {tl[v]: ms[v] for v in range(4) if tl[v] > 0}))
+        return out
+
+    def results(self):
+        """[(payload numpy, summary)] per snapshot (synchronises)."""
+        import torch
+        torch.cuda.synchronize()
+        res = []
+        for b in self.bufs:
+            sm = summary_from(b)
+            res.append((b.payload[: sm.payload_bytes].cpu().numpy(), sm))
+        return res
+
+    def close(self):
+        if self.handle:
+            _lib.semr_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------- serving
+
+class Server:
+    """Continuous-batching server (semr_server_* entry points)."""
+
+    def __init__(self, device: int = 0, slots: int = 8, mem_budget_bytes: int = 0):
+        h = ctypes.c_void_p()
+        _check(_lib.semr_server_create(ctypes.byref(h), device, slots, mem_budget_bytes), "semr_server_create")
+        self.handle = h.value
+        self._keep = {}
+
+    def submit(self, fields, jac, lx: int, tau: float, precision: int = SEMR_FP32) -> int:
+        fs = make_fieldset(fields, tau, precision)
+        mesh = make_mesh(lx, jac)
+        rid = ctypes.c_uint64(0)
+        _check(_lib.semr_server_submit(self.handle, ctypes.byref(fs), ctypes.byref(mesh), ctypes.byref(rid)),
+               "semr_server_submit")
+        self._keep[rid.value] = (fields, jac)  # inputs stay alive until release
+        return rid.value
+
+    def wait(self, rid: int, block: bool = True) -> tuple[int, semr_request_info]:
+        info = semr_request_info()
+        rc = _lib.semr_server_wait(self.handle, rid, 1 if block else 0, ctypes.byref(info))
+        return rc, info
+
+    def release(self, rid: int, payload: np.ndarray | None = None) -> tuple[int, int]:
+        n = ctypes.c_uint64(0)
+        rc = _lib.semr_server_release(self.handle, rid, None if payload is None else payload.ctypes.data_as(_P),
+                                      0 if payload is None else payload.nbytes, ctypes.byref(n))
+        self._keep.pop(rid, None)
+        return rc, n.value
+
+    def stats(self) -> dict:
+        a, c, q, h, b = (ctypes.c_uint64() for _ in range(5))
+        busy = ctypes.c_double()
+        _check(_lib.semr_server_stats(self.handle, ctypes.byref(a), ctypes.byref(c), ctypes.byref(q),
+                                      ctypes.byref(h), ctypes.byref(busy), ctypes.byref(b)), "semr_server_stats")
+        return dict(admitted=a.value, completed=c.value, queued=q.value, held_bytes=h.value,
+                    busy_seconds=busy.value, bytes_done=b.value)
+
+    def close(self):
+        if self.handle:
+            _lib.semr_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -90,7 +90,9 @@ extern "C" int semr_reduce_async_timed(const semr_fieldset* fs, const semr_mesh*
     p.payload_cap = out->payload_cap;
     p.elem_report = out->elem_report;
     p.summary = out->summary;
-    p.scratch = static_cast<uint8_t*>(out->scratch);
+    split_scratch(p, static_cast<uint8_t*>(out->scratch), sz.tiles);
+    p.lx = mesh->lx;
+    p.tile = tile_elems(mesh->lx);
     p.n_elem = mesh->n_elem;
     p.n_fields = fs->n_fields;
     p.tiles_per_field = (int32_t)tiles_per_field(mesh->lx, mesh->n_elem);

@@ -34,11 +34,11 @@ struct FastTables {
     float wh[LX], wl[LX];              // GLL weights (hi, lo)
 };
 
-template <int LX>
+template <int LX, int TILE_>
 struct FCfg {
     static constexpr int NP = LX * LX;             // threads (pencils) per element
     static constexpr int N3 = LX * LX * LX;
-    static constexpr int TILE = tile_elems(LX);    // elements per tile
+    static constexpr int TILE = TILE_;             // elements per tile
     static constexpr int NT = TILE * NP;
     static constexpr int BLOCK = (NT + 31) / 32 * 32;
     static constexpr int NW = BLOCK / 32;
@@ -56,9 +56,9 @@ struct FCfg {
     static constexpr bool BALLOT = (NP % 32 == 0);
 };
 
-template <int LX, int MODE>
+template <int LX, int MODE, int TILE_>
 struct FSmem {
-    using C = FCfg<LX>;
+    using C = FCfg<LX, TILE_>;
     static constexpr size_t vb = (MODE == MODE_DF64) ? 8 : 4;   // float2 or float per value
     static constexpr size_t buf_bytes = vb * C::TILE * C::BUFN;
     static constexpr size_t off_t1 = 0;
@@ -80,10 +80,10 @@ struct FSmem {
 // Results: out[lt*8 + slot_sum], out[lt*8 + slot_max] (doubles).  The sum is
 // a pair-of-float tree in FP64 mode, an FP32 tree inside a warp in FP32 mode;
 // partials across warps are added in FP64.  Fixed order: deterministic.
-template <int LX, bool DF>
+template <int LX, int TILE_, bool DF>
 __device__ __forceinline__ void elem_reduce(float* red, double* out, f2 s, unsigned long long mx, bool mx_double,
                                             int slot_sum, int slot_max, int n_here) {
-    using C = FCfg<LX>;
+    using C = FCfg<LX, TILE_>;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if constexpr (C::ALIGNED) {
 #pragma unroll
@@ -150,11 +150,14 @@ __device__ __forceinline__ void elem_reduce(float* red, double* out, f2 s, unsig
     }
 }
 
-template <int LX, int MODE>
-__global__ void __launch_bounds__(FCfg<LX>::BLOCK, FCfg<LX>::BLOCK <= 256 ? (MODE == MODE_F32 ? 3 : 2) : 1)
-reduce_fast_kernel(const LaunchParams p, const FastTables<LX> tab) {
-    using C = FCfg<LX>;
-    using S = FSmem<LX, MODE>;
+// BATCH = false: one reduction, parameters p0.  BATCH = true: the work queue
+// q of several reductions of this lx (each with its own payload and scratch).
+template <int LX, int MODE, int TILE_, bool BATCH>
+__global__ void __launch_bounds__(FCfg<LX, TILE_>::BLOCK,
+                                  FCfg<LX, TILE_>::BLOCK <= 256 ? (MODE == MODE_F32 ? 3 : 2) : 1)
+reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<LX> tab) {
+    using C = FCfg<LX, TILE_>;
+    using S = FSmem<LX, MODE, TILE_>;
     constexpr int NP = C::NP, N3 = C::N3, TILE = C::TILE, MW = C::MW, SX = C::SX, SY = C::SY, PT = C::PT;
     constexpr bool DF = (MODE == MODE_DF64);
     using V = typename std::conditional<DF, float2, float>::type;  // one transposed value
@@ -185,10 +188,12 @@ reduce_fast_kernel(const LaunchParams p, const FastTables<LX> tab) {
     int* s_flag = s_bad + TILE;          // [2]: dense inverse needed
     float* s_g = reinterpret_cast<float*>(s_flag + 2);  // [2 * TILE]: threshold (hi, lo)
 
-    ScratchControl* ctl = reinterpret_cast<ScratchControl*>(p.scratch);
-    uint64_t* tile_state = reinterpret_cast<uint64_t*>(p.scratch + kScratchControlBytes);
-    const uint64_t n_tiles = (uint64_t)p.n_fields * p.tiles_per_field;
-    double* tile_part = reinterpret_cast<double*>(p.scratch + kScratchControlBytes + pad16(8 * n_tiles));
+    // parameters of the reduction the current tile belongs to
+    __shared__ LaunchParams sp;
+    __shared__ int s_item;
+    const LaunchParams& p = sp;
+    constexpr int PW = sizeof(LaunchParams) / 4;
+    static_assert(sizeof(LaunchParams) % 4 == 0, "descriptor copy by words");
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int lt = tid / NP;
@@ -198,7 +203,6 @@ reduce_fast_kernel(const LaunchParams p, const FastTables<LX> tab) {
     const int lts = in_tile ? lt : 0;
     V* b1 = t1 + lts * C::BUFN;
     V* b2 = t2 + lts * C::BUFN;
-    const int width = p.width;
 
     for (int i = tid; i < LX * LX; i += C::BLOCK) {
         const int r = i / LX, c = i % LX;  // Phi[r][c]
@@ -215,10 +219,30 @@ reduce_fast_kernel(const LaunchParams p, const FastTables<LX> tab) {
         for (int i = 0; i < LX; ++i) wq[i] = DF ? df_mul({tab.wh[i], tab.wl[i]}, wjk) : f2{tab.wh[i] * wjk.h, 0.0f};
     }
 
+    if (!BATCH) {
+        for (int i = tid; i < PW; i += C::BLOCK) reinterpret_cast<int*>(&sp)[i] = reinterpret_cast<const int*>(&p0)[i];
+    }
+    if (tid == 0) s_item = -1;
+    const uint64_t total_tiles = BATCH ? q.total_tiles : (uint64_t)p0.n_fields * p0.tiles_per_field;
+    unsigned* counter = BATCH ? q.counter : &p0.ctl->tile_counter;
+
     // persistent CTA: claim tiles in increasing order until none are left
     for (;;) {
     if (tid == 0) {
-        s_tile[0] = atomicAdd(&ctl->tile_counter, 1u);
+        const uint64_t g = atomicAdd(counter, 1u);
+        uint64_t local = g;
+        int item = 0;
+        if (BATCH && g < total_tiles) {  // last item whose first tile is <= g
+            int lo = 0, hi = q.n_items - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) / 2;
+                if (q.tile_base[mid] <= g) lo = mid; else hi = mid - 1;
+            }
+            item = lo;
+            local = g - q.tile_base[lo];
+        }
+        s_tile[0] = (g < total_tiles) ? local : ~0ull;
+        s_flag[1] = item;
         s_flag[0] = 0;
     }
     if constexpr (!C::BALLOT) {
@@ -227,7 +251,19 @@ reduce_fast_kernel(const LaunchParams p, const FastTables<LX> tab) {
     if (tid < TILE) s_bad[tid] = 0;
     __syncthreads();
     const uint64_t tile = s_tile[0];
-    if (tile >= n_tiles) break;
+    if (tile == ~0ull) break;
+    if (BATCH && s_flag[1] != s_item) {  // load the item's parameters
+        const int item = s_flag[1];
+        __syncthreads();
+        for (int i = tid; i < PW; i += C::BLOCK)
+            reinterpret_cast<int*>(&sp)[i] = reinterpret_cast<const int*>(&q.items[item])[i];
+        if (tid == 0) s_item = item;
+        __syncthreads();
+    }
+    ScratchControl* ctl = p.ctl;
+    uint64_t* tile_state = p.tile_state;
+    double* tile_part = p.tile_part;
+    const int width = p.width;
     const int f = (int)(tile / p.tiles_per_field);
     const int64_t e0 = (int64_t)(tile % p.tiles_per_field) * TILE;
     const int n_here = (p.n_elem - e0 < TILE) ? (int)(p.n_elem - e0) : TILE;
@@ -354,7 +390,7 @@ reduce_fast_kernel(const LaunchParams p, const FastTables<LX> tab) {
             for (int r = 0; r < LX; ++r) sp.h = fmaf(ah[r], ah[r], sp.h);
         }
     }
-    elem_reduce<LX, DF>(red, selem, sp, umax_bits, DF, 0, 2, n_here);  // S -> [0], max|u| -> [2]
+    elem_reduce<LX, TILE_, DF>(red, selem, sp, umax_bits, DF, 0, 2, n_here);  // S -> [0], max|u| -> [2]
 
     // ---- per element (one thread each): t = tau S, step s, magnitude threshold g
     if (tid < TILE) {
@@ -637,7 +673,7 @@ reduce_fast_kernel(const LaunchParams p, const FastTables<LX> tab) {
             for (int i = 0; i < LX; ++i) dst[i] = (double)vh[i] + (double)vl[i];
         }
     }
-    elem_reduce<LX, DF>(red, selem, e2p, linf_bits, DF, 1, 3, n_here);  // e2/J -> [1], Linf -> [3]
+    elem_reduce<LX, TILE_, DF>(red, selem, e2p, linf_bits, DF, 1, 3, n_here);  // e2/J -> [1], Linf -> [3]
 
     // ---- look-back (one warp) and tile partials
     if (tid < 32) {
@@ -732,12 +768,11 @@ reduce_fast_kernel(const LaunchParams p, const FastTables<LX> tab) {
 namespace semr {
 namespace {
 
-template <int LX, int MODE>
-int launch_fast_lx(const LaunchParams& p, void* stream) {
-    using C = FCfg<LX>;
+template <int LX>
+FastTables<LX> make_tables() {
     FastTables<LX> tab;
     double A[LX * LX], Phi[LX * LX], w[LX];
-    if (basis_tables(LX, A, Phi, w)) return (int)cudaErrorInvalidValue;
+    basis_tables(LX, A, Phi, w);
     for (int i = 0; i < LX * LX; ++i) {
         tab.Ah[i] = (float)A[i];
         tab.Al[i] = (float)(A[i] - (double)tab.Ah[i]);
@@ -748,46 +783,113 @@ int launch_fast_lx(const LaunchParams& p, void* stream) {
         tab.wh[i] = (float)w[i];
         tab.wl[i] = (float)(w[i] - (double)tab.wh[i]);
     }
-    const size_t smem = FSmem<LX, MODE>::bytes;
-    cudaError_t err =
-        cudaFuncSetAttribute(reduce_fast_kernel<LX, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return (int)err;
-    // persistent grid: as many CTAs as fit on the GPU at once (never more than tiles)
-    const uint64_t tiles = (uint64_t)p.n_fields * p.tiles_per_field;
+    return tab;
+}
+
+// Persistent grid: as many CTAs as fit on the GPU at once, never more than tiles.
+template <typename K>
+int persistent_grid(K kernel, int block, size_t smem, uint64_t tiles, unsigned* grid) {
+    cudaError_t err;
     int dev = 0, sms = 0, per_sm = 0;
+    if ((err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return (int)err;
     if ((err = cudaGetDevice(&dev)) != cudaSuccess) return (int)err;
     if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return (int)err;
-    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reduce_fast_kernel<LX, MODE>, C::BLOCK, smem)) !=
-        cudaSuccess)
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem)) != cudaSuccess)
         return (int)err;
-    const uint64_t grid = std::min<uint64_t>(tiles, (uint64_t)std::max(1, sms * std::max(per_sm, 1)));
-    reduce_fast_kernel<LX, MODE><<<(unsigned)grid, C::BLOCK, smem, (cudaStream_t)stream>>>(p, tab);
+    if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
+    *grid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)sms * per_sm);
+    return 0;
+}
+
+template <int LX, int MODE, int TILE_>
+int launch_fast_single(const LaunchParams& p, void* stream) {
+    using C = FCfg<LX, TILE_>;
+    const FastTables<LX> tab = make_tables<LX>();
+    const size_t smem = FSmem<LX, MODE, TILE_>::bytes;
+    unsigned grid = 0;
+    const uint64_t tiles = (uint64_t)p.n_fields * p.tiles_per_field;
+    int rc = persistent_grid(reduce_fast_kernel<LX, MODE, TILE_, false>, C::BLOCK, smem, tiles, &grid);
+    if (rc) return rc;
+    BatchQueue q{};
+    reduce_fast_kernel<LX, MODE, TILE_, false><<<grid, C::BLOCK, smem, (cudaStream_t)stream>>>(p, q, tab);
+    return (int)cudaGetLastError();
+}
+
+template <int LX, int MODE, int TILE_>
+int launch_fast_batch(const BatchQueue& q, void* stream) {
+    using C = FCfg<LX, TILE_>;
+    const FastTables<LX> tab = make_tables<LX>();
+    const size_t smem = FSmem<LX, MODE, TILE_>::bytes;
+    unsigned grid = 0;
+    int rc = persistent_grid(reduce_fast_kernel<LX, MODE, TILE_, true>, C::BLOCK, smem, q.total_tiles, &grid);
+    if (rc) return rc;
+    LaunchParams p0{};
+    reduce_fast_kernel<LX, MODE, TILE_, true><<<grid, C::BLOCK, smem, (cudaStream_t)stream>>>(p0, q, tab);
     return (int)cudaGetLastError();
 }
 
 template <int MODE>
-int launch_fast_mode(const LaunchParams& p, int lx, void* stream) {
+int single_mode(const LaunchParams& p, int lx, void* stream) {
     switch (lx) {
-        case 2: return launch_fast_lx<2, MODE>(p, stream);
-        case 3: return launch_fast_lx<3, MODE>(p, stream);
-        case 4: return launch_fast_lx<4, MODE>(p, stream);
-        case 5: return launch_fast_lx<5, MODE>(p, stream);
-        case 6: return launch_fast_lx<6, MODE>(p, stream);
-        case 7: return launch_fast_lx<7, MODE>(p, stream);
-        case 8: return launch_fast_lx<8, MODE>(p, stream);
-        case 9: return launch_fast_lx<9, MODE>(p, stream);
-        case 10: return launch_fast_lx<10, MODE>(p, stream);
-        case 11: return launch_fast_lx<11, MODE>(p, stream);
-        case 12: return launch_fast_lx<12, MODE>(p, stream);
+        case 2: return launch_fast_single<2, MODE, tile_elems(2)>(p, stream);
+        case 3: return launch_fast_single<3, MODE, tile_elems(3)>(p, stream);
+        case 4: return launch_fast_single<4, MODE, tile_elems(4)>(p, stream);
+        case 5: return launch_fast_single<5, MODE, tile_elems(5)>(p, stream);
+        case 6: return launch_fast_single<6, MODE, tile_elems(6)>(p, stream);
+        case 7: return launch_fast_single<7, MODE, tile_elems(7)>(p, stream);
+        case 8: return launch_fast_single<8, MODE, tile_elems(8)>(p, stream);
+        case 9: return launch_fast_single<9, MODE, tile_elems(9)>(p, stream);
+        case 10: return launch_fast_single<10, MODE, tile_elems(10)>(p, stream);
+        case 11: return launch_fast_single<11, MODE, tile_elems(11)>(p, stream);
+        case 12: return launch_fast_single<12, MODE, tile_elems(12)>(p, stream);
         default: return (int)cudaErrorInvalidValue;
     }
 }
 
+// Batched launches: every lx with its default tile; lx 6, 8, 10 with a second
+// tile size the autotuner may pick.
+template <int MODE>
+int batch_mode(const BatchQueue& q, int lx, int tile, void* stream) {
+#define SEMR_BATCH_CASE(L, T) \
+    if (lx == L && tile == T) return launch_fast_batch<L, MODE, T>(q, stream);
+    SEMR_BATCH_CASE(2, tile_elems(2))
+    SEMR_BATCH_CASE(3, tile_elems(3))
+    SEMR_BATCH_CASE(4, tile_elems(4))
+    SEMR_BATCH_CASE(5, tile_elems(5))
+    SEMR_BATCH_CASE(6, tile_elems(6))
+    SEMR_BATCH_CASE(6, 16)
+    SEMR_BATCH_CASE(7, tile_elems(7))
+    SEMR_BATCH_CASE(8, tile_elems(8))
+    SEMR_BATCH_CASE(8, 8)
+    SEMR_BATCH_CASE(9, tile_elems(9))
+    SEMR_BATCH_CASE(10, tile_elems(10))
+    SEMR_BATCH_CASE(10, 2)
+    SEMR_BATCH_CASE(11, tile_elems(11))
+    SEMR_BATCH_CASE(12, tile_elems(12))
+#undef SEMR_BATCH_CASE
+    return (int)cudaErrorInvalidValue;
+}
+
 }  // namespace
 
+int tile_variants(int lx, int* out, int cap) {
+    int v[2] = {tile_elems(lx), 0};
+    int n = 1;
+    if (lx == 6) v[n++] = 16;
+    if (lx == 8) v[n++] = 8;
+    if (lx == 10) v[n++] = 2;
+    for (int i = 0; i < n && i < cap; ++i) out[i] = v[i];
+    return n;
+}
+
 int launch_reduce_fast(const LaunchParams& p, int lx, void* stream) {
-    return p.precision == SEMR_FP32 ? launch_fast_mode<MODE_F32>(p, lx, stream)
-                                    : launch_fast_mode<MODE_DF64>(p, lx, stream);
+    return p.precision == SEMR_FP32 ? single_mode<MODE_F32>(p, lx, stream) : single_mode<MODE_DF64>(p, lx, stream);
+}
+
+int launch_reduce_fast_batch(const BatchQueue& q, int lx, int precision, int tile, void* stream) {
+    return precision == SEMR_FP32 ? batch_mode<MODE_F32>(q, lx, tile, stream)
+                                  : batch_mode<MODE_DF64>(q, lx, tile, stream);
 }
 
 }  // namespace semr

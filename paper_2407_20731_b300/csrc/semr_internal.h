@@ -39,10 +39,6 @@ constexpr uint64_t kFlagPrefix = 2ull << 62;
 constexpr uint64_t kValueMask = (1ull << 62) - 1;
 
 // Scratch layout: [control 256 B][tile_state u64 x tiles][tile_part 4 x f64 x tiles]
-struct ScratchControl {
-    uint32_t tile_counter;
-    uint32_t status;
-};
 constexpr uint64_t kScratchControlBytes = 256;
 SEMR_HD inline uint64_t scratch_bytes(uint64_t tiles) {
     return kScratchControlBytes + pad16(8 * tiles) + 32 * tiles;
@@ -54,6 +50,11 @@ SEMR_HD inline uint64_t scratch_zero_bytes(uint64_t tiles) { return kScratchCont
 SEMR_HD constexpr int tile_elems(int lx) {
     return lx <= 2 ? 64 : lx <= 3 ? 32 : lx <= 5 ? 16 : lx <= 7 ? 8 : lx <= 10 ? 4 : 2;
 }
+
+struct ScratchControl {
+    uint32_t tile_counter;
+    uint32_t status;
+};
 
 struct LaunchParams {
     const double* fields[SEMR_MAX_FIELDS];
@@ -75,7 +76,40 @@ struct LaunchParams {
     uint64_t header_bytes;
     uint64_t fixed_bytes;
     uint64_t code_base;
+    // scratch, split: control word block, look-back states, per-tile norm partials
+    ScratchControl* ctl;
+    uint64_t* tile_state;
+    double* tile_part;
+    int32_t lx;
+    int32_t tile;   // elements per tile of the kernel variant that runs this item
 };
+
+// Default scratch split of one contiguous scratch buffer.
+inline void split_scratch(LaunchParams& p, uint8_t* scratch, uint64_t tiles) {
+    p.scratch = scratch;
+    p.ctl = reinterpret_cast<ScratchControl*>(scratch);
+    p.tile_state = reinterpret_cast<uint64_t*>(scratch + kScratchControlBytes);
+    p.tile_part = reinterpret_cast<double*>(scratch + kScratchControlBytes + pad16(8 * tiles));
+}
+
+// Work queue of a batched launch: items of one (lx, precision) group; item i
+// owns global tiles [tile_base[i], tile_base[i+1]) and fields
+// [field_base[i], field_base[i+1]).
+struct BatchQueue {
+    const LaunchParams* items;   // device, n_items descriptors
+    const uint64_t* tile_base;   // device, n_items + 1
+    const uint32_t* field_base;  // device, n_items + 1
+    unsigned* counter;           // device, zeroed before the launch
+    int32_t n_items;
+    int32_t pad_;
+    uint64_t total_tiles;
+};
+
+// Kernel variants (elements per tile) available for a given lx; the first is the default.
+int tile_variants(int lx, int* out, int cap);
+// Batched launches (semr_fast.cu / semr_kernels.cu).
+int launch_reduce_fast_batch(const BatchQueue& q, int lx, int precision, int tile, void* stream);
+int launch_finalize_batch(const BatchQueue& q, uint32_t total_fields, void* stream);
 
 // Kernel launchers (semr_kernels.cu).  Return a cudaError_t value.
 int launch_reduce(const LaunchParams& p, int lx, void* stream);

@@ -129,10 +129,10 @@ reduce_kernel(const LaunchParams p, const Tables<LX, T> tab) {
     int* s_step = smisc + 2 * TILE + 1; // [TILE]
     unsigned long long* s_tile = reinterpret_cast<unsigned long long*>(smisc + 4 * TILE + 2);
 
-    ScratchControl* ctl = reinterpret_cast<ScratchControl*>(p.scratch);
-    uint64_t* tile_state = reinterpret_cast<uint64_t*>(p.scratch + kScratchControlBytes);
+    ScratchControl* ctl = p.ctl;
+    uint64_t* tile_state = p.tile_state;
     const uint64_t n_tiles = (uint64_t)p.n_fields * p.tiles_per_field;
-    double* tile_part = reinterpret_cast<double*>(p.scratch + kScratchControlBytes + pad16(8 * n_tiles));
+    double* tile_part = p.tile_part;
 
     const int tid = threadIdx.x;
     if (tid == 0) s_tile[0] = atomicAdd(&ctl->tile_counter, 1u);
@@ -471,13 +471,14 @@ reduce_kernel(const LaunchParams p, const Tables<LX, T> tab) {
 
 // ------------------------------------------------------ finalize kernel
 
-__global__ void __launch_bounds__(256) finalize_kernel(const LaunchParams p, int lx) {
-    __shared__ double red[4][256];
-    const int f = blockIdx.x, tid = threadIdx.x;
-    ScratchControl* ctl = reinterpret_cast<ScratchControl*>(p.scratch);
-    const uint64_t* tile_state = reinterpret_cast<const uint64_t*>(p.scratch + kScratchControlBytes);
+// Field f of one reduction: deterministic tree sum of the tile partials,
+// field report, the field's code count in the header; field 0 also writes the
+// rest of the header and the summary.  256 threads.
+__device__ void finalize_field(const LaunchParams& p, int f, int lx, double (*red)[256]) {
+    const int tid = threadIdx.x;
+    const uint64_t* tile_state = p.tile_state;
     const uint64_t n_tiles = (uint64_t)p.n_fields * p.tiles_per_field;
-    const double* tile_part = reinterpret_cast<const double*>(p.scratch + kScratchControlBytes + pad16(8 * n_tiles));
+    const double* tile_part = p.tile_part;
     double s0 = 0.0, s1 = 0.0, m2 = 0.0, m3 = 0.0;
     const uint64_t t0 = (uint64_t)f * p.tiles_per_field;
     for (uint64_t t = t0 + tid; t < t0 + p.tiles_per_field; t += 256) {
@@ -519,7 +520,6 @@ __global__ void __launch_bounds__(256) finalize_kernel(const LaunchParams p, int
     fr->bytes = p.fixed_bytes + (uint64_t)p.width * kept;
     const double orig = 8.0 * lx * lx * lx * (double)p.n_elem;
     fr->cr = 1.0 - (double)fr->bytes / orig;
-    // header: code_count[f]; block 0 writes the rest
     uint8_t* h = p.payload;
     *reinterpret_cast<uint64_t*>(h + kHeaderFixed + 8 * f) = kept;
     if (f == 0) {
@@ -543,8 +543,30 @@ __global__ void __launch_bounds__(256) finalize_kernel(const LaunchParams p, int
         p.summary->code_total = total;
         p.summary->n_fields = (uint32_t)p.n_fields;
         p.summary->cr = 1.0 - (double)bytes / (orig * p.n_fields);
-        p.summary->status = ctl->status;
+        p.summary->status = p.ctl->status;
     }
+}
+
+__global__ void __launch_bounds__(256) finalize_kernel(const LaunchParams p, int lx) {
+    __shared__ double red[4][256];
+    finalize_field(p, blockIdx.x, lx, red);
+}
+
+// One block per (item, field) of a batched launch.
+__global__ void __launch_bounds__(256) finalize_batch_kernel(const BatchQueue q) {
+    __shared__ double red[4][256];
+    __shared__ int s_item;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = q.n_items - 1;  // last item with field_base <= blockIdx.x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (q.field_base[mid] <= blockIdx.x) lo = mid; else hi = mid - 1;
+        }
+        s_item = lo;
+    }
+    __syncthreads();
+    const LaunchParams& p = q.items[s_item];
+    finalize_field(p, (int)(blockIdx.x - q.field_base[s_item]), p.lx, red);
 }
 
 // ------------------------------------------------------------ launchers
@@ -598,6 +620,11 @@ int launch_reduce(const LaunchParams& p, int lx, void* stream) {
 
 int launch_finalize(const LaunchParams& p, int lx, void* stream) {
     finalize_kernel<<<p.n_fields, 256, 0, (cudaStream_t)stream>>>(p, lx);
+    return (int)cudaGetLastError();
+}
+
+int launch_finalize_batch(const BatchQueue& q, uint32_t total_fields, void* stream) {
+    finalize_batch_kernel<<<total_fields, 256, 0, (cudaStream_t)stream>>>(q);
     return (int)cudaGetLastError();
 }
 

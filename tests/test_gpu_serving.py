@@ -1,0 +1,82 @@
+"""The serving form: requests submitted while others run are admitted into
+device slots as slots and memory free up, and their kernels overlap on the
+GPU.  Each result must be the same alone and in the mix (byte-identical:
+the kernels are deterministic and each request has its own buffers)."""
+import threading
+
+import numpy as np
+import pytest
+
+import paper_2407_20731_b300 as semr
+from parity import make_case
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(4096, 8, 3, 1e-6), (700, 6, 1, 1e-5), (2500, 10, 2, 1e-6), (64, 8, 4, 1e-4), (3000, 6, 2, 1e-6),
+          (1500, 8, 1, 1e-5), (900, 10, 3, 1e-6), (5000, 8, 2, 1e-7)]
+
+
+def _requests():
+    reqs = []
+    for i, (ne, lx, nf, tau) in enumerate(SHAPES):
+        f, j = make_case(ne, lx, nf, seed=80 + i)
+        reqs.append(([f[k] for k in range(nf)], j, lx, tau))
+    return reqs
+
+
+def _alone(req, precision):
+    fields, jac, lx, tau = req
+    return semr.reduce(fields, jac, lx, tau, precision=precision).payload
+
+
+@pytest.mark.parametrize("precision", [semr.SEMR_FP32, semr.SEMR_FP64])
+def test_each_result_same_alone_and_in_the_mix(precision):
+    reqs = _requests()
+    alone = [_alone(r, precision) for r in reqs]
+    srv = semr.Server(slots=4)
+    ids = []
+    lock = threading.Lock()
+
+    def producer(sub):
+        for i in sub:
+            rid = srv.submit(*reqs[i], precision=precision)
+            with lock:
+                ids.append((rid, i))
+
+    threads = [threading.Thread(target=producer, args=(list(range(len(reqs)))[k::3],)) for k in range(3)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for rid, i in ids:
+        rc, info = srv.wait(rid)
+        assert rc == semr.SEMR_OK
+        assert info.t_submit <= info.t_admit <= info.t_done
+        buf = np.zeros(int(info.summary.payload_bytes), dtype=np.uint8)
+        rc, n = srv.release(rid, buf)
+        assert rc == semr.SEMR_OK and n == buf.size
+        assert np.array_equal(buf, alone[i])
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["held_bytes"] == 0
+    srv.close()
+
+
+def test_budget_queues_and_rejects():
+    reqs = _requests()
+    sizes = [semr.semr_sizes_for(r[2], r[1].numel(), len(r[0]), r[3]).payload_worst for r in reqs]
+    budget = int(max(sizes) * 1.3)  # only about one request fits at a time
+    srv = semr.Server(slots=4, mem_budget_bytes=budget)
+    ids = [srv.submit(*r) for r in reqs]
+    slots_seen = set()
+    for rid in ids:
+        rc, info = srv.wait(rid)
+        assert rc == semr.SEMR_OK
+        slots_seen.add(info.slot)
+        srv.release(rid)
+    assert srv.stats()["held_bytes"] == 0
+    srv.close()
+    tiny = semr.Server(slots=1, mem_budget_bytes=1024)
+    with pytest.raises(semr.SemrError) as e:
+        tiny.submit(*reqs[0])
+    assert e.value.code == semr.SEMR_EBUDGET
+    tiny.close()
