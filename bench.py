@@ -55,6 +55,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--n-side", type=int, default=64, help="elements per side (profiling a smaller case)")
+    ap.add_argument("--serving-requests", type=int, default=800, help="requests per serving run in the extras")
+    ap.add_argument("--serving-only", action="store_true", help="print only the serving report (JSON)")
+    ap.add_argument("--batched-only", action="store_true", help="print only the batched report (JSON)")
     return ap.parse_args()
 
 
@@ -285,12 +288,18 @@ def run_semr(args):
                 "kernel_ms": round(kernel_ms, 4), "algorithmic_bytes_per_launch": algo}
 
     # ---- end to end through the public stream API: pinned host input -> H2D -> submit -> fetch (D2H)
+    progress(f"device leg done: {ms_step:.3f} ms/step")
     e2e = None if args.no_e2e else run_e2e(args, world, dev, fields, jac, bufs, prec, stream, snapshot_bytes)
+    progress("e2e leg done")
     extras = {}
     if not args.no_extras:
         extras = run_extras(dev, flist, jac, E, snapshot_bytes, peaks)
+        progress("tau and precision extras done")
         del bufs
         extras["batched"] = run_batched(dev, prec)
+        progress("batched leg done")
+        extras["serving"] = serving_report(dev, args.serving_requests)
+        progress("serving leg done")
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(fields.cpu().numpy(), jac.cpu().numpy(), args.tau, args.cpu_seconds)
@@ -429,6 +438,118 @@ def run_batched(dev, precision, reps=5, tau=1e-3):
     return out
 
 
+def make_pool(dev, tau=1e-3):
+    """The 64 uneven snapshots of the batched form, on the device."""
+    import synth
+    pool = []
+    for c in synth.batched_cases():
+        f, j = synth.snapshot(c["n_elem"], c["lx"], c["seeds"], slope=c["slope"], device=dev)
+        f = f.reshape(len(c["seeds"]), c["n_elem"], c["lx"] ** 3)
+        pool.append(([f[k] for k in range(f.shape[0])], j.contiguous(), c["lx"], f.numel() * 8))
+    return pool
+
+
+def calibrate_tau(pool, precision, target=1e-3):
+    """Per lx, the largest tau on a ladder whose worst field L2_rel <= target
+    on that lx's first pool snapshot."""
+    import paper_2407_20731_b300 as semr
+    ladder = [1e-4, 3e-5, 1e-5, 3e-6, 1e-6, 3e-7, 1e-7, 3e-8, 1e-8, 3e-9]
+    out = {}
+    for lx in sorted({p[2] for p in pool}):
+        fields, jac, _, _ = next(p for p in pool if p[2] == lx)
+        for tau in ladder:
+            r = semr.reduce(fields, jac, lx, tau, precision=precision, elem_report=False)
+            if max(r.summary.field[i].l2_rel for i in range(len(fields))) <= target:
+                out[lx] = tau
+                break
+        else:
+            out[lx] = ladder[-1]
+    return out
+
+
+def run_serving(pool, taus, n_requests=800, producers=8, mean_ms=50.0, slots=8, budget=120 << 30,
+                precision=1, seed=5):
+    """Producers emit snapshots by seeded Poisson arrivals; a collector waits
+    for each result and releases it.  Latency = completion - submission."""
+    import queue
+    import threading
+
+    import paper_2407_20731_b300 as semr
+    rng = np.random.Generator(np.random.PCG64(seed))
+    per = n_requests // producers
+    traces = []
+    for _ in range(producers):
+        arrivals = np.cumsum(rng.exponential(mean_ms * 1e-3, size=per))
+        picks = rng.integers(0, len(pool), size=per)
+        traces.append(list(zip(arrivals, picks)))
+    srv = semr.Server(slots=slots, mem_budget_bytes=budget)
+    # warm-up, untimed: every pool snapshot once (grows the memory pool, loads kernels)
+    for fields, jac, lx, _ in pool:
+        srv.release(srv.submit(fields, jac, lx, taus[lx], precision))
+    srv_stats0 = srv.stats()
+    done_q: queue.Queue = queue.Queue()
+    lat, errors, span = [], [], []
+    t0 = time.perf_counter() + 0.05
+
+    def producer(trace):
+        for at, k in trace:
+            d = t0 + at - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            fields, jac, lx, _ = pool[k]
+            done_q.put(srv.submit(fields, jac, lx, taus[lx], precision))
+        done_q.put(None)
+
+    def collector():
+        ends = 0
+        while ends < producers:
+            rid = done_q.get()
+            if rid is None:
+                ends += 1
+                continue
+            rc, info = srv.wait(rid)
+            if rc:
+                errors.append(rc)
+            lat.append(info.t_done - info.t_submit)
+            span.append((info.t_submit, info.t_done))
+            srv.release(rid)
+
+    th = [threading.Thread(target=producer, args=(t,)) for t in traces] + [threading.Thread(target=collector)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    st = srv.stats()
+    st["bytes_done"] -= srv_stats0["bytes_done"]
+    srv.close()
+    lat_ms = np.array(lat) * 1e3
+    return {"requests": len(lat), "slots": slots, "producers": producers, "mean_interarrival_ms": mean_ms,
+            "p50_ms": round(float(np.percentile(lat_ms, 50)), 3), "p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
+            "mean_ms": round(float(lat_ms.mean()), 3), "errors": len(errors),
+            "sustained_GB_s": round(st["bytes_done"] / max(max(b for a, b in span) - min(a for a, b in span), 1e-9)
+                                    / 1e9, 2),
+            "input_GB": round(st["bytes_done"] / 1e9, 2)}
+
+
+def serving_report(dev, n_requests, precision=1):
+    pool = make_pool(dev)
+    taus = calibrate_tau(pool, precision)
+    progress(f"serving: tau per lx {taus}")
+    served = run_serving(pool, taus, n_requests, slots=8, precision=precision)
+    progress(f"serving: served run done ({served['p50_ms']} / {served['p99_ms']} ms)")
+    plain = run_serving(pool, taus, n_requests, slots=1, precision=precision)
+    # the same trace at ten times the arrival rate (a loaded server)
+    served_x10 = run_serving(pool, taus, max(n_requests // 2, 64), mean_ms=5.0, slots=8, precision=precision)
+    plain_x10 = run_serving(pool, taus, max(n_requests // 2, 64), mean_ms=5.0, slots=1, precision=precision)
+    return {"precision": "fp32 transforms, FP64 in" if precision == 1 else "fp64", "budget_GB": 120,
+            "tau_per_lx": {str(k): v for k, v in taus.items()}, "served": served, "plain": plain,
+            "served_10x_load": served_x10, "plain_10x_load": plain_x10}
+
+
+def progress(msg):
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 def emit(args, rank, world, value, ms_step, prec, roofline, cpu, e2e, clk, sm, extras):
     import paper_2407_20731_b300 as semr
     if rank == 0:
@@ -487,6 +608,17 @@ def main():
     global N_SIDE
     args = parse_args()
     N_SIDE = args.n_side
+    if args.batched_only:
+        import torch
+        torch.cuda.set_device(0)
+        prec = 0 if args.precision == "fp64" else 1
+        print(json.dumps({"batched": run_batched(torch.device("cuda", 0), prec)}), flush=True)
+        return
+    if args.serving_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"serving": serving_report(torch.device("cuda", 0), args.serving_requests)}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

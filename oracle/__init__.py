@@ -24,7 +24,7 @@ _SRC = os.path.join(_HERE, "semr_oracle.c")
 _LIB = os.path.join(_HERE, "libsemr_oracle.so")
 
 OK, EINVAL, ENOSPACE = 0, 1, 2
-FLAG_LOSSLESS, FLAG_CODE32 = 1, 2
+FLAG_LOSSLESS, FLAG_CODE32, FLAG_CUMULATIVE = 1, 2, 8
 
 
 def build(force: bool = False) -> str:
@@ -60,7 +60,7 @@ def lib() -> ctypes.CDLL:
         _lib.oracle_field_fixed_bytes.restype = i64
         _lib.oracle_field_fixed_bytes.argtypes = [i, i64]
         _lib.oracle_reduce.restype = i
-        _lib.oracle_reduce.argtypes = [i, i64, i, P, P, d, P, i64, P, P, P, P, P, P, i64, P, i]
+        _lib.oracle_reduce.argtypes = [i, i64, i, P, P, d, P, i64, P, P, P, P, P, P, i64, P, i, i]
         _lib.oracle_decode.restype = i
         _lib.oracle_decode.argtypes = [P, i64, P, i64]
         _lib.oracle_max_threads.restype = i
@@ -136,10 +136,11 @@ class Result:
 
 
 def reduce(fields: np.ndarray, jac: np.ndarray, tau: float, *, want_recon: bool = True,
-           want_coeffs: bool = True, fragile_cap: int = 4096, n_threads: int = 0) -> Result:
+           want_coeffs: bool = True, fragile_cap: int = 4096, n_threads: int = 0, cumulative: bool = False) -> Result:
     """Run the whole reduction of one snapshot.
 
     ``fields`` is [F, E, lx^3] (or [F, E, lx, lx, lx]) FP64, ``jac`` is [E].
+    ``cumulative`` selects the cumulative-energy truncation variant.
     """
     fields = np.ascontiguousarray(fields, dtype=np.float64)
     F, E = fields.shape[0], fields.shape[1]
@@ -160,14 +161,15 @@ def reduce(fields: np.ndarray, jac: np.ndarray, tau: float, *, want_recon: bool 
     nfr = ctypes.c_int64(0)
     # First call sizes the payload (ENOSPACE with cap 0), second call fills it.
     args = [lx, E, F, _ptr(fields), _ptr(jac), float(tau)]
+    trunc = 1 if cumulative else 0
     rc = L.oracle_reduce(*args, None, 0, ctypes.byref(nbytes), None, None, None, None,
-                         None, 0, ctypes.byref(nfr), n_threads)
+                         None, 0, ctypes.byref(nfr), n_threads, trunc)
     if rc not in (OK, ENOSPACE):
         raise ValueError(f"oracle_reduce -> {rc}")
     payload = np.zeros(nbytes.value, dtype=np.uint8)
     rc = L.oracle_reduce(*args, _ptr(payload), payload.size, ctypes.byref(nbytes), _ptr(elem),
                          _ptr(frep), _ptr(recon), _ptr(coeffs), _ptr(fragile), fragile_cap,
-                         ctypes.byref(nfr), n_threads)
+                         ctypes.byref(nfr), n_threads, trunc)
     if rc != OK:
         raise ValueError(f"oracle_reduce -> {rc}")
     k = min(nfr.value, fragile_cap)

@@ -45,6 +45,13 @@
  *  10. Fragile list: the decisions that rounding could flip (see
  *      oracle_reduce below).
  *
+ * Variant (truncation = 1, cumulative energy): the maximal allowed error read
+ * as a budget on the discarded energy, the sort-based form behind the paper's
+ * "two sorting kernels" (Sec. IV-B): sort the element's mode energies a_m^2
+ * ascending, drop the longest prefix whose running sum (in that order) stays
+ * <= tau S_e, and keep every mode whose energy is at least the first energy
+ * not dropped (equal energies are kept together).  Step and codes as above.
+ *
  * Special cases: tau = 0 is lossless mode (keep every mode, store the raw
  * FP64 coefficients).  An element whose threshold t = tau * S_e is below the
  * smallest normal double (this includes S_e = 0) keeps nothing and stores the
@@ -71,6 +78,7 @@
 /* Payload flag bits. */
 #define ORACLE_FLAG_LOSSLESS 1u
 #define ORACLE_FLAG_CODE32 2u
+#define ORACLE_FLAG_CUMULATIVE 8u
 
 /* Legendre polynomial P_k(x) by the three-term (Bonnet) recurrence
  * (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1}. */
@@ -253,6 +261,39 @@ static int oracle_step_exponent(double t, double *mu_out)
     return (num >= 0) ? num / 2 : -((-num + 1) / 2);
 }
 
+/* Sort helper: indices by energy ascending, ties by index (per-thread key array). */
+static _Thread_local const double *g_sort_e;
+static int cmp_energy(const void *x, const void *y)
+{
+    int i = *(const int *)x, j = *(const int *)y;
+    if (g_sort_e[i] < g_sort_e[j]) return -1;
+    if (g_sort_e[i] > g_sort_e[j]) return 1;
+    return (i > j) - (i < j);
+}
+
+/* Cumulative-energy boundary: energies e[0..n-1], budget t.  Returns the
+ * smallest kept energy T (keep m iff e[m] >= T), or +inf when everything
+ * fits the budget; *c_drop / *c_next get the running sums just before and
+ * after the boundary (for the fragile list). */
+static double cumulative_boundary(int n, const double *e, double t, double *c_drop, double *c_next)
+{
+    int *idx = (int *)malloc(sizeof(int) * n);
+    for (int m = 0; m < n; ++m) idx[m] = m;
+    g_sort_e = e;
+    qsort(idx, (size_t)n, sizeof(int), cmp_energy);
+    double c = 0.0;
+    int k = 0;
+    while (k < n && c + e[idx[k]] <= t) {
+        c += e[idx[k]];
+        ++k;
+    }
+    *c_drop = c;
+    *c_next = (k < n) ? c + e[idx[k]] : c;
+    double T = (k < n) ? e[idx[k]] : INFINITY;
+    free(idx);
+    return T;
+}
+
 /*
  * oracle_reduce: the whole reduction of one snapshot.
  *
@@ -270,7 +311,10 @@ static int oracle_step_exponent(double t, double *mu_out)
  *               kind 2: kept and |frac(|a_m|/q) - 1/2| <= 1e-9 |a_m|/q
  *                                                        (rounding decision)
  *               kind 3: mode -1, mu within 1e-9 of 1/2 or 1 (step exponent)
+ *               kind 4: mode -1, cumulative variant: the running sum at the
+ *                       boundary (last dropped or first kept) within 1e-9 t
  *   n_threads   OpenMP threads for the per-element loop (<= 0: default)
+ *   truncation  0: per-coefficient threshold, 1: cumulative energy
  *
  * Returns ORACLE_OK, ORACLE_EINVAL or ORACLE_ENOSPACE (payload capacity; the
  * required size is still stored in *payload_bytes).  Fragile entries beyond
@@ -279,12 +323,13 @@ static int oracle_step_exponent(double t, double *mu_out)
 int oracle_reduce(int lx, int64_t n_elem, int n_fields, const double *fields, const double *jac,
                   double tau, uint8_t *payload, int64_t cap, int64_t *payload_bytes,
                   double *elem_report, double *field_report, double *recon, double *coeffs,
-                  int64_t *fragile, int64_t fragile_cap, int64_t *n_fragile, int n_threads)
+                  int64_t *fragile, int64_t fragile_cap, int64_t *n_fragile, int n_threads, int truncation)
 {
     if (lx < ORACLE_LX_MIN || lx > ORACLE_LX_MAX || n_elem < 0 || n_fields < 1 || n_fields > 64)
         return ORACLE_EINVAL;
     if (!(tau >= 0.0) || isinf(tau) || !payload_bytes || !n_fragile) return ORACLE_EINVAL;
     if (n_elem > 0 && (!fields || !jac)) return ORACLE_EINVAL;
+    if (truncation != 0 && truncation != 1) return ORACLE_EINVAL;
 
     const int n = lx * lx * lx;
     const int mb = (n + 7) / 8;
@@ -335,8 +380,15 @@ int oracle_reduce(int lx, int64_t n_elem, int n_fields, const double *fields, co
             double t = tau * S;
             if (t >= DBL_MIN) {
                 s = oracle_step_exponent(t, NULL);
+                double T = t, cd, cn;
+                if (truncation == 1) {
+                    double *en = (double *)malloc(sizeof(double) * n);
+                    for (int m = 0; m < n; ++m) en[m] = a[m] * a[m];
+                    T = cumulative_boundary(n, en, t, &cd, &cn);
+                    free(en);
+                }
                 for (int m = 0; m < n; ++m) {
-                    if (a[m] * a[m] >= t) {
+                    if (a[m] * a[m] >= T) {
                         kp[m] = 1;
                         double c = nearbyint(ldexp(a[m], -s));
                         at[m] = ldexp(c, s);
@@ -429,10 +481,24 @@ int oracle_reduce(int lx, int64_t n_elem, int n_fields, const double *fields, co
                 }
                 ++nfr;
             }
+            if (truncation == 1) {
+                double *en = (double *)malloc(sizeof(double) * n);
+                for (int m = 0; m < n; ++m) en[m] = a[m] * a[m];
+                double cd, cn;
+                cumulative_boundary(n, en, t, &cd, &cn);
+                free(en);
+                if (fabs(cd - t) <= 1e-9 * t || fabs(cn - t) <= 1e-9 * t) {
+                    if (fragile && nfr < fragile_cap) {
+                        fragile[4 * nfr + 0] = f; fragile[4 * nfr + 1] = e;
+                        fragile[4 * nfr + 2] = -1; fragile[4 * nfr + 3] = 4;
+                    }
+                    ++nfr;
+                }
+            }
             for (int m = 0; m < n; ++m) {
                 double a2 = a[m] * a[m];
                 int kind = 0;
-                if (fabs(a2 - t) <= 1e-9 * t) kind = 1;
+                if (truncation == 0 && fabs(a2 - t) <= 1e-9 * t) kind = 1;
                 else if (keep[fe * n + m]) {
                     double y = fabs(a[m]) / q;
                     double fr = y - floor(y);
@@ -460,7 +526,8 @@ int oracle_reduce(int lx, int64_t n_elem, int n_fields, const double *fields, co
         put_u16(payload + 6, (uint16_t)lx);
         put_u16(payload + 8, (uint16_t)n_fields);
         put_u16(payload + 10, (uint16_t)((lossless ? ORACLE_FLAG_LOSSLESS : 0u) |
-                                         (code32 ? ORACLE_FLAG_CODE32 : 0u)));
+                                         (code32 ? ORACLE_FLAG_CODE32 : 0u) |
+                                         (truncation == 1 && !lossless ? ORACLE_FLAG_CUMULATIVE : 0u)));
         put_u32(payload + 12, (uint32_t)hdr);
         put_u64(payload + 16, (uint64_t)n_elem);
         put_f64(payload + 24, tau);

@@ -44,7 +44,7 @@ struct Request {
     int state = 0;  // 0 queued, 1 running, 2 done, 3 failed
     int status = SEMR_OK;
     uint8_t* dev = nullptr;
-    semr_summary* host_summary = nullptr;  // pinned, filled by a copy before completion
+    semr_summary summary{};  // copied from the slot's pinned buffer when the request completes
     struct semr_server* owner = nullptr;
 };
 
@@ -58,7 +58,9 @@ struct semr_server {
     uint64_t budget = 0;
     uint64_t held = 0;  // bytes of admitted, unreleased requests
     std::vector<cudaStream_t> streams;
-    std::vector<int> slot_req;  // request index per slot, -1 free
+    std::vector<int> slot_req;              // 1 busy, -1 free
+    std::vector<semr_summary*> slot_summary;  // pinned, one per slot
+    cudaStream_t copy_stream = nullptr;     // payload copies and frees on release
     std::mutex mu;
     std::condition_variable cv;     // dispatcher wake-up
     std::condition_variable done_cv;  // producers waiting for results
@@ -80,6 +82,7 @@ void CUDART_CB on_done(void* arg) {
     {
         std::lock_guard<std::mutex> lk(s->mu);
         r->t_done = now_s();
+        std::memcpy(&r->summary, s->slot_summary[r->slot], sizeof(semr_summary));
         r->state = 2;
         s->completed += 1;
         s->busy_end = r->t_done;
@@ -90,7 +93,9 @@ void CUDART_CB on_done(void* arg) {
     s->done_cv.notify_all();
 }
 
-// Launch an admitted request on its slot's stream (called with the lock held).
+// Launch an admitted request on its slot's stream.  Called WITHOUT the lock:
+// the completion callback takes the lock, and some CUDA calls wait for
+// pending callbacks, so no CUDA call may run while the lock is held.
 int launch(semr_server* s, Request* r) {
     cudaStream_t st = s->streams[r->slot];
     if (cudaMallocAsync(reinterpret_cast<void**>(&r->dev), r->bytes, st) != cudaSuccess) return SEMR_ENOMEM;
@@ -103,7 +108,8 @@ int launch(semr_server* s, Request* r) {
     o.scratch_bytes = r->sz.scratch_bytes;
     int rc = semr_reduce_async(&r->fs, &r->mesh, &o, st);
     if (rc) return rc;
-    if (cudaMemcpyAsync(r->host_summary, o.summary, sizeof(semr_summary), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    if (cudaMemcpyAsync(s->slot_summary[r->slot], o.summary, sizeof(semr_summary), cudaMemcpyDeviceToHost, st) !=
+        cudaSuccess)
         return SEMR_ECUDA;
     if (cudaLaunchHostFunc(st, on_done, r) != cudaSuccess) return SEMR_ECUDA;
     return SEMR_OK;
@@ -132,7 +138,9 @@ void dispatch_loop(semr_server* s) {
             s->held += r->bytes;
             if (s->admitted == 0) s->busy_start = r->t_admit;
             s->admitted += 1;
+            lk.unlock();
             const int rc = launch(s, r);
+            lk.lock();
             if (rc) {  // failed to start: report and free the slot and memory
                 r->status = rc;
                 r->state = 3;
@@ -160,14 +168,22 @@ extern "C" int semr_server_create(semr_server** out, int device, uint32_t slots,
     s->device = device;
     s->slots = slots;
     s->budget = mem_budget_bytes;
-    s->streams.resize(slots);
+    s->streams.assign(slots, nullptr);
     s->slot_req.assign(slots, -1);
-    for (uint32_t k = 0; k < slots; ++k) {
-        if (cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking) != cudaSuccess) {
-            for (uint32_t j = 0; j < k; ++j) cudaStreamDestroy(s->streams[j]);
-            delete s;
-            return SEMR_ECUDA;
+    s->slot_summary.assign(slots, nullptr);
+    bool ok = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
+    for (uint32_t k = 0; k < slots && ok; ++k) {
+        ok = cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaMallocHost(&s->slot_summary[k], sizeof(semr_summary)) == cudaSuccess;
+    }
+    if (!ok) {
+        for (uint32_t k = 0; k < slots; ++k) {
+            if (s->streams[k]) cudaStreamDestroy(s->streams[k]);
+            if (s->slot_summary[k]) cudaFreeHost(s->slot_summary[k]);
         }
+        if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+        delete s;
+        return SEMR_ECUDA;
     }
     // keep freed request memory in the pool instead of returning it to the driver
     cudaMemPool_t pool;
@@ -199,10 +215,6 @@ extern "C" int semr_server_submit(semr_server* s, const semr_fieldset* fs, const
         delete r;
         return SEMR_EBUDGET;  // could never be admitted
     }
-    if (cudaMallocHost(&r->host_summary, sizeof(semr_summary)) != cudaSuccess) {
-        delete r;
-        return SEMR_ENOMEM;
-    }
     r->owner = s;
     {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -231,10 +243,10 @@ extern "C" int semr_server_wait(semr_server* s, uint64_t id, int wait, semr_requ
         info->slot = r->slot;
         info->status = r->status;
         info->device_bytes = r->bytes;
-        if (r->state == 2) std::memcpy(&info->summary, r->host_summary, sizeof(semr_summary));
+        if (r->state == 2) std::memcpy(&info->summary, &r->summary, sizeof(semr_summary));
     }
     if (r->state == 3) return r->status;
-    const uint32_t st = r->host_summary->status;
+    const uint32_t st = r->summary.status;
     if (st & SEMR_STATUS_TIMEOUT) return SEMR_ETIMEDOUT;
     if (st & SEMR_STATUS_OVERFLOW) return SEMR_ENOSPACE;
     if (st & SEMR_STATUS_NONFINITE) return SEMR_ENONFINITE;
@@ -252,22 +264,24 @@ extern "C" int semr_server_release(semr_server* s, uint64_t id, void* payload, u
         s->done_cv.wait(lk, [&] { return r->state >= 2; });
         s->reqs.erase(it);
     }
+    // no lock held below: CUDA calls only
     int rc = SEMR_OK;
     if (r->state == 2) {
-        const uint64_t n = r->host_summary->payload_bytes;
+        const uint64_t n = r->summary.payload_bytes;
         if (bytes) *bytes = n;
         if (payload) {
             if (cap < n) rc = SEMR_ENOSPACE;
-            else if (cudaMemcpy(payload, r->dev, n, cudaMemcpyDeviceToHost) != cudaSuccess) rc = SEMR_ECUDA;
+            else if (cudaMemcpyAsync(payload, r->dev, n, cudaMemcpyDeviceToHost, s->copy_stream) != cudaSuccess ||
+                     cudaStreamSynchronize(s->copy_stream) != cudaSuccess)
+                rc = SEMR_ECUDA;
         }
     }
-    if (r->dev) cudaFreeAsync(r->dev, s->streams[r->slot >= 0 ? r->slot : 0]);
+    if (r->dev) cudaFreeAsync(r->dev, s->copy_stream);
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (r->state == 2) s->held -= r->bytes;
     }
     s->cv.notify_all();
-    cudaFreeHost(r->host_summary);
     delete r;
     return rc;
 }
@@ -295,12 +309,15 @@ extern "C" void semr_server_destroy(semr_server* s) {
     if (s->dispatcher.joinable()) s->dispatcher.join();
     cudaSetDevice(s->device);
     for (cudaStream_t st : s->streams) cudaStreamSynchronize(st);
+    cudaStreamSynchronize(s->copy_stream);
     for (auto& kv : s->reqs) {
         Request* r = kv.second;
-        if (r->dev) cudaFree(r->dev);
-        if (r->host_summary) cudaFreeHost(r->host_summary);
+        if (r->dev) cudaFreeAsync(r->dev, s->copy_stream);
         delete r;
     }
+    cudaStreamSynchronize(s->copy_stream);
     for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+    for (semr_summary* p : s->slot_summary) cudaFreeHost(p);
+    cudaStreamDestroy(s->copy_stream);
     delete s;
 }

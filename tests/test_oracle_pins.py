@@ -372,3 +372,74 @@ def test_compression_ratio_eq1():
     orig = f.size * 8
     cr = (orig - r.payload.size) / orig
     assert 0.9 < cr < 1.0
+
+
+# --------------------------------------------------- cumulative-energy variant
+
+def _cum_bruteforce(e, t):
+    """Largest energy value v with sum of strictly smaller energies <= t
+    (exact rational sums); keep e >= v.  None when every mode fits."""
+    vals = sorted(set(e.tolist()))
+    best = None
+    for v in vals:
+        d = sum(Fraction(x) for x in e.tolist() if x < v)
+        if d <= Fraction(t):
+            best = v
+    if sum(Fraction(x) for x in e.tolist()) <= Fraction(t):
+        return None
+    return best
+
+
+@pytest.mark.parametrize("lx", [2, 3, 4])
+def test_cumulative_bruteforce_tiny(lx):
+    rng = np.random.default_rng(200 + lx)
+    ne = 30
+    f = rng.normal(size=(1, ne, lx ** 3)) * np.exp(rng.normal(size=(1, ne, lx ** 3)))
+    j = rng.uniform(0.5, 2.0, size=ne)
+    for tau in (0.02, 0.2):
+        r = oracle.reduce(f, j, tau, cumulative=True)
+        s = oracle.sections(r.payload)
+        assert s["header"]["flags"] & oracle.FLAG_CUMULATIVE
+        flagged = {int(e) for _, e, m, k in r.fragile if k == 4}
+        for e in range(ne):
+            if e in flagged:
+                continue
+            a = r.coeffs[0, e]
+            en = a * a
+            S = 0.0
+            for v in a:
+                S += v * v
+            v = _cum_bruteforce(en, tau * S)
+            expect = np.zeros(lx ** 3, bool) if v is None else en >= v
+            np.testing.assert_array_equal(s["masks"][0, e], expect)
+
+
+def test_cumulative_budget_invariants():
+    f, j = _case(ne=125, lx=8, seed=37)
+    for tau in (1e-5, 1e-3, 1e-1):
+        r = oracle.reduce(f, j, tau, cumulative=True)
+        s = oracle.sections(r.payload)
+        flagged = {int(e) for _, e, m, k in r.fragile if k == 4}
+        for e in range(125):
+            if e in flagged:
+                continue
+            en = r.coeffs[0, e] ** 2
+            S = float(np.sum(en))
+            kept = s["masks"][0, e]
+            dropped = float(np.sum(en[~kept]))
+            assert dropped <= tau * S * (1 + 1e-12)
+            if kept.any():  # dropping the smallest kept energy as well would break the budget
+                assert dropped + en[kept].min() > tau * S * (1 - 1e-12)
+
+
+def test_cumulative_monotone_and_limits():
+    f, j = _case(ne=64, lx=6, seed=39)
+    prev = None
+    for tau in (1e-6, 1e-4, 1e-2, 0.5):
+        m = oracle.sections(oracle.reduce(f, j, tau, cumulative=True).payload)["masks"]
+        if prev is not None:
+            assert not np.any(m & ~prev)
+        prev = m
+    assert oracle.sections(oracle.reduce(f, j, 1.5, cumulative=True).payload)["counts"].sum() == 0
+    r = oracle.reduce(f, j, 0.0, cumulative=True)  # tau = 0 stays lossless
+    assert oracle.sections(r.payload)["masks"].all()
