@@ -135,6 +135,8 @@ typedef struct {
     uint32_t status;          /* SEMR_STATUS_* bits, 0 when everything is valid */
     uint32_t n_fields;
     double cr;                /* Eq. 1 over the whole snapshot */
+    uint64_t recomputed;      /* FP64 mode: coefficients whose FP32 value could not settle a
+                                 decision and were recomputed exactly */
     semr_field_report field[SEMR_MAX_FIELDS];
 } semr_summary;
 

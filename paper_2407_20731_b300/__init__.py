@@ -53,7 +53,7 @@ class semr_field_report(ctypes.Structure):
 
 class semr_summary(ctypes.Structure):
     _fields_ = [("payload_bytes", ctypes.c_uint64), ("code_total", ctypes.c_uint64), ("status", ctypes.c_uint32),
-                ("n_fields", ctypes.c_uint32), ("cr", ctypes.c_double),
+                ("n_fields", ctypes.c_uint32), ("cr", ctypes.c_double), ("recomputed", ctypes.c_uint64),
                 ("field", semr_field_report * SEMR_MAX_FIELDS)]
 
 

@@ -56,6 +56,9 @@ struct FCfg {
     static constexpr bool BALLOT = (NP % 32 == 0);
 };
 
+// Coefficients per tile whose decisions are recomputed exactly in one round.
+constexpr int AMB_CAP = 64;
+
 template <int LX, int MODE, int TILE_>
 struct FSmem {
     using C = FCfg<LX, TILE_>;
@@ -69,10 +72,12 @@ struct FSmem {
     static constexpr size_t off_red = (off_km + 2ull * C::TILE * C::N3 + 15) / 16 * 16;  // BLOCK x 16 B
     static constexpr size_t off_elem = off_red + 16ull * C::BLOCK;         // TILE x 8 doubles
     static constexpr size_t off_phi = off_elem + 64ull * C::TILE;          // 4 tables x LX x PT floats
-    static constexpr size_t off_mask = off_phi + 16ull * LX * C::PT;       // TILE x MW u32
+    static constexpr size_t off_amat = off_phi + 16ull * LX * C::PT;       // 2 tables x LX x PT floats
+    static constexpr size_t off_amb = off_amat + 8ull * LX * C::PT;        // AMB_CAP entries + values
+    static constexpr size_t off_mask = off_amb + 12ull * AMB_CAP + 16;     // TILE x MW u32
     static constexpr size_t off_wpre = off_mask + 4ull * C::TILE * C::MW;
     static constexpr size_t off_misc = (off_wpre + 4ull * C::TILE * C::MW + 15) / 16 * 16;
-    static constexpr size_t bytes = off_misc + 4ull * (8 * C::TILE + 16);
+    static constexpr size_t bytes = off_misc + 4ull * (9 * C::TILE + 16);
 };
 
 // Per-element reduction of one sum (a float pair) and one maximum (a 64-bit
@@ -176,6 +181,13 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
     float* sPl = sPh + LX * PT;
     float* sPTh = sPl + LX * PT;                                 // Phi[i][p] stored as [p][i]
     float* sPTl = sPTh + LX * PT;
+    float* sAh = reinterpret_cast<float*>(smem + S::off_amat);  // A[p][i], rows padded
+    float* sAl = sAh + LX * PT;
+    int* s_amb = reinterpret_cast<int*>(smem + S::off_amb);          // [AMB_CAP]: (element << 16) | mode
+    float* s_ambv = reinterpret_cast<float*>(s_amb + AMB_CAP);       // [2 * AMB_CAP]: exact values
+    int* s_namb = reinterpret_cast<int*>(s_ambv + 2 * AMB_CAP);      // [1]
+    float* t1f = reinterpret_cast<float*>(smem + S::off_t1);         // FP32 views of the transpose buffers
+    float* t2f = reinterpret_cast<float*>(smem + S::off_t2);
     uint32_t* smask = reinterpret_cast<uint32_t*>(smem + S::off_mask);
     uint32_t* swpre = reinterpret_cast<uint32_t*>(smem + S::off_wpre);
     int* smisc = reinterpret_cast<int*>(smem + S::off_misc);
@@ -187,6 +199,7 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
     int* s_bad = s_mode + TILE;          // [TILE]
     int* s_flag = s_bad + TILE;          // [2]: dense inverse needed
     float* s_g = reinterpret_cast<float*>(s_flag + 2);  // [2 * TILE]: threshold (hi, lo)
+    float* s_marg = s_g + 2 * TILE;                       // [TILE]: bound on |a_fp32 - a|
 
     // parameters of the reduction the current tile belongs to
     __shared__ LaunchParams sp;
@@ -210,6 +223,8 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
         sPl[r * PT + c] = tab.Pl[i];
         sPTh[c * PT + r] = tab.Ph[i];
         sPTl[c * PT + r] = tab.Pl[i];
+        sAh[r * PT + c] = tab.Ah[i];
+        sAl[r * PT + c] = tab.Al[i];
     }
     // quadrature weight products w_i w_j w_k of this pencil (j = pb, k = pa)
     f2 wq[LX];
@@ -308,67 +323,33 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
         if (bad) s_bad[lt] = 1;  // read after the next barrier
     }
 
-    // ---- forward transform along i (registers), j, k (shared-memory transposes)
+    // ---- forward transform in FP32 along i (registers), j, k (shared-memory
+    // transposes).  In FP64 mode the FP32 coefficients settle every decision
+    // they are provably on the right side of; the others are recomputed exactly.
     float ah[LX], al[LX];  // modal coefficients a[r][q=pa][p=pb], mode m = P + NP r
-    if constexpr (DF) {
-        f2 x[LX], y[LX];
-#pragma unroll
-        for (int i = 0; i < LX; ++i) x[i] = {uh[i], ul[i]};
-        fwd1d_df<LX>(tab.Ah, tab.Al, x, y);
-        if (in_tile) {
-#pragma unroll
-            for (int q = 0; q < LX; ++q) b1[pa * SX + pb * SY + q] = make_float2(y[q].h, y[q].l);
-        }
-        __syncthreads();
-        if (in_tile) {
-#pragma unroll
-            for (int j = 0; j < LX; ++j) {
-                const float2 v = b1[pa * SX + j * SY + pb];
-                x[j] = {v.x, v.y};
-            }
-        }
-        fwd1d_df<LX>(tab.Ah, tab.Al, x, y);
-        if (in_tile) {
-#pragma unroll
-            for (int q = 0; q < LX; ++q) b2[pa * SX + q * SY + pb] = make_float2(y[q].h, y[q].l);
-        }
-        __syncthreads();
-        if (in_tile) {
-#pragma unroll
-            for (int k = 0; k < LX; ++k) {
-                const float2 v = b2[k * SX + pa * SY + pb];
-                x[k] = {v.x, v.y};
-            }
-        }
-        fwd1d_df<LX>(tab.Ah, tab.Al, x, y);
-#pragma unroll
-        for (int r = 0; r < LX; ++r) {
-            ah[r] = y[r].h;
-            al[r] = y[r].l;
-        }
-    } else {
+    {
         float x[LX], y[LX];
 #pragma unroll
         for (int i = 0; i < LX; ++i) x[i] = uh[i];
         fwd1d<LX, float>(tab.Ah, x, y);
         if (in_tile) {
 #pragma unroll
-            for (int q = 0; q < LX; ++q) b1[pa * SX + pb * SY + q] = y[q];
+            for (int q = 0; q < LX; ++q) t1f[lts * C::BUFN + pa * SX + pb * SY + q] = y[q];
         }
         __syncthreads();
         if (in_tile) {
 #pragma unroll
-            for (int j = 0; j < LX; ++j) x[j] = b1[pa * SX + j * SY + pb];
+            for (int j = 0; j < LX; ++j) x[j] = t1f[lts * C::BUFN + pa * SX + j * SY + pb];
         }
         fwd1d<LX, float>(tab.Ah, x, y);
         if (in_tile) {
 #pragma unroll
-            for (int q = 0; q < LX; ++q) b2[pa * SX + q * SY + pb] = y[q];
+            for (int q = 0; q < LX; ++q) t2f[lts * C::BUFN + pa * SX + q * SY + pb] = y[q];
         }
         __syncthreads();
         if (in_tile) {
 #pragma unroll
-            for (int k = 0; k < LX; ++k) x[k] = b2[k * SX + pa * SY + pb];
+            for (int k = 0; k < LX; ++k) x[k] = t2f[lts * C::BUFN + k * SX + pa * SY + pb];
         }
         fwd1d<LX, float>(tab.Ah, x, y);
 #pragma unroll
@@ -378,12 +359,18 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
         }
     }
 
-    // ---- element energy S_e = sum a^2, and max |u|
+    // ---- element energy and max |u|.  FP64 mode: S_e = sum w_i w_j w_k u^2
+    // over the GLL points (Parseval's identity in nodal form), in float pairs
+    // from the exact split of u.  FP32 mode: S_e = sum a^2 of the coefficients.
     f2 sp = {0.0f, 0.0f};
     if (active) {
         if constexpr (DF) {
 #pragma unroll
-            for (int r = 0; r < LX; ++r) df_fma_acc(sp, {ah[r], al[r]}, {ah[r], al[r]});
+            for (int i = 0; i < LX; ++i) {
+                const float ph = uh[i] * uh[i];
+                const float pl = fmaf(2.0f * uh[i], ul[i], fmaf(uh[i], uh[i], -ph));
+                df_fma_acc(sp, wq[i], {ph, pl});
+            }
             sp = df_norm(sp);
         } else {
 #pragma unroll
@@ -426,11 +413,101 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
         s_g[2 * l + 1] = gp.l;
         s_step[l] = step;
         s_mode[l] = mode;
+        // bound on |a_fp32 - a|: (H + 2) roundings per folded contraction (H terms, the fold,
+        // the table), 3 contractions, 2 more for the input split; (|A|^3 |u|)_m <= 2^1.5 max|u|
+        // because every row of A has sum |A_pi| <= sqrt(2); a factor 2 of safety on top.
+        constexpr float kMarg = (3.0f * ((LX + 1) / 2 + 2) + 2.0f) * 5.9604645e-8f * 2.8285f * 2.0f;
+        s_marg[l] = kMarg * (float)selem[l * 8 + 2] * 1.0000002f;
     }
     __syncthreads();
     const int emode = in_tile ? s_mode[lt] : 0;
     const int step = (in_tile && emode == 1) ? s_step[lt] : 0;
     const f2 g2 = in_tile ? f2{s_g[2 * lt], s_g[2 * lt + 1]} : f2{0.0f, 0.0f};
+
+    if constexpr (DF) {
+        // ---- decisions the FP32 coefficients cannot settle: recompute them exactly
+        const int sdn1 = (-step) >> 1, sdn2 = -step - sdn1;
+        const float sc = pow2f(sdn1) * pow2f(sdn2);  // 2^-s, exact
+        uint32_t amb = 0;
+        if (active && emode == 1) {
+            const float Mg = s_marg[lt] + g2.h * 2.4e-7f;  // plus the float rounding of g +- M
+            const float Mq = Mg * sc;
+#pragma unroll
+            for (int r = 0; r < LX; ++r) {
+                const float aa = fabsf(ah[r]);
+                if (aa >= g2.h + Mg) {  // surely kept: is the rounding decision sure too?
+                    const float y = aa * sc;
+                    if (fabsf((y - floorf(y)) - 0.5f) <= Mq + y * 1.2e-7f) amb |= 1u << r;
+                } else if (!(aa < g2.h - Mg)) {
+                    amb |= 1u << r;  // too close to the threshold
+                }
+            }
+        }
+        for (int round = 0;; ++round) {  // rounds of up to AMB_CAP entries per tile
+            if (tid == 0) s_namb[0] = 0;
+            __syncthreads();
+            int ent[LX];
+#pragma unroll
+            for (int r = 0; r < LX; ++r) {
+                ent[r] = -1;
+                if (amb & (1u << r)) {
+                    const int k = atomicAdd(&s_namb[0], 1);
+                    if (k < AMB_CAP) {
+                        s_amb[k] = (lt << 16) | (P + NP * r);
+                        ent[r] = k;
+                    }
+                }
+            }
+            __syncthreads();
+            const int total = s_namb[0];
+            if (total == 0) break;
+            if (tid == 0) atomicAdd(&ctl->recomputed, (unsigned)(total < AMB_CAP ? total : AMB_CAP));
+            const int n_amb = total < AMB_CAP ? total : AMB_CAP;
+            for (int k = 0; k < n_amb; ++k) {
+                const int code = s_amb[k];
+                const int el = code >> 16, m = code & 0xffff;
+                f2 c = {0.0f, 0.0f};
+                if (lt == el && active) {
+                    const int pp = m % LX, qq = (m / LX) % LX, rr = m / NP;
+                    f2 xs = {0.0f, 0.0f};
+#pragma unroll
+                    for (int i = 0; i < LX; ++i) df_fma_acc(xs, {sAh[pp * PT + i], sAl[pp * PT + i]}, {uh[i], ul[i]});
+                    xs = df_norm(xs);
+                    c = df_mul(df_mul(xs, {sAh[qq * PT + pb], sAl[qq * PT + pb]}), {sAh[rr * PT + pa], sAl[rr * PT + pa]});
+                }
+                // CTA-wide pair sum (only element el contributes)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float h = __shfl_xor_sync(0xffffffffu, c.h, o);
+                    const float l2 = __shfl_xor_sync(0xffffffffu, c.l, o);
+                    const f2 t = two_sum(c.h, h);
+                    c = {t.h, t.l + (c.l + l2)};
+                }
+                if (lane == 0) reinterpret_cast<float2*>(red)[tid >> 5] = make_float2(c.h, c.l);
+                __syncthreads();
+                if (tid == 0) {
+                    f2 a = {0.0f, 0.0f};
+                    for (int w = 0; w < C::NW; ++w) {
+                        const float2 v = reinterpret_cast<float2*>(red)[w];
+                        a = df_add(a, {v.x, v.y});
+                    }
+                    s_ambv[2 * k] = a.h;
+                    s_ambv[2 * k + 1] = a.l;
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int r = 0; r < LX; ++r) {
+                if (ent[r] >= 0) {  // exact coefficient replaces the FP32 one
+                    ah[r] = s_ambv[2 * ent[r]];
+                    al[r] = s_ambv[2 * ent[r] + 1];
+                    amb &= ~(1u << r);
+                }
+            }
+            if (total <= AMB_CAP) break;
+            __syncthreads();
+        }
+    }
 
     // ---- mask bits: ballots when elements are whole warps, else shared atomics
     uint32_t keepbits = 0;

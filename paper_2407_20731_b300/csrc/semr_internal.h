@@ -54,6 +54,7 @@ SEMR_HD constexpr int tile_elems(int lx) {
 struct ScratchControl {
     uint32_t tile_counter;
     uint32_t status;
+    uint32_t recomputed;  // coefficients recomputed exactly (FP64 mode)
 };
 
 struct LaunchParams {

@@ -544,6 +544,7 @@ __device__ void finalize_field(const LaunchParams& p, int f, int lx, double (*re
         p.summary->n_fields = (uint32_t)p.n_fields;
         p.summary->cr = 1.0 - (double)bytes / (orig * p.n_fields);
         p.summary->status = p.ctl->status;
+        p.summary->recomputed = p.ctl->recomputed;
     }
 }
 
@@ -614,7 +615,9 @@ int launch_dispatch(const LaunchParams& p, int lx, void* stream) {
 }  // namespace
 
 int launch_reduce(const LaunchParams& p, int lx, void* stream) {
-    if (p.precision == SEMR_FP64_NATIVE) return launch_dispatch<double>(p, lx, stream);
+    // lossless FP64 stores every coefficient as an FP64 value: hardware FP64 path
+    if (p.precision == SEMR_FP64_NATIVE || (p.precision == SEMR_FP64 && p.lossless))
+        return launch_dispatch<double>(p, lx, stream);
     return launch_reduce_fast(p, lx, stream);
 }
 
