@@ -74,7 +74,8 @@ struct FSmem {
     static constexpr size_t off_phi = off_elem + 64ull * C::TILE;          // 4 tables x LX x PT floats
     static constexpr size_t off_amat = off_phi + 16ull * LX * C::PT;       // 2 tables x LX x PT floats
     static constexpr size_t off_amb = off_amat + 8ull * LX * C::PT;        // AMB_CAP entries + values
-    static constexpr size_t off_mask = off_amb + 12ull * AMB_CAP + 16;     // TILE x MW u32
+    static constexpr size_t off_wq = (off_amb + 12ull * AMB_CAP + 4ull * C::TILE + 16 + 15) / 16 * 16;
+    static constexpr size_t off_mask = off_wq + (MODE == MODE_DF64 ? 8ull * C::NP * LX : 0);  // TILE x MW u32
     static constexpr size_t off_wpre = off_mask + 4ull * C::TILE * C::MW;
     static constexpr size_t off_misc = (off_wpre + 4ull * C::TILE * C::MW + 15) / 16 * 16;
     static constexpr size_t bytes = off_misc + 4ull * (9 * C::TILE + 16);
@@ -155,15 +156,22 @@ __device__ __forceinline__ void elem_reduce(float* red, double* out, f2 s, unsig
     }
 }
 
+// Resident threads per SM the register budget aims at: enough warps to hide
+// the latency of the tile's barrier phases, without spilling the larger orders.
+constexpr int min_ctas_per_sm(int lx, int mode, int block) {
+    const int target = (mode == MODE_F32) ? (lx <= 10 ? 1024 : 768) : (lx <= 8 ? 768 : 512);
+    return target / block > 0 ? target / block : 1;
+}
+
 // BATCH = false: one reduction, parameters p0.  BATCH = true: the work queue
 // q of several reductions of this lx (each with its own payload and scratch).
 template <int LX, int MODE, int TILE_, bool BATCH>
-__global__ void __launch_bounds__(FCfg<LX, TILE_>::BLOCK,
-                                  FCfg<LX, TILE_>::BLOCK <= 256 ? (MODE == MODE_F32 ? 3 : 2) : 1)
+__global__ void __launch_bounds__(FCfg<LX, TILE_>::BLOCK, min_ctas_per_sm(LX, MODE, FCfg<LX, TILE_>::BLOCK))
 reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<LX> tab) {
     using C = FCfg<LX, TILE_>;
     using S = FSmem<LX, MODE, TILE_>;
     constexpr int NP = C::NP, N3 = C::N3, TILE = C::TILE, MW = C::MW, SX = C::SX, SY = C::SY, PT = C::PT;
+    constexpr int CS = (LX % 4 == 0) ? LX : PT;  // row stride of the column table (16-byte rows when possible)
     constexpr bool DF = (MODE == MODE_DF64);
     using V = typename std::conditional<DF, float2, float>::type;  // one transposed value
     // dense inverse once any element of the tile keeps more modes than this
@@ -185,7 +193,8 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
     float* sAl = sAh + LX * PT;
     int* s_amb = reinterpret_cast<int*>(smem + S::off_amb);          // [AMB_CAP]: (element << 16) | mode
     float* s_ambv = reinterpret_cast<float*>(s_amb + AMB_CAP);       // [2 * AMB_CAP]: exact values
-    int* s_namb = reinterpret_cast<int*>(s_ambv + 2 * AMB_CAP);      // [1]
+    int* s_namb = reinterpret_cast<int*>(s_ambv + 2 * AMB_CAP);      // [1 + TILE]: count, per-element flags
+    float2* sWq = reinterpret_cast<float2*>(smem + S::off_wq);        // [NP][LX] weight products (pairs)
     float* t1f = reinterpret_cast<float*>(smem + S::off_t1);         // FP32 views of the transpose buffers
     float* t2f = reinterpret_cast<float*>(smem + S::off_t2);
     uint32_t* smask = reinterpret_cast<uint32_t*>(smem + S::off_mask);
@@ -221,17 +230,26 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
         const int r = i / LX, c = i % LX;  // Phi[r][c]
         sPh[r * PT + c] = tab.Ph[i];
         sPl[r * PT + c] = tab.Pl[i];
-        sPTh[c * PT + r] = tab.Ph[i];
-        sPTl[c * PT + r] = tab.Pl[i];
+        sPTh[c * CS + r] = tab.Ph[i];
+        sPTl[c * CS + r] = tab.Pl[i];
         sAh[r * PT + c] = tab.Ah[i];
         sAl[r * PT + c] = tab.Al[i];
     }
-    // quadrature weight products w_i w_j w_k of this pencil (j = pb, k = pa)
-    f2 wq[LX];
+    // quadrature weight products w_i w_j w_k of this pencil (j = pb, k = pa):
+    // FP32 mode keeps them in registers, FP64 mode as pairs in a shared table
+    float wq32[LX];
     {
         const f2 wjk = df_mul({tab.wh[pa], tab.wl[pa]}, {tab.wh[pb], tab.wl[pb]});
 #pragma unroll
-        for (int i = 0; i < LX; ++i) wq[i] = DF ? df_mul({tab.wh[i], tab.wl[i]}, wjk) : f2{tab.wh[i] * wjk.h, 0.0f};
+        for (int i = 0; i < LX; ++i) {
+            if constexpr (DF) {
+                const f2 w3 = df_mul({tab.wh[i], tab.wl[i]}, wjk);
+                if (in_tile && lt == 0) sWq[P * LX + i] = make_float2(w3.h, w3.l);
+                wq32[i] = 0.0f;
+            } else {
+                wq32[i] = tab.wh[i] * wjk.h;
+            }
+        }
     }
 
     if (!BATCH) {
@@ -369,7 +387,8 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
             for (int i = 0; i < LX; ++i) {
                 const float ph = uh[i] * uh[i];
                 const float pl = fmaf(2.0f * uh[i], ul[i], fmaf(uh[i], uh[i], -ph));
-                df_fma_acc(sp, wq[i], {ph, pl});
+                const float2 w = sWq[P * LX + i];
+                df_fma_acc(sp, {w.x, w.y}, {ph, pl});
             }
             sp = df_norm(sp);
         } else {
@@ -399,7 +418,9 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
                     if (st >= -250 && st <= 250) {  // 2^-s as a product of two normal floats
                         step = st;
                         mode = 1;
-                        g = DF ? threshold_abs64(t) : (double)threshold_abs32_fast(t);
+                        // FP64 mode refines g to the exact double threshold only for elements
+                        // with coefficients it recomputes; the float threshold settles the rest
+                        g = (double)threshold_abs32_fast(t);
                     } else {
                         atomicOr(&ctl->status, (unsigned)SEMR_STATUS_NONFINITE);
                     }
@@ -422,7 +443,7 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
     __syncthreads();
     const int emode = in_tile ? s_mode[lt] : 0;
     const int step = (in_tile && emode == 1) ? s_step[lt] : 0;
-    const f2 g2 = in_tile ? f2{s_g[2 * lt], s_g[2 * lt + 1]} : f2{0.0f, 0.0f};
+    f2 g2 = in_tile ? f2{s_g[2 * lt], s_g[2 * lt + 1]} : f2{0.0f, 0.0f};
 
     if constexpr (DF) {
         // ---- decisions the FP32 coefficients cannot settle: recompute them exactly
@@ -445,7 +466,9 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
         }
         for (int round = 0;; ++round) {  // rounds of up to AMB_CAP entries per tile
             if (tid == 0) s_namb[0] = 0;
+            if (tid < TILE) s_namb[1 + tid] = 0;
             __syncthreads();
+            if (amb) s_namb[1 + lt] = 1;
             int ent[LX];
 #pragma unroll
             for (int r = 0; r < LX; ++r) {
@@ -462,6 +485,11 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
             const int total = s_namb[0];
             if (total == 0) break;
             if (tid == 0) atomicAdd(&ctl->recomputed, (unsigned)(total < AMB_CAP ? total : AMB_CAP));
+            if (tid < TILE && s_namb[1 + tid] && s_mode[tid] == 1) {  // exact double threshold of the element
+                const f2 ge = df_from_double(threshold_abs64(p.tau * selem[tid * 8 + 0]));
+                s_g[2 * tid] = ge.h;
+                s_g[2 * tid + 1] = ge.l;
+            }
             const int n_amb = total < AMB_CAP ? total : AMB_CAP;
             for (int k = 0; k < n_amb; ++k) {
                 const int code = s_amb[k];
@@ -507,6 +535,7 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
             if (total <= AMB_CAP) break;
             __syncthreads();
         }
+        if (in_tile) g2 = f2{s_g[2 * lt], s_g[2 * lt + 1]};  // exact where it was refined
     }
 
     // ---- mask bits: ballots when elements are whole warps, else shared atomics
@@ -633,21 +662,45 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
                 const int m = skm[lt * N3 + t];
                 const float cs = (skc[lt * N3 + t] * qu1) * qu2;  // c 2^s, exact
                 const int pp = m % LX, qq = (m / LX) % LX, rr = m / NP;
-                const int col = pp * PT;
+                float ch_[LX], cl_[LX];  // column p of Phi: Phi[i][pp], i = 0..LX-1
+                if constexpr (LX % 4 == 0) {
+#pragma unroll
+                    for (int i = 0; i < LX; i += 4) {
+                        const float4 h4 = *reinterpret_cast<const float4*>(sPTh + pp * CS + i);
+                        ch_[i] = h4.x; ch_[i + 1] = h4.y; ch_[i + 2] = h4.z; ch_[i + 3] = h4.w;
+                        if constexpr (DF) {
+                            const float4 l4 = *reinterpret_cast<const float4*>(sPTl + pp * CS + i);
+                            cl_[i] = l4.x; cl_[i + 1] = l4.y; cl_[i + 2] = l4.z; cl_[i + 3] = l4.w;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < LX; ++i) {
+                        ch_[i] = sPTh[pp * CS + i];
+                        if constexpr (DF) cl_[i] = sPTl[pp * CS + i];
+                    }
+                }
                 if constexpr (DF) {
                     const f2 b = df_mulf(df_mul({sPh[rowj + qq], sPl[rowj + qq]}, {sPh[rowk + rr], sPl[rowk + rr]}), cs);
 #pragma unroll
-                    for (int i = 0; i < LX; ++i) {
+                    for (int i = 0; i < LX; ++i) {  // renormalised once after the loop
                         f2 acc = {vh[i], vl[i]};
-                        df_fma_acc(acc, b, {sPTh[col + i], sPTl[col + i]});
-                        const f2 n = df_norm(acc);
-                        vh[i] = n.h;
-                        vl[i] = n.l;
+                        df_fma_acc(acc, b, {ch_[i], cl_[i]});
+                        vh[i] = acc.h;
+                        vl[i] = acc.l;
                     }
                 } else {
                     const float b = cs * sPh[rowj + qq] * sPh[rowk + rr];
 #pragma unroll
-                    for (int i = 0; i < LX; ++i) vh[i] = fmaf(b, sPTh[col + i], vh[i]);
+                    for (int i = 0; i < LX; ++i) vh[i] = fmaf(b, ch_[i], vh[i]);
+                }
+            }
+            if constexpr (DF) {
+#pragma unroll
+                for (int i = 0; i < LX; ++i) {
+                    const f2 n = df_norm({vh[i], vl[i]});
+                    vh[i] = n.h;
+                    vl[i] = n.l;
                 }
             }
         }
@@ -728,7 +781,8 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
 #pragma unroll
             for (int i = 0; i < LX; ++i) {
                 const f2 d = df_sub({uh[i], ul[i]}, {vh[i], vl[i]});
-                df_fma_acc(e2p, df_mul(wq[i], d), d);
+                const float2 w = sWq[P * LX + i];
+                df_fma_acc(e2p, df_mul({w.x, w.y}, d), d);
                 const f2 ad = df_abs(d);
                 if (df_ge(ad, dmax)) dmax = ad;
             }
@@ -739,7 +793,7 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
 #pragma unroll
             for (int i = 0; i < LX; ++i) {
                 const float d = uh[i] - vh[i];
-                e2p.h = fmaf(wq[i].h * d, d, e2p.h);
+                e2p.h = fmaf(wq32[i] * d, d, e2p.h);
                 dm = max(dm, __float_as_uint(fabsf(d)));
             }
             linf_bits = dm;
