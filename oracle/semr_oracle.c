@@ -274,8 +274,9 @@ static int cmp_energy(const void *x, const void *y)
 /* Cumulative-energy boundary: energies e[0..n-1], budget t.  Returns the
  * smallest kept energy T (keep m iff e[m] >= T), or +inf when everything
  * fits the budget; *c_drop / *c_next get the running sums just before and
- * after the boundary (for the fragile list). */
-static double cumulative_boundary(int n, const double *e, double t, double *c_drop, double *c_next)
+ * after the boundary, *e_last the largest dropped energy (-1 when none is
+ * dropped), all for the fragile list. */
+static double cumulative_boundary(int n, const double *e, double t, double *c_drop, double *c_next, double *e_last)
 {
     int *idx = (int *)malloc(sizeof(int) * n);
     for (int m = 0; m < n; ++m) idx[m] = m;
@@ -289,6 +290,7 @@ static double cumulative_boundary(int n, const double *e, double t, double *c_dr
     }
     *c_drop = c;
     *c_next = (k < n) ? c + e[idx[k]] : c;
+    *e_last = (k > 0) ? e[idx[k - 1]] : -1.0;
     double T = (k < n) ? e[idx[k]] : INFINITY;
     free(idx);
     return T;
@@ -312,7 +314,9 @@ static double cumulative_boundary(int n, const double *e, double t, double *c_dr
  *                                                        (rounding decision)
  *               kind 3: mode -1, mu within 1e-9 of 1/2 or 1 (step exponent)
  *               kind 4: mode -1, cumulative variant: the running sum at the
- *                       boundary (last dropped or first kept) within 1e-9 t
+ *                       boundary (last dropped or first kept) within 1e-9 t,
+ *                       or the last dropped and first kept energies within
+ *                       1e-9 t of each other
  *   n_threads   OpenMP threads for the per-element loop (<= 0: default)
  *   truncation  0: per-coefficient threshold, 1: cumulative energy
  *
@@ -380,11 +384,11 @@ int oracle_reduce(int lx, int64_t n_elem, int n_fields, const double *fields, co
             double t = tau * S;
             if (t >= DBL_MIN) {
                 s = oracle_step_exponent(t, NULL);
-                double T = t, cd, cn;
+                double T = t, cd, cn, el;
                 if (truncation == 1) {
                     double *en = (double *)malloc(sizeof(double) * n);
                     for (int m = 0; m < n; ++m) en[m] = a[m] * a[m];
-                    T = cumulative_boundary(n, en, t, &cd, &cn);
+                    T = cumulative_boundary(n, en, t, &cd, &cn, &el);
                     free(en);
                 }
                 for (int m = 0; m < n; ++m) {
@@ -484,10 +488,14 @@ int oracle_reduce(int lx, int64_t n_elem, int n_fields, const double *fields, co
             if (truncation == 1) {
                 double *en = (double *)malloc(sizeof(double) * n);
                 for (int m = 0; m < n; ++m) en[m] = a[m] * a[m];
-                double cd, cn;
-                cumulative_boundary(n, en, t, &cd, &cn);
+                double cd, cn, el;
+                const double T = cumulative_boundary(n, en, t, &cd, &cn, &el);
                 free(en);
-                if (fabs(cd - t) <= 1e-9 * t || fabs(cn - t) <= 1e-9 * t) {
+                /* a running sum at the boundary within rounding of the budget, or the
+                 * last dropped and the first kept energy within rounding of each other
+                 * (then the order of the two, and with it the kept set, is fragile) */
+                if (fabs(cd - t) <= 1e-9 * t || fabs(cn - t) <= 1e-9 * t ||
+                    (el >= 0.0 && isfinite(T) && T - el <= 1e-9 * t)) {
                     if (fragile && nfr < fragile_cap) {
                         fragile[4 * nfr + 0] = f; fragile[4 * nfr + 1] = e;
                         fragile[4 * nfr + 2] = -1; fragile[4 * nfr + 3] = 4;

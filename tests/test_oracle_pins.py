@@ -443,3 +443,33 @@ def test_cumulative_monotone_and_limits():
     assert oracle.sections(oracle.reduce(f, j, 1.5, cumulative=True).payload)["counts"].sum() == 0
     r = oracle.reduce(f, j, 0.0, cumulative=True)  # tau = 0 stays lossless
     assert oracle.sections(r.payload)["masks"].all()
+
+
+def test_cumulative_near_tie_flagged():
+    """Two modes of (nearly) equal energy straddle the cumulative boundary (the
+    budget fits one of them, not both): which one is kept depends on rounding,
+    so the element is fragile (kind 4).  An exact tie keeps both (equal
+    energies are kept together); moving one energy well away clears the flag."""
+    lx, tau = 4, 1e-2
+    n = lx ** 3
+    blocks = []
+    for x2 in (0.6, 0.6 * (1 + 1e-12), 0.6 * 1.5):  # exact tie, near tie, clear gap
+        a = np.zeros(n)
+        a[0] = 1.0
+        a[5] = math.sqrt(0.6 * tau)  # energy 0.6 t (with S ~ 1)
+        a[9] = math.sqrt(x2 * tau)
+        blocks.append(oracle.inverse(lx, a).reshape(-1))
+    f = np.stack(blocks)[None]
+    r = oracle.reduce(f, np.ones(3), tau, cumulative=True)
+    kinds = {(int(e), int(k)) for _, e, m, k in r.fragile}
+    assert (0, 4) in kinds and (1, 4) in kinds
+    assert (2, 4) not in kinds
+    c = r.coeffs[0]
+    m = oracle.sections(r.payload)["masks"][0]
+    for e in range(3):
+        assert m[e, 0]
+        # the larger of the pair always survives; the smaller only on an exact tie
+        big, small = (9, 5) if c[e, 9] ** 2 >= c[e, 5] ** 2 else (5, 9)
+        assert m[e, big]
+        assert m[e, small] == (c[e, 5] ** 2 == c[e, 9] ** 2)
+    assert m[2, 9] and not m[2, 5]
