@@ -86,11 +86,20 @@ extern "C" {
 
 /* fieldset flags */
 #define SEMR_WRITE_RECON 1   /* also write the reconstruction to fieldset.recon[f] */
+#define SEMR_CUMULATIVE 2    /* cumulative-energy truncation (the sort-based reading of Sec. IV-B's
+                                maximal allowed error as a budget on the discarded energy): drop the
+                                least energetic modes while their summed energy stays <= tau S_e,
+                                keep every mode whose energy is at least the smallest one not
+                                dropped (equal energies together).  Step and codes as in the
+                                threshold form.  SEMR_FP64 and SEMR_FP32 only, single launches and
+                                the stream API (SEMR_EUNSUPPORTED with SEMR_FP64_NATIVE or in a
+                                batch); ignored in lossless mode (tau == 0). */
 
 /* payload header flag bits */
 #define SEMR_PAYLOAD_LOSSLESS 1
 #define SEMR_PAYLOAD_CODE32 2
 #define SEMR_PAYLOAD_FP32 4
+#define SEMR_PAYLOAD_CUMULATIVE 8  /* modes selected by SEMR_CUMULATIVE */
 
 /* summary.status bits (device-written) */
 #define SEMR_STATUS_OVERFLOW 1    /* payload_cap too small: codes not written */
@@ -108,7 +117,7 @@ typedef struct {
     int32_t n_fields;                 /* 1..SEMR_MAX_FIELDS */
     int32_t precision;                /* SEMR_FP64 or SEMR_FP32 */
     double tau;                       /* threshold, finite, >= 0; 0 = lossless mode */
-    int32_t flags;                    /* SEMR_WRITE_RECON or 0 */
+    int32_t flags;                    /* SEMR_WRITE_RECON | SEMR_CUMULATIVE, or 0 */
     int32_t pad_;
     const double* fields[SEMR_MAX_FIELDS];  /* device, n_elem*lx^3 FP64 each */
     double* recon[SEMR_MAX_FIELDS];         /* device outputs when SEMR_WRITE_RECON, else ignored */

@@ -28,8 +28,8 @@ SEMR_OK, SEMR_EINVAL, SEMR_ENOMEM, SEMR_EBUDGET, SEMR_EAGAIN = 0, 1, 2, 3, 4
 SEMR_ETIMEDOUT, SEMR_ECUDA, SEMR_ENOSPACE, SEMR_ENONFINITE, SEMR_EUNSUPPORTED = 5, 6, 7, 8, 9
 SEMR_MAX_FIELDS, SEMR_LX_MIN, SEMR_LX_MAX = 16, 2, 12
 SEMR_FP64, SEMR_FP32, SEMR_FP64_NATIVE = 0, 1, 2
-SEMR_WRITE_RECON = 1
-SEMR_PAYLOAD_LOSSLESS, SEMR_PAYLOAD_CODE32, SEMR_PAYLOAD_FP32 = 1, 2, 4
+SEMR_WRITE_RECON, SEMR_CUMULATIVE = 1, 2
+SEMR_PAYLOAD_LOSSLESS, SEMR_PAYLOAD_CODE32, SEMR_PAYLOAD_FP32, SEMR_PAYLOAD_CUMULATIVE = 1, 2, 4, 8
 SEMR_STATUS_OVERFLOW, SEMR_STATUS_TIMEOUT, SEMR_STATUS_NONFINITE = 1, 2, 4
 
 
@@ -229,13 +229,15 @@ def semr_gll(lx: int) -> tuple[np.ndarray, np.ndarray]:
 
 # ----------------------------------------------------- torch marshalling
 
-def make_fieldset(fields, tau: float, precision: int = SEMR_FP64, recon=None) -> semr_fieldset:
-    """fields: sequence of CUDA FP64 tensors (contiguous, n_elem*lx^3 each)."""
+def make_fieldset(fields, tau: float, precision: int = SEMR_FP64, recon=None,
+                  cumulative: bool = False) -> semr_fieldset:
+    """fields: sequence of CUDA FP64 tensors (contiguous, n_elem*lx^3 each).
+    ``cumulative`` selects the cumulative-energy truncation (SEMR_CUMULATIVE)."""
     fs = semr_fieldset()
     fs.n_fields = len(fields)
     fs.precision = precision
     fs.tau = float(tau)
-    fs.flags = SEMR_WRITE_RECON if recon is not None else 0
+    fs.flags = (SEMR_WRITE_RECON if recon is not None else 0) | (SEMR_CUMULATIVE if cumulative else 0)
     for i, t in enumerate(fields):
         _require_cuda_f64(t)
         fs.fields[i] = t.data_ptr()
@@ -292,12 +294,12 @@ def alloc_buffers(lx: int, n_elem: int, n_fields: int, tau: float, device="cuda"
 
 
 def reduce_async(fields, jac, lx: int, tau: float, bufs: DeviceBuffers, precision: int = SEMR_FP64,
-                 recon=None, stream=None, events=None) -> None:
+                 recon=None, stream=None, events=None, cumulative: bool = False) -> None:
     """Launch one reduction on ``stream`` (default: torch's current stream).
     ``events``: optional (begin, end) torch.cuda.Event pair recorded around the
     fused reduce kernel alone."""
     import torch
-    fs = make_fieldset(fields, tau, precision, recon)
+    fs = make_fieldset(fields, tau, precision, recon, cumulative)
     mesh = make_mesh(lx, jac)
     st = (stream or torch.cuda.current_stream()).cuda_stream
     if events is None:
@@ -323,13 +325,13 @@ class Result:
 
 
 def reduce(fields, jac, lx: int, tau: float, precision: int = SEMR_FP64, recon=None,
-           elem_report: bool = True) -> Result:
+           elem_report: bool = True, cumulative: bool = False) -> Result:
     """Blocking convenience: reduce, then copy payload, summary and element
     report to the host."""
     import torch
     n_elem = jac.numel()
     bufs = alloc_buffers(lx, n_elem, len(fields), tau, fields[0].device, elem_report=elem_report)
-    reduce_async(fields, jac, lx, tau, bufs, precision, recon)
+    reduce_async(fields, jac, lx, tau, bufs, precision, recon, cumulative=cumulative)
     torch.cuda.current_stream().synchronize()
     sm = summary_from(bufs)
     payload = bufs.payload[: sm.payload_bytes].cpu().numpy()

@@ -65,6 +65,9 @@ extern "C" int semr_reduce_async_timed(const semr_fieldset* fs, const semr_mesh*
     if (rc) return rc;
     if (fs->precision != SEMR_FP64 && fs->precision != SEMR_FP32 && fs->precision != SEMR_FP64_NATIVE)
         return SEMR_EUNSUPPORTED;
+    if (fs->flags & ~(SEMR_WRITE_RECON | SEMR_CUMULATIVE)) return SEMR_EINVAL;
+    const bool cumulative = (fs->flags & SEMR_CUMULATIVE) && fs->tau != 0.0;
+    if (cumulative && fs->precision == SEMR_FP64_NATIVE) return SEMR_EUNSUPPORTED;
     if (!mesh->jac || !out->payload || !out->summary || !out->scratch) return SEMR_EINVAL;
     if ((reinterpret_cast<uintptr_t>(out->scratch) & 255u) != 0 || !aligned16(out->payload)) return SEMR_EINVAL;
     // even lx: element blocks are loaded as 16-byte vectors; odd lx: 8-byte scalars
@@ -101,6 +104,7 @@ extern "C" int semr_reduce_async_timed(const semr_fieldset* fs, const semr_mesh*
     p.width = (int32_t)sz.code_width;
     p.write_recon = (fs->flags & SEMR_WRITE_RECON) ? 1 : 0;
     p.precision = fs->precision;
+    p.cumulative = cumulative ? 1 : 0;
     p.header_bytes = sz.header_bytes;
     p.fixed_bytes = field_fixed_bytes(mesh->lx, mesh->n_elem);
     p.code_base = sz.code_base;

@@ -43,6 +43,7 @@ int fill_params(const semr_batch_item& it, int tile, LaunchParams& p) {
     if (rc) return rc;
     if (fs.precision != SEMR_FP64 && fs.precision != SEMR_FP32) return SEMR_EUNSUPPORTED;
     if (fs.precision == SEMR_FP64 && fs.tau == 0.0) return SEMR_EUNSUPPORTED;  // lossless FP64: single launches
+    if (fs.flags & SEMR_CUMULATIVE) return SEMR_EUNSUPPORTED;  // cumulative variant: single launches
     if (!m.jac || !it.out.payload || !it.out.summary) return SEMR_EINVAL;
     if (it.out.payload_cap < sz.code_base) return SEMR_EINVAL;
     const uintptr_t amask = (m.lx % 2 == 0) ? 15u : 7u;

@@ -1,7 +1,8 @@
 // Device helpers shared by the reduce kernels: look-back state access,
 // exact power-of-two scaling, magnitude thresholds, the even-odd folded 1-D
 // transforms, FP32-pair ("df64") arithmetic, integer double->float
-// conversion and exact fixed-point warp sums.
+// conversion, exact fixed-point warp sums, and a warp sort and scan of
+// 64-bit keys.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -263,6 +264,32 @@ __device__ __forceinline__ unsigned long long warp_sum_u62(unsigned long long v)
     const unsigned long long s1 = __reduce_add_sync(0xffffffffu, c1);
     const unsigned long long s2 = __reduce_add_sync(0xffffffffu, c2);
     return s0 + (s1 << 20) + (s2 << 40);
+}
+
+// Ascending bitonic sort of one 64-bit key per lane across the warp.
+__device__ __forceinline__ unsigned long long warp_sort_u64(unsigned long long v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, j);
+            const bool up = (lane & k) == 0, low = (lane & j) == 0;  // block direction, lower lane of the pair
+            v = (low == up) ? (v < o ? v : o) : (v < o ? o : v);
+        }
+    }
+    return v;
+}
+
+// Inclusive prefix sum of one 64-bit value per lane (exact, lane order).
+__device__ __forceinline__ unsigned long long warp_incl_scan_u64(unsigned long long v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += n;
+    }
+    return v;
 }
 
 // ------------------------------------------------ 1-D folded transforms

@@ -12,6 +12,20 @@
 // are pair-of-float tree sums (deterministic), and only once per element do
 // a few FP64 instructions form t = tau S_e, the step and the threshold.
 //
+// Cumulative-energy truncation (MODE_CUM): the modes kept are those whose
+// energy is at least T, the smallest energy value v with
+//   sum of all energies <= v  >  t = tau S_e,
+// which is exactly what sorting the energies and dropping the longest
+// prefix whose sum fits the budget t selects (equal energies kept together),
+// without a sort.  Energies become 64-bit fixed-point keys floor(a^2 2^K),
+// t 2^K in [2^47, 2^48), so every sum is an exact integer sum (deterministic
+// in any order): an octave histogram of key sums (shared atomics) finds the
+// octave that holds T, one warp sorts that octave's few keys (or bisects
+// when there are more than 32) and scans them against the budget.  FP64
+// mode computes the forward transform in float pairs for this variant: the
+// boundary depends on the sum of every small energy, which FP32 coefficients
+// cannot settle.
+//
 // The reconstruction exploits how few modes survive (2-3 per element at
 // tau = 1e-3): each thread rebuilds its pencil from the element's list of
 // kept modes, u~(i) = sum_m c_m 2^s phi_p(x_i) phi_q(x_j) phi_r(x_k).  When a
@@ -25,7 +39,8 @@
 namespace semr {
 
 constexpr int MODE_F32 = 0;
-constexpr int MODE_DF64 = 1;
+constexpr int MODE_DF64 = 1;  // bit 0: float-pair (FP64-accurate) arithmetic
+constexpr int MODE_CUM = 2;   // bit 1: cumulative-energy truncation
 
 template <int LX>
 struct FastTables {
@@ -62,7 +77,7 @@ constexpr int AMB_CAP = 64;
 template <int LX, int MODE, int TILE_>
 struct FSmem {
     using C = FCfg<LX, TILE_>;
-    static constexpr size_t vb = (MODE == MODE_DF64) ? 8 : 4;   // float2 or float per value
+    static constexpr size_t vb = (MODE & MODE_DF64) ? 8 : 4;   // float2 or float per value
     static constexpr size_t buf_bytes = vb * C::TILE * C::BUFN;
     static constexpr size_t off_t1 = 0;
     static constexpr size_t off_t2 = off_t1 + buf_bytes;
@@ -75,10 +90,15 @@ struct FSmem {
     static constexpr size_t off_amat = off_phi + 16ull * LX * C::PT;       // 2 tables x LX x PT floats
     static constexpr size_t off_amb = off_amat + 8ull * LX * C::PT;        // AMB_CAP entries + values
     static constexpr size_t off_wq = (off_amb + 12ull * AMB_CAP + 4ull * C::TILE + 16 + 15) / 16 * 16;
-    static constexpr size_t off_mask = off_wq + (MODE == MODE_DF64 ? 8ull * C::NP * LX : 0);  // TILE x MW u32
+    static constexpr size_t off_mask = off_wq + ((MODE & MODE_DF64) ? 8ull * C::NP * LX : 0);  // TILE x MW u32
     static constexpr size_t off_wpre = off_mask + 4ull * C::TILE * C::MW;
     static constexpr size_t off_misc = (off_wpre + 4ull * C::TILE * C::MW + 15) / 16 * 16;
-    static constexpr size_t bytes = off_misc + 4ull * (9 * C::TILE + 16);
+    // cumulative variant: per element 64 octave sums (unless one warp holds all
+    // the keys), then boundary key, base sum, budget, octave, count, K
+    static constexpr bool CUM_DIRECT = C::N3 <= 32;
+    static constexpr size_t off_cum = (off_misc + 4ull * (9 * C::TILE + 16) + 15) / 16 * 16;
+    static constexpr size_t cum_bytes = (MODE & MODE_CUM) ? (CUM_DIRECT ? 0 : 512ull * C::TILE) + 40ull * C::TILE : 0;
+    static constexpr size_t bytes = off_cum + cum_bytes;
 };
 
 // Per-element reduction of one sum (a float pair) and one maximum (a 64-bit
@@ -159,7 +179,7 @@ __device__ __forceinline__ void elem_reduce(float* red, double* out, f2 s, unsig
 // Resident threads per SM the register budget aims at: enough warps to hide
 // the latency of the tile's barrier phases, without spilling the larger orders.
 constexpr int min_ctas_per_sm(int lx, int mode, int block) {
-    const int target = (mode == MODE_F32) ? (lx <= 10 ? 1024 : 768) : (lx <= 8 ? 768 : 512);
+    const int target = !(mode & MODE_DF64) ? (lx <= 10 ? 1024 : 768) : (lx <= 8 ? 768 : 512);
     return target / block > 0 ? target / block : 1;
 }
 
@@ -172,7 +192,9 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
     using S = FSmem<LX, MODE, TILE_>;
     constexpr int NP = C::NP, N3 = C::N3, TILE = C::TILE, MW = C::MW, SX = C::SX, SY = C::SY, PT = C::PT;
     constexpr int CS = (LX % 4 == 0) ? LX : PT;  // row stride of the column table (16-byte rows when possible)
-    constexpr bool DF = (MODE == MODE_DF64);
+    constexpr bool DF = (MODE & MODE_DF64) != 0;
+    constexpr bool CUM = (MODE & MODE_CUM) != 0;
+    constexpr bool DIRECT = S::CUM_DIRECT;  // cumulative: one warp holds all keys of an element
     using V = typename std::conditional<DF, float2, float>::type;  // one transposed value
     // dense inverse once any element of the tile keeps more modes than this
     constexpr int SPARSE_MAX = DF ? 12 : 5;
@@ -209,6 +231,15 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
     int* s_flag = s_bad + TILE;          // [2]: dense inverse needed
     float* s_g = reinterpret_cast<float*>(s_flag + 2);  // [2 * TILE]: threshold (hi, lo)
     float* s_marg = s_g + 2 * TILE;                       // [TILE]: bound on |a_fp32 - a|
+    // cumulative variant
+    unsigned long long* sbk = reinterpret_cast<unsigned long long*>(smem + S::off_cum);  // [TILE][64] octave sums
+    unsigned long long* s_T = sbk + (DIRECT ? 0 : 64 * TILE);  // [TILE] smallest kept key (~0: none)
+    unsigned long long* s_base = s_T + TILE;                    // [TILE] key sum below the octave of T
+    unsigned long long* s_tint = s_base + TILE;                 // [TILE] floor(t 2^K)
+    int* s_bstar = reinterpret_cast<int*>(s_tint + TILE);       // [TILE] octave (bit length) of T
+    int* s_ncand = s_bstar + TILE;                              // [TILE] keys in that octave
+    int* s_cK = s_ncand + TILE;                                 // [TILE] K
+    unsigned long long* scand = reinterpret_cast<unsigned long long*>(scodes);  // [TILE][N3] keys of the octave
 
     // parameters of the reduction the current tile belongs to
     __shared__ LaunchParams sp;
@@ -345,7 +376,43 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
     // transposes).  In FP64 mode the FP32 coefficients settle every decision
     // they are provably on the right side of; the others are recomputed exactly.
     float ah[LX], al[LX];  // modal coefficients a[r][q=pa][p=pb], mode m = P + NP r
-    {
+    if constexpr (DF && CUM) {  // the whole transform in float pairs
+        f2 x[LX], y[LX];
+#pragma unroll
+        for (int i = 0; i < LX; ++i) x[i] = {uh[i], ul[i]};
+        fwd1d_df<LX>(tab.Ah, tab.Al, x, y);
+        if (in_tile) {
+#pragma unroll
+            for (int q = 0; q < LX; ++q) b1[pa * SX + pb * SY + q] = make_float2(y[q].h, y[q].l);
+        }
+        __syncthreads();
+        if (in_tile) {
+#pragma unroll
+            for (int j = 0; j < LX; ++j) {
+                const float2 v = b1[pa * SX + j * SY + pb];
+                x[j] = {v.x, v.y};
+            }
+        }
+        fwd1d_df<LX>(tab.Ah, tab.Al, x, y);
+        if (in_tile) {
+#pragma unroll
+            for (int q = 0; q < LX; ++q) b2[pa * SX + q * SY + pb] = make_float2(y[q].h, y[q].l);
+        }
+        __syncthreads();
+        if (in_tile) {
+#pragma unroll
+            for (int k = 0; k < LX; ++k) {
+                const float2 v = b2[k * SX + pa * SY + pb];
+                x[k] = {v.x, v.y};
+            }
+        }
+        fwd1d_df<LX>(tab.Ah, tab.Al, x, y);
+#pragma unroll
+        for (int r = 0; r < LX; ++r) {
+            ah[r] = y[r].h;
+            al[r] = y[r].l;
+        }
+    } else {
         float x[LX], y[LX];
 #pragma unroll
         for (int i = 0; i < LX; ++i) x[i] = uh[i];
@@ -396,6 +463,12 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
             for (int r = 0; r < LX; ++r) sp.h = fmaf(ah[r], ah[r], sp.h);
         }
     }
+    if constexpr (CUM) {  // cleared here, used after the barriers of the element reduction
+        if constexpr (!DIRECT) {
+            for (int i = tid; i < 64 * TILE; i += C::BLOCK) sbk[i] = 0ull;
+        }
+        if (tid < TILE) s_ncand[tid] = 0;
+    }
     elem_reduce<LX, TILE_, DF>(red, selem, sp, umax_bits, DF, 0, 2, n_here);  // S -> [0], max|u| -> [2]
 
     // ---- per element (one thread each): t = tau S, step s, magnitude threshold g
@@ -404,6 +477,10 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
         const double Se = selem[l * 8 + 0];
         int step = INT16_MIN, mode = 0;  // 0: keep none, 1: threshold, 2: keep all (lossless)
         double g = 0.0;
+        if constexpr (CUM) {
+            s_cK[l] = 0;
+            s_tint[l] = 0ull;
+        }
         if (l < n_here) {
             if (!isfinite(Se) || s_bad[l]) {
                 atomicOr(&ctl->status, (unsigned)SEMR_STATUS_NONFINITE);
@@ -418,6 +495,10 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
                     if (st >= -250 && st <= 250) {  // 2^-s as a product of two normal floats
                         step = st;
                         mode = 1;
+                        if constexpr (CUM) {  // t in [2^(ex-1), 2^ex): K = 48 - ex, floor(t 2^K) = M >> 5
+                            s_cK[l] = 48 - ex;
+                            s_tint[l] = (((unsigned long long)bits & 0xfffffffffffffull) | (1ull << 52)) >> 5;
+                        }
                         // FP64 mode refines g to the exact double threshold only for elements
                         // with coefficients it recomputes; the float threshold settles the rest
                         g = (double)threshold_abs32_fast(t);
@@ -445,7 +526,7 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
     const int step = (in_tile && emode == 1) ? s_step[lt] : 0;
     f2 g2 = in_tile ? f2{s_g[2 * lt], s_g[2 * lt + 1]} : f2{0.0f, 0.0f};
 
-    if constexpr (DF) {
+    if constexpr (DF && !CUM) {
         // ---- decisions the FP32 coefficients cannot settle: recompute them exactly
         const int sdn1 = (-step) >> 1, sdn2 = -step - sdn1;
         const float sc = pow2f(sdn1) * pow2f(sdn2);  // 2^-s, exact
@@ -538,13 +619,112 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
         if (in_tile) g2 = f2{s_g[2 * lt], s_g[2 * lt + 1]};  // exact where it was refined
     }
 
+    // ---- cumulative variant: the boundary key T of each element
+    constexpr unsigned long long KCLAMP = 1ull << 50;  // key of every energy >= 2t: always kept
+    const int cK = (CUM && in_tile) ? s_cK[lt] : 0;
+    auto energy_key = [&](int r) -> unsigned long long {  // floor(a^2 2^K) from the exact square
+        const f2 e2 = df_mul({ah[r], al[r]}, {ah[r], al[r]});
+        const long long v = (long long)fixp(e2.h, cK) + fixp_signed(e2.l, cK);
+        if (v <= 0) return 0ull;
+        return ((unsigned long long)v >= (1ull << 49)) ? KCLAMP : (unsigned long long)v;
+    };
+    unsigned long long sT = ~0ull;
+    if constexpr (CUM) {
+        const int wid = tid >> 5;
+        const bool sel = active && emode == 1;
+        if constexpr (DIRECT) {
+            if (sel) {
+#pragma unroll
+                for (int r = 0; r < LX; ++r) scand[lt * N3 + P + NP * r] = energy_key(r);
+            }
+        } else {
+            if (sel) {
+#pragma unroll
+                for (int r = 0; r < LX; ++r) {
+                    const unsigned long long k = energy_key(r);
+                    if (k) atomicAdd(&sbk[lt * 64 + (64 - __clzll((long long)k))], k);
+                }
+            }
+            __syncthreads();
+            for (int l = wid; l < TILE; l += C::NW) {  // octave of T: first prefix of octave sums above t
+                const unsigned long long lo = sbk[l * 64 + lane], hi = sbk[l * 64 + 32 + lane];
+                const unsigned long long ilo = warp_incl_scan_u64(lo), ihi = warp_incl_scan_u64(hi);
+                const unsigned long long tot = __shfl_sync(0xffffffffu, ilo, 31);
+                const unsigned long long tt = s_tint[l];
+                const bool ok = l < n_here && s_mode[l] == 1;
+                const unsigned m1 = __ballot_sync(0xffffffffu, ok && ilo > tt);
+                const unsigned m2 = __ballot_sync(0xffffffffu, ok && tot + ihi > tt);
+                int bs = -1;
+                unsigned long long base = 0ull;
+                if (m1) {
+                    bs = __ffs(m1) - 1;
+                    base = __shfl_sync(0xffffffffu, ilo - lo, bs);
+                } else if (m2) {
+                    const int j = __ffs(m2) - 1;
+                    bs = 32 + j;
+                    base = tot + __shfl_sync(0xffffffffu, ihi - hi, j);
+                }
+                if (lane == 0) {
+                    s_bstar[l] = bs;
+                    s_base[l] = base;
+                }
+            }
+            __syncthreads();
+            const int bs = in_tile ? s_bstar[lt] : -1;
+            if (sel && bs > 0) {  // gather the keys of that octave
+#pragma unroll
+                for (int r = 0; r < LX; ++r) {
+                    const unsigned long long k = energy_key(r);
+                    if (k && (64 - __clzll((long long)k)) == bs) scand[lt * N3 + atomicAdd(&s_ncand[lt], 1)] = k;
+                }
+            }
+        }
+        __syncthreads();
+        for (int l = wid; l < TILE; l += C::NW) {  // one warp per element: T from the octave's keys
+            unsigned long long T = ~0ull;
+            const bool ok = l < n_here && s_mode[l] == 1 && (DIRECT || s_bstar[l] > 0);
+            if (ok) {
+                const int c = DIRECT ? N3 : s_ncand[l];
+                const unsigned long long base = DIRECT ? 0ull : s_base[l];
+                const unsigned long long tt = s_tint[l];
+                const unsigned long long* cand = scand + (size_t)l * N3;
+                if (c <= 32) {  // sort, scan, first inclusive sum above the budget
+                    unsigned long long v = (lane < c) ? cand[lane] : ~0ull;
+                    v = warp_sort_u64(v);
+                    const unsigned long long inc = warp_incl_scan_u64(lane < c ? v : 0ull);
+                    const unsigned m = __ballot_sync(0xffffffffu, lane < c && base + inc > tt);
+                    if (m) T = __shfl_sync(0xffffffffu, v, __ffs(m) - 1);
+                } else {  // bisection on the key value: smallest v with base + sum(keys <= v) > t
+                    const int bs = DIRECT ? 1 : s_bstar[l];
+                    unsigned long long lo = 1ull << (bs - 1), hi = (bs > 50) ? KCLAMP : (1ull << bs) - 1ull;
+                    while (lo < hi) {
+                        const unsigned long long mid = lo + (hi - lo) / 2;
+                        unsigned long long sm = 0ull;
+                        for (int i = lane; i < c; i += 32) {
+                            const unsigned long long k = cand[i];
+                            if (k <= mid) sm += k;
+                        }
+                        sm = warp_sum_u62(sm);
+                        if (base + sm > tt) hi = mid;
+                        else lo = mid + 1;
+                    }
+                    T = lo;
+                }
+            }
+            if (lane == 0) s_T[l] = T;
+        }
+        __syncthreads();
+        if (in_tile) sT = s_T[lt];
+    }
+
     // ---- mask bits: ballots when elements are whole warps, else shared atomics
     uint32_t keepbits = 0;
     uint32_t bw[LX];  // ballot word of mode P + NP r (ballot path)
 #pragma unroll
     for (int r = 0; r < LX; ++r) {
         bool k;
-        if constexpr (DF) k = df_ge(df_abs({ah[r], al[r]}), g2);
+        if constexpr (CUM) k = energy_key(r) >= sT;
+        else if constexpr (DF) k = df_ge(df_abs({ah[r], al[r]}), g2);
         else k = fabsf(ah[r]) >= g2.h;
         k = active && (emode == 2 || (emode == 1 && k));
         keepbits |= (k ? 1u : 0u) << r;
@@ -1015,6 +1195,9 @@ int tile_variants(int lx, int* out, int cap) {
 }
 
 int launch_reduce_fast(const LaunchParams& p, int lx, void* stream) {
+    if (p.cumulative)
+        return p.precision == SEMR_FP32 ? single_mode<MODE_F32 | MODE_CUM>(p, lx, stream)
+                                        : single_mode<MODE_DF64 | MODE_CUM>(p, lx, stream);
     return p.precision == SEMR_FP32 ? single_mode<MODE_F32>(p, lx, stream) : single_mode<MODE_DF64>(p, lx, stream);
 }
 

@@ -83,6 +83,8 @@ struct LaunchParams {
     double* tile_part;
     int32_t lx;
     int32_t tile;   // elements per tile of the kernel variant that runs this item
+    int32_t cumulative;  // cumulative-energy truncation (never together with lossless)
+    int32_t pad2_;
 };
 
 // Default scratch split of one contiguous scratch buffer.

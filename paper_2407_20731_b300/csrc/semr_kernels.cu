@@ -532,6 +532,7 @@ __device__ void finalize_field(const LaunchParams& p, int f, int lx, double (*re
         if (p.lossless) flags |= SEMR_PAYLOAD_LOSSLESS;
         if (p.width == 4) flags |= SEMR_PAYLOAD_CODE32;
         if (p.precision == SEMR_FP32) flags |= SEMR_PAYLOAD_FP32;
+        if (p.cumulative) flags |= SEMR_PAYLOAD_CUMULATIVE;
         *reinterpret_cast<uint16_t*>(h + 10) = flags;
         *reinterpret_cast<uint32_t*>(h + 12) = (uint32_t)p.header_bytes;
         *reinterpret_cast<uint64_t*>(h + 16) = (uint64_t)p.n_elem;

@@ -29,10 +29,11 @@ def make_case(n_elem, lx, n_fields, seed=1, slope=-5.0 / 3.0, device="cuda"):
     return f.reshape(n_fields, n_elem, lx ** 3).contiguous(), j.contiguous()
 
 
-def run_gpu(fields, jac, lx, tau, precision=semr.SEMR_FP64, recon=True):
+def run_gpu(fields, jac, lx, tau, precision=semr.SEMR_FP64, recon=True, cumulative=False):
     F, E = fields.shape[0], fields.shape[1]
     rec = [torch.empty_like(fields[i]) for i in range(F)] if recon else None
-    res = semr.reduce([fields[i] for i in range(F)], jac, lx, tau, precision=precision, recon=rec)
+    res = semr.reduce([fields[i] for i in range(F)], jac, lx, tau, precision=precision, recon=rec,
+                      cumulative=cumulative)
     torch.cuda.synchronize()
     rec_np = torch.stack(rec).cpu().numpy() if recon else None
     return res, rec_np

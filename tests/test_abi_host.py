@@ -49,6 +49,13 @@ def test_argument_validation_needs_no_gpu():
     assert semr.semr_reduce_async(fs, mesh, out, 0) in (semr.SEMR_EINVAL, semr.SEMR_EUNSUPPORTED)
     mesh.lx = 13
     assert semr.semr_reduce_async(fs, mesh, out, 0) == semr.SEMR_EUNSUPPORTED
+    # flags: unknown bits are rejected; the cumulative variant has no native-FP64 form
+    mesh.lx, fs.precision = 8, semr.SEMR_FP64
+    fs.flags = 4
+    assert semr.semr_reduce_async(fs, mesh, out, 0) == semr.SEMR_EINVAL
+    fs.flags, fs.precision = semr.SEMR_CUMULATIVE, semr.SEMR_FP64_NATIVE
+    assert semr.semr_reduce_async(fs, mesh, out, 0) == semr.SEMR_EUNSUPPORTED
+    fs.flags = 0
     with pytest.raises(semr.SemrError):
         semr.semr_sizes_for(1, 10, 1, 1e-3)
     with pytest.raises(semr.SemrError):
