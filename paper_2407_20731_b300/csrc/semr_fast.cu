@@ -179,7 +179,8 @@ __device__ __forceinline__ void elem_reduce(float* red, double* out, f2 s, unsig
 // Resident threads per SM the register budget aims at: enough warps to hide
 // the latency of the tile's barrier phases, without spilling the larger orders.
 constexpr int min_ctas_per_sm(int lx, int mode, int block) {
-    const int target = !(mode & MODE_DF64) ? (lx <= 10 ? 1024 : 768) : (lx <= 8 ? 768 : 512);
+    const int target = (mode & MODE_CUM) ? (!(mode & MODE_DF64) ? 768 : 512)
+                       : !(mode & MODE_DF64) ? (lx <= 10 ? 1024 : 768) : (lx <= 8 ? 768 : 512);
     return target / block > 0 ? target / block : 1;
 }
 
@@ -629,20 +630,22 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
         return ((unsigned long long)v >= (1ull << 49)) ? KCLAMP : (unsigned long long)v;
     };
     unsigned long long sT = ~0ull;
+    unsigned long long ek[CUM ? LX : 1];  // energy keys of the pencil's coefficients (0 when not selecting)
     if constexpr (CUM) {
         const int wid = tid >> 5;
         const bool sel = active && emode == 1;
+#pragma unroll
+        for (int r = 0; r < LX; ++r) ek[r] = sel ? energy_key(r) : 0ull;
         if constexpr (DIRECT) {
             if (sel) {
 #pragma unroll
-                for (int r = 0; r < LX; ++r) scand[lt * N3 + P + NP * r] = energy_key(r);
+                for (int r = 0; r < LX; ++r) scand[lt * N3 + P + NP * r] = ek[r];
             }
         } else {
             if (sel) {
 #pragma unroll
                 for (int r = 0; r < LX; ++r) {
-                    const unsigned long long k = energy_key(r);
-                    if (k) atomicAdd(&sbk[lt * 64 + (64 - __clzll((long long)k))], k);
+                    if (ek[r]) atomicAdd(&sbk[lt * 64 + (64 - __clzll((long long)ek[r]))], ek[r]);
                 }
             }
             __syncthreads();
@@ -674,8 +677,8 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
             if (sel && bs > 0) {  // gather the keys of that octave
 #pragma unroll
                 for (int r = 0; r < LX; ++r) {
-                    const unsigned long long k = energy_key(r);
-                    if (k && (64 - __clzll((long long)k)) == bs) scand[lt * N3 + atomicAdd(&s_ncand[lt], 1)] = k;
+                    if (ek[r] && (64 - __clzll((long long)ek[r])) == bs)
+                        scand[lt * N3 + atomicAdd(&s_ncand[lt], 1)] = ek[r];
                 }
             }
         }
@@ -723,7 +726,7 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
 #pragma unroll
     for (int r = 0; r < LX; ++r) {
         bool k;
-        if constexpr (CUM) k = energy_key(r) >= sT;
+        if constexpr (CUM) k = ek[r] >= sT;
         else if constexpr (DF) k = df_ge(df_abs({ah[r], al[r]}), g2);
         else k = fabsf(ah[r]) >= g2.h;
         k = active && (emode == 2 || (emode == 1 && k));
