@@ -39,7 +39,10 @@ N_SIDE, LX, N_FIELDS = 64, 8, 4
 SEEDS = [10, 11, 12, 13]
 METRIC = "snapshot GB/s reduced (FP64 input ingested per second)"
 L2_NOTE = "inputs 4.29 GB per snapshot > 126 MB L2; no flush needed"
-KERNEL_SOURCES = ["paper_2407_20731_b300/csrc/semr_kernels.cu", "paper_2407_20731_b300/csrc/semr_internal.h"]
+KERNEL_SOURCES = ["paper_2407_20731_b300/csrc/semr_fast.cu", "paper_2407_20731_b300/csrc/semr_device.cuh",
+                  "paper_2407_20731_b300/csrc/semr_internal.h"]
+# FP64 pipe of B300, nominal (the FP32 pipes run ~50x faster; FP64 mode runs on them)
+FP64_PIPE_TFLOPS_NOMINAL = 1.25
 
 
 def parse_args():
@@ -81,7 +84,7 @@ def measured_peaks() -> dict:
 def profiled_traffic(precision: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", f"reduce_kernel_{precision}_lx8_64cube.md")
+    path = os.path.join(ROOT, "profiles", f"reduce_fast_kernel_{precision}_lx8_64cube.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
@@ -208,6 +211,12 @@ def cpu_baseline(fields_host, jac_host, tau, target_s):
 
 # ------------------------------------------------------------------ helpers
 
+def algorithmic_flops(n_elem, n_fields):
+    """FLOPs of the method at FP64 accuracy: forward and inverse tensor-product
+    transforms with even-odd folding, 2 x 3 lx^4 / 2 FMA per element-field."""
+    return 2 * 3 * LX ** 4 * n_fields * n_elem
+
+
 def algorithmic_bytes(n_elem, n_fields, code_total, width):
     """Bytes the fused kernel must move per launch: read every input value
     once and the Jacobians once; write masks, steps, counts, codes and the
@@ -284,8 +293,13 @@ def run_semr(args):
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "peak_source": f"{peaks['source']} (MEASURED_PEAKS hbm_gbs, copy)",
-                "kernel": f"reduce_kernel<{LX},{'double' if prec == semr.SEMR_FP64 else 'float'}>",
+                "kernel": f"reduce_fast_kernel<{LX}, {'float pairs (FP64 accuracy)' if prec == semr.SEMR_FP64 else 'FP32'}>",
                 "kernel_ms": round(kernel_ms, 4), "algorithmic_bytes_per_launch": algo}
+    flops = algorithmic_flops(E, N_FIELDS)
+    roofline["alu"] = {"algorithmic_flops_per_launch": flops,
+                       "achieved_tflops": round(flops / (kernel_ms * 1e-3) / 1e12, 3),
+                       "fp64_pipe_peak_tflops_nominal": FP64_PIPE_TFLOPS_NOMINAL,
+                       "frac_of_fp64_pipe": round(flops / (kernel_ms * 1e-3) / 1e12 / FP64_PIPE_TFLOPS_NOMINAL, 3)}
 
     # ---- end to end through the public stream API: pinned host input -> H2D -> submit -> fetch (D2H)
     progress(f"device leg done: {ms_step:.3f} ms/step")
@@ -359,13 +373,13 @@ def run_extras(dev, flist, jac, E, snapshot_bytes, peaks):
 
     import paper_2407_20731_b300 as semr
 
-    def timed(tau, p, n=10):
+    def timed(tau, p, n=10, cumulative=False):
         b = semr.alloc_buffers(LX, E, N_FIELDS, tau, dev)
         for _ in range(2):
-            semr.reduce_async(flist, jac, LX, tau, b, p)
+            semr.reduce_async(flist, jac, LX, tau, b, p, cumulative=cumulative)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
         for a in ev:
-            semr.reduce_async(flist, jac, LX, tau, b, p, events=a)
+            semr.reduce_async(flist, jac, LX, tau, b, p, events=a, cumulative=cumulative)
         torch.cuda.synchronize()
         kms = statistics.mean(a.elapsed_time(c) for a, c in ev)
         s = semr.summary_from(b)
@@ -373,12 +387,15 @@ def run_extras(dev, flist, jac, E, snapshot_bytes, peaks):
                "hbm_frac": round(algorithmic_bytes(E, N_FIELDS, s.code_total, int(b.sizes.code_width))
                                  / (kms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
                "cr": round(s.cr, 5), "l2_rel": [round(s.field[i].l2_rel, 6) for i in range(N_FIELDS)],
-               "linf_rel": [round(s.field[i].linf_rel, 6) for i in range(N_FIELDS)], "status": s.status}
+               "linf_rel": [round(s.field[i].linf_rel, 6) for i in range(N_FIELDS)], "status": s.status,
+               "codes_per_element_field": round(s.code_total / (N_FIELDS * E), 3)}
         del b
         return res
 
     return {"by_tau_fp64": {f"{t:g}": timed(t, semr.SEMR_FP64) for t in (1e-2, 1e-3, 1e-4)},
-            "precision_form_fp32": {f"{t:g}": timed(t, semr.SEMR_FP32) for t in (1e-3, 1e-5)}}
+            "precision_form_fp32": {f"{t:g}": timed(t, semr.SEMR_FP32) for t in (1e-3, 1e-5)},
+            "cumulative_energy": {"fp64 tau=1e-3": timed(1e-3, semr.SEMR_FP64, cumulative=True),
+                                  "fp32 tau=1e-3": timed(1e-3, semr.SEMR_FP32, cumulative=True)}}
 
 
 def run_batched(dev, precision, reps=5, tau=1e-3):

@@ -74,6 +74,10 @@ struct FCfg {
 // Coefficients per tile whose decisions are recomputed exactly in one round.
 constexpr int AMB_CAP = 64;
 
+// Sparse reconstruction from the kept-mode list while no element of the tile
+// keeps more modes than this; the dense folded inverse otherwise.
+__host__ __device__ constexpr int sparse_max(int mode) { return (mode & 1) ? 12 : 5; }
+
 template <int LX, int MODE, int TILE_>
 struct FSmem {
     using C = FCfg<LX, TILE_>;
@@ -81,10 +85,14 @@ struct FSmem {
     static constexpr size_t buf_bytes = vb * C::TILE * C::BUFN;
     static constexpr size_t off_t1 = 0;
     static constexpr size_t off_t2 = off_t1 + buf_bytes;
-    static constexpr size_t off_codes = off_t2 + buf_bytes;               // staging, 8 B max per code
-    static constexpr size_t off_kc = off_codes + 8ull * C::TILE * C::N3;  // kept codes (f32)
-    static constexpr size_t off_km = off_kc + 4ull * C::TILE * C::N3;     // kept modes (u16)
-    static constexpr size_t off_red = (off_km + 2ull * C::TILE * C::N3 + 15) / 16 * 16;  // BLOCK x 16 B
+    // code staging: 8 B per code for lossless FP32 codes and the cumulative keys,
+    // 4 B in FP64 threshold mode (its lossless form runs on the hardware-FP64 kernel)
+    static constexpr size_t code_b = (MODE == 1) ? 4 : 8;
+    static constexpr int KL = sparse_max(MODE) < C::N3 ? sparse_max(MODE) : C::N3;  // kept-list entries per element
+    static constexpr size_t off_codes = off_t2 + buf_bytes;
+    static constexpr size_t off_kc = off_codes + code_b * C::TILE * C::N3;  // kept codes (f32)
+    static constexpr size_t off_km = off_kc + 4ull * C::TILE * KL;          // kept modes (u16)
+    static constexpr size_t off_red = (off_km + 2ull * C::TILE * KL + 15) / 16 * 16;  // BLOCK x 16 B
     static constexpr size_t off_elem = off_red + 16ull * C::BLOCK;         // TILE x 8 doubles
     static constexpr size_t off_phi = off_elem + 64ull * C::TILE;          // 4 tables x LX x PT floats
     static constexpr size_t off_amat = off_phi + 16ull * LX * C::PT;       // 2 tables x LX x PT floats
@@ -198,7 +206,8 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
     constexpr bool DIRECT = S::CUM_DIRECT;  // cumulative: one warp holds all keys of an element
     using V = typename std::conditional<DF, float2, float>::type;  // one transposed value
     // dense inverse once any element of the tile keeps more modes than this
-    constexpr int SPARSE_MAX = DF ? 12 : 5;
+    constexpr int SPARSE_MAX = sparse_max(MODE);
+    constexpr int KL = S::KL;
 
     extern __shared__ __align__(16) uint8_t smem[];
     V* t1 = reinterpret_cast<V*>(smem + S::off_t1);
@@ -217,7 +226,7 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
     int* s_amb = reinterpret_cast<int*>(smem + S::off_amb);          // [AMB_CAP]: (element << 16) | mode
     float* s_ambv = reinterpret_cast<float*>(s_amb + AMB_CAP);       // [2 * AMB_CAP]: exact values
     int* s_namb = reinterpret_cast<int*>(s_ambv + 2 * AMB_CAP);      // [1 + TILE]: count, per-element flags
-    float2* sWq = reinterpret_cast<float2*>(smem + S::off_wq);        // [NP][LX] weight products (pairs)
+    float2* sWq = reinterpret_cast<float2*>(smem + S::off_wq);        // [LX][NP] weight products (pairs)
     float* t1f = reinterpret_cast<float*>(smem + S::off_t1);         // FP32 views of the transpose buffers
     float* t2f = reinterpret_cast<float*>(smem + S::off_t2);
     uint32_t* smask = reinterpret_cast<uint32_t*>(smem + S::off_mask);
@@ -276,7 +285,7 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
         for (int i = 0; i < LX; ++i) {
             if constexpr (DF) {
                 const f2 w3 = df_mul({tab.wh[i], tab.wl[i]}, wjk);
-                if (in_tile && lt == 0) sWq[P * LX + i] = make_float2(w3.h, w3.l);
+                if (in_tile && lt == 0) sWq[i * NP + P] = make_float2(w3.h, w3.l);
                 wq32[i] = 0.0f;
             } else {
                 wq32[i] = tab.wh[i] * wjk.h;
@@ -455,7 +464,7 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
             for (int i = 0; i < LX; ++i) {
                 const float ph = uh[i] * uh[i];
                 const float pl = fmaf(2.0f * uh[i], ul[i], fmaf(uh[i], uh[i], -ph));
-                const float2 w = sWq[P * LX + i];
+                const float2 w = sWq[i * NP + P];
                 df_fma_acc(sp, {w.x, w.y}, {ph, pl});
             }
             sp = df_norm(sp);
@@ -793,7 +802,8 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
                 const int m = P + NP * r;
                 const int rank = (int)swpre[lt * MW + (m >> 5)] +
                                  __popc(smask[lt * MW + (m >> 5)] & ((1u << (m & 31)) - 1u));
-                reinterpret_cast<double*>(scodes)[s_epre[lt] + rank] = (double)ah[r] + (double)al[r];
+                if constexpr (S::code_b == 8)  // the launcher sends lossless work only to kernels with 8-B staging
+                    reinterpret_cast<double*>(scodes)[s_epre[lt] + rank] = (double)ah[r] + (double)al[r];
             }
         }
     } else {
@@ -823,8 +833,10 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
                 const int pos = s_epre[lt] + rank;
                 if (width == 2) reinterpret_cast<int16_t*>(scodes)[pos] = (int16_t)(int)c;
                 else reinterpret_cast<int32_t*>(scodes)[pos] = (int32_t)c;
-                skm[lt * N3 + rank] = (uint16_t)m;
-                skc[lt * N3 + rank] = c;
+                if (rank < KL) {  // only read while every element keeps at most SPARSE_MAX <= KL modes
+                    skm[lt * KL + rank] = (uint16_t)m;
+                    skc[lt * KL + rank] = c;
+                }
             }
         }
     }
@@ -842,8 +854,8 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
             const int nk = s_cnt[lt];
             const int rowj = pb * PT, rowk = pa * PT;
             for (int t = 0; t < nk; ++t) {
-                const int m = skm[lt * N3 + t];
-                const float cs = (skc[lt * N3 + t] * qu1) * qu2;  // c 2^s, exact
+                const int m = skm[lt * KL + t];
+                const float cs = (skc[lt * KL + t] * qu1) * qu2;  // c 2^s, exact
                 const int pp = m % LX, qq = (m / LX) % LX, rr = m / NP;
                 float ch_[LX], cl_[LX];  // column p of Phi: Phi[i][pp], i = 0..LX-1
                 if constexpr (LX % 4 == 0) {
@@ -964,7 +976,7 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
 #pragma unroll
             for (int i = 0; i < LX; ++i) {
                 const f2 d = df_sub({uh[i], ul[i]}, {vh[i], vl[i]});
-                const float2 w = sWq[P * LX + i];
+                const float2 w = sWq[i * NP + P];
                 df_fma_acc(e2p, df_mul({w.x, w.y}, d), d);
                 const f2 ad = df_abs(d);
                 if (df_ge(ad, dmax)) dmax = ad;
@@ -1020,8 +1032,10 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
         if (gbyte + nbytes <= p.payload_cap) {
             uint8_t* dst = p.payload + gbyte;
             if (width == 8) {
-                const double* sc = reinterpret_cast<const double*>(scodes);
-                for (uint64_t i = tid; i < ncodes; i += C::BLOCK) reinterpret_cast<double*>(dst)[i] = sc[i];
+                if constexpr (S::code_b == 8) {
+                    const double* sc = reinterpret_cast<const double*>(scodes);
+                    for (uint64_t i = tid; i < ncodes; i += C::BLOCK) reinterpret_cast<double*>(dst)[i] = sc[i];
+                }
             } else if (width == 4) {
                 const int32_t* sc = reinterpret_cast<const int32_t*>(scodes);
                 for (uint64_t i = tid; i < ncodes; i += C::BLOCK) reinterpret_cast<int32_t*>(dst)[i] = sc[i];
@@ -1198,6 +1212,8 @@ int tile_variants(int lx, int* out, int cap) {
 }
 
 int launch_reduce_fast(const LaunchParams& p, int lx, void* stream) {
+    // lossless FP64 (8-byte raw coefficients) belongs to the hardware-FP64 kernel
+    if (p.lossless && p.precision != SEMR_FP32) return (int)cudaErrorInvalidValue;
     if (p.cumulative)
         return p.precision == SEMR_FP32 ? single_mode<MODE_F32 | MODE_CUM>(p, lx, stream)
                                         : single_mode<MODE_DF64 | MODE_CUM>(p, lx, stream);
@@ -1205,6 +1221,7 @@ int launch_reduce_fast(const LaunchParams& p, int lx, void* stream) {
 }
 
 int launch_reduce_fast_batch(const BatchQueue& q, int lx, int precision, int tile, void* stream) {
+    // items are validated on the host: FP64 lossless items are refused when the batch is created
     return precision == SEMR_FP32 ? batch_mode<MODE_F32>(q, lx, tile, stream)
                                   : batch_mode<MODE_DF64>(q, lx, tile, stream);
 }
