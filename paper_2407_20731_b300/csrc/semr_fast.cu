@@ -92,8 +92,10 @@ struct FSmem {
     static constexpr size_t off_codes = off_t2 + buf_bytes;
     static constexpr size_t off_kc = off_codes + code_b * C::TILE * C::N3;  // kept codes (f32)
     static constexpr size_t off_km = off_kc + 4ull * C::TILE * KL;          // kept modes (u16)
-    static constexpr size_t off_red = (off_km + 2ull * C::TILE * KL + 15) / 16 * 16;  // BLOCK x 16 B
-    static constexpr size_t off_elem = off_red + 16ull * C::BLOCK;         // TILE x 8 doubles
+    // reduction slots: one per (warp, element segment) when elements line up with warps, else one per thread
+    static constexpr int RED_N = C::ALIGNED ? C::NW * (32 / C::SEG) : C::BLOCK;
+    static constexpr size_t off_red = (off_km + 2ull * C::TILE * KL + 15) / 16 * 16;  // RED_N x 16 B
+    static constexpr size_t off_elem = off_red + 16ull * RED_N;            // TILE x 8 doubles
     static constexpr size_t off_phi = off_elem + 64ull * C::TILE;          // 4 tables x LX x PT floats
     static constexpr size_t off_amat = off_phi + 16ull * LX * C::PT;       // 2 tables x LX x PT floats
     static constexpr size_t off_amb = off_amat + 8ull * LX * C::PT;        // AMB_CAP entries + values
@@ -188,7 +190,7 @@ __device__ __forceinline__ void elem_reduce(float* red, double* out, f2 s, unsig
 // the latency of the tile's barrier phases, without spilling the larger orders.
 constexpr int min_ctas_per_sm(int lx, int mode, int block) {
     const int target = (mode & MODE_CUM) ? (!(mode & MODE_DF64) ? 768 : 512)
-                       : !(mode & MODE_DF64) ? (lx <= 10 ? 1024 : 768) : (lx <= 8 ? 768 : 512);
+                       : !(mode & MODE_DF64) ? (lx <= 10 ? 1024 : 768) : (lx <= 8 ? 1024 : 512);
     return target / block > 0 ? target / block : 1;
 }
 
