@@ -473,3 +473,102 @@ def test_cumulative_near_tie_flagged():
         assert m[e, big]
         assert m[e, small] == (c[e, 5] ** 2 == c[e, 9] ** 2)
     assert m[2, 9] and not m[2, 5]
+
+
+# --------------------------------------------------- slice image (Sec. IV-A)
+
+import oracle.slice as oslice  # noqa: E402
+
+
+@pytest.mark.parametrize("lx", [2, 5, 8, 12])
+def test_slice_basis_partition_kronecker_polynomials(lx):
+    nodes, _ = oracle.gll(lx)
+    x = np.linspace(-1.0, 1.0, 37)
+    L = oslice.lagrange(nodes, x)
+    np.testing.assert_allclose(L.sum(axis=1), 1.0, atol=1e-13)         # partition of unity
+    np.testing.assert_allclose(oslice.lagrange(nodes, nodes), np.eye(lx), atol=1e-14)  # Kronecker
+    for d in range(lx):                                                 # degree <= N reproduced
+        np.testing.assert_allclose(L @ nodes ** d, x ** d, atol=1e-12)
+
+
+def _poly_mesh(lx, n, mo, h, seed):
+    """Nodal values of a polynomial of per-axis degree lx - 1 on a lattice,
+    and the closed form."""
+    rng = np.random.default_rng(seed)
+    cx, cy, cz = (rng.normal(size=lx) for _ in range(3))
+    f = lambda X, Y, Z: (np.polyval(cx, X / 3.0) * np.polyval(cy, Y / 3.0) + np.polyval(cz, Z / 3.0))  # noqa: E731
+    nodes, _ = oracle.gll(lx)
+    ex, ey, ez = np.meshgrid(np.arange(n[0]), np.arange(n[1]), np.arange(n[2]), indexing="ij")
+    # element e = ex + nx (ey + ny ez); block [k][j][i]
+    E = n[0] * n[1] * n[2]
+    u = np.zeros((E, lx, lx, lx))
+    for e in range(E):
+        ix, iy, iz = e % n[0], (e // n[0]) % n[1], e // (n[0] * n[1])
+        X = mo[0] + h[0] * (ix + 0.5 * (nodes + 1.0))
+        Y = mo[1] + h[1] * (iy + 0.5 * (nodes + 1.0))
+        Z = mo[2] + h[2] * (iz + 0.5 * (nodes + 1.0))
+        u[e] = f(X[None, None, :], Y[None, :, None], Z[:, None, None])
+    return u, f
+
+
+@pytest.mark.parametrize("lx", [3, 6, 8])
+def test_slice_reproduces_polynomials(lx):
+    n, mo, h = (3, 4, 2), (-1.0, 0.5, 2.0), (0.7, 0.45, 1.3)
+    u, f = _poly_mesh(lx, n, mo, h, seed=lx)
+    # an oblique plane through the box, image rectangle inside the box
+    origin = np.array([-0.9, 0.6, 2.1])
+    U = np.array([1.9, 0.3, 0.4])
+    V = np.array([0.1, 1.3, 2.0])
+    rgba, s, y = oslice.slice_rgba(u[None], lx, n, mo, h, origin, U, V, 23, 17, -3.0, 3.0,
+                                   [[0, 0, 0, 1], [1, 1, 0, 0]])
+    p = oslice.pixel_points(origin, U, V, 23, 17)
+    assert np.all(np.isfinite(s))
+    np.testing.assert_allclose(s, f(p[..., 0], p[..., 1], p[..., 2]), rtol=1e-11, atol=1e-11)
+
+
+def test_slice_location_faces_and_outside():
+    n, mo, h = (2, 2, 2), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0)
+    pts = np.array([[1.0, 0.25, 0.25],    # shared face x = 1 belongs to the upper element, xi = -1
+                    [2.0, 2.0, 2.0],      # top corner belongs to the last element, xi = +1
+                    [0.0, 0.0, 0.0],      # lower corner, xi = -1
+                    [-1e-12, 0.5, 0.5],   # just outside
+                    [0.5, 2.0 + 1e-12, 0.5]])
+    e, xi, inside = oslice.locate(pts, n, mo, h)
+    assert list(inside) == [True, True, True, False, False]
+    assert e[0] == 1 and xi[0, 0] == -1.0 and xi[0, 1] == -0.5
+    assert e[1] == 7 and np.all(xi[1] == 1.0)
+    assert e[2] == 0 and np.all(xi[2] == -1.0)
+
+
+def test_slice_colour_table_and_background():
+    ctrl = [[0.0, 0.2, 0.3, 0.8], [0.5, 0.902, 0.902, 0.902], [1.0, 0.7, 0.0, 0.1]]  # 255 c off the .5 ties
+    s = np.array([-5.0, 0.0, 0.25, 0.5, 0.75, 1.0, 7.0])
+    y = oslice.colour_channels(s, 0.0, 1.0, ctrl)
+    c = np.asarray(ctrl)[:, 1:]
+    np.testing.assert_allclose(y[0] / 255, c[0])            # clamped below
+    np.testing.assert_allclose(y[1] / 255, c[0])
+    np.testing.assert_allclose(y[2] / 255, (c[0] + c[1]) / 2)  # midpoint of segment 0
+    np.testing.assert_allclose(y[3] / 255, c[1])            # at a control point
+    np.testing.assert_allclose(y[4] / 255, (c[1] + c[2]) / 2)
+    np.testing.assert_allclose(y[5] / 255, c[2])
+    np.testing.assert_allclose(y[6] / 255, c[2])            # clamped above
+    # a plane partly outside the mesh: background there, opaque inside
+    u = np.ones((1, 8, 4, 4, 4))
+    rgba, s2, _ = oslice.slice_rgba(u, 4, (2, 2, 2), (0, 0, 0), (1, 1, 1), (-1, 0.5, 0.5), (4, 0, 0),
+                                    (0, 1, 0), 8, 2, 0.0, 2.0, ctrl, background=(1, 2, 3, 4))
+    assert np.all(rgba[:, :2] == [1, 2, 3, 4]) and np.all(rgba[:, 6:] == [1, 2, 3, 4])
+    assert np.all(rgba[:, 2:6, 3] == 255) and np.allclose(s2[:, 2:6], 1.0)
+    assert np.all(rgba[:, 2:6, :3] == np.floor(255 * np.asarray(ctrl[1][1:]) + 0.5))
+
+
+def test_slice_magnitude():
+    lx, n, mo, h = 4, (2, 1, 1), (0, 0, 0), (1, 1, 1)
+    rng = np.random.default_rng(3)
+    u = rng.normal(size=(3, 2, lx, lx, lx))
+    pts = np.array([[0.3, 0.2, 0.9], [1.7, 0.5, 0.1]])
+    e, xi, inside = oslice.locate(pts, n, mo, h)
+    v = oslice.interpolate(u, lx, e, xi)
+    np.testing.assert_allclose(oslice.scalar(v), np.sqrt(v[0] ** 2 + v[1] ** 2 + v[2] ** 2))
+    # each component separately equals the one-component interpolation
+    for c in range(3):
+        np.testing.assert_array_equal(oslice.interpolate(u[c:c + 1], lx, e, xi)[0], v[c])
