@@ -379,6 +379,71 @@ int semr_server_stats(semr_server* s, uint64_t* admitted, uint64_t* completed, u
 /* Stop the dispatcher, wait for running requests, free everything. */
 void semr_server_destroy(semr_server* s);
 
+/* ------------------------------------------------- in-situ slice image
+ *
+ * The other in-situ task of arXiv 2407.20731 (Sec. IV-A): an image of a
+ * slice through the fields, rendered while the simulation runs (there by
+ * ParaView/Catalyst on the host, with a pipeline that fixes the camera, the
+ * image size and the slice position).  Here one call renders the slice into
+ * a headless RGBA8 device buffer:
+ *   1. pixel (column c, row r) of a W x H image sits at the world point
+ *        p = (origin + ((c + 0.5)/W) axis_u) + ((r + 0.5)/H) axis_v
+ *      (row 0 nearest origin along axis_v, each operation rounded once);
+ *   2. per axis q = (p - mesh.origin) / mesh.h, element index floor(q) (the
+ *      top face q == n belongs to the last element), reference coordinate
+ *      2 (q - floor(q)) - 1; points outside the lattice get `background`;
+ *   3. the value is the element's tensor-product Lagrange interpolant
+ *      through its lx^3 GLL nodal values (the spectral-element field itself),
+ *      or with n_comp = 2 or 3 the magnitude of the interpolated vector;
+ *   4. t = clamp((s - vmin)/(vmax - vmin), 0, 1), each colour channel
+ *      linear in t between the control points (t_k, r_k, g_k, b_k) of the
+ *      segment that holds t, byte = floor(255 c + 0.5), alpha 255.
+ * Steps 1-2 run in FP64 (they decide which element owns a pixel); steps 3-4
+ * in FP32 (ample for 8-bit colour): a channel may differ by one from an FP64
+ * evaluation only where 255 c lies within the FP32 error of a rounding tie.
+ * A slice whose axis_u and axis_v each lie along one (different) lattice
+ * axis is rendered one element per thread block (the element is contracted
+ * along the slice normal once, then each pixel costs lx^2 + lx FMAs per
+ * component); any other plane takes the per-pixel lx^3 path.
+ */
+typedef struct {
+    int32_t lx;            /* GLL points per direction, SEMR_LX_MIN..SEMR_LX_MAX */
+    int32_t nx, ny, nz;    /* element lattice, >= 1 each; element e = ex + nx*(ey + ny*ez), nx*ny*nz < 2^31 */
+    double origin[3];      /* lower corner of the box */
+    double h[3];           /* element edge lengths, > 0 (affine, axis-aligned hexahedra) */
+} semr_lattice;
+
+#define SEMR_SLICE_MAX_CTRL 16
+#define SEMR_SLICE_MAX_COMP 3
+#define SEMR_SLICE_MAX_SIDE 16384
+
+typedef struct {
+    double origin[3];      /* world point of the image corner (pixel (0,0) is half a pixel inside) */
+    double axis_u[3];      /* world vector along the image width (columns) */
+    double axis_v[3];      /* world vector along the image height (rows) */
+    int32_t width, height; /* pixels, 1..SEMR_SLICE_MAX_SIDE each */
+    int32_t n_comp;        /* 1: colour by fields[0]; 2-3: by the magnitude of (fields[0], ...) */
+    int32_t n_ctrl;        /* colour-table control points, 2..SEMR_SLICE_MAX_CTRL */
+    double vmin, vmax;     /* scalar range mapped to t in [0, 1], vmax > vmin, finite */
+    double ctrl[SEMR_SLICE_MAX_CTRL][4];  /* (t, r, g, b): t_0 = 0 < t_1 < ... < t_{n-1} = 1, r, g, b in [0, 1] */
+    uint32_t background;   /* RGBA8 of pixels outside the mesh, R in the low byte */
+    int32_t pad_;
+} semr_slice;
+
+/* Render one slice image, stream ordered on cuda_stream; allocates nothing.
+ *   fields  host array of n_comp device pointers, each lattice n_elem*lx^3
+ *           FP64 values in the layout of semr_fieldset (16-byte aligned for
+ *           even lx, 8-byte for odd)
+ *   rgba    device, width*height*4 bytes: pixel (c, r) at 4 (r width + c),
+ *           bytes R, G, B, A
+ *   values  device, width*height floats, the coloured scalar (NaN outside
+ *           the mesh), or NULL
+ * Errors: SEMR_EINVAL (null pointer, sizes, non-finite or non-positive
+ * geometry, colour table not as above, vmax <= vmin), SEMR_EUNSUPPORTED (lx),
+ * SEMR_ECUDA (launch).  Inputs are read only; caller owns every buffer. */
+int semr_slice_rgba(const semr_lattice* mesh, const double* const* fields, const semr_slice* sl,
+                    uint8_t* rgba, float* values, void* cuda_stream);
+
 /* semr_strerror: static text for a status code. */
 const char* semr_strerror(int code);
 

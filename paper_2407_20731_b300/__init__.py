@@ -81,6 +81,22 @@ class semr_request_info(ctypes.Structure):
                 ("slot", ctypes.c_int32), ("status", ctypes.c_int32), ("device_bytes", ctypes.c_uint64),
                 ("summary", semr_summary)]
 
+class semr_lattice(ctypes.Structure):
+    _fields_ = [("lx", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("origin", ctypes.c_double * 3), ("h", ctypes.c_double * 3)]
+
+
+SEMR_SLICE_MAX_CTRL, SEMR_SLICE_MAX_COMP, SEMR_SLICE_MAX_SIDE = 16, 3, 16384
+
+
+class semr_slice(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_double * 3), ("axis_u", ctypes.c_double * 3), ("axis_v", ctypes.c_double * 3),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("n_comp", ctypes.c_int32),
+                ("n_ctrl", ctypes.c_int32), ("vmin", ctypes.c_double), ("vmax", ctypes.c_double),
+                ("ctrl", (ctypes.c_double * 4) * SEMR_SLICE_MAX_CTRL), ("background", ctypes.c_uint32),
+                ("pad_", ctypes.c_int32)]
+
+
 # (name, restype, argtypes) of every exported entry point
 _P = ctypes.c_void_p
 EXPORTS = [
@@ -122,6 +138,8 @@ EXPORTS = [
     ("semr_server_destroy", None, [_P]),
     ("semr_reduce_async_noalloc", ctypes.c_int, [ctypes.POINTER(semr_fieldset), ctypes.POINTER(semr_mesh), _P,
                                                  ctypes.c_uint64, _P, _P, _P]),
+    ("semr_slice_rgba", ctypes.c_int, [ctypes.POINTER(semr_lattice), ctypes.POINTER(_P), ctypes.POINTER(semr_slice),
+                                       _P, _P, _P]),
 ]
 SEMR_NOALLOC_SCRATCH_BYTES = 16 << 20
 
@@ -467,3 +485,69 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------ slice image
+
+# A diverging blue - grey - red colour table (t, r, g, b).
+COOL_WARM = [(0.0, 0.23, 0.30, 0.75), (0.5, 0.87, 0.87, 0.87), (1.0, 0.71, 0.02, 0.15)]
+
+
+def make_lattice(lx: int, n, origin=(0.0, 0.0, 0.0), h=None) -> semr_lattice:
+    """Lattice of n = (nx, ny, nz) affine elements; h defaults to the
+    [0, 2 pi)^3 box of the synthetic snapshots."""
+    m = semr_lattice()
+    m.lx = lx
+    m.nx, m.ny, m.nz = (int(v) for v in n)
+    if h is None:
+        h = tuple(2.0 * np.pi / int(v) for v in n)
+    for d in range(3):
+        m.origin[d] = float(origin[d])
+        m.h[d] = float(h[d])
+    return m
+
+
+def make_slice(origin, axis_u, axis_v, width: int, height: int, vmin: float, vmax: float, n_comp: int = 1,
+               ctrl=COOL_WARM, background: int = 0) -> semr_slice:
+    s = semr_slice()
+    for d in range(3):
+        s.origin[d], s.axis_u[d], s.axis_v[d] = float(origin[d]), float(axis_u[d]), float(axis_v[d])
+    s.width, s.height, s.n_comp = int(width), int(height), int(n_comp)
+    s.vmin, s.vmax = float(vmin), float(vmax)
+    s.n_ctrl = len(ctrl)
+    for k, row in enumerate(ctrl):
+        for c in range(4):
+            s.ctrl[k][c] = float(row[c])
+    s.background = int(background)
+    return s
+
+
+def semr_slice_rgba(mesh: semr_lattice, field_ptrs, sl: semr_slice, rgba: int, values: int | None,
+                    stream: int) -> int:
+    arr = (_P * SEMR_SLICE_MAX_COMP)(*[int(p) for p in field_ptrs])
+    return _lib.semr_slice_rgba(ctypes.byref(mesh), arr, ctypes.byref(sl), rgba, values, stream)
+
+
+def slice_rgba(fields, mesh: semr_lattice, sl: semr_slice, rgba=None, values=None, stream=None):
+    """Render one slice image into device buffers (torch tensors): returns
+    (rgba [H, W, 4] uint8, values [H, W] float32 or None).  ``fields``: the
+    n_comp CUDA FP64 tensors (n_elem * lx^3 each)."""
+    import torch
+    for t in fields:
+        _require_cuda_f64(t)
+    dev = fields[0].device
+    if rgba is None:
+        rgba = torch.empty((sl.height, sl.width, 4), dtype=torch.uint8, device=dev)
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(semr_slice_rgba(mesh, [t.data_ptr() for t in fields], sl, rgba.data_ptr(),
+                           values.data_ptr() if values is not None else None, st), "semr_slice_rgba")
+    return rgba, values
+
+
+def write_ppm(path: str, rgba: np.ndarray) -> None:
+    """Write an [H, W, 4] RGBA image as a binary PPM (RGB), row 0 of the
+    array at the bottom (the rows run along axis_v, away from the origin)."""
+    img = np.ascontiguousarray(np.asarray(rgba)[::-1, :, :3])
+    with open(path, "wb") as f:
+        f.write(b"P6\n%d %d\n255\n" % (img.shape[1], img.shape[0]))
+        f.write(img.tobytes())

@@ -91,3 +91,36 @@ def test_host_decoder_rejects_malformed():
         semr.semr_decode(bad)
     with pytest.raises(semr.SemrError):
         semr.semr_decode(r.payload[:-2])  # truncated code section
+
+
+def test_slice_argument_validation_needs_no_gpu():
+    """Every case below is invalid, so the call returns before any CUDA work."""
+    good_mesh = semr.make_lattice(8, (4, 4, 4))
+    ok = dict(origin=(0, 0, 1), axis_u=(6, 0, 0), axis_v=(0, 6, 0), width=16, height=16, vmin=0.0, vmax=1.0,
+              n_comp=1)
+    fake = [256, 256, 256]
+
+    def call(mesh=good_mesh, rgba=4096, fields=fake, **kw):
+        a = dict(ok)
+        a.update(kw)
+        sl = semr.make_slice(a["origin"], a["axis_u"], a["axis_v"], a["width"], a["height"], a["vmin"], a["vmax"],
+                             a["n_comp"], a.get("ctrl", semr.COOL_WARM))
+        return semr.semr_slice_rgba(mesh, fields, sl, rgba, None, 0)
+
+    assert call(rgba=0) == semr.SEMR_EINVAL
+    assert call(mesh=semr.make_lattice(13, (4, 4, 4))) == semr.SEMR_EUNSUPPORTED
+    assert call(mesh=semr.make_lattice(8, (0, 4, 4), h=(1.0, 1.0, 1.0))) == semr.SEMR_EINVAL
+    assert call(mesh=semr.make_lattice(8, (4, 4, 4), h=(1.0, -1.0, 1.0))) == semr.SEMR_EINVAL
+    assert call(width=0) == semr.SEMR_EINVAL
+    assert call(height=semr.SEMR_SLICE_MAX_SIDE + 1) == semr.SEMR_EINVAL
+    assert call(n_comp=4) == semr.SEMR_EINVAL
+    assert call(vmax=0.0) == semr.SEMR_EINVAL
+    assert call(vmin=float("nan")) == semr.SEMR_EINVAL
+    assert call(origin=(0, float("inf"), 0)) == semr.SEMR_EINVAL
+    assert call(ctrl=[(0.0, 0, 0, 0)]) == semr.SEMR_EINVAL                          # one control point
+    assert call(ctrl=[(0.0, 0, 0, 0), (0.9, 1, 1, 1)]) == semr.SEMR_EINVAL          # does not end at 1
+    assert call(ctrl=[(0.0, 0, 0, 0), (0.6, 1, 1, 1), (0.5, 1, 1, 1), (1, 0, 0, 0)]) == semr.SEMR_EINVAL
+    assert call(ctrl=[(0.0, 0, 0, 0), (1.0, 1.5, 1, 1)]) == semr.SEMR_EINVAL         # channel above 1
+    assert call(rgba=4098) == semr.SEMR_EINVAL                                       # unaligned output
+    assert call(fields=[264, 256, 256]) == semr.SEMR_EINVAL                          # unaligned field (even lx)
+    assert call(fields=[0, 0, 0]) == semr.SEMR_EINVAL
