@@ -61,6 +61,9 @@ def parse_args():
     ap.add_argument("--serving-requests", type=int, default=800, help="requests per serving run in the extras")
     ap.add_argument("--serving-only", action="store_true", help="print only the serving report (JSON)")
     ap.add_argument("--batched-only", action="store_true", help="print only the batched report (JSON)")
+    ap.add_argument("--cumulative", action="store_true", help="cumulative-energy truncation on the device leg")
+    ap.add_argument("--slice-only", action="store_true", help="print only the slice-image report (JSON)")
+    ap.add_argument("--slice-size", type=int, default=2048, help="slice image width and height (pixels)")
     return ap.parse_args()
 
 
@@ -81,10 +84,11 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6400.0, "source": "fallback"}
 
 
-def profiled_traffic(precision: str):
+def profiled_traffic(precision: str, cumulative: bool = False):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", f"reduce_fast_kernel_{precision}_lx8_64cube.md")
+    name = f"reduce_fast_kernel_{precision}{'_cumulative' if cumulative else ''}_lx8_64cube.md"
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     text = open(path).read()
@@ -235,7 +239,8 @@ def make_snapshot(rank, device):
 
 def workload_config(args, world):
     return {"workload": f"SEM snapshot reduction: {N_SIDE}^3 = {N_SIDE ** 3} hex elements, lx={LX}, "
-                        f"{N_FIELDS} FP64 fields (u,v,w,p), tau={args.tau:g}, {args.precision} transforms",
+                        f"{N_FIELDS} FP64 fields (u,v,w,p), tau={args.tau:g}, {args.precision} transforms"
+                        + (", cumulative-energy truncation" if args.cumulative else ""),
             "n_elem": N_SIDE ** 3, "lx": LX, "n_fields": N_FIELDS, "tau": args.tau,
             "precision": args.precision, "snapshot_bytes": N_FIELDS * N_SIDE ** 3 * LX ** 3 * 8,
             "l2": L2_NOTE, "parallelism": f"replicas x{world} (one independent snapshot per GPU)"}
@@ -260,7 +265,7 @@ def run_semr(args):
     snapshot_bytes = N_FIELDS * E * LX ** 3 * 8
 
     def step(events=None):
-        semr.reduce_async(flist, jac, LX, args.tau, bufs, prec, events=events)
+        semr.reduce_async(flist, jac, LX, args.tau, bufs, prec, events=events, cumulative=args.cumulative)
 
     for _ in range(args.warmup):
         step()
@@ -289,11 +294,12 @@ def run_semr(args):
     algo = algorithmic_bytes(E, N_FIELDS, sm.code_total, int(bufs.sizes.code_width))
     peaks = measured_peaks()
     achieved = algo / (kernel_ms * 1e-3) / 1e9
-    traffic = profiled_traffic(args.precision)
+    traffic = profiled_traffic(args.precision, args.cumulative)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "peak_source": f"{peaks['source']} (MEASURED_PEAKS hbm_gbs, copy)",
-                "kernel": f"reduce_fast_kernel<{LX}, {'float pairs (FP64 accuracy)' if prec == semr.SEMR_FP64 else 'FP32'}>",
+                "kernel": f"reduce_fast_kernel<{LX}, {'float pairs (FP64 accuracy)' if prec == semr.SEMR_FP64 else 'FP32'}"
+                          + (", cumulative" if args.cumulative else "") + ">",
                 "kernel_ms": round(kernel_ms, 4), "algorithmic_bytes_per_launch": algo}
     flops = algorithmic_flops(E, N_FIELDS)
     roofline["alu"] = {"algorithmic_flops_per_launch": flops,
@@ -333,7 +339,7 @@ def run_e2e(args, world, dev, fields, jac, bufs, prec, stream, snapshot_bytes):
     dev_j = torch.empty_like(jac)
     host_payload = torch.empty(int(bufs.sizes.payload_worst), dtype=torch.uint8, pin_memory=True).numpy()
     handle = semr.semr_open(dev.index, stream.cuda_stream, 0)
-    fs = semr.make_fieldset([dev_f[i] for i in range(N_FIELDS)], args.tau, prec)
+    fs = semr.make_fieldset([dev_f[i] for i in range(N_FIELDS)], args.tau, prec, cumulative=args.cumulative)
     mesh = semr.make_mesh(LX, dev_j)
     pbytes = 0
 
@@ -392,10 +398,37 @@ def run_extras(dev, flist, jac, E, snapshot_bytes, peaks):
         del b
         return res
 
-    return {"by_tau_fp64": {f"{t:g}": timed(t, semr.SEMR_FP64) for t in (1e-2, 1e-3, 1e-4)},
+    return {"slice_image": slice_report(dev, flist[:3], peaks),
+            "by_tau_fp64": {f"{t:g}": timed(t, semr.SEMR_FP64) for t in (1e-2, 1e-3, 1e-4)},
             "precision_form_fp32": {f"{t:g}": timed(t, semr.SEMR_FP32) for t in (1e-3, 1e-5)},
             "cumulative_energy": {"fp64 tau=1e-3": timed(1e-3, semr.SEMR_FP64, cumulative=True),
                                   "fp32 tau=1e-3": timed(1e-3, semr.SEMR_FP32, cumulative=True)}}
+
+
+def slice_report(dev, uvw, peaks, W=2048, H=2048, z0=2.0, n=20):
+    """In-situ slice image of the snapshot (Sec. IV-A): |(u, v, w)| on the
+    plane z = z0 over the whole x-y extent, cool-warm colours, RGBA8."""
+    import torch
+
+    import paper_2407_20731_b300 as semr
+    T = 2.0 * math.pi
+    mesh = semr.make_lattice(LX, (N_SIDE, N_SIDE, N_SIDE))
+    sl = semr.make_slice((0.0, 0.0, z0), (T, 0, 0), (0, T, 0), W, H, 0.0, 3.0, 3)
+    rgba = torch.empty((H, W, 4), dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        semr.slice_rgba(uvw, mesh, sl, rgba=rgba)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(n):
+        semr.slice_rgba(uvw, mesh, sl, rgba=rgba)
+    e1.record()
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) / n * 1e3
+    algo = 3 * N_SIDE * N_SIDE * LX ** 3 * 8 + W * H * 4  # the sliced layer of u, v, w read, the image written
+    return {"workload": f"|(u,v,w)| on z = {z0}, {W}x{H} RGBA8, {N_SIDE}^2 elements of the layer, lx={LX}",
+            "us_per_image": round(us, 2), "gpixel_per_s": round(W * H / us / 1e3, 2), "algorithmic_bytes": algo,
+            "achieved_GB_s": round(algo / us / 1e3, 1), "hbm_frac": round(algo / us / 1e3 / peaks["hbm_gbs"], 4),
+            "kernel": f"slice_axis_kernel<{LX}>", "launches_per_image": 1}
 
 
 def run_batched(dev, precision, reps=5, tau=1e-3):
@@ -630,6 +663,16 @@ def main():
         torch.cuda.set_device(0)
         prec = 0 if args.precision == "fp64" else 1
         print(json.dumps({"batched": run_batched(torch.device("cuda", 0), prec)}), flush=True)
+        return
+    if args.slice_only:
+        import torch
+        torch.cuda.set_device(0)
+        import synth
+        f, _ = synth.snapshot(N_SIDE ** 3, LX, SEEDS[:3], device="cuda")
+        f = f.reshape(3, N_SIDE ** 3, LX ** 3).contiguous()
+        rep = slice_report(torch.device("cuda", 0), [f[i] for i in range(3)], measured_peaks(),
+                           W=args.slice_size, H=args.slice_size)
+        print(json.dumps({"slice_image": rep}), flush=True)
         return
     if args.serving_only:
         import torch
