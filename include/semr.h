@@ -157,7 +157,7 @@ typedef struct {
     uint64_t scratch_bytes;      /* device scratch for semr_reduce_async */
     uint64_t elem_report_bytes;  /* n_fields * n_elem * 3 doubles */
     uint32_t code_width;         /* 2, 4 or 8 bytes */
-    uint32_t tiles;              /* work tiles of the fused kernel */
+    uint32_t tiles;              /* work tiles of the CTA-per-tile kernels (saturates at 2^32-1) */
 } semr_sizes;
 
 /* Device buffers of one reduction (all caller-owned device memory). */
@@ -267,12 +267,14 @@ int semr_gll(int32_t lx, double* nodes, double* weights);
  * The caller still passes the inputs and the outputs (payload of
  * payload_cap bytes, optional elem_report, summary), all device memory, as
  * in semr_outputs.  The kernel's scratch comes from one file-scope device
- * array of SEMR_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU loading the
+ * array of SEMR_NOALLOC_SCRATCH_BYTES (64 MiB) that every GPU loading the
  * library holds until the process exits; nothing is allocated or freed
  * (no cudaMalloc, cudaFree or allocating library routine).  A snapshot
- * whose scratch (semr_sizes.scratch_bytes, 40 bytes per work tile) exceeds
- * that size is rejected with SEMR_EINVAL; at lx = 8 that is about 1.6
- * million element-fields (e.g. 64^3 elements x 6 fields).
+ * whose scratch (semr_sizes.scratch_bytes) exceeds that size is rejected
+ * with SEMR_EINVAL.  At lx = 8 the scratch is about 10 bytes per
+ * element-field (at least 24 MiB once a snapshot has 768 x 32 element-fields),
+ * so snapshots up to about 6.7 million element-fields fit (e.g. 128^3 elements
+ * x 3 fields).
  *
  * The first call on a device looks up the array's device address (with that
  * device current) and caches it: make that first call before any stream
@@ -283,7 +285,7 @@ int semr_gll(int32_t lx, double* nodes, double* weights);
  * order them on one stream.  Errors as semr_reduce_async, plus SEMR_ECUDA if
  * the address lookup fails.
  */
-#define SEMR_NOALLOC_SCRATCH_BYTES (16ull << 20)
+#define SEMR_NOALLOC_SCRATCH_BYTES (64ull << 20)
 int semr_reduce_async_noalloc(const semr_fieldset* fs, const semr_mesh* mesh, uint8_t* payload,
                               uint64_t payload_cap, double* elem_report, semr_summary* summary,
                               void* cuda_stream);

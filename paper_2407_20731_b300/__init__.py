@@ -141,7 +141,7 @@ EXPORTS = [
     ("semr_slice_rgba", ctypes.c_int, [ctypes.POINTER(semr_lattice), ctypes.POINTER(_P), ctypes.POINTER(semr_slice),
                                        _P, _P, _P]),
 ]
-SEMR_NOALLOC_SCRATCH_BYTES = 16 << 20
+SEMR_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libsemr.so is not built ({LIB_PATH}); run __graft_entry__.build() "

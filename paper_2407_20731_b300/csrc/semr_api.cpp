@@ -3,6 +3,7 @@
 // budget, and the host-side payload decoder.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -31,6 +32,13 @@ uint64_t tiles_per_field(int lx, int64_t n_elem) {
     return (uint64_t(n_elem) + t - 1) / t;
 }
 
+// Scratch of one reduction: the CTA kernels' layout, and at lx = 8 also the
+// warp kernel's (whichever of the two runs, the buffer holds it).
+uint64_t scratch_need(int lx, int64_t n_elem, int32_t n_fields) {
+    const uint64_t cta = scratch_bytes(uint64_t(n_fields) * tiles_per_field(lx, n_elem));
+    return lx == 8 ? std::max(cta, warp_scratch_bytes(n_elem, n_fields)) : cta;
+}
+
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 }  // namespace
@@ -45,10 +53,10 @@ extern "C" int semr_sizes_for(int32_t lx, int64_t n_elem, int32_t n_fields, doub
     out->header_bytes = header_bytes(n_fields);
     out->code_base = out->header_bytes + uint64_t(n_fields) * field_fixed_bytes(lx, n_elem);
     out->payload_worst = out->code_base + uint64_t(width) * n3 * uint64_t(n_elem) * n_fields;
-    out->scratch_bytes = scratch_bytes(tiles);
+    out->scratch_bytes = scratch_need(lx, n_elem, n_fields);
     out->elem_report_bytes = 24ull * uint64_t(n_elem) * n_fields;
     out->code_width = (uint32_t)width;
-    out->tiles = (uint32_t)tiles;
+    out->tiles = (uint32_t)std::min<uint64_t>(tiles, 0xffffffffull);
     return SEMR_OK;
 }
 
@@ -93,7 +101,8 @@ extern "C" int semr_reduce_async_timed(const semr_fieldset* fs, const semr_mesh*
     p.payload_cap = out->payload_cap;
     p.elem_report = out->elem_report;
     p.summary = out->summary;
-    split_scratch(p, static_cast<uint8_t*>(out->scratch), sz.tiles);
+    const uint64_t tiles = uint64_t(fs->n_fields) * tiles_per_field(mesh->lx, mesh->n_elem);
+    split_scratch(p, static_cast<uint8_t*>(out->scratch), tiles);
     p.lx = mesh->lx;
     p.tile = tile_elems(mesh->lx);
     p.n_elem = mesh->n_elem;
@@ -108,13 +117,22 @@ extern "C" int semr_reduce_async_timed(const semr_fieldset* fs, const semr_mesh*
     p.header_bytes = sz.header_bytes;
     p.fixed_bytes = field_fixed_bytes(mesh->lx, mesh->n_elem);
     p.code_base = sz.code_base;
+    // lx = 8 threshold truncation runs on the warp-per-element kernel: one look-back unit per element
+    const bool warp = warp_applicable(p);
+    uint64_t zero = scratch_zero_bytes(tiles);
+    if (warp) {
+        split_scratch_warp(p, static_cast<uint8_t*>(out->scratch), mesh->n_elem, fs->n_fields);
+        p.tile = kWarpTile;
+        p.tiles_per_field = (int32_t)((uint64_t(mesh->n_elem) + kWarpTile - 1) / kWarpTile);
+        zero = scratch_zero_bytes(warp_tiles(mesh->n_elem, fs->n_fields));
+    }
 
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    if (cudaMemsetAsync(out->scratch, 0, scratch_zero_bytes(sz.tiles), st) != cudaSuccess) return SEMR_ECUDA;
+    if (cudaMemsetAsync(out->scratch, 0, zero, st) != cudaSuccess) return SEMR_ECUDA;
     if (ev_begin && cudaEventRecord(static_cast<cudaEvent_t>(ev_begin), st) != cudaSuccess) return SEMR_ECUDA;
-    if (launch_reduce(p, mesh->lx, st) != cudaSuccess) return SEMR_ECUDA;
+    if ((warp ? launch_reduce_warp(p, st) : launch_reduce(p, mesh->lx, st)) != cudaSuccess) return SEMR_ECUDA;
     if (ev_end && cudaEventRecord(static_cast<cudaEvent_t>(ev_end), st) != cudaSuccess) return SEMR_ECUDA;
-    if (launch_finalize(p, mesh->lx, st) != cudaSuccess) return SEMR_ECUDA;
+    if ((warp ? launch_finalize_warp(p, st) : launch_finalize(p, mesh->lx, st)) != cudaSuccess) return SEMR_ECUDA;
     return SEMR_OK;
 }
 

@@ -401,4 +401,96 @@ __device__ __forceinline__ void inv1d_df(const float* __restrict__ Ph, const flo
     }
 }
 
+// ------------------------------------------------------ finalize
+
+// Deterministic tree sum of a field's partials part[(f * nper + u) * 4 + {J e2,
+// J E, Linf, max|u|}], u < nper: afterwards red[0..3][0] hold the two sums and
+// the two maxima (256 threads; every thread passes the final barrier).
+__device__ inline void finalize_tree(const double* part, int f, uint64_t nper, double (*red)[256]) {
+    const int tid = threadIdx.x;
+    double s0 = 0.0, s1 = 0.0, m2 = 0.0, m3 = 0.0;
+    for (uint64_t u = tid; u < nper; u += 256) {
+        const double* tp = part + 4 * ((uint64_t)f * nper + u);
+        s0 += tp[0];
+        s1 += tp[1];
+        m2 = fmax(m2, tp[2]);
+        m3 = fmax(m3, tp[3]);
+    }
+    red[0][tid] = s0;
+    red[1][tid] = s1;
+    red[2][tid] = m2;
+    red[3][tid] = m3;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (tid < h) {
+            red[0][tid] += red[0][tid + h];
+            red[1][tid] += red[1][tid + h];
+            red[2][tid] = fmax(red[2][tid], red[2][tid + h]);
+            red[3][tid] = fmax(red[3][tid], red[3][tid + h]);
+        }
+        __syncthreads();
+    }
+}
+
+// Field report of field f from its sums and maxima, the field's code count in
+// the header (from the look-back states, p.tiles_per_field per field); field 0
+// also writes the rest of the header and the summary.  One thread.
+__device__ inline void finalize_report(const LaunchParams& p, int f, int lx, double se2, double sen, double linf,
+                                       double umax) {
+    const uint64_t* tile_state = p.tile_state;
+    const uint64_t n_tiles = (uint64_t)p.n_fields * p.tiles_per_field;
+    const uint64_t t0 = (uint64_t)f * p.tiles_per_field;
+    const uint64_t incl_end = tile_state[t0 + p.tiles_per_field - 1] & kValueMask;
+    const uint64_t incl_beg = (f == 0) ? 0 : (tile_state[t0 - 1] & kValueMask);
+    const uint64_t kept = incl_end - incl_beg;
+    const uint64_t total = tile_state[n_tiles - 1] & kValueMask;
+    semr_field_report* fr = &p.summary->field[f];
+    fr->l2_abs = sqrt(se2);
+    fr->l2_rel = sen > 0.0 ? sqrt(se2 / sen) : 0.0;
+    fr->linf_abs = linf;
+    fr->linf_rel = umax > 0.0 ? linf / umax : 0.0;
+    fr->sum_err2 = se2;
+    fr->sum_energy = sen;
+    fr->umax = umax;
+    fr->kept = kept;
+    fr->bytes = p.fixed_bytes + (uint64_t)p.width * kept;
+    const double orig = 8.0 * lx * lx * lx * (double)p.n_elem;
+    fr->cr = 1.0 - (double)fr->bytes / orig;
+    uint8_t* h = p.payload;
+    *reinterpret_cast<uint64_t*>(h + kHeaderFixed + 8 * f) = kept;
+    if (f == 0) {
+        const uint64_t bytes = p.code_base + (uint64_t)p.width * total;
+        h[0] = 'S'; h[1] = 'E'; h[2] = 'M'; h[3] = 'R';
+        *reinterpret_cast<uint16_t*>(h + 4) = kPayloadVersion;
+        *reinterpret_cast<uint16_t*>(h + 6) = (uint16_t)lx;
+        *reinterpret_cast<uint16_t*>(h + 8) = (uint16_t)p.n_fields;
+        uint16_t flags = 0;
+        if (p.lossless) flags |= SEMR_PAYLOAD_LOSSLESS;
+        if (p.width == 4) flags |= SEMR_PAYLOAD_CODE32;
+        if (p.precision == SEMR_FP32) flags |= SEMR_PAYLOAD_FP32;
+        if (p.cumulative) flags |= SEMR_PAYLOAD_CUMULATIVE;
+        *reinterpret_cast<uint16_t*>(h + 10) = flags;
+        *reinterpret_cast<uint32_t*>(h + 12) = (uint32_t)p.header_bytes;
+        *reinterpret_cast<uint64_t*>(h + 16) = (uint64_t)p.n_elem;
+        *reinterpret_cast<double*>(h + 24) = p.tau;
+        *reinterpret_cast<uint64_t*>(h + 32) = p.code_base;
+        *reinterpret_cast<uint64_t*>(h + 40) = total;
+        for (uint64_t b = kHeaderFixed + 8ull * p.n_fields; b < p.header_bytes; ++b) h[b] = 0;
+        p.summary->payload_bytes = bytes;
+        p.summary->code_total = total;
+        p.summary->n_fields = (uint32_t)p.n_fields;
+        p.summary->cr = 1.0 - (double)bytes / (orig * p.n_fields);
+        p.summary->status = p.ctl->status;
+        p.summary->recomputed = p.ctl->recomputed;
+    }
+}
+
+
+// Field f of one reduction: tree over its partials, then the report.  256 threads.
+__device__ inline void finalize_field(const LaunchParams& p, int f, int lx, double (*red)[256], const double* part,
+                                      uint64_t nper) {
+    finalize_tree(part, f, nper, red);
+    if (threadIdx.x == 0) finalize_report(p, f, lx, red[0][0], red[1][0], red[2][0], red[3][0]);
+}
+
 }  // namespace semr

@@ -43,6 +43,23 @@ constexpr uint64_t kScratchControlBytes = 256;
 SEMR_HD inline uint64_t scratch_bytes(uint64_t tiles) {
     return kScratchControlBytes + pad16(8 * tiles) + 32 * tiles;
 }
+
+// Warp-per-element kernel (lx = 8): look-back tiles of kWarpTile elements of one
+// field.  Scratch: [control][tile_state][tile_part][umax_elem f32 x n_fields *
+// n_elem][code staging: kWarpTile x 512 int16 per resident CTA, at most
+// kWarpStageCtas CTAs].
+constexpr int kWarpTile = 32;
+constexpr uint64_t kWarpStageCtas = 768;
+constexpr uint64_t kWarpStageBytes = uint64_t(kWarpTile) * 512 * 2;  // per CTA
+SEMR_HD inline uint64_t warp_tiles(int64_t n_elem, int32_t n_fields) {
+    return uint64_t(n_fields) * ((uint64_t(n_elem) + kWarpTile - 1) / kWarpTile);
+}
+SEMR_HD inline uint64_t warp_stage_ctas(uint64_t tiles) { return tiles < kWarpStageCtas ? tiles : kWarpStageCtas; }
+SEMR_HD inline uint64_t warp_scratch_bytes(int64_t n_elem, int32_t n_fields) {
+    const uint64_t t = warp_tiles(n_elem, n_fields);
+    const uint64_t head = (scratch_bytes(t) + pad16(4ull * uint64_t(n_fields) * uint64_t(n_elem)) + 255) & ~uint64_t(255);
+    return head + warp_stage_ctas(t) * kWarpStageBytes;
+}
 // bytes that must be zero before each launch (control + tile states)
 SEMR_HD inline uint64_t scratch_zero_bytes(uint64_t tiles) { return kScratchControlBytes + pad16(8 * tiles); }
 
@@ -84,7 +101,9 @@ struct LaunchParams {
     int32_t lx;
     int32_t tile;   // elements per tile of the kernel variant that runs this item
     int32_t cumulative;  // cumulative-energy truncation (never together with lossless)
-    int32_t pad2_;
+    int32_t stage_ctas;  // warp kernel: CTAs the code staging holds (its grid is at most this)
+    float* umax_elem;    // warp kernel: max |u| per element-field, rounded toward zero to float
+    int16_t* code_stage; // warp kernel: kWarpTile x 512 staged codes per CTA
 };
 
 // Default scratch split of one contiguous scratch buffer.
@@ -93,6 +112,16 @@ inline void split_scratch(LaunchParams& p, uint8_t* scratch, uint64_t tiles) {
     p.ctl = reinterpret_cast<ScratchControl*>(scratch);
     p.tile_state = reinterpret_cast<uint64_t*>(scratch + kScratchControlBytes);
     p.tile_part = reinterpret_cast<double*>(scratch + kScratchControlBytes + pad16(8 * tiles));
+}
+
+// Scratch split of the warp kernel (layout of warp_scratch_bytes).
+inline void split_scratch_warp(LaunchParams& p, uint8_t* scratch, int64_t n_elem, int32_t n_fields) {
+    const uint64_t t = warp_tiles(n_elem, n_fields);
+    split_scratch(p, scratch, t);
+    p.umax_elem = reinterpret_cast<float*>(scratch + scratch_bytes(t));
+    const uint64_t head = (scratch_bytes(t) + pad16(4ull * uint64_t(n_fields) * uint64_t(n_elem)) + 255) & ~uint64_t(255);
+    p.code_stage = reinterpret_cast<int16_t*>(scratch + head);
+    p.stage_ctas = (int32_t)warp_stage_ctas(t);
 }
 
 // Work queue of a batched launch: items of one (lx, precision) group; item i
@@ -113,6 +142,14 @@ int tile_variants(int lx, int* out, int cap);
 // Batched launches (semr_fast.cu / semr_kernels.cu).
 int launch_reduce_fast_batch(const BatchQueue& q, int lx, int precision, int tile, void* stream);
 int launch_finalize_batch(const BatchQueue& q, uint32_t total_fields, void* stream);
+
+// Warp-per-element kernel (semr_warp.cu): lx = 8 threshold truncation in
+// SEMR_FP64 / SEMR_FP32 with int16 codes.  warp_applicable() says whether it
+// takes a reduction; launch_reduce_warp / launch_finalize_warp run it and its
+// finalize (scratch split by split_scratch_warp, p.tile = kWarpTile).
+bool warp_applicable(const LaunchParams& p);
+int launch_reduce_warp(const LaunchParams& p, void* stream);
+int launch_finalize_warp(const LaunchParams& p, void* stream);
 
 // Kernel launchers (semr_kernels.cu).  Return a cudaError_t value.
 int launch_reduce(const LaunchParams& p, int lx, void* stream);

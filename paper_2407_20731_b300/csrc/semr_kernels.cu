@@ -471,87 +471,9 @@ reduce_kernel(const LaunchParams p, const Tables<LX, T> tab) {
 
 // ------------------------------------------------------ finalize kernel
 
-// Field f of one reduction: deterministic tree sum of the tile partials,
-// field report, the field's code count in the header; field 0 also writes the
-// rest of the header and the summary.  256 threads.
-__device__ void finalize_field(const LaunchParams& p, int f, int lx, double (*red)[256]) {
-    const int tid = threadIdx.x;
-    const uint64_t* tile_state = p.tile_state;
-    const uint64_t n_tiles = (uint64_t)p.n_fields * p.tiles_per_field;
-    const double* tile_part = p.tile_part;
-    double s0 = 0.0, s1 = 0.0, m2 = 0.0, m3 = 0.0;
-    const uint64_t t0 = (uint64_t)f * p.tiles_per_field;
-    for (uint64_t t = t0 + tid; t < t0 + p.tiles_per_field; t += 256) {
-        const double* tp = tile_part + 4 * t;
-        s0 += tp[0];
-        s1 += tp[1];
-        m2 = fmax(m2, tp[2]);
-        m3 = fmax(m3, tp[3]);
-    }
-    red[0][tid] = s0;
-    red[1][tid] = s1;
-    red[2][tid] = m2;
-    red[3][tid] = m3;
-    __syncthreads();
-    for (int h = 128; h > 0; h >>= 1) {
-        if (tid < h) {
-            red[0][tid] += red[0][tid + h];
-            red[1][tid] += red[1][tid + h];
-            red[2][tid] = fmax(red[2][tid], red[2][tid + h]);
-            red[3][tid] = fmax(red[3][tid], red[3][tid + h]);
-        }
-        __syncthreads();
-    }
-    if (tid != 0) return;
-    const uint64_t incl_end = tile_state[t0 + p.tiles_per_field - 1] & kValueMask;
-    const uint64_t incl_beg = (f == 0) ? 0 : (tile_state[t0 - 1] & kValueMask);
-    const uint64_t kept = incl_end - incl_beg;
-    const uint64_t total = tile_state[n_tiles - 1] & kValueMask;
-    const double se2 = red[0][0], sen = red[1][0], linf = red[2][0], umax = red[3][0];
-    semr_field_report* fr = &p.summary->field[f];
-    fr->l2_abs = sqrt(se2);
-    fr->l2_rel = sen > 0.0 ? sqrt(se2 / sen) : 0.0;
-    fr->linf_abs = linf;
-    fr->linf_rel = umax > 0.0 ? linf / umax : 0.0;
-    fr->sum_err2 = se2;
-    fr->sum_energy = sen;
-    fr->umax = umax;
-    fr->kept = kept;
-    fr->bytes = p.fixed_bytes + (uint64_t)p.width * kept;
-    const double orig = 8.0 * lx * lx * lx * (double)p.n_elem;
-    fr->cr = 1.0 - (double)fr->bytes / orig;
-    uint8_t* h = p.payload;
-    *reinterpret_cast<uint64_t*>(h + kHeaderFixed + 8 * f) = kept;
-    if (f == 0) {
-        const uint64_t bytes = p.code_base + (uint64_t)p.width * total;
-        h[0] = 'S'; h[1] = 'E'; h[2] = 'M'; h[3] = 'R';
-        *reinterpret_cast<uint16_t*>(h + 4) = kPayloadVersion;
-        *reinterpret_cast<uint16_t*>(h + 6) = (uint16_t)lx;
-        *reinterpret_cast<uint16_t*>(h + 8) = (uint16_t)p.n_fields;
-        uint16_t flags = 0;
-        if (p.lossless) flags |= SEMR_PAYLOAD_LOSSLESS;
-        if (p.width == 4) flags |= SEMR_PAYLOAD_CODE32;
-        if (p.precision == SEMR_FP32) flags |= SEMR_PAYLOAD_FP32;
-        if (p.cumulative) flags |= SEMR_PAYLOAD_CUMULATIVE;
-        *reinterpret_cast<uint16_t*>(h + 10) = flags;
-        *reinterpret_cast<uint32_t*>(h + 12) = (uint32_t)p.header_bytes;
-        *reinterpret_cast<uint64_t*>(h + 16) = (uint64_t)p.n_elem;
-        *reinterpret_cast<double*>(h + 24) = p.tau;
-        *reinterpret_cast<uint64_t*>(h + 32) = p.code_base;
-        *reinterpret_cast<uint64_t*>(h + 40) = total;
-        for (uint64_t b = kHeaderFixed + 8ull * p.n_fields; b < p.header_bytes; ++b) h[b] = 0;
-        p.summary->payload_bytes = bytes;
-        p.summary->code_total = total;
-        p.summary->n_fields = (uint32_t)p.n_fields;
-        p.summary->cr = 1.0 - (double)bytes / (orig * p.n_fields);
-        p.summary->status = p.ctl->status;
-        p.summary->recomputed = p.ctl->recomputed;
-    }
-}
-
 __global__ void __launch_bounds__(256) finalize_kernel(const LaunchParams p, int lx) {
     __shared__ double red[4][256];
-    finalize_field(p, blockIdx.x, lx, red);
+    finalize_field(p, blockIdx.x, lx, red, p.tile_part, (uint64_t)p.tiles_per_field);
 }
 
 // One block per (item, field) of a batched launch.
@@ -568,7 +490,7 @@ __global__ void __launch_bounds__(256) finalize_batch_kernel(const BatchQueue q)
     }
     __syncthreads();
     const LaunchParams& p = q.items[s_item];
-    finalize_field(p, (int)(blockIdx.x - q.field_base[s_item]), p.lx, red);
+    finalize_field(p, (int)(blockIdx.x - q.field_base[s_item]), p.lx, red, p.tile_part, (uint64_t)p.tiles_per_field);
 }
 
 // ------------------------------------------------------------ launchers

@@ -1,0 +1,1034 @@
+// Warp-per-element fused reduce kernel for lx = 8 (arXiv 2407.20731, Sec. IV-B:
+// JPEG-like truncation of the modal Legendre coefficients of SEM element
+// blocks, keeping the most energetic modes; Eq. 1 for the compression ratio).
+//
+// One warp reduces one element-field (an 8^3 block, 4 KB of FP64) at a time
+// and claims the next one from a global counter, so nothing in the loop waits
+// on the rest of the CTA:
+//   * TMA: the block arrives in the warp's shared-memory stage as a 2-D tile
+//     (64 pencils x 8 doubles, 64-byte swizzle), so every lane reads its two
+//     pencils with conflict-free 16-byte loads; the next element is requested
+//     as soon as these values are in registers and streams in meanwhile;
+//   * lane L owns the pencils P = L and L + 32 (P = j + 8k) in every phase:
+//     the forward transform contracts i in registers, then j and k after two
+//     padded transposes in shared memory private to the warp; the inverse
+//     runs the other way round, so each lane ends with the pencils it loaded;
+//   * coefficient a[r][q][p] of mode m = p + 8q + 64r lands in lane m & 31,
+//     slot (m >> 5) & 1, register r: each of the 16 ballots over (slot, r) is
+//     exactly mask word m >> 5 of the payload;
+//   * element sums are warp shuffles; the code count is published for the
+//     decoupled look-back right after the mask, the predecessors' states are
+//     read before the reconstruction and consumed after it;
+//   * per-element norm partials are collected for 32 elements and converted
+//     to FP64 by all lanes at once: B300's FP64 pipe runs at ~1/64 of the
+//     FP32 rate, so no FP64 instruction runs per point or per element.
+// Precision modes as in semr_fast.cu: SEMR_FP32 runs FP32 transforms with an
+// exact float-pair threshold test; SEMR_FP64 runs the forward transform in
+// FP32 under a proven error bound, recomputes exactly (float pairs) every
+// coefficient whose keep or rounding decision that bound cannot settle, and
+// does the energy, reconstruction and error norms in float pairs.
+#include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched at run time)
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "semr_device.cuh"
+
+namespace semr {
+namespace {
+
+constexpr int WLX = 8, WNP = 64, WN3 = 512;
+constexpr int WPB = 4;               // warps per CTA
+constexpr int TSK = 104, TSJ = 12;   // FP32 transpose strides (plane, row) in floats
+constexpr int TSK2 = 72, TSJ2 = 9;   // float-pair transpose strides (dense inverse, FP64 mode)
+constexpr int WSPARSE = 10;          // sparse reconstruction up to this many kept modes
+constexpr uint32_t kWaitPolls = 1u << 20;  // bounded mbarrier polls (each try_wait suspends a while)
+constexpr unsigned FULL = 0xffffffffu;
+
+struct WTables {         // lx = 8 tables, as kernel parameters (constant bank)
+    float Ah[64], Al[64];  // analysis A[p][i] (hi, lo)
+    float Ph[64], Pl[64];  // synthesis Phi[i][p] (hi, lo)
+    float wh[8], wl[8];    // GLL weights (hi, lo)
+};
+
+struct WStash {    // one element's results, kept until the end of its tile
+    uint32_t pad;
+    float umax;    // max |u| rounded toward zero to float
+    float sh, sl;  // S = sum w u^2 (pair; FP32 form: sl = 0)
+    float eh, el;  // e2 = sum w (u - u~)^2 (pair)
+    float lh, ll;  // Linf = max |u - u~| (pair)
+};
+static_assert(sizeof(WStash) == 32, "stash entry");
+
+struct WArgs {
+    CUtensorMap tm[SEMR_MAX_FIELDS];  // one 2-D map per field: [n_elem * 64 pencils][8 doubles]
+    LaunchParams p;
+    WTables tab;
+    float tau_h, tau_l;  // tau as a float pair
+    uint32_t n_elem;
+    uint32_t tiles_per_field;  // ceil(n_elem / kWarpTile)
+    uint32_t total_tiles;      // n_fields * tiles_per_field
+};
+
+template <bool DF>
+struct WSmem {
+    static constexpr size_t stage = 4096;                 // one element block per warp
+    static constexpr size_t off_tab = WPB * stage;        // Phi^T (hi, lo), A (hi, lo): 4 x 64 floats
+    static constexpr size_t off_wq = off_tab + 1024;      // [8][64] weight products
+    static constexpr size_t off_warp = off_wq + (DF ? 8 : 4) * 512;
+    // per warp
+    static constexpr size_t o_tb = 0;
+    static constexpr size_t tb_bytes = DF ? 8 * 8 * TSK2 : 4 * 8 * TSK;
+    static constexpr size_t o_mask = o_tb + tb_bytes;     // 16 mask words
+    static constexpr size_t o_wpre = o_mask + 64;         // 16 word prefixes
+    static constexpr size_t o_kl = o_wpre + 64;           // kept list (mode, code)
+    static constexpr size_t o_bar = o_kl + 96;
+    static constexpr size_t wbytes = o_bar + 16;
+    static constexpr size_t bytes = off_warp + WPB * wbytes + 1024;  // + alignment slack
+};
+static_assert(8 * 8 * TSK2 >= 4 * 8 * TSK, "pair buffer holds the FP32 one");
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// Request `bytes` into dst from the 2-D tensor map at (x, y); completion on bar.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar,
+                                            uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for phase `parity` of bar (uniform over the warp).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    bool ok = false;
+    for (uint32_t it = 0; it < kWaitPolls && !ok; ++it) ok = mbar_try_wait(bar, parity);
+    return __all_sync(FULL, ok);
+}
+// Round-toward-zero float of a double (integer instructions; |u| >= 2^-126 or it comes out ~0).
+__device__ __forceinline__ float w_d2f_rz(uint32_t lo, uint32_t hi) {
+    const int t = max(static_cast<int>(hi & 0x7fffffffu) - 0x38000000, 0);  // rebias 1023 -> 127
+    return __uint_as_float(__funnelshift_l(lo, static_cast<uint32_t>(t), 3) | (hi & 0x80000000u));
+}
+// u = uh + ul: uh rounded toward zero to 24 bits, ul the next 23 bits (|u - uh - ul| < 2^-46 |u|);
+// both zero-ish below 2^-80.
+__device__ __forceinline__ void w_split(uint32_t lo, uint32_t hi, float& uh, float& ul) {
+    uh = w_d2f_rz(lo, hi);
+    // mantissa bits 28..6 of the low word, an exact float integer via the 2^23 magic number
+    const float m = __uint_as_float(((lo >> 6) & 0x7fffffu) | 0x4b000000u) - 8388608.0f;
+    // their unit is 2^(E - 46) for uh = 1.x 2^E: exponent field of uh minus 46 (clamped at 0)
+    const int ex = static_cast<int>(__float_as_uint(uh) & 0x7f800000u) - (46 << 23);
+    ul = m * __uint_as_float(static_cast<uint32_t>(max(ex, 0)) | (hi & 0x80000000u));
+}
+
+// 8-point even-odd folded transforms (FP32, tables from the constant bank).
+__device__ __forceinline__ void w_fwd(const float* __restrict__ A, const float (&x)[8], float (&y)[8]) {
+    const float e0 = x[0] + x[7], e1 = x[1] + x[6], e2 = x[2] + x[5], e3 = x[3] + x[4];
+    const float o0 = x[0] - x[7], o1 = x[1] - x[6], o2 = x[2] - x[5], o3 = x[3] - x[4];
+#pragma unroll
+    for (int p = 0; p < 8; p += 2) {
+        y[p] = fmaf(A[p * 8 + 3], e3, fmaf(A[p * 8 + 2], e2, fmaf(A[p * 8 + 1], e1, A[p * 8] * e0)));
+        y[p + 1] = fmaf(A[p * 8 + 11], o3, fmaf(A[p * 8 + 10], o2, fmaf(A[p * 8 + 9], o1, A[p * 8 + 8] * o0)));
+    }
+}
+__device__ __forceinline__ void w_inv(const float* __restrict__ Ph, const float (&x)[8], float (&y)[8]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float e = fmaf(Ph[i * 8 + 6], x[6], fmaf(Ph[i * 8 + 4], x[4], fmaf(Ph[i * 8 + 2], x[2], Ph[i * 8] * x[0])));
+        const float o =
+            fmaf(Ph[i * 8 + 7], x[7], fmaf(Ph[i * 8 + 5], x[5], fmaf(Ph[i * 8 + 3], x[3], Ph[i * 8 + 1] * x[1])));
+        y[i] = e + o;
+        y[7 - i] = e - o;
+    }
+}
+
+// Pair sum over the warp (butterfly: every lane ends with the same value).
+__device__ __forceinline__ f2 warp_sum_pair(f2 s) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = df_add(s, {__shfl_xor_sync(FULL, s.h, o), __shfl_xor_sync(FULL, s.l, o)});
+    return s;
+}
+__device__ __forceinline__ float warp_sum_f(float s) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    return s;
+}
+// Largest non-negative float over the warp (its bits order like unsigned integers).
+__device__ __forceinline__ float warp_max_nonneg(float v) {
+    return __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(v)));
+}
+// g^2 >= t exactly, for a float g and a normalised pair t.
+__device__ __forceinline__ bool sq_ge(float g, f2 t) {
+    const float ph = g * g;
+    const float pl = fmaf(g, g, -ph);
+    return ph > t.h || (ph == t.h && pl >= t.l);
+}
+
+// Dense folded inverse in float pairs for an element that keeps many modes (a
+// rare path, kept out of line so that its registers do not weigh on the
+// common one): r (registers) -> k, q -> j, p -> i through the warp's buffer.
+// Result: the lane's nodal pencils (k0 + 4s, j) at buf[(lane + 32 s) * 9 + i].
+__device__ __noinline__ void dense_inverse_pairs(float2* buf, const int16_t* scodes, const uint32_t* smask,
+                                                 const uint32_t* swpre, uint32_t kb, float qu1, float qu2,
+                                                 const float* Ph, const float* Pl) {
+    const int lane = threadIdx.x & 31, j = lane & 7, k0 = lane >> 3;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    f2 x[8], y[2][8];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            float v = 0.0f;
+            if ((kb >> (8 * s + r)) & 1u) {
+                const int rank = static_cast<int>(swpre[s + 2 * r]) + __popc(smask[s + 2 * r] & lt_mask);
+                v = (static_cast<float>(scodes[rank]) * qu1) * qu2;
+            }
+            x[r] = {v, 0.0f};
+        }
+        inv1d_df<8>(Ph, Pl, x, y[s]);  // lane (q = k0 + 4s, p = j): values over k
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) buf[(k0 + 4 * s) * TSK2 + j * TSJ2 + kk] = make_float2(y[s][kk].h, y[s][kk].l);
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {  // lane (k = k0 + 4s, p = j): values over q
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float2 v = buf[q * TSK2 + j * TSJ2 + k0 + 4 * s];
+            x[q] = {v.x, v.y};
+        }
+        inv1d_df<8>(Ph, Pl, x, y[s]);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) buf[(k0 + 4 * s) * TSK2 + j * TSJ2 + jj] = make_float2(y[s][jj].h, y[s][jj].l);
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {  // lane (k = k0 + 4s, j): values over p
+#pragma unroll
+        for (int pp = 0; pp < 8; ++pp) {
+            const float2 v = buf[(k0 + 4 * s) * TSK2 + pp * TSJ2 + j];
+            x[pp] = {v.x, v.y};
+        }
+        inv1d_df<8>(Ph, Pl, x, y[s]);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) buf[(lane + 32 * s) * 9 + i] = make_float2(y[s][i].h, y[s][i].l);
+    __syncwarp();
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 5) reduce_warp_kernel(const __grid_constant__ WArgs A) {
+    constexpr bool DF = MODE != 0;
+    using SM = WSmem<DF>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const LaunchParams& p = A.p;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+
+    float* sPTh = reinterpret_cast<float*>(smem + SM::off_tab);  // [p][i] = Phi[i][p]
+    float* sPTl = sPTh + 64;
+    float* sAh = sPTl + 64;  // [p][i] = A[p][i]
+    float* sAl = sAh + 64;
+    for (int t = threadIdx.x; t < 64; t += WPB * 32) {
+        const int i = t >> 3, c = t & 7;  // Ph[t] = Phi[i][c]
+        sPTh[c * 8 + i] = A.tab.Ph[t];
+        sPTl[c * 8 + i] = A.tab.Pl[t];
+        sAh[t] = A.tab.Ah[t];
+        sAl[t] = A.tab.Al[t];
+    }
+    // quadrature weight products w_i w_j w_k at [i][P], P = j + 8k
+    for (int t = threadIdx.x; t < 512; t += WPB * 32) {
+        const int i = t >> 6, P = t & 63, jj = P & 7, kk = P >> 3;
+        const f2 w3 = df_mul({A.tab.wh[i], A.tab.wl[i]},
+                             df_mul({A.tab.wh[jj], A.tab.wl[jj]}, {A.tab.wh[kk], A.tab.wl[kk]}));
+        if constexpr (DF) reinterpret_cast<float2*>(smem + SM::off_wq)[t] = make_float2(w3.h, w3.l);
+        else reinterpret_cast<float*>(smem + SM::off_wq)[t] = w3.h;
+    }
+    uint8_t* wb = smem + SM::off_warp + wid * SM::wbytes;
+    uint8_t* stage = smem + wid * SM::stage;
+    float* tb = reinterpret_cast<float*>(wb + SM::o_tb);
+    float2* tb2 = reinterpret_cast<float2*>(wb + SM::o_tb);
+    uint32_t* smask = reinterpret_cast<uint32_t*>(wb + SM::o_mask);
+    uint32_t* swpre = reinterpret_cast<uint32_t*>(wb + SM::o_wpre);
+    int2* skl = reinterpret_cast<int2*>(wb + SM::o_kl);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(wb + SM::o_bar);
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    // this lane's pencils: (k, j) = (k0 + 4s, j) in nodal phases, (k0 + 4s, j) -> (q, p) in modal ones
+    const int j = lane & 7, k0 = lane >> 3;
+    const int sw = (lane >> 1) & 3;  // 64-byte swizzle of rows lane and lane + 32
+    float w3f[2][8];                 // FP32 form: weight products of this lane's points
+    if constexpr (!DF) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) w3f[s][i] = reinterpret_cast<const float*>(smem + SM::off_wq)[i * 64 + lane + 32 * s];
+    }
+    const float2* sWq2 = reinterpret_cast<const float2*>(smem + SM::off_wq);
+
+    const uint32_t E = A.n_elem, tpf = A.tiles_per_field, total_tiles = A.total_tiles;
+    unsigned* counter = &p.ctl->tile_counter;
+    unsigned* status = &p.ctl->status;
+    int16_t* stage_codes = p.code_stage + static_cast<uint64_t>(blockIdx.x) * kWarpTile * WN3;
+
+    // tiles: kWarpTile consecutive elements of one field; warp w takes elements w, w + 4, ...
+    __shared__ uint32_t s_tile[2];  // current tile; the next one, claimed when the current one is computed
+    __shared__ uint32_t s_cnt[kWarpTile], s_pre[kWarpTile];
+    __shared__ WStash s_res[kWarpTile];
+    __shared__ unsigned long long s_excl;
+    __shared__ int s_abort;
+    if (threadIdx.x == 0) {
+        s_tile[0] = atomicAdd(counter, 1u);
+        s_abort = 0;
+    }
+    __syncthreads();
+    auto geom = [&](uint32_t tt, uint32_t& f, uint32_t& e0, int& nh) {
+        f = tt / tpf;
+        e0 = (tt - f * tpf) * kWarpTile;
+        nh = static_cast<int>(min(static_cast<uint32_t>(kWarpTile), E - e0));
+    };
+    auto issue = [&](uint32_t f, uint32_t e) {  // lane 0: element block (f, e) into the stage
+        tma_load_2d(stage, &A.tm[f], 0, static_cast<int>(e * WNP), bar, SM::stage);
+    };
+    uint32_t parity = 0;
+    bool inflight = false;  // a block is on its way into this warp's stage
+    unsigned recomputed = 0;
+
+    for (;;) {
+    // Tiles are claimed only once the previous one is computed, so they start in about
+    // the order of their claims and a look-back never waits for a tile not yet begun.
+    const uint32_t tcur = s_tile[0];
+    if (tcur >= total_tiles) break;
+    uint32_t f, e0;
+    int nh;
+    geom(tcur, f, e0, nh);
+    for (int il = wid; il < nh; il += WPB) {
+        const uint32_t e = e0 + static_cast<uint32_t>(il);
+        if (!inflight && lane == 0) issue(f, e);
+        if (!mbar_wait_bounded(bar, parity)) {
+            if (lane == 0) {
+                atomicOr(status, static_cast<unsigned>(SEMR_STATUS_TIMEOUT));
+                s_abort = 1;
+            }
+            mbar_wait_bounded(bar, parity);  // the copy may still land: wait once more, bounded
+            inflight = false;
+            break;
+        }
+        parity ^= 1u;
+        inflight = false;
+        int16_t* scodes = stage_codes + il * WN3;  // this element's staged codes (global, L2-resident)
+
+        // ---- the lane's two pencils, split into floats with integer instructions
+        float uh[2][8], ul[2][8];
+        uint32_t hmax = 0;
+        float umx = 0.0f;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const uint8_t* row = stage + (lane + 32 * s) * 64;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const uint4 v = *reinterpret_cast<const uint4*>(row + ((c ^ sw) << 4));
+                const uint32_t lo[2] = {v.x, v.z}, hi[2] = {v.y, v.w};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int i = 2 * c + h;
+                    hmax = max(hmax, hi[h] & 0x7fffffffu);
+                    if constexpr (DF) {
+                        w_split(lo[h], hi[h], uh[s][i], ul[s][i]);
+                    } else {
+                        uh[s][i] = w_d2f_rz(lo[h], hi[h]);
+                        ul[s][i] = 0.0f;
+                    }
+                    umx = fmaxf(umx, fabsf(uh[s][i]));
+                }
+            }
+        }
+        // every lane has consumed its loads: the stage may be refilled with this warp's next element
+        __syncwarp();
+        if (il + WPB < nh) {
+            if (lane == 0) {
+                fence_proxy_async();
+                issue(f, e + WPB);
+            }
+            inflight = true;
+        }
+        const bool bad = __any_sync(FULL, hmax >= (static_cast<uint32_t>(1023 + 127) << 20));
+        const float umax_e = warp_max_nonneg(umx);
+
+        // ---- forward transform (FP32): i in registers, then j and k through the warp's buffer
+        float a[2][8];
+        {
+            float y[8];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                w_fwd(A.tab.Ah, uh[s], y);
+                float4* d = reinterpret_cast<float4*>(tb + (k0 + 4 * s) * TSK + j * TSJ);
+                d[0] = make_float4(y[0], y[1], y[2], y[3]);
+                d[1] = make_float4(y[4], y[5], y[6], y[7]);
+            }
+            __syncwarp();
+            float z[2][8];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {  // lane owns (k, p = j): values over j'
+                float x[8];
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) x[jj] = tb[(k0 + 4 * s) * TSK + jj * TSJ + j];
+                w_fwd(A.tab.Ah, x, z[s]);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                float4* d = reinterpret_cast<float4*>(tb + (k0 + 4 * s) * TSK + j * TSJ);
+                d[0] = make_float4(z[s][0], z[s][1], z[s][2], z[s][3]);
+                d[1] = make_float4(z[s][4], z[s][5], z[s][6], z[s][7]);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {  // lane owns (q = k0 + 4s, p = j): values over k
+                float x[8];
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) x[kk] = tb[kk * TSK + j * TSJ + k0 + 4 * s];
+                w_fwd(A.tab.Ah, x, a[s]);
+            }
+        }
+
+        // ---- element energy S: FP64 mode sum w u^2 at the nodes in pairs (Parseval's
+        // identity in nodal form), FP32 form sum a^2 of the coefficients
+        f2 S;
+        if constexpr (DF) {
+            f2 sp = {0.0f, 0.0f};
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const float2 w = sWq2[i * 64 + lane + 32 * s];
+                    const float ph = uh[s][i] * uh[s][i];
+                    const float pl = fmaf(uh[s][i], ul[s][i] + ul[s][i], fmaf(uh[s][i], uh[s][i], -ph));
+                    df_fma_acc(sp, {w.x, w.y}, {ph, pl});
+                }
+            S = warp_sum_pair(df_norm(sp));
+        } else {
+            float sp = 0.0f;
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int r = 0; r < 8; ++r) sp = fmaf(a[s][r], a[s][r], sp);
+            S = {warp_sum_f(sp), 0.0f};
+        }
+
+        // ---- per element (warp-uniform): t = tau S, step s_e = floor((ex - 1) / 2) for
+        // t = mu 2^ex, and g = the smallest float with g^2 >= t
+        int emode = 0;  // 0: keep none, 1: threshold
+        int step = INT16_MIN;
+        f2 t = {0.0f, 0.0f};
+        float g = 0.0f;
+        if (bad || !isfinite(S.h)) {
+            if (lane == 0) atomicOr(status, static_cast<unsigned>(SEMR_STATUS_NONFINITE));
+        } else {
+            t = df_norm(df_mul({A.tau_h, A.tau_l}, S));
+            if (t.h >= 1.0e-30f && t.h <= 1.0e37f) {
+                const uint32_t tb_ = __float_as_uint(t.h);
+                int ex = static_cast<int>(tb_ >> 23) - 126;
+                if ((tb_ & 0x7fffffu) == 0u && t.l < 0.0f) --ex;  // t just below a power of two
+                step = (ex - 1) >> 1;
+                emode = 1;
+                g = sqrtf(t.h);
+#pragma unroll 1
+                for (int it = 0; it < 4 && !sq_ge(g, t); ++it) g = __uint_as_float(__float_as_uint(g) + 1u);
+#pragma unroll 1
+                for (int it = 0; it < 4; ++it) {
+                    const float pr = __uint_as_float(__float_as_uint(g) - 1u);
+                    if (sq_ge(pr, t)) g = pr; else break;
+                }
+            }
+        }
+        const int sd1 = (-step) >> 1, sd2 = -step - sd1;  // 2^-s = 2^sd1 2^sd2 (exact)
+        const float qd1 = pow2f(emode ? sd1 : 0), qd2 = pow2f(emode ? sd2 : 0);
+        const int su1 = step >> 1, su2 = step - su1;      // 2^s = 2^su1 2^su2
+        const float qu1 = pow2f(emode ? su1 : 0), qu2 = pow2f(emode ? su2 : 0);
+
+        // ---- keep decisions; FP64 mode recomputes exactly what FP32 cannot settle
+        uint32_t kb = 0;  // keep bit (8 s + r)
+        if (emode == 1) {
+            if constexpr (DF) {
+                // |a_fp32 - a| <= M: (H + 2) roundings per folded contraction (H = 4 terms, the fold,
+                // the table), 3 contractions, 2 more for the input split; every row of A has
+                // sum |A_pi| <= sqrt(2), so (|A|^3 |u|)_m <= 2^1.5 max|u|; a factor 2 of safety
+                constexpr float kMarg = (3.0f * (4 + 2) + 2.0f) * 5.9604645e-8f * 2.8285f * 2.0f;
+                const float M = kMarg * umax_e * 1.0000002f;
+                const float Mg = M + g * 2.4e-7f;  // plus the float rounding of g +- M
+                const float Mq = Mg * qd1 * qd2;
+                uint32_t amb = 0;
+#pragma unroll
+                for (int s = 0; s < 2; ++s)
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) {
+                        const float aa = fabsf(a[s][r]);
+                        const int b = 8 * s + r;
+                        if (aa >= g + Mg) {  // surely kept: is its rounding decision sure too?
+                            const float y = (aa * qd1) * qd2;
+                            kb |= 1u << b;
+                            if (fabsf((y - floorf(y)) - 0.5f) <= Mq + y * 1.2e-7f) amb |= 1u << b;
+                        } else if (!(aa < g - Mg)) {
+                            amb |= 1u << b;
+                        }
+                    }
+                // exact (float-pair) coefficient of each ambiguous mode, one at a time over the warp
+                while (__any_sync(FULL, amb != 0u)) {
+                    const int src = __ffs(__ballot_sync(FULL, amb != 0u)) - 1;
+                    const int bsel = __shfl_sync(FULL, __ffs(amb) - 1, src);
+                    const int ms = bsel >> 3, mr = bsel & 7;
+                    const int pp = src & 7, qq = (src >> 3) + 4 * ms;
+                    f2 c = {0.0f, 0.0f};
+#pragma unroll
+                    for (int s = 0; s < 2; ++s) {
+                        f2 xs = {0.0f, 0.0f};
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) df_fma_acc(xs, {sAh[pp * 8 + i], sAl[pp * 8 + i]}, {uh[s][i], ul[s][i]});
+                        xs = df_norm(xs);
+                        const int kk = k0 + 4 * s;
+                        c = df_add(c, df_mul(df_mul(xs, {sAh[qq * 8 + j], sAl[qq * 8 + j]}),
+                                             {sAh[mr * 8 + kk], sAl[mr * 8 + kk]}));
+                    }
+                    c = warp_sum_pair(c);
+                    ++recomputed;
+                    if (lane == src) {
+                        const bool keep = df_ge(df_mul(c, c), t);
+                        // a kept coefficient becomes its code times 2^s (exact), so the
+                        // quantisation below reproduces the code of the exact value
+                        float v = c.h;
+                        if (keep) {
+                            const float yh = (c.h * qd1) * qd2, yl = (c.l * qd1) * qd2;
+                            float cc = (yh + 12582912.0f) - 12582912.0f;
+                            const float diff = (yh - cc) + yl;
+                            cc += (diff > 0.5f) ? 1.0f : ((diff < -0.5f) ? -1.0f : 0.0f);
+                            v = (cc * qu1) * qu2;
+                        }
+#pragma unroll
+                        for (int s = 0; s < 2; ++s)
+#pragma unroll
+                            for (int r = 0; r < 8; ++r)
+                                if (8 * s + r == bsel) a[s][r] = v;
+                        kb = keep ? (kb | (1u << bsel)) : (kb & ~(1u << bsel));
+                        amb &= ~(1u << bsel);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < 2; ++s)
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) kb |= (fabsf(a[s][r]) >= g ? 1u : 0u) << (8 * s + r);
+            }
+        }
+
+        // ---- mask words: ballot over (slot s, row r) is word s + 2r (bit = lane)
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {  // words 4 q4 .. 4 q4 + 3: (s, r) = (0, 2q4), (1, 2q4), (0, 2q4+1), (1, 2q4+1)
+            const uint32_t w0 = __ballot_sync(FULL, (kb >> (2 * q4)) & 1u);
+            const uint32_t w1 = __ballot_sync(FULL, (kb >> (8 + 2 * q4)) & 1u);
+            const uint32_t w2 = __ballot_sync(FULL, (kb >> (2 * q4 + 1)) & 1u);
+            const uint32_t w3 = __ballot_sync(FULL, (kb >> (8 + 2 * q4 + 1)) & 1u);
+            if (lane == 0) reinterpret_cast<uint4*>(smask)[q4] = make_uint4(w0, w1, w2, w3);
+        }
+        __syncwarp();
+        uint32_t n_e;
+        {
+            const uint32_t mw = (lane < 16) ? smask[lane] : 0u;
+            const uint32_t c = __popc(mw);
+            uint32_t incl = c;
+#pragma unroll
+            for (int o = 1; o < 16; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (lane < 16) swpre[lane] = incl - c;
+            n_e = __shfl_sync(FULL, incl, 15);
+            // payload: mask words, step, count
+            uint8_t* fsec = p.payload + p.header_bytes + static_cast<uint64_t>(f) * p.fixed_bytes;
+            if (lane < 16) reinterpret_cast<uint32_t*>(fsec)[static_cast<uint64_t>(e) * 16 + lane] = mw;
+            const uint64_t mb = static_cast<uint64_t>(E) * 64;  // mask section (a multiple of 16)
+            int16_t* sdst = reinterpret_cast<int16_t*>(fsec + mb);
+            uint16_t* cdst = reinterpret_cast<uint16_t*>(fsec + mb + pad16(2ull * E));
+            if (lane == 0) {
+                sdst[e] = static_cast<int16_t>(step);
+                cdst[e] = static_cast<uint16_t>(n_e);
+                s_cnt[il] = n_e;
+            }
+            if (e + 1 == E && lane < 16) {  // zero the padding after the step and count sections
+                const uint64_t se = 2ull * E;
+                if (se + lane < pad16(se)) {
+                    reinterpret_cast<uint8_t*>(sdst)[se + lane] = 0;
+                    reinterpret_cast<uint8_t*>(cdst)[se + lane] = 0;
+                }
+            }
+        }
+        __syncwarp();
+
+        // ---- quantise: code = rint(a 2^-s), ties to even (exact: a 2^-s is a power-of-two scaling)
+        const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const uint32_t wd = smask[s + 2 * r];
+                if (wd == 0u) continue;  // warp-uniform
+                if ((kb >> (8 * s + r)) & 1u) {
+                    const float yh = (a[s][r] * qd1) * qd2;
+                    const float c = (yh + 12582912.0f) - 12582912.0f;  // round half to even (|y| < 2^22)
+                    const int rank = static_cast<int>(swpre[s + 2 * r]) + __popc(wd & lt_mask);
+                    scodes[rank] = static_cast<int16_t>(c);
+                    if (rank < WSPARSE) skl[rank] = make_int2(lane + 32 * s + 64 * r, __float_as_int(c));
+                }
+            }
+        __syncwarp();
+        // kept code value of coefficient (s, r) times 2^s, for the dense inverse
+        auto code_value = [&](int s, int r) -> float {
+            if (!((kb >> (8 * s + r)) & 1u)) return 0.0f;
+            const int rank = static_cast<int>(swpre[s + 2 * r]) + __popc(smask[s + 2 * r] & lt_mask);
+            return (static_cast<float>(scodes[rank]) * qu1) * qu2;
+        };
+
+        // ---- reconstruction u~ of the lane's nodal pencils (pairs in FP64 mode)
+        float vh[2][8], vl[2][8];
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                vh[s][i] = 0.0f;
+                vl[s][i] = 0.0f;
+            }
+        if (n_e <= static_cast<uint32_t>(WSPARSE)) {
+            for (uint32_t tk = 0; tk < n_e; ++tk) {
+                const int2 kv = skl[tk];
+                const int m = kv.x, pp = m & 7, qq = (m >> 3) & 7, rr = m >> 6;
+                const float cs = (__int_as_float(kv.y) * qu1) * qu2;  // c 2^s, exact
+                const float4* ph4 = reinterpret_cast<const float4*>(sPTh + pp * 8);
+                const float4 h0 = ph4[0], h1 = ph4[1];
+                const float colh[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+                if constexpr (DF) {
+                    const float4* pl4 = reinterpret_cast<const float4*>(sPTl + pp * 8);
+                    const float4 l0 = pl4[0], l1 = pl4[1];
+                    const float coll[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+                    const f2 fj = {sPTh[qq * 8 + j], sPTl[qq * 8 + j]};
+#pragma unroll
+                    for (int s = 0; s < 2; ++s) {
+                        const int kk = k0 + 4 * s;
+                        const f2 b = df_mulf(df_mul(fj, {sPTh[rr * 8 + kk], sPTl[rr * 8 + kk]}), cs);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            f2 acc = {vh[s][i], vl[s][i]};
+                            df_fma_acc(acc, b, {colh[i], coll[i]});
+                            vh[s][i] = acc.h;
+                            vl[s][i] = acc.l;
+                        }
+                    }
+                } else {
+                    const float fj = sPTh[qq * 8 + j];
+#pragma unroll
+                    for (int s = 0; s < 2; ++s) {
+                        const float b = cs * fj * sPTh[rr * 8 + k0 + 4 * s];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) vh[s][i] = fmaf(b, colh[i], vh[s][i]);
+                    }
+                }
+            }
+            if constexpr (DF) {
+#pragma unroll
+                for (int s = 0; s < 2; ++s)
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const f2 nn = df_norm({vh[s][i], vl[s][i]});
+                        vh[s][i] = nn.h;
+                        vl[s][i] = nn.l;
+                    }
+            }
+        } else if constexpr (DF) {
+            dense_inverse_pairs(tb2, scodes, smask, swpre, kb, qu1, qu2, A.tab.Ph, A.tab.Pl);
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const float2 v = tb2[(lane + 32 * s) * 9 + i];
+                    vh[s][i] = v.x;
+                    vl[s][i] = v.y;
+                }
+            __syncwarp();
+        } else {
+            // dense folded inverse in FP32
+            float y[8];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                float x[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) x[r] = code_value(s, r);
+                w_inv(A.tab.Ph, x, y);  // lane (q = k0 + 4s, p = j): values over k
+                float4* d = reinterpret_cast<float4*>(tb + (k0 + 4 * s) * TSK + j * TSJ);
+                d[0] = make_float4(y[0], y[1], y[2], y[3]);
+                d[1] = make_float4(y[4], y[5], y[6], y[7]);
+            }
+            __syncwarp();
+            float z[2][8];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {  // lane (k = k0 + 4s, p = j): values over q
+                float x[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) x[q] = tb[q * TSK + j * TSJ + k0 + 4 * s];
+                w_inv(A.tab.Ph, x, z[s]);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                float4* d = reinterpret_cast<float4*>(tb + (k0 + 4 * s) * TSK + j * TSJ);
+                d[0] = make_float4(z[s][0], z[s][1], z[s][2], z[s][3]);
+                d[1] = make_float4(z[s][4], z[s][5], z[s][6], z[s][7]);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {  // lane (k = k0 + 4s, j): values over p
+                float x[8];
+#pragma unroll
+                for (int pp = 0; pp < 8; ++pp) x[pp] = tb[(k0 + 4 * s) * TSK + pp * TSJ + j];
+                w_inv(A.tab.Ph, x, vh[s]);
+            }
+            __syncwarp();
+        }
+
+        // ---- errors of the lane's points: e2 = sum w (u - u~)^2, Linf = max |u - u~|
+        f2 e2;
+        float lh = 0.0f, ll = 0.0f;  // Linf as a pair (|dh| first, then the signed low word)
+        if constexpr (DF) {
+            f2 ep = {0.0f, 0.0f};
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const f2 d = df_sub({uh[s][i], ul[s][i]}, {vh[s][i], vl[s][i]});
+                    const float2 wv = sWq2[i * 64 + lane + 32 * s];
+                    const float ph = d.h * d.h;
+                    const float pl = fmaf(d.h, d.l + d.l, fmaf(d.h, d.h, -ph));
+                    df_fma_acc(ep, {wv.x, wv.y}, {ph, pl});
+                    const float ad = fabsf(d.h);
+                    const float adl = __uint_as_float(__float_as_uint(d.l) ^ (__float_as_uint(d.h) & 0x80000000u));
+                    ll = (ad > lh) ? adl : ((ad == lh) ? fmaxf(ll, adl) : ll);
+                    lh = fmaxf(lh, ad);
+                }
+            e2 = warp_sum_pair(df_norm(ep));
+            const float LH = warp_max_nonneg(lh);
+            // largest low word among the lanes holding LH: order-preserving integer key of a float
+            const uint32_t kb_ = (lh == LH) ? (__float_as_uint(ll) ^ ((__float_as_uint(ll) >> 31) ? 0xffffffffu : 0x80000000u)) : 0u;
+            const uint32_t kmax = __reduce_max_sync(FULL, kb_);
+            lh = LH;
+            ll = __uint_as_float((kmax >> 31) ? (kmax ^ 0x80000000u) : ~kmax);
+            if (LH == 0.0f) ll = 0.0f;
+        } else {
+            float ep = 0.0f, dm = 0.0f;
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const float d = uh[s][i] - vh[s][i];
+                    ep = fmaf(w3f[s][i] * d, d, ep);
+                    dm = fmaxf(dm, fabsf(d));
+                }
+            e2 = {warp_sum_f(ep), 0.0f};
+            lh = warp_max_nonneg(dm);
+        }
+        if (p.write_recon && p.recon[f]) {
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                double2* dst = reinterpret_cast<double2*>(p.recon[f] + static_cast<uint64_t>(e) * WN3 + (lane + 32 * s) * 8);
+#pragma unroll
+                for (int i = 0; i < 8; i += 2)
+                    dst[i / 2] = make_double2(static_cast<double>(vh[s][i]) + static_cast<double>(vl[s][i]),
+                                              static_cast<double>(vh[s][i + 1]) + static_cast<double>(vl[s][i + 1]));
+            }
+        }
+
+        if (lane == 0) {
+            WStash st;
+            st.pad = 0;
+            st.umax = umax_e;
+            st.sh = S.h;
+            st.sl = S.l;
+            st.eh = e2.h;
+            st.el = e2.l;
+            st.lh = lh;
+            st.ll = ll;
+            s_res[il] = st;
+        }
+        __syncwarp();  // the kept list and mask words are reused by the next element
+    }
+    if (threadIdx.x == 0) s_tile[1] = atomicAdd(counter, 1u);
+    __syncthreads();  // every element of the tile is done
+    {  // this warp's first block of the next tile streams in during the tile's bookkeeping
+        const uint32_t tn = s_tile[1];
+        if (tn < total_tiles && !s_abort) {
+            uint32_t fn, e0n;
+            int nhn;
+            geom(tn, fn, e0n, nhn);
+            if (wid < nhn) {
+                if (lane == 0) {
+                    fence_proxy_async();
+                    issue(fn, e0n + static_cast<uint32_t>(wid));
+                }
+                inflight = true;
+            }
+        }
+    }
+    if (wid == 0) {
+        // tile aggregate, within-tile prefixes, decoupled look-back for the tile's code offset
+        const uint32_t c = (lane < nh) ? s_cnt[lane] : 0u;
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        s_pre[lane] = incl - c;
+        const uint32_t tot = __shfl_sync(FULL, incl, 31);
+        if (lane == 0) st_release_u64(&p.tile_state[tcur], (tcur == 0 ? kFlagPrefix : kFlagAggregate) | tot);
+        const uint64_t excl = lookback_warp(p.tile_state, tcur, tot, status);
+        if (lane == 0) s_excl = excl;
+    } else if (wid == 1) {
+        // FP64 partials of the tile (fixed order) and the element report, one element per lane
+        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+        if (lane < nh) {
+            const WStash st = s_res[lane];
+            const uint64_t ge = static_cast<uint64_t>(f) * E + e0 + lane;
+            const double J = p.jac[e0 + lane];
+            const double Sd = static_cast<double>(st.sh) + static_cast<double>(st.sl);
+            const double e2d = static_cast<double>(st.eh) + static_cast<double>(st.el);
+            v0 = J * e2d;
+            v1 = J * Sd;
+            v2 = static_cast<double>(st.lh) + static_cast<double>(st.ll);
+            v3 = static_cast<double>(st.umax);
+            p.umax_elem[ge] = st.umax;
+            if (p.elem_report) {
+                double* er = p.elem_report + 3 * ge;
+                er[0] = v0;
+                er[1] = v1;
+                er[2] = v2;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            v0 += __shfl_down_sync(FULL, v0, o);
+            v1 += __shfl_down_sync(FULL, v1, o);
+            v2 = fmax(v2, __shfl_down_sync(FULL, v2, o));
+            v3 = fmax(v3, __shfl_down_sync(FULL, v3, o));
+        }
+        if (lane == 0) {
+            double* tp = p.tile_part + 4ull * tcur;
+            tp[0] = v0;
+            tp[1] = v1;
+            tp[2] = v2;
+            tp[3] = v3;
+        }
+    } else if (wid == 2 && lane == 0) {
+        s_tile[0] = s_tile[1];
+    }
+    __syncthreads();
+    // codes of this warp's elements at code_base + 2 (tile prefix + within-tile prefix)
+    {
+        const uint64_t excl = s_excl;
+        for (int il = wid; il < nh; il += WPB) {
+            const uint32_t n = s_cnt[il];
+            const uint64_t gbyte = p.code_base + 2ull * (excl + s_pre[il]);
+            if (gbyte + 2ull * n <= p.payload_cap) {
+                int16_t* dst = reinterpret_cast<int16_t*>(p.payload + gbyte);
+                const int16_t* src = stage_codes + il * WN3;
+                for (uint32_t k = lane; k < n; k += 32) dst[k] = src[k];
+            } else if (lane == 0 && n > 0) {
+                atomicOr(status, static_cast<unsigned>(SEMR_STATUS_OVERFLOW));
+            }
+        }
+    }
+    if (s_abort) break;
+    __syncwarp();
+    }
+    if (inflight) mbar_wait_bounded(bar, parity);  // after an abort: let a requested block land
+    if (lane == 0 && recomputed) atomicAdd(&p.ctl->recomputed, recomputed);
+}
+
+// Finalize of field f: tree over its tile partials, then the exact maximum of
+// |u|.  The kernel records each element's maximum rounded toward zero to
+// float, which keeps their order, so the elements whose rounded maximum is
+// the field's hold the exact one: those few blocks are reread.  256 threads.
+__global__ void __launch_bounds__(256) finalize_warp_kernel(const LaunchParams p) {
+    __shared__ double red[4][256];
+    __shared__ int s_list[64];
+    __shared__ int s_cnt;
+    __shared__ unsigned long long s_umax;
+    const int tid = threadIdx.x, f = blockIdx.x;
+    finalize_tree(p.tile_part, f, static_cast<uint64_t>(p.tiles_per_field), red);
+    const double M = red[3][0];
+    if (tid == 0) {
+        s_cnt = 0;
+        s_umax = 0ull;
+    }
+    __syncthreads();
+    const uint64_t E = static_cast<uint64_t>(p.n_elem);
+    const float* um = p.umax_elem + static_cast<uint64_t>(f) * E;
+    const double* src = p.fields[f];
+    for (uint64_t t = tid; t < static_cast<uint64_t>(p.tiles_per_field); t += 256) {
+        if (p.tile_part[4 * (static_cast<uint64_t>(f) * p.tiles_per_field + t) + 3] != M) continue;
+        const uint64_t ee = min(E, (t + 1) * kWarpTile);
+        for (uint64_t e = t * kWarpTile; e < ee; ++e) {
+            if (static_cast<double>(um[e]) != M) continue;
+            const int k = atomicAdd(&s_cnt, 1);
+            if (k < 64) {
+                s_list[k] = static_cast<int>(e);
+            } else {  // many ties (e.g. constant fields): this thread scans the block itself
+                unsigned long long m = 0ull;
+                for (int i = 0; i < WN3; ++i)
+                    m = max(m, static_cast<unsigned long long>(__double_as_longlong(src[e * WN3 + i])) &
+                                   0x7fffffffffffffffull);
+                atomicMax(&s_umax, m);
+            }
+        }
+    }
+    __syncthreads();
+    const int nl = min(s_cnt, 64);
+    unsigned long long m = 0ull;
+    for (int l = 0; l < nl; ++l) {
+        const double* blk = src + static_cast<uint64_t>(s_list[l]) * WN3;
+        for (int i = tid; i < WN3; i += 256)
+            m = max(m, static_cast<unsigned long long>(__double_as_longlong(blk[i])) & 0x7fffffffffffffffull);
+    }
+    atomicMax(&s_umax, m);
+    __syncthreads();
+    if (tid == 0)
+        finalize_report(p, f, WLX, red[0][0], red[1][0], red[2][0], __longlong_as_double(static_cast<long long>(s_umax)));
+}
+
+// ------------------------------------------------------------ host side
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encoder() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    });
+    return fn;
+}
+
+WTables make_wtables() {
+    WTables t;
+    double Am[64], Phi[64], w[8];
+    basis_tables(8, Am, Phi, w);
+    for (int i = 0; i < 64; ++i) {
+        t.Ah[i] = static_cast<float>(Am[i]);
+        t.Al[i] = static_cast<float>(Am[i] - static_cast<double>(t.Ah[i]));
+        t.Ph[i] = static_cast<float>(Phi[i]);
+        t.Pl[i] = static_cast<float>(Phi[i] - static_cast<double>(t.Ph[i]));
+    }
+    for (int i = 0; i < 8; ++i) {
+        t.wh[i] = static_cast<float>(w[i]);
+        t.wl[i] = static_cast<float>(w[i] - static_cast<double>(t.wh[i]));
+    }
+    return t;
+}
+
+template <int MODE>
+int launch_mode(const WArgs& a, void* stream) {
+    using SM = WSmem<MODE != 0>;
+    cudaError_t err;
+    auto kern = reduce_warp_kernel<MODE>;
+    if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes)) != cudaSuccess)
+        return (int)err;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return (int)err;
+    if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return (int)err;
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPB * 32, SM::bytes)) != cudaSuccess)
+        return (int)err;
+    if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
+    // persistent: as many CTAs as fit at once, never more than tiles or staging slots
+    const uint64_t want = std::min<uint64_t>(a.total_tiles, static_cast<uint64_t>(a.p.stage_ctas));
+    const unsigned grid = (unsigned)std::min<uint64_t>(want, static_cast<uint64_t>(sms) * per_sm);
+    kern<<<grid, WPB * 32, SM::bytes, static_cast<cudaStream_t>(stream)>>>(a);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace
+
+bool warp_applicable(const LaunchParams& p) {
+    if (p.lx != 8 || p.cumulative || p.lossless || p.width != 2) return false;
+    if (p.precision != SEMR_FP64 && p.precision != SEMR_FP32) return false;
+    if (static_cast<uint64_t>(p.n_elem) * WNP >= (1ull << 31)) return false;  // TMA row coordinate
+    for (int f = 0; f < p.n_fields; ++f)
+        if (reinterpret_cast<uintptr_t>(p.fields[f]) & 15u) return false;  // TMA needs 16-byte aligned blocks
+    return encoder() != nullptr;
+}
+
+int launch_reduce_warp(const LaunchParams& p, void* stream) {
+    EncodeTiledFn enc = encoder();
+    if (!enc) return (int)cudaErrorNotSupported;
+    WArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.p = p;
+    a.tab = make_wtables();
+    a.tau_h = static_cast<float>(p.tau);
+    a.tau_l = static_cast<float>(p.tau - static_cast<double>(a.tau_h));
+    a.n_elem = static_cast<uint32_t>(p.n_elem);
+    a.tiles_per_field = static_cast<uint32_t>(p.tiles_per_field);
+    a.total_tiles = static_cast<uint32_t>(static_cast<uint64_t>(p.n_fields) * p.tiles_per_field);
+    for (int f = 0; f < p.n_fields; ++f) {
+        const cuuint64_t dims[2] = {8, static_cast<cuuint64_t>(p.n_elem) * WNP};
+        const cuuint64_t strides[1] = {64};
+        const cuuint32_t box[2] = {8, WNP};
+        const cuuint32_t estr[2] = {1, 1};
+        if (enc(&a.tm[f], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(p.fields[f]), dims, strides, box,
+                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return (int)cudaErrorInvalidValue;
+    }
+    return p.precision == SEMR_FP32 ? launch_mode<0>(a, stream) : launch_mode<1>(a, stream);
+}
+
+int launch_finalize_warp(const LaunchParams& p, void* stream) {
+    finalize_warp_kernel<<<p.n_fields, 256, 0, static_cast<cudaStream_t>(stream)>>>(p);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace semr

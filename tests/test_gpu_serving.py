@@ -63,7 +63,8 @@ def test_each_result_same_alone_and_in_the_mix(precision):
 
 def test_budget_queues_and_rejects():
     reqs = _requests()
-    sizes = [semr.semr_sizes_for(r[2], r[1].numel(), len(r[0]), r[3]).payload_worst for r in reqs]
+    sz = [semr.semr_sizes_for(r[2], r[1].numel(), len(r[0]), r[3]) for r in reqs]
+    sizes = [s.payload_worst + s.scratch_bytes for s in sz]  # what the server reserves per request
     budget = int(max(sizes) * 1.3)  # only about one request fits at a time
     srv = semr.Server(slots=4, mem_budget_bytes=budget)
     ids = [srv.submit(*r) for r in reqs]

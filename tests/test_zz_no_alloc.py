@@ -73,7 +73,7 @@ def _meaningful(raw: bytes, n_fields: int) -> bytes:
 
 
 def test_noalloc_rejects_snapshots_beyond_its_scratch():
-    lx, nf, n_elem = 8, 3, 600000  # 3 * 150000 tiles * 40 B > 16 MiB
+    lx, nf, n_elem = 8, 8, 1000000  # 8 million element-fields * ~10 B > 64 MiB
     assert semr.semr_sizes_for(lx, n_elem, nf, 1e-3).scratch_bytes > semr.SEMR_NOALLOC_SCRATCH_BYTES
     fs, mesh = semr.semr_fieldset(), semr.semr_mesh()
     fs.n_fields, fs.tau, mesh.lx, mesh.n_elem = nf, 1e-3, lx, n_elem
