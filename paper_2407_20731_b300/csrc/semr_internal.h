@@ -46,11 +46,12 @@ SEMR_HD inline uint64_t scratch_bytes(uint64_t tiles) {
 
 // Warp-per-element kernel (lx = 8): look-back tiles of kWarpTile elements of one
 // field.  Scratch: [control][tile_state][tile_part][umax_elem f32 x n_fields *
-// n_elem][code staging: kWarpTile x 512 int16 per resident CTA, at most
-// kWarpStageCtas CTAs].
-constexpr int kWarpTile = 32;
-constexpr uint64_t kWarpStageCtas = 768;
-constexpr uint64_t kWarpStageBytes = uint64_t(kWarpTile) * 512 * 2;  // per CTA
+// n_elem][code staging: kWarpTile slots of kWarpSlot int16 codes per resident CTA,
+// at most kWarpStageCtas CTAs].  An element with more codes writes them directly.
+constexpr int kWarpTile = 64;
+constexpr int kWarpSlot = 32;
+constexpr uint64_t kWarpStageCtas = 1024;
+constexpr uint64_t kWarpStageBytes = uint64_t(kWarpTile) * kWarpSlot * 2;  // per CTA
 SEMR_HD inline uint64_t warp_tiles(int64_t n_elem, int32_t n_fields) {
     return uint64_t(n_fields) * ((uint64_t(n_elem) + kWarpTile - 1) / kWarpTile);
 }

@@ -45,7 +45,8 @@ constexpr int WPB = 4;               // warps per CTA
 constexpr int TSK = 104, TSJ = 12;   // FP32 transpose strides (plane, row) in floats
 constexpr int TSK2 = 72, TSJ2 = 9;   // float-pair transpose strides (dense inverse, FP64 mode)
 constexpr int WSPARSE = 10;          // sparse reconstruction up to this many kept modes
-constexpr uint32_t kWaitPolls = 1u << 20;  // bounded mbarrier polls (each try_wait suspends a while)
+constexpr uint32_t kWaitPolls = 1000;      // bounded mbarrier polls, each suspending up to kWaitHintNs
+constexpr uint32_t kWaitHintNs = 1000000;
 constexpr unsigned FULL = 0xffffffffu;
 
 struct WTables {         // lx = 8 tables, as kernel parameters (constant bank)
@@ -113,13 +114,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, in
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}"
+        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2, %3;\n selp.u32 %0, 1, 0, P;\n}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kWaitHintNs)
         : "memory");
     return ok != 0;
 }
-// Bounded wait for phase `parity` of bar (uniform over the warp).
+// Bounded wait for phase `parity` of bar (uniform over the warp): each poll sleeps until the
+// phase completes or the hint elapses, so a waiting warp issues almost nothing.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
     bool ok = false;
     for (uint32_t it = 0; it < kWaitPolls && !ok; ++it) ok = mbar_try_wait(bar, parity);
@@ -184,29 +186,131 @@ __device__ __forceinline__ bool sq_ge(float g, f2 t) {
     return ph > t.h || (ph == t.h && pl >= t.l);
 }
 
+// Exclusive prefix of tile `tile` from its predecessors' states, as lookback_warp
+// computes it, without publishing anything (bounded; all 32 lanes).
+__device__ __forceinline__ uint64_t lookback_peek(const uint64_t* tile_state, uint64_t tile, unsigned* status) {
+    const int lane = threadIdx.x & 31;
+    uint64_t excl = 0;
+    int64_t base = static_cast<int64_t>(tile) - 1;
+    for (uint32_t spins = 0; base >= 0;) {
+        const int64_t jj = base - lane;
+        const uint64_t v = (jj >= 0) ? ld_acquire_u64(&tile_state[jj]) : kFlagPrefix;
+        const uint64_t flag = v & ~kValueMask;
+        const unsigned pmask = __ballot_sync(FULL, flag == kFlagPrefix);
+        const unsigned xmask = __ballot_sync(FULL, flag == 0);
+        const int first_p = pmask ? __ffs(pmask) - 1 : 32;
+        const unsigned before = (first_p == 32) ? FULL : ((1u << first_p) - 1u);
+        if (xmask & before) {
+            if (++spins > (1u << 22)) {
+                if (lane == 0) atomicOr(status, static_cast<unsigned>(SEMR_STATUS_TIMEOUT));
+                break;
+            }
+            __nanosleep(64);
+            continue;
+        }
+        uint64_t c = (lane <= first_p) ? (v & kValueMask) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+        excl += c;
+        if (first_p < 32) break;
+        base -= 32;
+    }
+    return excl;
+}
+
+// Exact (float-pair) coefficient a[r][q][p] of the element in `stage`: each lane
+// contracts its two pencils (k0 + 4s, j) with A[p][.], A[q][j], A[r][k] and the
+// warp sums them.  Rare (decisions the FP32 bound cannot settle): out of line.
+__device__ __noinline__ f2 exact_coef(const uint8_t* stage, int pp, int qq, int rr, const float* sAh,
+                                      const float* sAl) {
+    const int lane = threadIdx.x & 31, j = lane & 7, k0 = lane >> 3, sw = (lane >> 1) & 3;
+    f2 c = {0.0f, 0.0f};
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const uint8_t* row = stage + (lane + 32 * s) * 64;
+        f2 xs = {0.0f, 0.0f};
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+            const uint4 v = *reinterpret_cast<const uint4*>(row + ((cc ^ sw) << 4));
+            float h0, l0, h1, l1;
+            w_split(v.x, v.y, h0, l0);
+            w_split(v.z, v.w, h1, l1);
+            df_fma_acc(xs, {sAh[pp * 8 + 2 * cc], sAl[pp * 8 + 2 * cc]}, {h0, l0});
+            df_fma_acc(xs, {sAh[pp * 8 + 2 * cc + 1], sAl[pp * 8 + 2 * cc + 1]}, {h1, l1});
+        }
+        xs = df_norm(xs);
+        const int kk = k0 + 4 * s;
+        c = df_add(c, df_mul(df_mul(xs, {sAh[qq * 8 + j], sAl[qq * 8 + j]}), {sAh[rr * 8 + kk], sAl[rr * 8 + kk]}));
+    }
+    return warp_sum_pair(c);
+}
+
+// Dense folded inverse in FP32 for an element that keeps many modes (rare, out of
+// line): r (registers) -> k, q -> j, p -> i through the warp's buffer.  Input: the
+// kept values (code x 2^s, else 0) of the lane's coefficients (s, r) at
+// buf[(lane + 32 s) * 9 + r]; result: its nodal pencils (k0 + 4s, j) at
+// buf[(lane + 32 s) * 9 + i].
+__device__ __noinline__ void dense_inverse_f32(float* buf, const float* Ph) {
+    const int lane = threadIdx.x & 31, j = lane & 7, k0 = lane >> 3;
+    float x[8], y[2][8];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) x[r] = buf[(lane + 32 * s) * 9 + r];
+        w_inv(Ph, x, y[s]);  // lane (q = k0 + 4s, p = j): values over k
+    }
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        float4* d = reinterpret_cast<float4*>(buf + (k0 + 4 * s) * TSK + j * TSJ);
+        d[0] = make_float4(y[s][0], y[s][1], y[s][2], y[s][3]);
+        d[1] = make_float4(y[s][4], y[s][5], y[s][6], y[s][7]);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {  // lane (k = k0 + 4s, p = j): values over q
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x[q] = buf[q * TSK + j * TSJ + k0 + 4 * s];
+        w_inv(Ph, x, y[s]);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        float4* d = reinterpret_cast<float4*>(buf + (k0 + 4 * s) * TSK + j * TSJ);
+        d[0] = make_float4(y[s][0], y[s][1], y[s][2], y[s][3]);
+        d[1] = make_float4(y[s][4], y[s][5], y[s][6], y[s][7]);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {  // lane (k = k0 + 4s, j): values over p
+#pragma unroll
+        for (int pp = 0; pp < 8; ++pp) x[pp] = buf[(k0 + 4 * s) * TSK + pp * TSJ + j];
+        w_inv(Ph, x, y[s]);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) buf[(lane + 32 * s) * 9 + i] = y[s][i];
+    __syncwarp();
+}
+
 // Dense folded inverse in float pairs for an element that keeps many modes (a
 // rare path, kept out of line so that its registers do not weigh on the
 // common one): r (registers) -> k, q -> j, p -> i through the warp's buffer.
-// Result: the lane's nodal pencils (k0 + 4s, j) at buf[(lane + 32 s) * 9 + i].
-__device__ __noinline__ void dense_inverse_pairs(float2* buf, const int16_t* scodes, const uint32_t* smask,
-                                                 const uint32_t* swpre, uint32_t kb, float qu1, float qu2,
-                                                 const float* Ph, const float* Pl) {
+// Input as dense_inverse_f32 (floats); result: the lane's nodal pencils
+// (k0 + 4s, j) at buf[(lane + 32 s) * 9 + i] (pairs).
+__device__ __noinline__ void dense_inverse_pairs(float2* buf, const float* Ph, const float* Pl) {
     const int lane = threadIdx.x & 31, j = lane & 7, k0 = lane >> 3;
-    const uint32_t lt_mask = (1u << lane) - 1u;
+    const float* vin = reinterpret_cast<const float*>(buf);
     f2 x[8], y[2][8];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            float v = 0.0f;
-            if ((kb >> (8 * s + r)) & 1u) {
-                const int rank = static_cast<int>(swpre[s + 2 * r]) + __popc(smask[s + 2 * r] & lt_mask);
-                v = (static_cast<float>(scodes[rank]) * qu1) * qu2;
-            }
-            x[r] = {v, 0.0f};
-        }
+        for (int r = 0; r < 8; ++r) x[r] = {vin[(lane + 32 * s) * 9 + r], 0.0f};
         inv1d_df<8>(Ph, Pl, x, y[s]);  // lane (q = k0 + 4s, p = j): values over k
     }
+    __syncwarp();
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
@@ -245,7 +349,7 @@ __device__ __noinline__ void dense_inverse_pairs(float2* buf, const int16_t* sco
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 5) reduce_warp_kernel(const __grid_constant__ WArgs A) {
+__global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(const __grid_constant__ WArgs A) {
     constexpr bool DF = MODE != 0;
     using SM = WSmem<DF>;
     extern __shared__ uint8_t smem_raw[];
@@ -301,11 +405,12 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 5) reduce_warp_kernel(con
     const uint32_t E = A.n_elem, tpf = A.tiles_per_field, total_tiles = A.total_tiles;
     unsigned* counter = &p.ctl->tile_counter;
     unsigned* status = &p.ctl->status;
-    int16_t* stage_codes = p.code_stage + static_cast<uint64_t>(blockIdx.x) * kWarpTile * WN3;
+    int16_t* stage_codes = p.code_stage + static_cast<uint64_t>(blockIdx.x) * kWarpTile * kWarpSlot;
 
     // tiles: kWarpTile consecutive elements of one field; warp w takes elements w, w + 4, ...
     __shared__ uint32_t s_tile[2];  // current tile; the next one, claimed when the current one is computed
-    __shared__ uint32_t s_cnt[kWarpTile], s_pre[kWarpTile];
+    __shared__ uint32_t s_cnt[kWarpTile];  // tile tag << 16 | code count; tag 0xffff: nothing yet
+    __shared__ uint32_t s_pre[kWarpTile];
     __shared__ WStash s_res[kWarpTile];
     __shared__ unsigned long long s_excl;
     __shared__ int s_abort;
@@ -313,6 +418,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 5) reduce_warp_kernel(con
         s_tile[0] = atomicAdd(counter, 1u);
         s_abort = 0;
     }
+    for (int i = threadIdx.x; i < kWarpTile; i += WPB * 32) s_cnt[i] = 0xffff0000u;
     __syncthreads();
     auto geom = [&](uint32_t tt, uint32_t& f, uint32_t& e0, int& nh) {
         f = tt / tpf;
@@ -323,6 +429,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 5) reduce_warp_kernel(con
         tma_load_2d(stage, &A.tm[f], 0, static_cast<int>(e * WNP), bar, SM::stage);
     };
     uint32_t parity = 0;
+    uint32_t tag = 0;       // tags the counts of the current tile (0 .. 0xfffe, then wraps)
     bool inflight = false;  // a block is on its way into this warp's stage
     unsigned recomputed = 0;
 
@@ -348,7 +455,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 5) reduce_warp_kernel(con
         }
         parity ^= 1u;
         inflight = false;
-        int16_t* scodes = stage_codes + il * WN3;  // this element's staged codes (global, L2-resident)
+        int16_t* scodes = stage_codes + il * kWarpSlot;  // this element's first codes (global, L2-resident)
 
         // ---- the lane's two pencils, split into floats with integer instructions
         float uh[2][8], ul[2][8];
@@ -375,15 +482,19 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 5) reduce_warp_kernel(con
                 }
             }
         }
-        // every lane has consumed its loads: the stage may be refilled with this warp's next element
-        __syncwarp();
-        if (il + WPB < nh) {
-            if (lane == 0) {
-                fence_proxy_async();
-                issue(f, e + WPB);
+        // once every lane has consumed its loads (and, in FP64 mode, the exact recomputation
+        // has reread the block), the stage may be refilled with this warp's next element
+        auto prefetch_next = [&]() {
+            __syncwarp();
+            if (il + WPB < nh) {
+                if (lane == 0) {
+                    fence_proxy_async();
+                    issue(f, e + WPB);
+                }
+                inflight = true;
             }
-            inflight = true;
-        }
+        };
+        if constexpr (!DF) prefetch_next();
         const bool bad = __any_sync(FULL, hmax >= (static_cast<uint32_t>(1023 + 127) << 20));
         const float umax_e = warp_max_nonneg(umx);
 
@@ -464,7 +575,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 5) reduce_warp_kernel(con
                 if ((tb_ & 0x7fffffu) == 0u && t.l < 0.0f) --ex;  // t just below a power of two
                 step = (ex - 1) >> 1;
                 emode = 1;
-                g = sqrtf(t.h);
+                asm("sqrt.approx.f32 %0, %1;" : "=f"(g) : "f"(t.h));
 #pragma unroll 1
                 for (int it = 0; it < 4 && !sq_ge(g, t); ++it) g = __uint_as_float(__float_as_uint(g) + 1u);
 #pragma unroll 1
@@ -474,10 +585,8 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 5) reduce_warp_kernel(con
                 }
             }
         }
-        const int sd1 = (-step) >> 1, sd2 = -step - sd1;  // 2^-s = 2^sd1 2^sd2 (exact)
-        const float qd1 = pow2f(emode ? sd1 : 0), qd2 = pow2f(emode ? sd2 : 0);
-        const int su1 = step >> 1, su2 = step - su1;      // 2^s = 2^su1 2^su2
-        const float qu1 = pow2f(emode ? su1 : 0), qu2 = pow2f(emode ? su2 : 0);
+        // t in [1e-30, 1e37] keeps s in [-50, 61]: 2^-s and 2^s are normal floats (exact scalings)
+        const float qd = pow2f(emode ? -step : 0), qu = pow2f(emode ? step : 0);
 
         // ---- keep decisions; FP64 mode recomputes exactly what FP32 cannot settle
         uint32_t kb = 0;  // keep bit (8 s + r)
@@ -489,7 +598,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 5) reduce_warp_kernel(con
                 constexpr float kMarg = (3.0f * (4 + 2) + 2.0f) * 5.9604645e-8f * 2.8285f * 2.0f;
                 const float M = kMarg * umax_e * 1.0000002f;
                 const float Mg = M + g * 2.4e-7f;  // plus the float rounding of g +- M
-                const float Mq = Mg * qd1 * qd2;
+                const float Mq = Mg * qd;
                 uint32_t amb = 0;
 #pragma unroll
                 for (int s = 0; s < 2; ++s)
@@ -498,7 +607,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 5) reduce_warp_kernel(con
                         const float aa = fabsf(a[s][r]);
                         const int b = 8 * s + r;
                         if (aa >= g + Mg) {  // surely kept: is its rounding decision sure too?
-                            const float y = (aa * qd1) * qd2;
+                            const float y = aa * qd;
                             kb |= 1u << b;
                             if (fabsf((y - floorf(y)) - 0.5f) <= Mq + y * 1.2e-7f) amb |= 1u << b;
                         } else if (!(aa < g - Mg)) {
@@ -510,19 +619,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 5) reduce_warp_kernel(con
                     const int src = __ffs(__ballot_sync(FULL, amb != 0u)) - 1;
                     const int bsel = __shfl_sync(FULL, __ffs(amb) - 1, src);
                     const int ms = bsel >> 3, mr = bsel & 7;
-                    const int pp = src & 7, qq = (src >> 3) + 4 * ms;
-                    f2 c = {0.0f, 0.0f};
-#pragma unroll
-                    for (int s = 0; s < 2; ++s) {
-                        f2 xs = {0.0f, 0.0f};
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) df_fma_acc(xs, {sAh[pp * 8 + i], sAl[pp * 8 + i]}, {uh[s][i], ul[s][i]});
-                        xs = df_norm(xs);
-                        const int kk = k0 + 4 * s;
-                        c = df_add(c, df_mul(df_mul(xs, {sAh[qq * 8 + j], sAl[qq * 8 + j]}),
-                                             {sAh[mr * 8 + kk], sAl[mr * 8 + kk]}));
-                    }
-                    c = warp_sum_pair(c);
+                    const f2 c = exact_coef(stage, src & 7, (src >> 3) + 4 * ms, mr, sAh, sAl);
                     ++recomputed;
                     if (lane == src) {
                         const bool keep = df_ge(df_mul(c, c), t);
@@ -530,11 +627,11 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 5) reduce_warp_kernel(con
                         // quantisation below reproduces the code of the exact value
                         float v = c.h;
                         if (keep) {
-                            const float yh = (c.h * qd1) * qd2, yl = (c.l * qd1) * qd2;
+                            const float yh = c.h * qd, yl = c.l * qd;
                             float cc = (yh + 12582912.0f) - 12582912.0f;
                             const float diff = (yh - cc) + yl;
                             cc += (diff > 0.5f) ? 1.0f : ((diff < -0.5f) ? -1.0f : 0.0f);
-                            v = (cc * qu1) * qu2;
+                            v = cc * qu;
                         }
 #pragma unroll
                         for (int s = 0; s < 2; ++s)
@@ -552,6 +649,8 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 5) reduce_warp_kernel(con
                     for (int r = 0; r < 8; ++r) kb |= (fabsf(a[s][r]) >= g ? 1u : 0u) << (8 * s + r);
             }
         }
+
+        if constexpr (DF) prefetch_next();
 
         // ---- mask words: ballot over (slot s, row r) is word s + 2r (bit = lane)
 #pragma unroll
@@ -584,7 +683,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 5) reduce_warp_kernel(con
             if (lane == 0) {
                 sdst[e] = static_cast<int16_t>(step);
                 cdst[e] = static_cast<uint16_t>(n_e);
-                s_cnt[il] = n_e;
+                s_cnt[il] = (tag << 16) | n_e;
             }
             if (e + 1 == E && lane < 16) {  // zero the padding after the step and count sections
                 const uint64_t se = 2ull * E;
@@ -598,27 +697,66 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 5) reduce_warp_kernel(con
 
         // ---- quantise: code = rint(a 2^-s), ties to even (exact: a 2^-s is a power-of-two scaling)
         const uint32_t lt_mask = (1u << lane) - 1u;
+        // words holding kept modes (bit w = s + 2r), the same in every lane
+        uint32_t nzw = __ballot_sync(FULL, lane < 16 && smask[lane] != 0u);
+        while (nzw) {
+            const int wi = __ffs(nzw) - 1;
+            nzw &= nzw - 1;
+            const int bsel = 8 * (wi & 1) + (wi >> 1);  // register (s, r) of word wi
+            if ((kb >> bsel) & 1u) {
+                float av = 0.0f;
 #pragma unroll
-        for (int r = 0; r < 8; ++r)
+                for (int s2 = 0; s2 < 2; ++s2)
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                const uint32_t wd = smask[s + 2 * r];
-                if (wd == 0u) continue;  // warp-uniform
-                if ((kb >> (8 * s + r)) & 1u) {
-                    const float yh = (a[s][r] * qd1) * qd2;
-                    const float c = (yh + 12582912.0f) - 12582912.0f;  // round half to even (|y| < 2^22)
-                    const int rank = static_cast<int>(swpre[s + 2 * r]) + __popc(wd & lt_mask);
-                    scodes[rank] = static_cast<int16_t>(c);
-                    if (rank < WSPARSE) skl[rank] = make_int2(lane + 32 * s + 64 * r, __float_as_int(c));
+                    for (int r2 = 0; r2 < 8; ++r2)
+                        if (8 * s2 + r2 == bsel) av = a[s2][r2];
+                const float yh = av * qd;
+                const float c = (yh + 12582912.0f) - 12582912.0f;  // round half to even (|y| < 2^22)
+                const int rank = static_cast<int>(swpre[wi]) + __popc(smask[wi] & lt_mask);
+                if (rank < kWarpSlot) scodes[rank] = static_cast<int16_t>(c);
+                if (rank < WSPARSE) skl[rank] = make_int2(lane + 32 * wi, __float_as_int(c));
+            }
+        }
+        if (n_e > static_cast<uint32_t>(kWarpSlot)) {
+            // more codes than the slot holds (rare): write them at their final place, which needs
+            // the tile's exclusive prefix and the counts of the tile's earlier elements; every such
+            // wait points to smaller element indices, so it ends
+            uint64_t before = lookback_peek(p.tile_state, tcur, status);
+            uint32_t part = 0;
+            for (int jj = lane; jj < il; jj += 32) {
+                uint32_t v = 0;
+                for (uint32_t it = 0; it < (1u << 22); ++it) {
+                    v = *reinterpret_cast<volatile uint32_t*>(&s_cnt[jj]);
+                    if ((v >> 16) == tag) break;
+                    __nanosleep(64);
+                    if (it + 1 == (1u << 22)) atomicOr(status, static_cast<unsigned>(SEMR_STATUS_TIMEOUT));
+                }
+                part += v & 0xffffu;
+            }
+            before += __reduce_add_sync(FULL, part);
+            const uint64_t gbyte = p.code_base + 2ull * before;
+            const bool fits = gbyte + 2ull * n_e <= p.payload_cap;
+            if (!fits && lane == 0) atomicOr(status, static_cast<unsigned>(SEMR_STATUS_OVERFLOW));
+            int16_t* dst = reinterpret_cast<int16_t*>(p.payload + gbyte);
+            uint32_t nz = __ballot_sync(FULL, lane < 16 && smask[lane] != 0u);
+            while (fits && nz) {
+                const int wi = __ffs(nz) - 1;
+                nz &= nz - 1;
+                const int bsel = 8 * (wi & 1) + (wi >> 1);
+                if ((kb >> bsel) & 1u) {
+                    float av = 0.0f;
+#pragma unroll
+                    for (int s2 = 0; s2 < 2; ++s2)
+#pragma unroll
+                        for (int r2 = 0; r2 < 8; ++r2)
+                            if (8 * s2 + r2 == bsel) av = a[s2][r2];
+                    const float yh = av * qd;
+                    const float c = (yh + 12582912.0f) - 12582912.0f;
+                    dst[swpre[wi] + __popc(smask[wi] & lt_mask)] = static_cast<int16_t>(c);
                 }
             }
+        }
         __syncwarp();
-        // kept code value of coefficient (s, r) times 2^s, for the dense inverse
-        auto code_value = [&](int s, int r) -> float {
-            if (!((kb >> (8 * s + r)) & 1u)) return 0.0f;
-            const int rank = static_cast<int>(swpre[s + 2 * r]) + __popc(smask[s + 2 * r] & lt_mask);
-            return (static_cast<float>(scodes[rank]) * qu1) * qu2;
-        };
 
         // ---- reconstruction u~ of the lane's nodal pencils (pairs in FP64 mode)
         float vh[2][8], vl[2][8];
@@ -633,7 +771,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 5) reduce_warp_kernel(con
             for (uint32_t tk = 0; tk < n_e; ++tk) {
                 const int2 kv = skl[tk];
                 const int m = kv.x, pp = m & 7, qq = (m >> 3) & 7, rr = m >> 6;
-                const float cs = (__int_as_float(kv.y) * qu1) * qu2;  // c 2^s, exact
+                const float cs = __int_as_float(kv.y) * qu;  // c 2^s, exact
                 const float4* ph4 = reinterpret_cast<const float4*>(sPTh + pp * 8);
                 const float4 h0 = ph4[0], h1 = ph4[1];
                 const float colh[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
@@ -675,7 +813,13 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 5) reduce_warp_kernel(con
                     }
             }
         } else if constexpr (DF) {
-            dense_inverse_pairs(tb2, scodes, smask, swpre, kb, qu1, qu2, A.tab.Ph, A.tab.Pl);
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+                    tb[(lane + 32 * s) * 9 + r] =
+                        ((kb >> (8 * s + r)) & 1u) ? ((a[s][r] * qd + 12582912.0f) - 12582912.0f) * qu : 0.0f;
+            dense_inverse_pairs(tb2, A.tab.Ph, A.tab.Pl);
 #pragma unroll
             for (int s = 0; s < 2; ++s)
 #pragma unroll
@@ -686,42 +830,17 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 5) reduce_warp_kernel(con
                 }
             __syncwarp();
         } else {
-            // dense folded inverse in FP32
-            float y[8];
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                float x[8];
+            for (int s = 0; s < 2; ++s)
 #pragma unroll
-                for (int r = 0; r < 8; ++r) x[r] = code_value(s, r);
-                w_inv(A.tab.Ph, x, y);  // lane (q = k0 + 4s, p = j): values over k
-                float4* d = reinterpret_cast<float4*>(tb + (k0 + 4 * s) * TSK + j * TSJ);
-                d[0] = make_float4(y[0], y[1], y[2], y[3]);
-                d[1] = make_float4(y[4], y[5], y[6], y[7]);
-            }
-            __syncwarp();
-            float z[2][8];
+                for (int r = 0; r < 8; ++r)
+                    tb[(lane + 32 * s) * 9 + r] =
+                        ((kb >> (8 * s + r)) & 1u) ? ((a[s][r] * qd + 12582912.0f) - 12582912.0f) * qu : 0.0f;
+            dense_inverse_f32(tb, A.tab.Ph);
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {  // lane (k = k0 + 4s, p = j): values over q
-                float x[8];
+            for (int s = 0; s < 2; ++s)
 #pragma unroll
-                for (int q = 0; q < 8; ++q) x[q] = tb[q * TSK + j * TSJ + k0 + 4 * s];
-                w_inv(A.tab.Ph, x, z[s]);
-            }
-            __syncwarp();
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                float4* d = reinterpret_cast<float4*>(tb + (k0 + 4 * s) * TSK + j * TSJ);
-                d[0] = make_float4(z[s][0], z[s][1], z[s][2], z[s][3]);
-                d[1] = make_float4(z[s][4], z[s][5], z[s][6], z[s][7]);
-            }
-            __syncwarp();
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {  // lane (k = k0 + 4s, j): values over p
-                float x[8];
-#pragma unroll
-                for (int pp = 0; pp < 8; ++pp) x[pp] = tb[(k0 + 4 * s) * TSK + pp * TSJ + j];
-                w_inv(A.tab.Ph, x, vh[s]);
-            }
+                for (int i = 0; i < 8; ++i) vh[s][i] = tb[(lane + 32 * s) * 9 + i];
             __syncwarp();
         }
 
@@ -739,13 +858,23 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 5) reduce_warp_kernel(con
                     const float ph = d.h * d.h;
                     const float pl = fmaf(d.h, d.l + d.l, fmaf(d.h, d.h, -ph));
                     df_fma_acc(ep, {wv.x, wv.y}, {ph, pl});
-                    const float ad = fabsf(d.h);
-                    const float adl = __uint_as_float(__float_as_uint(d.l) ^ (__float_as_uint(d.h) & 0x80000000u));
-                    ll = (ad > lh) ? adl : ((ad == lh) ? fmaxf(ll, adl) : ll);
-                    lh = fmaxf(lh, ad);
+                    lh = fmaxf(lh, fabsf(d.h));
                 }
             e2 = warp_sum_pair(df_norm(ep));
             const float LH = warp_max_nonneg(lh);
+            // Linf = max |d| over normalised pairs, ordered by (|dh|, low word signed like dh):
+            // only points whose |dh| is the element's largest can hold it
+            ll = -FLT_MAX;
+            if (lh == LH) {
+#pragma unroll
+                for (int s = 0; s < 2; ++s)
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const f2 d = df_sub({uh[s][i], ul[s][i]}, {vh[s][i], vl[s][i]});
+                        if (fabsf(d.h) == LH)
+                            ll = fmaxf(ll, __uint_as_float(__float_as_uint(d.l) ^ (__float_as_uint(d.h) & 0x80000000u)));
+                    }
+            }
             // largest low word among the lanes holding LH: order-preserving integer key of a float
             const uint32_t kb_ = (lh == LH) ? (__float_as_uint(ll) ^ ((__float_as_uint(ll) >> 31) ? 0xffffffffu : 0x80000000u)) : 0u;
             const uint32_t kmax = __reduce_max_sync(FULL, kb_);
@@ -807,39 +936,49 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 5) reduce_warp_kernel(con
             }
         }
     }
+    static_assert(kWarpTile == 64, "tile bookkeeping: two elements per lane");
     if (wid == 0) {
-        // tile aggregate, within-tile prefixes, decoupled look-back for the tile's code offset
-        const uint32_t c = (lane < nh) ? s_cnt[lane] : 0u;
+        // tile aggregate, within-tile prefixes (lane l: elements 2l, 2l + 1), decoupled look-back
+        const int ia = 2 * lane, ib = 2 * lane + 1;
+        const uint32_t ca = (ia < nh) ? (s_cnt[ia] & 0xffffu) : 0u, cb = (ib < nh) ? (s_cnt[ib] & 0xffffu) : 0u;
+        const uint32_t c = ca + cb;
         uint32_t incl = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t v = __shfl_up_sync(FULL, incl, o);
             if (lane >= o) incl += v;
         }
-        s_pre[lane] = incl - c;
+        s_pre[ia] = incl - c;
+        s_pre[ib] = incl - c + ca;
         const uint32_t tot = __shfl_sync(FULL, incl, 31);
         if (lane == 0) st_release_u64(&p.tile_state[tcur], (tcur == 0 ? kFlagPrefix : kFlagAggregate) | tot);
         const uint64_t excl = lookback_warp(p.tile_state, tcur, tot, status);
         if (lane == 0) s_excl = excl;
     } else if (wid == 1) {
-        // FP64 partials of the tile (fixed order) and the element report, one element per lane
+        // FP64 partials of the tile (fixed order) and the element report, elements lane, lane + 32
         double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-        if (lane < nh) {
-            const WStash st = s_res[lane];
-            const uint64_t ge = static_cast<uint64_t>(f) * E + e0 + lane;
-            const double J = p.jac[e0 + lane];
-            const double Sd = static_cast<double>(st.sh) + static_cast<double>(st.sl);
-            const double e2d = static_cast<double>(st.eh) + static_cast<double>(st.el);
-            v0 = J * e2d;
-            v1 = J * Sd;
-            v2 = static_cast<double>(st.lh) + static_cast<double>(st.ll);
-            v3 = static_cast<double>(st.umax);
-            p.umax_elem[ge] = st.umax;
-            if (p.elem_report) {
-                double* er = p.elem_report + 3 * ge;
-                er[0] = v0;
-                er[1] = v1;
-                er[2] = v2;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int il = lane + 32 * h;
+            if (il < nh) {
+                const WStash st = s_res[il];
+                const uint64_t ge = static_cast<uint64_t>(f) * E + e0 + il;
+                const double J = p.jac[e0 + il];
+                const double Sd = static_cast<double>(st.sh) + static_cast<double>(st.sl);
+                const double e2d = static_cast<double>(st.eh) + static_cast<double>(st.el);
+                const double x0 = J * e2d, x1 = J * Sd;
+                const double x2 = static_cast<double>(st.lh) + static_cast<double>(st.ll);
+                v0 += x0;
+                v1 += x1;
+                v2 = fmax(v2, x2);
+                v3 = fmax(v3, static_cast<double>(st.umax));
+                p.umax_elem[ge] = st.umax;
+                if (p.elem_report) {
+                    double* er = p.elem_report + 3 * ge;
+                    er[0] = x0;
+                    er[1] = x1;
+                    er[2] = x2;
+                }
             }
         }
 #pragma unroll
@@ -864,11 +1003,12 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 5) reduce_warp_kernel(con
     {
         const uint64_t excl = s_excl;
         for (int il = wid; il < nh; il += WPB) {
-            const uint32_t n = s_cnt[il];
+            const uint32_t n = s_cnt[il] & 0xffffu;
+            if (n > static_cast<uint32_t>(kWarpSlot)) continue;  // written directly
             const uint64_t gbyte = p.code_base + 2ull * (excl + s_pre[il]);
             if (gbyte + 2ull * n <= p.payload_cap) {
                 int16_t* dst = reinterpret_cast<int16_t*>(p.payload + gbyte);
-                const int16_t* src = stage_codes + il * WN3;
+                const int16_t* src = stage_codes + il * kWarpSlot;
                 for (uint32_t k = lane; k < n; k += 32) dst[k] = src[k];
             } else if (lane == 0 && n > 0) {
                 atomicOr(status, static_cast<unsigned>(SEMR_STATUS_OVERFLOW));
@@ -876,6 +1016,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 5) reduce_warp_kernel(con
         }
     }
     if (s_abort) break;
+    tag = (tag + 1 == 0xffffu) ? 0u : tag + 1;
     __syncwarp();
     }
     if (inflight) mbar_wait_bounded(bar, parity);  // after an abort: let a requested block land

@@ -122,3 +122,41 @@ def test_nonfinite_input_flagged():
     res, _ = run_gpu(fields, jac, lx, 1e-3)
     assert res.summary.status & semr.SEMR_STATUS_NONFINITE
     assert oracle.sections(res.payload)["counts"][0, 4] == 0
+
+
+def _mixed(n_elem, n_fields, seed):
+    """lx = 8 snapshot where every 7th element is white noise (hundreds of codes:
+    more than a staging slot holds, and the dense inverse) among smooth ones."""
+    fields, jac = make_case(n_elem, 8, n_fields, seed)
+    g = torch.Generator().manual_seed(seed + 99)
+    noisy = torch.arange(n_elem) % 7 == 3
+    noise = torch.randn(n_fields, int(noisy.sum()), 512, dtype=torch.float64, generator=g)
+    fields[:, noisy.cuda()] = noise.cuda()
+    return fields.contiguous(), jac
+
+
+def test_elements_with_many_codes_among_few():
+    """Codes of elements that keep more than a staging slot go straight to
+    their final place; the others are staged and copied per tile.  Both kinds
+    interleave across ragged tiles and two fields: payload bytes identical."""
+    fields, jac = _mixed(300, 2, seed=21)
+    res, rec = run_gpu(fields, jac, 8, 1e-3)
+    assert res.summary.status == 0
+    f_np, j_np = fields.cpu().numpy(), jac.cpu().numpy()
+    o = oracle.reduce(f_np, j_np, 1e-3, fragile_cap=100000)
+    counts = oracle.sections(res.payload)["counts"]
+    assert counts.max() > 100 and counts.min() < 10
+    compare_payloads(res.payload, o.payload, o.fragile)
+    compare_reports(f_np, j_np, rec, o, res.elem_report, res.summary, 8)
+
+
+def test_fp32_form_many_codes_decode():
+    """The FP32 form places every code: the payload decodes to its own
+    reconstruction (up to FP32 rounding)."""
+    fields, jac = _mixed(300, 2, seed=22)
+    res, rec = run_gpu(fields, jac, 8, 1e-3, precision=semr.SEMR_FP32)
+    assert res.summary.status == 0
+    assert oracle.sections(res.payload)["counts"].max() > 100
+    dec = semr.semr_decode(res.payload)
+    umax = np.abs(fields.cpu().numpy()).reshape(2, -1).max(axis=1)
+    assert np.all(np.abs(dec - rec).reshape(2, -1).max(axis=1) <= 1e-5 * umax)
