@@ -48,7 +48,7 @@ SEMR_HD inline uint64_t scratch_bytes(uint64_t tiles) {
 // field.  Scratch: [control][tile_state][tile_part][umax_elem f32 x n_fields *
 // n_elem][code staging: kWarpTile slots of kWarpSlot int16 codes per resident CTA,
 // at most kWarpStageCtas CTAs].  An element with more codes writes them directly.
-constexpr int kWarpTile = 64;
+constexpr int kWarpTile = 128;
 constexpr int kWarpSlot = 32;
 constexpr uint64_t kWarpStageCtas = 1024;
 constexpr uint64_t kWarpStageBytes = uint64_t(kWarpTile) * kWarpSlot * 2;  // per CTA

@@ -79,7 +79,11 @@ struct WSmem {
     static constexpr size_t stage = 4096;                 // one element block per warp
     static constexpr size_t off_tab = WPB * stage;        // Phi^T (hi, lo), A (hi, lo): 4 x 64 floats
     static constexpr size_t off_wq = off_tab + 1024;      // [8][64] weight products
-    static constexpr size_t off_warp = off_wq + (DF ? 8 : 4) * 512;
+    // per-element results of the tile; the FP32 form reads its weight products into registers
+    // once, so there they overlay the table
+    static constexpr size_t off_res = DF ? off_wq + 8 * 512 : off_wq;
+    static constexpr size_t off_warp = off_res + (DF ? sizeof(WStash) * kWarpTile
+                                                     : (sizeof(WStash) * kWarpTile > 4 * 512 ? sizeof(WStash) * kWarpTile : 4 * 512));
     // per warp
     static constexpr size_t o_tb = 0;
     static constexpr size_t tb_bytes = DF ? 8 * 8 * TSK2 : 4 * 8 * TSK;
@@ -378,6 +382,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
     }
     uint8_t* wb = smem + SM::off_warp + wid * SM::wbytes;
     uint8_t* stage = smem + wid * SM::stage;
+    WStash* s_res = reinterpret_cast<WStash*>(smem + SM::off_res);
     float* tb = reinterpret_cast<float*>(wb + SM::o_tb);
     float2* tb2 = reinterpret_cast<float2*>(wb + SM::o_tb);
     uint32_t* smask = reinterpret_cast<uint32_t*>(wb + SM::o_mask);
@@ -401,6 +406,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
             for (int i = 0; i < 8; ++i) w3f[s][i] = reinterpret_cast<const float*>(smem + SM::off_wq)[i * 64 + lane + 32 * s];
     }
     const float2* sWq2 = reinterpret_cast<const float2*>(smem + SM::off_wq);
+    if constexpr (!DF) __syncthreads();  // the weight table is overlaid by the results table
 
     const uint32_t E = A.n_elem, tpf = A.tiles_per_field, total_tiles = A.total_tiles;
     unsigned* counter = &p.ctl->tile_counter;
@@ -411,7 +417,6 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
     __shared__ uint32_t s_tile[2];  // current tile; the next one, claimed when the current one is computed
     __shared__ uint32_t s_cnt[kWarpTile];  // tile tag << 16 | code count; tag 0xffff: nothing yet
     __shared__ uint32_t s_pre[kWarpTile];
-    __shared__ WStash s_res[kWarpTile];
     __shared__ unsigned long long s_excl;
     __shared__ int s_abort;
     if (threadIdx.x == 0) {
@@ -936,29 +941,38 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
             }
         }
     }
-    static_assert(kWarpTile == 64, "tile bookkeeping: two elements per lane");
+    constexpr int EPL = kWarpTile / 32;  // tile bookkeeping: elements per lane
+    static_assert(kWarpTile % 32 == 0, "tile of whole warps");
     if (wid == 0) {
-        // tile aggregate, within-tile prefixes (lane l: elements 2l, 2l + 1), decoupled look-back
-        const int ia = 2 * lane, ib = 2 * lane + 1;
-        const uint32_t ca = (ia < nh) ? (s_cnt[ia] & 0xffffu) : 0u, cb = (ib < nh) ? (s_cnt[ib] & 0xffffu) : 0u;
-        const uint32_t c = ca + cb;
+        // tile aggregate, within-tile prefixes (lane l: elements EPL l .. EPL l + EPL - 1), look-back
+        uint32_t cl[EPL], c = 0;
+#pragma unroll
+        for (int h = 0; h < EPL; ++h) {
+            const int ii = EPL * lane + h;
+            cl[h] = (ii < nh) ? (s_cnt[ii] & 0xffffu) : 0u;
+            c += cl[h];
+        }
         uint32_t incl = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t v = __shfl_up_sync(FULL, incl, o);
             if (lane >= o) incl += v;
         }
-        s_pre[ia] = incl - c;
-        s_pre[ib] = incl - c + ca;
+        uint32_t run = incl - c;
+#pragma unroll
+        for (int h = 0; h < EPL; ++h) {
+            s_pre[EPL * lane + h] = run;
+            run += cl[h];
+        }
         const uint32_t tot = __shfl_sync(FULL, incl, 31);
         if (lane == 0) st_release_u64(&p.tile_state[tcur], (tcur == 0 ? kFlagPrefix : kFlagAggregate) | tot);
         const uint64_t excl = lookback_warp(p.tile_state, tcur, tot, status);
         if (lane == 0) s_excl = excl;
     } else if (wid == 1) {
-        // FP64 partials of the tile (fixed order) and the element report, elements lane, lane + 32
+        // FP64 partials of the tile (fixed order) and the element report, elements lane + 32 h
         double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < EPL; ++h) {
             const int il = lane + 32 * h;
             if (il < nh) {
                 const WStash st = s_res[il];
