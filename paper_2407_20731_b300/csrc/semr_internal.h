@@ -46,12 +46,14 @@ SEMR_HD inline uint64_t scratch_bytes(uint64_t tiles) {
 
 // Warp-per-element kernel (lx = 8): look-back tiles of kWarpTile elements of one
 // field.  Scratch: [control][tile_state][tile_part][umax_elem f32 x n_fields *
-// n_elem][code staging: kWarpTile slots of kWarpSlot int16 codes per resident CTA,
-// at most kWarpStageCtas CTAs].  An element with more codes writes them directly.
+// n_elem][staging per resident CTA (at most kWarpStageCtas): for two tiles, codes in
+// kWarpSlot-code slots per element and the within-tile prefixes].  An element with
+// more codes writes them directly.
 constexpr int kWarpTile = 128;
 constexpr int kWarpSlot = 32;
 constexpr uint64_t kWarpStageCtas = 1024;
-constexpr uint64_t kWarpStageBytes = uint64_t(kWarpTile) * kWarpSlot * 2;  // per CTA
+constexpr uint64_t kWarpStageBytes =
+    (2ull * kWarpTile * kWarpSlot * 2 + 2ull * (kWarpTile + 1) * 4 + 255) & ~255ull;  // per CTA
 SEMR_HD inline uint64_t warp_tiles(int64_t n_elem, int32_t n_fields) {
     return uint64_t(n_fields) * ((uint64_t(n_elem) + kWarpTile - 1) / kWarpTile);
 }

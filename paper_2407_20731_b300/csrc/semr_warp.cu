@@ -92,7 +92,7 @@ struct WSmem {
     static constexpr size_t o_kl = o_wpre + 64;           // kept list (mode, code)
     static constexpr size_t o_bar = o_kl + 96;
     static constexpr size_t wbytes = o_bar + 16;
-    static constexpr size_t bytes = off_warp + WPB * wbytes + 1024;  // + alignment slack
+    static constexpr size_t bytes = off_warp + WPB * wbytes + 512;  // + alignment slack
 };
 static_assert(8 * 8 * TSK2 >= 4 * 8 * TSK, "pair buffer holds the FP32 one");
 
@@ -357,7 +357,8 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
     constexpr bool DF = MODE != 0;
     using SM = WSmem<DF>;
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    // the stages start 512-byte aligned: the 64-byte swizzle permutes 16-byte chunks by address bits 7-8
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 511) & ~uintptr_t(511));
     const LaunchParams& p = A.p;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 
@@ -411,13 +412,17 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
     const uint32_t E = A.n_elem, tpf = A.tiles_per_field, total_tiles = A.total_tiles;
     unsigned* counter = &p.ctl->tile_counter;
     unsigned* status = &p.ctl->status;
-    int16_t* stage_codes = p.code_stage + static_cast<uint64_t>(blockIdx.x) * kWarpTile * kWarpSlot;
+    // this CTA's staging: codes [2 tile parities][kWarpTile][kWarpSlot], then the within-tile
+    // prefixes [2][kWarpTile + 1] (a tile's codes are placed one tile later)
+    uint8_t* stage_cta = reinterpret_cast<uint8_t*>(p.code_stage) + static_cast<uint64_t>(blockIdx.x) * kWarpStageBytes;
+    int16_t* stage_codes = reinterpret_cast<int16_t*>(stage_cta);
+    uint32_t* stage_pre = reinterpret_cast<uint32_t*>(stage_cta + 2ull * kWarpTile * kWarpSlot * 2);
 
     // tiles: kWarpTile consecutive elements of one field; warp w takes elements w, w + 4, ...
     __shared__ uint32_t s_tile[2];  // current tile; the next one, claimed when the current one is computed
     __shared__ uint32_t s_cnt[kWarpTile];  // tile tag << 16 | code count; tag 0xffff: nothing yet
-    __shared__ uint32_t s_pre[kWarpTile];
     __shared__ unsigned long long s_excl;
+    __shared__ double s_wpart[WPB][4];  // per-warp partials of the tile
     __shared__ int s_abort;
     if (threadIdx.x == 0) {
         s_tile[0] = atomicAdd(counter, 1u);
@@ -437,7 +442,26 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
     uint32_t tag = 0;       // tags the counts of the current tile (0 .. 0xfffe, then wraps)
     bool inflight = false;  // a block is on its way into this warp's stage
     unsigned recomputed = 0;
+    uint32_t t_prev = 0xffffffffu;  // this CTA's previous tile, whose codes are still staged
+    int nh_prev = 0, par = 0;       // its element count; staging parity of the current tile
+    uint32_t tot_prev = 0;          // warp 0: its code count
 
+    // Copy the staged codes of a tile (staging parity pp, nhp elements) to code_base + 2 (excl + prefix).
+    auto place_codes = [&](int pp, int nhp, uint64_t excl) {
+        const uint32_t* pre = stage_pre + pp * (kWarpTile + 1);
+        for (int il = wid; il < nhp; il += WPB) {
+            const uint32_t b = pre[il], n = pre[il + 1] - b;
+            if (n > static_cast<uint32_t>(kWarpSlot)) continue;  // written directly
+            const uint64_t gbyte = p.code_base + 2ull * (excl + b);
+            if (gbyte + 2ull * n <= p.payload_cap) {
+                int16_t* dst = reinterpret_cast<int16_t*>(p.payload + gbyte);
+                const int16_t* src = stage_codes + (pp * kWarpTile + il) * kWarpSlot;
+                for (uint32_t k = lane; k < n; k += 32) dst[k] = src[k];
+            } else if (lane == 0 && n > 0) {
+                atomicOr(status, static_cast<unsigned>(SEMR_STATUS_OVERFLOW));
+            }
+        }
+    };
     for (;;) {
     // Tiles are claimed only once the previous one is computed, so they start in about
     // the order of their claims and a look-back never waits for a tile not yet begun.
@@ -460,7 +484,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
         }
         parity ^= 1u;
         inflight = false;
-        int16_t* scodes = stage_codes + il * kWarpSlot;  // this element's first codes (global, L2-resident)
+        int16_t* scodes = stage_codes + (par * kWarpTile + il) * kWarpSlot;  // first codes (global, L2-resident)
 
         // ---- the lane's two pencils, split into floats with integer instructions
         float uh[2][8], ul[2][8];
@@ -944,7 +968,9 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
     constexpr int EPL = kWarpTile / 32;  // tile bookkeeping: elements per lane
     static_assert(kWarpTile % 32 == 0, "tile of whole warps");
     if (wid == 0) {
-        // tile aggregate, within-tile prefixes (lane l: elements EPL l .. EPL l + EPL - 1), look-back
+        // tile aggregate and within-tile prefixes (lane l: elements EPL l .. EPL l + EPL - 1),
+        // published now; the look-back runs one tile later (for tile t_prev here), when the tiles
+        // before it have almost always finished, so it rarely waits
         uint32_t cl[EPL], c = 0;
 #pragma unroll
         for (int h = 0; h < EPL; ++h) {
@@ -958,80 +984,90 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
             const uint32_t v = __shfl_up_sync(FULL, incl, o);
             if (lane >= o) incl += v;
         }
+        uint32_t* pre = stage_pre + par * (kWarpTile + 1);
         uint32_t run = incl - c;
 #pragma unroll
         for (int h = 0; h < EPL; ++h) {
-            s_pre[EPL * lane + h] = run;
+            pre[EPL * lane + h] = run;
             run += cl[h];
         }
         const uint32_t tot = __shfl_sync(FULL, incl, 31);
-        if (lane == 0) st_release_u64(&p.tile_state[tcur], (tcur == 0 ? kFlagPrefix : kFlagAggregate) | tot);
-        const uint64_t excl = lookback_warp(p.tile_state, tcur, tot, status);
-        if (lane == 0) s_excl = excl;
-    } else if (wid == 1) {
-        // FP64 partials of the tile (fixed order) and the element report, elements lane + 32 h
-        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-#pragma unroll
-        for (int h = 0; h < EPL; ++h) {
-            const int il = lane + 32 * h;
-            if (il < nh) {
-                const WStash st = s_res[il];
-                const uint64_t ge = static_cast<uint64_t>(f) * E + e0 + il;
-                const double J = p.jac[e0 + il];
-                const double Sd = static_cast<double>(st.sh) + static_cast<double>(st.sl);
-                const double e2d = static_cast<double>(st.eh) + static_cast<double>(st.el);
-                const double x0 = J * e2d, x1 = J * Sd;
-                const double x2 = static_cast<double>(st.lh) + static_cast<double>(st.ll);
-                v0 += x0;
-                v1 += x1;
-                v2 = fmax(v2, x2);
-                v3 = fmax(v3, static_cast<double>(st.umax));
-                p.umax_elem[ge] = st.umax;
-                if (p.elem_report) {
-                    double* er = p.elem_report + 3 * ge;
-                    er[0] = x0;
-                    er[1] = x1;
-                    er[2] = x2;
-                }
+        if (lane == 0) {
+            pre[kWarpTile] = tot;
+            st_release_u64(&p.tile_state[tcur], (tcur == 0 ? kFlagPrefix : kFlagAggregate) | tot);
+        }
+        if (t_prev != 0xffffffffu) {
+            const uint64_t excl = lookback_warp(p.tile_state, t_prev, tot_prev, status);
+            if (lane == 0) s_excl = excl;
+        }
+        tot_prev = tot;
+    } else if (wid == 2 && lane == 0) {
+        s_tile[0] = s_tile[1];
+    }
+    {
+        // every warp: FP64 partials and element report of its own elements (lane k: element
+        // wid + 4k), so the FP64 conversions run on all four SMSPs' FP64 units at once
+        static_assert(kWarpTile == 32 * WPB, "one element of the tile per lane of each warp");
+        double v0 = 0.0, v1 = 0.0;
+        unsigned long long m2 = 0ull, m3 = 0ull;  // maxima of non-negative doubles as bit patterns
+        const int il = wid + WPB * lane;
+        if (il < nh) {
+            const WStash st = s_res[il];
+            const uint64_t ge = static_cast<uint64_t>(f) * E + e0 + il;
+            const double J = p.jac[e0 + il];
+            const double Sd = static_cast<double>(st.sh) + static_cast<double>(st.sl);
+            const double e2d = static_cast<double>(st.eh) + static_cast<double>(st.el);
+            v0 = J * e2d;
+            v1 = J * Sd;
+            const double x2 = static_cast<double>(st.lh) + static_cast<double>(st.ll);
+            m2 = static_cast<unsigned long long>(__double_as_longlong(x2));
+            m3 = static_cast<unsigned long long>(__double_as_longlong(static_cast<double>(st.umax)));
+            p.umax_elem[ge] = st.umax;
+            if (p.elem_report) {
+                double* er = p.elem_report + 3 * ge;
+                er[0] = v0;
+                er[1] = v1;
+                er[2] = x2;
             }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             v0 += __shfl_down_sync(FULL, v0, o);
             v1 += __shfl_down_sync(FULL, v1, o);
-            v2 = fmax(v2, __shfl_down_sync(FULL, v2, o));
-            v3 = fmax(v3, __shfl_down_sync(FULL, v3, o));
+            m2 = max(m2, __shfl_down_sync(FULL, m2, o));
+            m3 = max(m3, __shfl_down_sync(FULL, m3, o));
         }
         if (lane == 0) {
-            double* tp = p.tile_part + 4ull * tcur;
-            tp[0] = v0;
-            tp[1] = v1;
-            tp[2] = v2;
-            tp[3] = v3;
+            s_wpart[wid][0] = v0;
+            s_wpart[wid][1] = v1;
+            s_wpart[wid][2] = __longlong_as_double(static_cast<long long>(m2));
+            s_wpart[wid][3] = __longlong_as_double(static_cast<long long>(m3));
         }
-    } else if (wid == 2 && lane == 0) {
-        s_tile[0] = s_tile[1];
     }
     __syncthreads();
-    // codes of this warp's elements at code_base + 2 (tile prefix + within-tile prefix)
-    {
-        const uint64_t excl = s_excl;
-        for (int il = wid; il < nh; il += WPB) {
-            const uint32_t n = s_cnt[il] & 0xffffu;
-            if (n > static_cast<uint32_t>(kWarpSlot)) continue;  // written directly
-            const uint64_t gbyte = p.code_base + 2ull * (excl + s_pre[il]);
-            if (gbyte + 2ull * n <= p.payload_cap) {
-                int16_t* dst = reinterpret_cast<int16_t*>(p.payload + gbyte);
-                const int16_t* src = stage_codes + il * kWarpSlot;
-                for (uint32_t k = lane; k < n; k += 32) dst[k] = src[k];
-            } else if (lane == 0 && n > 0) {
-                atomicOr(status, static_cast<unsigned>(SEMR_STATUS_OVERFLOW));
-            }
-        }
+    if (threadIdx.x == 0) {  // tile partials: the warps' partials in a fixed order
+        double* tp = p.tile_part + 4ull * tcur;
+        tp[0] = ((s_wpart[0][0] + s_wpart[1][0]) + s_wpart[2][0]) + s_wpart[3][0];
+        tp[1] = ((s_wpart[0][1] + s_wpart[1][1]) + s_wpart[2][1]) + s_wpart[3][1];
+        tp[2] = fmax(fmax(s_wpart[0][2], s_wpart[1][2]), fmax(s_wpart[2][2], s_wpart[3][2]));
+        tp[3] = fmax(fmax(s_wpart[0][3], s_wpart[1][3]), fmax(s_wpart[2][3], s_wpart[3][3]));
     }
+    if (t_prev != 0xffffffffu) place_codes(par ^ 1, nh_prev, s_excl);  // the previous tile's codes
+    t_prev = tcur;
+    nh_prev = nh;
+    par ^= 1;
     if (s_abort) break;
     tag = (tag + 1 == 0xffffu) ? 0u : tag + 1;
     __syncwarp();
+    }
+    // the last tile: its look-back, then its codes
+    if (t_prev != 0xffffffffu && !s_abort) {
+        if (wid == 0) {
+            const uint64_t excl = lookback_warp(p.tile_state, t_prev, tot_prev, status);
+            if (lane == 0) s_excl = excl;
+        }
+        __syncthreads();
+        place_codes(par ^ 1, nh_prev, s_excl);
     }
     if (inflight) mbar_wait_bounded(bar, parity);  // after an abort: let a requested block land
     if (lane == 0 && recomputed) atomicAdd(&p.ctl->recomputed, recomputed);
