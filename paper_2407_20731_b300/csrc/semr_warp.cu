@@ -190,6 +190,28 @@ __device__ __forceinline__ bool sq_ge(float g, f2 t) {
     return ph > t.h || (ph == t.h && pl >= t.l);
 }
 
+// Coefficient (s, r) = (w & 1, w >> 1) of a lane, for a warp-uniform mask word w.
+__device__ __forceinline__ float pick(const float (&a)[2][8], int w) {
+    switch (w) {
+        case 0: return a[0][0];
+        case 1: return a[1][0];
+        case 2: return a[0][1];
+        case 3: return a[1][1];
+        case 4: return a[0][2];
+        case 5: return a[1][2];
+        case 6: return a[0][3];
+        case 7: return a[1][3];
+        case 8: return a[0][4];
+        case 9: return a[1][4];
+        case 10: return a[0][5];
+        case 11: return a[1][5];
+        case 12: return a[0][6];
+        case 13: return a[1][6];
+        case 14: return a[0][7];
+        default: return a[1][7];
+    }
+}
+
 // Exclusive prefix of tile `tile` from its predecessors' states, as lookback_warp
 // computes it, without publishing anything (bounded; all 32 lanes).
 __device__ __forceinline__ uint64_t lookback_peek(const uint64_t* tile_state, uint64_t tile, unsigned* status) {
@@ -488,8 +510,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
 
         // ---- the lane's two pencils, split into floats with integer instructions
         float uh[2][8], ul[2][8];
-        uint32_t hmax = 0;
-        float umx = 0.0f;
+        uint32_t hmax = 0;  // largest high word of |u|
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             const uint8_t* row = stage + (lane + 32 * s) * 64;
@@ -507,7 +528,6 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
                         uh[s][i] = w_d2f_rz(lo[h], hi[h]);
                         ul[s][i] = 0.0f;
                     }
-                    umx = fmaxf(umx, fabsf(uh[s][i]));
                 }
             }
         }
@@ -525,7 +545,10 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
         };
         if constexpr (!DF) prefetch_next();
         const bool bad = __any_sync(FULL, hmax >= (static_cast<uint32_t>(1023 + 127) << 20));
-        const float umax_e = warp_max_nonneg(umx);
+        // max |u| of the element from its largest high word, rounded toward zero to float: it
+        // keeps the order of |u| (the finalize rereads the blocks that attain the field maximum)
+        // and is within a factor 1 + 2^-20 of it
+        const float umax_e = w_d2f_rz(0u, __reduce_max_sync(FULL, hmax));
 
         // ---- forward transform (FP32): i in registers, then j and k through the warp's buffer
         float a[2][8];
@@ -625,7 +648,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
                 // the table), 3 contractions, 2 more for the input split; every row of A has
                 // sum |A_pi| <= sqrt(2), so (|A|^3 |u|)_m <= 2^1.5 max|u|; a factor 2 of safety
                 constexpr float kMarg = (3.0f * (4 + 2) + 2.0f) * 5.9604645e-8f * 2.8285f * 2.0f;
-                const float M = kMarg * umax_e * 1.0000002f;
+                const float M = kMarg * umax_e * 1.000002f;
                 const float Mg = M + g * 2.4e-7f;  // plus the float rounding of g +- M
                 const float Mq = Mg * qd;
                 uint32_t amb = 0;
@@ -671,11 +694,6 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
                         amb &= ~(1u << bsel);
                     }
                 }
-            } else {
-#pragma unroll
-                for (int s = 0; s < 2; ++s)
-#pragma unroll
-                    for (int r = 0; r < 8; ++r) kb |= (fabsf(a[s][r]) >= g ? 1u : 0u) << (8 * s + r);
             }
         }
 
@@ -684,10 +702,19 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
         // ---- mask words: ballot over (slot s, row r) is word s + 2r (bit = lane)
 #pragma unroll
         for (int q4 = 0; q4 < 4; ++q4) {  // words 4 q4 .. 4 q4 + 3: (s, r) = (0, 2q4), (1, 2q4), (0, 2q4+1), (1, 2q4+1)
-            const uint32_t w0 = __ballot_sync(FULL, (kb >> (2 * q4)) & 1u);
-            const uint32_t w1 = __ballot_sync(FULL, (kb >> (8 + 2 * q4)) & 1u);
-            const uint32_t w2 = __ballot_sync(FULL, (kb >> (2 * q4 + 1)) & 1u);
-            const uint32_t w3 = __ballot_sync(FULL, (kb >> (8 + 2 * q4 + 1)) & 1u);
+            uint32_t w0, w1, w2, w3;
+            if constexpr (DF) {
+                w0 = __ballot_sync(FULL, (kb >> (2 * q4)) & 1u);
+                w1 = __ballot_sync(FULL, (kb >> (8 + 2 * q4)) & 1u);
+                w2 = __ballot_sync(FULL, (kb >> (2 * q4 + 1)) & 1u);
+                w3 = __ballot_sync(FULL, (kb >> (8 + 2 * q4 + 1)) & 1u);
+            } else {  // keep iff |a| >= g, the exact float threshold
+                const bool th = emode == 1;
+                w0 = __ballot_sync(FULL, th && fabsf(a[0][2 * q4]) >= g);
+                w1 = __ballot_sync(FULL, th && fabsf(a[1][2 * q4]) >= g);
+                w2 = __ballot_sync(FULL, th && fabsf(a[0][2 * q4 + 1]) >= g);
+                w3 = __ballot_sync(FULL, th && fabsf(a[1][2 * q4 + 1]) >= g);
+            }
             if (lane == 0) reinterpret_cast<uint4*>(smask)[q4] = make_uint4(w0, w1, w2, w3);
         }
         __syncwarp();
@@ -731,17 +758,11 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
         while (nzw) {
             const int wi = __ffs(nzw) - 1;
             nzw &= nzw - 1;
-            const int bsel = 8 * (wi & 1) + (wi >> 1);  // register (s, r) of word wi
-            if ((kb >> bsel) & 1u) {
-                float av = 0.0f;
-#pragma unroll
-                for (int s2 = 0; s2 < 2; ++s2)
-#pragma unroll
-                    for (int r2 = 0; r2 < 8; ++r2)
-                        if (8 * s2 + r2 == bsel) av = a[s2][r2];
-                const float yh = av * qd;
+            const uint32_t wd = smask[wi];
+            if ((wd >> lane) & 1u) {
+                const float yh = pick(a, wi) * qd;
                 const float c = (yh + 12582912.0f) - 12582912.0f;  // round half to even (|y| < 2^22)
-                const int rank = static_cast<int>(swpre[wi]) + __popc(smask[wi] & lt_mask);
+                const int rank = static_cast<int>(swpre[wi]) + __popc(wd & lt_mask);
                 if (rank < kWarpSlot) scodes[rank] = static_cast<int16_t>(c);
                 if (rank < WSPARSE) skl[rank] = make_int2(lane + 32 * wi, __float_as_int(c));
             }
@@ -771,15 +792,8 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
             while (fits && nz) {
                 const int wi = __ffs(nz) - 1;
                 nz &= nz - 1;
-                const int bsel = 8 * (wi & 1) + (wi >> 1);
-                if ((kb >> bsel) & 1u) {
-                    float av = 0.0f;
-#pragma unroll
-                    for (int s2 = 0; s2 < 2; ++s2)
-#pragma unroll
-                        for (int r2 = 0; r2 < 8; ++r2)
-                            if (8 * s2 + r2 == bsel) av = a[s2][r2];
-                    const float yh = av * qd;
+                if ((smask[wi] >> lane) & 1u) {
+                    const float yh = pick(a, wi) * qd;
                     const float c = (yh + 12582912.0f) - 12582912.0f;
                     dst[swpre[wi] + __popc(smask[wi] & lt_mask)] = static_cast<int16_t>(c);
                 }
@@ -847,7 +861,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
 #pragma unroll
                 for (int r = 0; r < 8; ++r)
                     tb[(lane + 32 * s) * 9 + r] =
-                        ((kb >> (8 * s + r)) & 1u) ? ((a[s][r] * qd + 12582912.0f) - 12582912.0f) * qu : 0.0f;
+                        ((smask[s + 2 * r] >> lane) & 1u) ? ((a[s][r] * qd + 12582912.0f) - 12582912.0f) * qu : 0.0f;
             dense_inverse_pairs(tb2, A.tab.Ph, A.tab.Pl);
 #pragma unroll
             for (int s = 0; s < 2; ++s)
@@ -864,7 +878,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
 #pragma unroll
                 for (int r = 0; r < 8; ++r)
                     tb[(lane + 32 * s) * 9 + r] =
-                        ((kb >> (8 * s + r)) & 1u) ? ((a[s][r] * qd + 12582912.0f) - 12582912.0f) * qu : 0.0f;
+                        ((smask[s + 2 * r] >> lane) & 1u) ? ((a[s][r] * qd + 12582912.0f) - 12582912.0f) * qu : 0.0f;
             dense_inverse_f32(tb, A.tab.Ph);
 #pragma unroll
             for (int s = 0; s < 2; ++s)
