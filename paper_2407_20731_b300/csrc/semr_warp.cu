@@ -811,41 +811,54 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
                 vl[s][i] = 0.0f;
             }
         if (n_e <= static_cast<uint32_t>(WSPARSE)) {
-            for (uint32_t tk = 0; tk < n_e; ++tk) {
-                const int2 kv = skl[tk];
-                const int m = kv.x, pp = m & 7, qq = (m >> 3) & 7, rr = m >> 6;
-                const float cs = __int_as_float(kv.y) * qu;  // c 2^s, exact
-                const float4* ph4 = reinterpret_cast<const float4*>(sPTh + pp * 8);
-                const float4 h0 = ph4[0], h1 = ph4[1];
-                const float colh[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
-                if constexpr (DF) {
-                    const float4* pl4 = reinterpret_cast<const float4*>(sPTl + pp * 8);
-                    const float4 l0 = pl4[0], l1 = pl4[1];
-                    const float coll[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
-                    const f2 fj = {sPTh[qq * 8 + j], sPTl[qq * 8 + j]};
+            if constexpr (DF) {
+                // kept modes grouped by their index p along i: u~(i) = sum_p B_p phi_p(x_i), with
+                // B_p = sum over the group of c 2^s phi_q(x_j) phi_r(x_k) for each pencil; phi_0 is
+                // constant, so the p = 0 group sets the pencil and costs nothing per point
+                uint32_t pmask = 0;
+                for (uint32_t tk = 0; tk < n_e; ++tk) pmask |= 1u << (skl[tk].x & 7);
+                for (uint32_t pm = pmask; pm; pm &= pm - 1) {
+                    const int pp = __ffs(pm) - 1;
+                    f2 B[2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+                    for (uint32_t tk = 0; tk < n_e; ++tk) {
+                        const int2 kv = skl[tk];
+                        if ((kv.x & 7) != pp) continue;
+                        const int qq = (kv.x >> 3) & 7, rr = kv.x >> 6;
+                        const float cs = __int_as_float(kv.y) * qu;  // c 2^s, exact
+                        const f2 fj = {sPTh[qq * 8 + j], sPTl[qq * 8 + j]};
 #pragma unroll
-                    for (int s = 0; s < 2; ++s) {
-                        const int kk = k0 + 4 * s;
-                        const f2 b = df_mulf(df_mul(fj, {sPTh[rr * 8 + kk], sPTl[rr * 8 + kk]}), cs);
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            f2 acc = {vh[s][i], vl[s][i]};
-                            df_fma_acc(acc, b, {colh[i], coll[i]});
-                            vh[s][i] = acc.h;
-                            vl[s][i] = acc.l;
+                        for (int s = 0; s < 2; ++s) {
+                            const int kk = k0 + 4 * s;
+                            B[s] = df_add(B[s], df_mulf(df_mul(fj, {sPTh[rr * 8 + kk], sPTl[rr * 8 + kk]}), cs));
                         }
                     }
-                } else {
-                    const float fj = sPTh[qq * 8 + j];
+                    if (pp == 0) {  // the first group: u~ = B_0 phi_0 at every point of the pencil
 #pragma unroll
-                    for (int s = 0; s < 2; ++s) {
-                        const float b = cs * fj * sPTh[rr * 8 + k0 + 4 * s];
+                        for (int s = 0; s < 2; ++s) {
+                            const f2 c0 = df_mul(B[s], {sPTh[0], sPTl[0]});
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) vh[s][i] = fmaf(b, colh[i], vh[s][i]);
+                            for (int i = 0; i < 8; ++i) {
+                                vh[s][i] = c0.h;
+                                vl[s][i] = c0.l;
+                            }
+                        }
+                    } else {
+                        const float4* ph4 = reinterpret_cast<const float4*>(sPTh + pp * 8);
+                        const float4* pl4 = reinterpret_cast<const float4*>(sPTl + pp * 8);
+                        const float4 h0 = ph4[0], h1 = ph4[1], l0 = pl4[0], l1 = pl4[1];
+                        const float colh[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+                        const float coll[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+#pragma unroll
+                        for (int s = 0; s < 2; ++s)
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                f2 acc = {vh[s][i], vl[s][i]};
+                                df_fma_acc(acc, B[s], {colh[i], coll[i]});
+                                vh[s][i] = acc.h;
+                                vl[s][i] = acc.l;
+                            }
                     }
                 }
-            }
-            if constexpr (DF) {
 #pragma unroll
                 for (int s = 0; s < 2; ++s)
 #pragma unroll
@@ -854,6 +867,22 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
                         vh[s][i] = nn.h;
                         vl[s][i] = nn.l;
                     }
+            } else {
+                for (uint32_t tk = 0; tk < n_e; ++tk) {
+                    const int2 kv = skl[tk];
+                    const int m = kv.x, pp = m & 7, qq = (m >> 3) & 7, rr = m >> 6;
+                    const float cs = __int_as_float(kv.y) * qu;  // c 2^s, exact
+                    const float4* ph4 = reinterpret_cast<const float4*>(sPTh + pp * 8);
+                    const float4 h0 = ph4[0], h1 = ph4[1];
+                    const float colh[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+                    const float fj = sPTh[qq * 8 + j];
+#pragma unroll
+                    for (int s = 0; s < 2; ++s) {
+                        const float b = cs * fj * sPTh[rr * 8 + k0 + 4 * s];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) vh[s][i] = fmaf(b, colh[i], vh[s][i]);
+                    }
+                }
             }
         } else if constexpr (DF) {
 #pragma unroll
