@@ -39,8 +39,8 @@ N_SIDE, LX, N_FIELDS = 64, 8, 4
 SEEDS = [10, 11, 12, 13]
 METRIC = "snapshot GB/s reduced (FP64 input ingested per second)"
 L2_NOTE = "inputs 4.29 GB per snapshot > 126 MB L2; no flush needed"
-KERNEL_SOURCES = ["paper_2407_20731_b300/csrc/semr_fast.cu", "paper_2407_20731_b300/csrc/semr_device.cuh",
-                  "paper_2407_20731_b300/csrc/semr_internal.h"]
+KERNEL_SOURCES = ["paper_2407_20731_b300/csrc/semr_warp.cu", "paper_2407_20731_b300/csrc/semr_fast.cu",
+                  "paper_2407_20731_b300/csrc/semr_device.cuh", "paper_2407_20731_b300/csrc/semr_internal.h"]
 # FP64 pipe of B300, nominal (the FP32 pipes run ~50x faster; FP64 mode runs on them)
 FP64_PIPE_TFLOPS_NOMINAL = 1.25
 
@@ -87,7 +87,8 @@ def measured_peaks() -> dict:
 def profiled_traffic(precision: str, cumulative: bool = False):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source (else None)."""
-    name = f"reduce_fast_kernel_{precision}{'_cumulative' if cumulative else ''}_lx8_64cube.md"
+    name = (f"reduce_fast_kernel_{precision}_cumulative_lx8_64cube.md" if cumulative
+            else f"reduce_warp_kernel_{precision}_lx8_64cube.md")
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
@@ -298,7 +299,8 @@ def run_semr(args):
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "peak_source": f"{peaks['source']} (MEASURED_PEAKS hbm_gbs, copy)",
-                "kernel": f"reduce_fast_kernel<{LX}, {'float pairs (FP64 accuracy)' if prec == semr.SEMR_FP64 else 'FP32'}"
+                "kernel": (f"reduce_fast_kernel<{LX}, " if args.cumulative else f"reduce_warp_kernel<{LX}, ")
+                          + ('float pairs (FP64 accuracy)' if prec == semr.SEMR_FP64 else 'FP32')
                           + (", cumulative" if args.cumulative else "") + ">",
                 "kernel_ms": round(kernel_ms, 4), "algorithmic_bytes_per_launch": algo}
     flops = algorithmic_flops(E, N_FIELDS)
