@@ -50,6 +50,7 @@ constexpr uint32_t kWaitHintNs = 1000000;
 constexpr unsigned FULL = 0xffffffffu;
 
 struct WTables {         // lx = 8 tables, as kernel parameters (constant bank)
+    float2 A2[64];         // analysis A[p][i] (hi), duplicated for the packed transforms
     float Ah[64], Al[64];  // analysis A[p][i] (hi, lo)
     float Ph[64], Pl[64];  // synthesis Phi[i][p] (hi, lo)
     float wh[8], wl[8];    // GLL weights (hi, lo)
@@ -78,7 +79,8 @@ template <bool DF>
 struct WSmem {
     static constexpr size_t stage = 4096;                 // one element block per warp
     static constexpr size_t off_tab = WPB * stage;        // Phi^T (hi, lo), A (hi, lo): 4 x 64 floats
-    static constexpr size_t off_wq = off_tab + 1024;      // [8][64] weight products
+    static constexpr size_t off_dup = off_tab + 1024;     // Phi^T duplicated (hi[, lo]): 64 float2 each
+    static constexpr size_t off_wq = off_dup + (DF ? 1024 : 512);  // weight products
     // per-element results of the tile; the FP32 form reads its weight products into registers
     // once, so there they overlay the table
     static constexpr size_t off_res = DF ? off_wq + 8 * 512 : off_wq;
@@ -147,16 +149,7 @@ __device__ __forceinline__ void w_split(uint32_t lo, uint32_t hi, float& uh, flo
     ul = m * __uint_as_float(static_cast<uint32_t>(max(ex, 0)) | (hi & 0x80000000u));
 }
 
-// 8-point even-odd folded transforms (FP32, tables from the constant bank).
-__device__ __forceinline__ void w_fwd(const float* __restrict__ A, const float (&x)[8], float (&y)[8]) {
-    const float e0 = x[0] + x[7], e1 = x[1] + x[6], e2 = x[2] + x[5], e3 = x[3] + x[4];
-    const float o0 = x[0] - x[7], o1 = x[1] - x[6], o2 = x[2] - x[5], o3 = x[3] - x[4];
-#pragma unroll
-    for (int p = 0; p < 8; p += 2) {
-        y[p] = fmaf(A[p * 8 + 3], e3, fmaf(A[p * 8 + 2], e2, fmaf(A[p * 8 + 1], e1, A[p * 8] * e0)));
-        y[p + 1] = fmaf(A[p * 8 + 11], o3, fmaf(A[p * 8 + 10], o2, fmaf(A[p * 8 + 9], o1, A[p * 8 + 8] * o0)));
-    }
-}
+// 8-point even-odd folded inverse transform (FP32, tables from the constant bank).
 __device__ __forceinline__ void w_inv(const float* __restrict__ Ph, const float (&x)[8], float (&y)[8]) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -166,6 +159,53 @@ __device__ __forceinline__ void w_inv(const float* __restrict__ Ph, const float 
         y[i] = e + o;
         y[7 - i] = e - o;
     }
+}
+
+// ---- packed FP32x2 arithmetic: the two pencils of a lane travel together as (s = 0, s = 1)
+__device__ __forceinline__ float2 f2dup(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+// 8-point even-odd folded forward transform of both pencils (coefficients duplicated (A, A)).
+__device__ __forceinline__ void w_fwd2(const float2* __restrict__ A2, const float2 (&x)[8], float2 (&y)[8]) {
+    const float2 e0 = f2add(x[0], x[7]), e1 = f2add(x[1], x[6]), e2 = f2add(x[2], x[5]), e3 = f2add(x[3], x[4]);
+    const float2 o0 = f2sub(x[0], x[7]), o1 = f2sub(x[1], x[6]), o2 = f2sub(x[2], x[5]), o3 = f2sub(x[3], x[4]);
+#pragma unroll
+    for (int p = 0; p < 8; p += 2) {
+        y[p] = f2fma(A2[p * 8 + 3], e3, f2fma(A2[p * 8 + 2], e2, f2fma(A2[p * 8 + 1], e1, f2mul(A2[p * 8], e0))));
+        y[p + 1] = f2fma(A2[p * 8 + 11], o3,
+                         f2fma(A2[p * 8 + 10], o2, f2fma(A2[p * 8 + 9], o1, f2mul(A2[p * 8 + 8], o0))));
+    }
+}
+
+// Float pairs (hi + lo) of both pencils at once.
+struct p2 {
+    float2 h, l;
+};
+__device__ __forceinline__ p2 two_sum2(float2 a, float2 b) {
+    const float2 s = f2add(a, b);
+    const float2 bb = f2sub(s, a);
+    return {s, f2add(f2sub(a, f2sub(s, bb)), f2sub(b, bb))};
+}
+__device__ __forceinline__ p2 fast_two_sum2(float2 a, float2 b) {
+    const float2 s = f2add(a, b);
+    return {s, f2sub(b, f2sub(s, a))};
+}
+__device__ __forceinline__ p2 df_norm2(p2 a) { return fast_two_sum2(a.h, a.l); }
+__device__ __forceinline__ p2 df_sub2(p2 a, p2 b) {
+    const p2 s = two_sum2(a.h, f2neg(b.h));
+    return fast_two_sum2(s.h, f2add(s.l, f2sub(a.l, b.l)));
+}
+// acc += a * b; the low word collects the rounding errors (renormalise with df_norm2).
+__device__ __forceinline__ void df_fma_acc2(p2& acc, p2 a, p2 b) {
+    const float2 pr = f2mul(a.h, b.h);
+    const float2 e = f2fma(a.h, b.l, f2fma(a.l, b.h, f2fma(a.h, b.h, f2neg(pr))));
+    const p2 s = two_sum2(acc.h, pr);
+    acc.h = s.h;
+    acc.l = f2add(acc.l, f2add(s.l, e));
 }
 
 // Pair sum over the warp (butterfly: every lane ends with the same value).
@@ -191,24 +231,24 @@ __device__ __forceinline__ bool sq_ge(float g, f2 t) {
 }
 
 // Coefficient (s, r) = (w & 1, w >> 1) of a lane, for a warp-uniform mask word w.
-__device__ __forceinline__ float pick(const float (&a)[2][8], int w) {
+__device__ __forceinline__ float pick(const float2 (&a)[8], int w) {
     switch (w) {
-        case 0: return a[0][0];
-        case 1: return a[1][0];
-        case 2: return a[0][1];
-        case 3: return a[1][1];
-        case 4: return a[0][2];
-        case 5: return a[1][2];
-        case 6: return a[0][3];
-        case 7: return a[1][3];
-        case 8: return a[0][4];
-        case 9: return a[1][4];
-        case 10: return a[0][5];
-        case 11: return a[1][5];
-        case 12: return a[0][6];
-        case 13: return a[1][6];
-        case 14: return a[0][7];
-        default: return a[1][7];
+        case 0: return a[0].x;
+        case 1: return a[0].y;
+        case 2: return a[1].x;
+        case 3: return a[1].y;
+        case 4: return a[2].x;
+        case 5: return a[2].y;
+        case 6: return a[3].x;
+        case 7: return a[3].y;
+        case 8: return a[4].x;
+        case 9: return a[4].y;
+        case 10: return a[5].x;
+        case 11: return a[5].y;
+        case 12: return a[6].x;
+        case 13: return a[6].y;
+        case 14: return a[7].x;
+        default: return a[7].y;
     }
 }
 
@@ -388,20 +428,30 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
     float* sPTl = sPTh + 64;
     float* sAh = sPTl + 64;  // [p][i] = A[p][i]
     float* sAl = sAh + 64;
+    float2* sPT2h = reinterpret_cast<float2*>(smem + SM::off_dup);  // [p][i] = (Phi[i][p], Phi[i][p])
+    float2* sPT2l = sPT2h + 64;                                        // FP64 mode: low words
     for (int t = threadIdx.x; t < 64; t += WPB * 32) {
         const int i = t >> 3, c = t & 7;  // Ph[t] = Phi[i][c]
         sPTh[c * 8 + i] = A.tab.Ph[t];
         sPTl[c * 8 + i] = A.tab.Pl[t];
         sAh[t] = A.tab.Ah[t];
         sAl[t] = A.tab.Al[t];
+        sPT2h[c * 8 + i] = f2dup(A.tab.Ph[t]);
+        if constexpr (DF) sPT2l[c * 8 + i] = f2dup(A.tab.Pl[t]);
     }
-    // quadrature weight products w_i w_j w_k at [i][P], P = j + 8k
+    // quadrature weight products w_i w_j w_k of point i of pencils P = lane and lane + 32 (P = j + 8k):
+    // FP64 mode [i][lane] = (hi0, hi1, lo0, lo1), FP32 form [i][P] (hi)
     for (int t = threadIdx.x; t < 512; t += WPB * 32) {
         const int i = t >> 6, P = t & 63, jj = P & 7, kk = P >> 3;
         const f2 w3 = df_mul({A.tab.wh[i], A.tab.wl[i]},
                              df_mul({A.tab.wh[jj], A.tab.wl[jj]}, {A.tab.wh[kk], A.tab.wl[kk]}));
-        if constexpr (DF) reinterpret_cast<float2*>(smem + SM::off_wq)[t] = make_float2(w3.h, w3.l);
-        else reinterpret_cast<float*>(smem + SM::off_wq)[t] = w3.h;
+        if constexpr (DF) {
+            float* wt = reinterpret_cast<float*>(smem + SM::off_wq) + (i * 32 + (P & 31)) * 4;
+            wt[P >> 5] = w3.h;
+            wt[2 + (P >> 5)] = w3.l;
+        } else {
+            reinterpret_cast<float*>(smem + SM::off_wq)[t] = w3.h;
+        }
     }
     uint8_t* wb = smem + SM::off_warp + wid * SM::wbytes;
     uint8_t* stage = smem + wid * SM::stage;
@@ -421,14 +471,13 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
     // this lane's pencils: (k, j) = (k0 + 4s, j) in nodal phases, (k0 + 4s, j) -> (q, p) in modal ones
     const int j = lane & 7, k0 = lane >> 3;
     const int sw = (lane >> 1) & 3;  // 64-byte swizzle of rows lane and lane + 32
-    float w3f[2][8];                 // FP32 form: weight products of this lane's points
+    float2 w3f[8];                   // FP32 form: weight products of this lane's points (s = 0, 1)
     if constexpr (!DF) {
+        const float* wt = reinterpret_cast<const float*>(smem + SM::off_wq);
 #pragma unroll
-        for (int s = 0; s < 2; ++s)
-#pragma unroll
-            for (int i = 0; i < 8; ++i) w3f[s][i] = reinterpret_cast<const float*>(smem + SM::off_wq)[i * 64 + lane + 32 * s];
+        for (int i = 0; i < 8; ++i) w3f[i] = make_float2(wt[i * 64 + lane], wt[i * 64 + lane + 32]);
     }
-    const float2* sWq2 = reinterpret_cast<const float2*>(smem + SM::off_wq);
+    const float4* sWq4 = reinterpret_cast<const float4*>(smem + SM::off_wq);
     if constexpr (!DF) __syncthreads();  // the weight table is overlaid by the results table
 
     const uint32_t E = A.n_elem, tpf = A.tiles_per_field, total_tiles = A.total_tiles;
@@ -509,8 +558,8 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
         int16_t* scodes = stage_codes + (par * kWarpTile + il) * kWarpSlot;  // first codes (global, L2-resident)
 
         // ---- the lane's two pencils, split into floats with integer instructions
-        float uh[2][8], ul[2][8];
-        uint32_t hmax = 0;  // largest high word of |u|
+        float2 uh[8], ul[8];  // (pencil lane, pencil lane + 32) at point i
+        uint32_t hmax = 0;    // largest high word of |u|
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             const uint8_t* row = stage + (lane + 32 * s) * 64;
@@ -522,11 +571,15 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
                 for (int h = 0; h < 2; ++h) {
                     const int i = 2 * c + h;
                     hmax = max(hmax, hi[h] & 0x7fffffffu);
-                    if constexpr (DF) {
-                        w_split(lo[h], hi[h], uh[s][i], ul[s][i]);
+                    float vh_, vl_ = 0.0f;
+                    if constexpr (DF) w_split(lo[h], hi[h], vh_, vl_);
+                    else vh_ = w_d2f_rz(lo[h], hi[h]);
+                    if (s == 0) {
+                        uh[i].x = vh_;
+                        ul[i].x = vl_;
                     } else {
-                        uh[s][i] = w_d2f_rz(lo[h], hi[h]);
-                        ul[s][i] = 0.0f;
+                        uh[i].y = vh_;
+                        ul[i].y = vl_;
                     }
                 }
             }
@@ -550,65 +603,55 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
         // and is within a factor 1 + 2^-20 of it
         const float umax_e = w_d2f_rz(0u, __reduce_max_sync(FULL, hmax));
 
-        // ---- forward transform (FP32): i in registers, then j and k through the warp's buffer
-        float a[2][8];
+        // ---- forward transform (FP32, both pencils packed): i in registers, then j and k through
+        // the warp's buffer.  Layout A [k0][j][p][s] (plane 176, row 20 floats) lets a lane read its
+        // two values with one 8-byte load; layout B [k][p][q'] (plane 96, row 12) with the columns
+        // in the order q' = (q & 3) 2 + (q >> 2) does the same for the last contraction.  Both are
+        // free of bank conflicts for the 16-byte stores and 8-byte loads of a warp.
+        float2 a2[8];  // coefficient r of modal pencils (q = k0 + 4s, p = j): mode lane + 32 s + 64 r
         {
-            float y[8];
+            float2 y[8];
+            w_fwd2(A.tab.A2, uh, y);
+            float4* d = reinterpret_cast<float4*>(tb + k0 * 176 + j * 20);
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                w_fwd(A.tab.Ah, uh[s], y);
-                float4* d = reinterpret_cast<float4*>(tb + (k0 + 4 * s) * TSK + j * TSJ);
-                d[0] = make_float4(y[0], y[1], y[2], y[3]);
-                d[1] = make_float4(y[4], y[5], y[6], y[7]);
-            }
+            for (int c = 0; c < 4; ++c) d[c] = make_float4(y[2 * c].x, y[2 * c].y, y[2 * c + 1].x, y[2 * c + 1].y);
             __syncwarp();
-            float z[2][8];
+            float2 x[8];
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {  // lane owns (k, p = j): values over j'
-                float x[8];
-#pragma unroll
-                for (int jj = 0; jj < 8; ++jj) x[jj] = tb[(k0 + 4 * s) * TSK + jj * TSJ + j];
-                w_fwd(A.tab.Ah, x, z[s]);
-            }
+            for (int jj = 0; jj < 8; ++jj) x[jj] = *reinterpret_cast<const float2*>(tb + k0 * 176 + jj * 20 + 2 * j);
+            w_fwd2(A.tab.A2, x, y);  // y[q] of pencils (k0, p = j) and (k0 + 4, p = j)
             __syncwarp();
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                float4* d = reinterpret_cast<float4*>(tb + (k0 + 4 * s) * TSK + j * TSJ);
-                d[0] = make_float4(z[s][0], z[s][1], z[s][2], z[s][3]);
-                d[1] = make_float4(z[s][4], z[s][5], z[s][6], z[s][7]);
-            }
+            float4* d0 = reinterpret_cast<float4*>(tb + k0 * 96 + j * 12);
+            float4* d1 = reinterpret_cast<float4*>(tb + (k0 + 4) * 96 + j * 12);
+            d0[0] = make_float4(y[0].x, y[4].x, y[1].x, y[5].x);
+            d0[1] = make_float4(y[2].x, y[6].x, y[3].x, y[7].x);
+            d1[0] = make_float4(y[0].y, y[4].y, y[1].y, y[5].y);
+            d1[1] = make_float4(y[2].y, y[6].y, y[3].y, y[7].y);
             __syncwarp();
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {  // lane owns (q = k0 + 4s, p = j): values over k
-                float x[8];
-#pragma unroll
-                for (int kk = 0; kk < 8; ++kk) x[kk] = tb[kk * TSK + j * TSJ + k0 + 4 * s];
-                w_fwd(A.tab.Ah, x, a[s]);
-            }
+            for (int kk = 0; kk < 8; ++kk) x[kk] = *reinterpret_cast<const float2*>(tb + kk * 96 + j * 12 + 2 * k0);
+            w_fwd2(A.tab.A2, x, a2);
         }
 
         // ---- element energy S: FP64 mode sum w u^2 at the nodes in pairs (Parseval's
         // identity in nodal form), FP32 form sum a^2 of the coefficients
         f2 S;
         if constexpr (DF) {
-            f2 sp = {0.0f, 0.0f};
+            p2 sp = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
 #pragma unroll
-            for (int s = 0; s < 2; ++s)
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const float2 w = sWq2[i * 64 + lane + 32 * s];
-                    const float ph = uh[s][i] * uh[s][i];
-                    const float pl = fmaf(uh[s][i], ul[s][i] + ul[s][i], fmaf(uh[s][i], uh[s][i], -ph));
-                    df_fma_acc(sp, {w.x, w.y}, {ph, pl});
-                }
-            S = warp_sum_pair(df_norm(sp));
+            for (int i = 0; i < 8; ++i) {
+                const float4 w = sWq4[i * 32 + lane];
+                const float2 ph = f2mul(uh[i], uh[i]);
+                const float2 pl = f2fma(uh[i], f2add(ul[i], ul[i]), f2fma(uh[i], uh[i], f2neg(ph)));
+                df_fma_acc2(sp, {make_float2(w.x, w.y), make_float2(w.z, w.w)}, {ph, pl});
+            }
+            sp = df_norm2(sp);
+            S = warp_sum_pair(df_add({sp.h.x, sp.l.x}, {sp.h.y, sp.l.y}));
         } else {
-            float sp = 0.0f;
+            float2 sp = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int s = 0; s < 2; ++s)
-#pragma unroll
-                for (int r = 0; r < 8; ++r) sp = fmaf(a[s][r], a[s][r], sp);
-            S = {warp_sum_f(sp), 0.0f};
+            for (int r = 0; r < 8; ++r) sp = f2fma(a2[r], a2[r], sp);
+            S = {warp_sum_f(sp.x + sp.y), 0.0f};
         }
 
         // ---- per element (warp-uniform): t = tau S, step s_e = floor((ex - 1) / 2) for
@@ -656,7 +699,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
                 for (int s = 0; s < 2; ++s)
 #pragma unroll
                     for (int r = 0; r < 8; ++r) {
-                        const float aa = fabsf(a[s][r]);
+                        const float aa = fabsf(s ? a2[r].y : a2[r].x);
                         const int b = 8 * s + r;
                         if (aa >= g + Mg) {  // surely kept: is its rounding decision sure too?
                             const float y = aa * qd;
@@ -689,7 +732,10 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
                         for (int s = 0; s < 2; ++s)
 #pragma unroll
                             for (int r = 0; r < 8; ++r)
-                                if (8 * s + r == bsel) a[s][r] = v;
+                                if (8 * s + r == bsel) {
+                                    if (s == 0) a2[r].x = v;
+                                    else a2[r].y = v;
+                                }
                         kb = keep ? (kb | (1u << bsel)) : (kb & ~(1u << bsel));
                         amb &= ~(1u << bsel);
                     }
@@ -710,10 +756,10 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
                 w3 = __ballot_sync(FULL, (kb >> (8 + 2 * q4 + 1)) & 1u);
             } else {  // keep iff |a| >= g, the exact float threshold
                 const bool th = emode == 1;
-                w0 = __ballot_sync(FULL, th && fabsf(a[0][2 * q4]) >= g);
-                w1 = __ballot_sync(FULL, th && fabsf(a[1][2 * q4]) >= g);
-                w2 = __ballot_sync(FULL, th && fabsf(a[0][2 * q4 + 1]) >= g);
-                w3 = __ballot_sync(FULL, th && fabsf(a[1][2 * q4 + 1]) >= g);
+                w0 = __ballot_sync(FULL, th && fabsf(a2[2 * q4].x) >= g);
+                w1 = __ballot_sync(FULL, th && fabsf(a2[2 * q4].y) >= g);
+                w2 = __ballot_sync(FULL, th && fabsf(a2[2 * q4 + 1].x) >= g);
+                w3 = __ballot_sync(FULL, th && fabsf(a2[2 * q4 + 1].y) >= g);
             }
             if (lane == 0) reinterpret_cast<uint4*>(smask)[q4] = make_uint4(w0, w1, w2, w3);
         }
@@ -760,7 +806,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
             nzw &= nzw - 1;
             const uint32_t wd = smask[wi];
             if ((wd >> lane) & 1u) {
-                const float yh = pick(a, wi) * qd;
+                const float yh = pick(a2, wi) * qd;
                 const float c = (yh + 12582912.0f) - 12582912.0f;  // round half to even (|y| < 2^22)
                 const int rank = static_cast<int>(swpre[wi]) + __popc(wd & lt_mask);
                 if (rank < kWarpSlot) scodes[rank] = static_cast<int16_t>(c);
@@ -793,7 +839,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
                 const int wi = __ffs(nz) - 1;
                 nz &= nz - 1;
                 if ((smask[wi] >> lane) & 1u) {
-                    const float yh = pick(a, wi) * qd;
+                    const float yh = pick(a2, wi) * qd;
                     const float c = (yh + 12582912.0f) - 12582912.0f;
                     dst[swpre[wi] + __popc(smask[wi] & lt_mask)] = static_cast<int16_t>(c);
                 }
@@ -801,15 +847,13 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
         }
         __syncwarp();
 
-        // ---- reconstruction u~ of the lane's nodal pencils (pairs in FP64 mode)
-        float vh[2][8], vl[2][8];
+        // ---- reconstruction u~ of the lane's nodal pencils (both packed; pairs in FP64 mode)
+        float2 vh[8], vl[8];
 #pragma unroll
-        for (int s = 0; s < 2; ++s)
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                vh[s][i] = 0.0f;
-                vl[s][i] = 0.0f;
-            }
+        for (int i = 0; i < 8; ++i) {
+            vh[i] = make_float2(0.0f, 0.0f);
+            vl[i] = make_float2(0.0f, 0.0f);
+        }
         if (n_e <= static_cast<uint32_t>(WSPARSE)) {
             if constexpr (DF) {
                 // kept modes grouped by their index p along i: u~(i) = sum_p B_p phi_p(x_i), with
@@ -819,68 +863,59 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
                 for (uint32_t tk = 0; tk < n_e; ++tk) pmask |= 1u << (skl[tk].x & 7);
                 for (uint32_t pm = pmask; pm; pm &= pm - 1) {
                     const int pp = __ffs(pm) - 1;
-                    f2 B[2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+                    f2 B0 = {0.0f, 0.0f}, B1 = {0.0f, 0.0f};
                     for (uint32_t tk = 0; tk < n_e; ++tk) {
                         const int2 kv = skl[tk];
                         if ((kv.x & 7) != pp) continue;
                         const int qq = (kv.x >> 3) & 7, rr = kv.x >> 6;
                         const float cs = __int_as_float(kv.y) * qu;  // c 2^s, exact
                         const f2 fj = {sPTh[qq * 8 + j], sPTl[qq * 8 + j]};
-#pragma unroll
-                        for (int s = 0; s < 2; ++s) {
-                            const int kk = k0 + 4 * s;
-                            B[s] = df_add(B[s], df_mulf(df_mul(fj, {sPTh[rr * 8 + kk], sPTl[rr * 8 + kk]}), cs));
-                        }
+                        B0 = df_add(B0, df_mulf(df_mul(fj, {sPTh[rr * 8 + k0], sPTl[rr * 8 + k0]}), cs));
+                        B1 = df_add(B1, df_mulf(df_mul(fj, {sPTh[rr * 8 + k0 + 4], sPTl[rr * 8 + k0 + 4]}), cs));
                     }
                     if (pp == 0) {  // the first group: u~ = B_0 phi_0 at every point of the pencil
+                        const f2 c0 = df_mul(B0, {sPTh[0], sPTl[0]}), c1 = df_mul(B1, {sPTh[0], sPTl[0]});
 #pragma unroll
-                        for (int s = 0; s < 2; ++s) {
-                            const f2 c0 = df_mul(B[s], {sPTh[0], sPTl[0]});
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) {
-                                vh[s][i] = c0.h;
-                                vl[s][i] = c0.l;
-                            }
+                        for (int i = 0; i < 8; ++i) {
+                            vh[i] = make_float2(c0.h, c1.h);
+                            vl[i] = make_float2(c0.l, c1.l);
                         }
                     } else {
-                        const float4* ph4 = reinterpret_cast<const float4*>(sPTh + pp * 8);
-                        const float4* pl4 = reinterpret_cast<const float4*>(sPTl + pp * 8);
-                        const float4 h0 = ph4[0], h1 = ph4[1], l0 = pl4[0], l1 = pl4[1];
-                        const float colh[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
-                        const float coll[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+                        const p2 Bp = {make_float2(B0.h, B1.h), make_float2(B0.l, B1.l)};
+                        const float4* ch4 = reinterpret_cast<const float4*>(sPT2h + pp * 8);
+                        const float4* cl4 = reinterpret_cast<const float4*>(sPT2l + pp * 8);
 #pragma unroll
-                        for (int s = 0; s < 2; ++s)
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) {
-                                f2 acc = {vh[s][i], vl[s][i]};
-                                df_fma_acc(acc, B[s], {colh[i], coll[i]});
-                                vh[s][i] = acc.h;
-                                vl[s][i] = acc.l;
-                            }
+                        for (int i2 = 0; i2 < 4; ++i2) {
+                            const float4 ch = ch4[i2], cl = cl4[i2];  // points 2 i2, 2 i2 + 1 (duplicated)
+                            p2 acc0 = {vh[2 * i2], vl[2 * i2]}, acc1 = {vh[2 * i2 + 1], vl[2 * i2 + 1]};
+                            df_fma_acc2(acc0, Bp, {make_float2(ch.x, ch.y), make_float2(cl.x, cl.y)});
+                            df_fma_acc2(acc1, Bp, {make_float2(ch.z, ch.w), make_float2(cl.z, cl.w)});
+                            vh[2 * i2] = acc0.h;
+                            vl[2 * i2] = acc0.l;
+                            vh[2 * i2 + 1] = acc1.h;
+                            vl[2 * i2 + 1] = acc1.l;
+                        }
                     }
                 }
 #pragma unroll
-                for (int s = 0; s < 2; ++s)
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const f2 nn = df_norm({vh[s][i], vl[s][i]});
-                        vh[s][i] = nn.h;
-                        vl[s][i] = nn.l;
-                    }
+                for (int i = 0; i < 8; ++i) {
+                    const p2 nn = df_norm2({vh[i], vl[i]});
+                    vh[i] = nn.h;
+                    vl[i] = nn.l;
+                }
             } else {
                 for (uint32_t tk = 0; tk < n_e; ++tk) {
                     const int2 kv = skl[tk];
                     const int m = kv.x, pp = m & 7, qq = (m >> 3) & 7, rr = m >> 6;
                     const float cs = __int_as_float(kv.y) * qu;  // c 2^s, exact
-                    const float4* ph4 = reinterpret_cast<const float4*>(sPTh + pp * 8);
-                    const float4 h0 = ph4[0], h1 = ph4[1];
-                    const float colh[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
-                    const float fj = sPTh[qq * 8 + j];
+                    const float fj = cs * sPTh[qq * 8 + j];
+                    const float2 b = make_float2(fj * sPTh[rr * 8 + k0], fj * sPTh[rr * 8 + k0 + 4]);
+                    const float4* ch4 = reinterpret_cast<const float4*>(sPT2h + pp * 8);
 #pragma unroll
-                    for (int s = 0; s < 2; ++s) {
-                        const float b = cs * fj * sPTh[rr * 8 + k0 + 4 * s];
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) vh[s][i] = fmaf(b, colh[i], vh[s][i]);
+                    for (int i2 = 0; i2 < 4; ++i2) {
+                        const float4 ch = ch4[i2];
+                        vh[2 * i2] = f2fma(b, make_float2(ch.x, ch.y), vh[2 * i2]);
+                        vh[2 * i2 + 1] = f2fma(b, make_float2(ch.z, ch.w), vh[2 * i2 + 1]);
                     }
                 }
             }
@@ -890,16 +925,14 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
 #pragma unroll
                 for (int r = 0; r < 8; ++r)
                     tb[(lane + 32 * s) * 9 + r] =
-                        ((smask[s + 2 * r] >> lane) & 1u) ? ((a[s][r] * qd + 12582912.0f) - 12582912.0f) * qu : 0.0f;
+                        ((smask[s + 2 * r] >> lane) & 1u) ? (((s ? a2[r].y : a2[r].x) * qd + 12582912.0f) - 12582912.0f) * qu : 0.0f;
             dense_inverse_pairs(tb2, A.tab.Ph, A.tab.Pl);
 #pragma unroll
-            for (int s = 0; s < 2; ++s)
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const float2 v = tb2[(lane + 32 * s) * 9 + i];
-                    vh[s][i] = v.x;
-                    vl[s][i] = v.y;
-                }
+            for (int i = 0; i < 8; ++i) {
+                const float2 v0 = tb2[lane * 9 + i], v1 = tb2[(lane + 32) * 9 + i];
+                vh[i] = make_float2(v0.x, v1.x);
+                vl[i] = make_float2(v0.y, v1.y);
+            }
             __syncwarp();
         } else {
 #pragma unroll
@@ -907,12 +940,10 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
 #pragma unroll
                 for (int r = 0; r < 8; ++r)
                     tb[(lane + 32 * s) * 9 + r] =
-                        ((smask[s + 2 * r] >> lane) & 1u) ? ((a[s][r] * qd + 12582912.0f) - 12582912.0f) * qu : 0.0f;
+                        ((smask[s + 2 * r] >> lane) & 1u) ? (((s ? a2[r].y : a2[r].x) * qd + 12582912.0f) - 12582912.0f) * qu : 0.0f;
             dense_inverse_f32(tb, A.tab.Ph);
 #pragma unroll
-            for (int s = 0; s < 2; ++s)
-#pragma unroll
-                for (int i = 0; i < 8; ++i) vh[s][i] = tb[(lane + 32 * s) * 9 + i];
+            for (int i = 0; i < 8; ++i) vh[i] = make_float2(tb[lane * 9 + i], tb[(lane + 32) * 9 + i]);
             __syncwarp();
         }
 
@@ -920,32 +951,31 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
         f2 e2;
         float lh = 0.0f, ll = 0.0f;  // Linf as a pair (|dh| first, then the signed low word)
         if constexpr (DF) {
-            f2 ep = {0.0f, 0.0f};
+            p2 ep = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
 #pragma unroll
-            for (int s = 0; s < 2; ++s)
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const f2 d = df_sub({uh[s][i], ul[s][i]}, {vh[s][i], vl[s][i]});
-                    const float2 wv = sWq2[i * 64 + lane + 32 * s];
-                    const float ph = d.h * d.h;
-                    const float pl = fmaf(d.h, d.l + d.l, fmaf(d.h, d.h, -ph));
-                    df_fma_acc(ep, {wv.x, wv.y}, {ph, pl});
-                    lh = fmaxf(lh, fabsf(d.h));
-                }
-            e2 = warp_sum_pair(df_norm(ep));
+            for (int i = 0; i < 8; ++i) {
+                const p2 d = df_sub2({uh[i], ul[i]}, {vh[i], vl[i]});
+                const float4 w = sWq4[i * 32 + lane];
+                const float2 ph = f2mul(d.h, d.h);
+                const float2 pl = f2fma(d.h, f2add(d.l, d.l), f2fma(d.h, d.h, f2neg(ph)));
+                df_fma_acc2(ep, {make_float2(w.x, w.y), make_float2(w.z, w.w)}, {ph, pl});
+                lh = fmaxf(lh, fmaxf(fabsf(d.h.x), fabsf(d.h.y)));
+            }
+            ep = df_norm2(ep);
+            e2 = warp_sum_pair(df_add({ep.h.x, ep.l.x}, {ep.h.y, ep.l.y}));
             const float LH = warp_max_nonneg(lh);
             // Linf = max |d| over normalised pairs, ordered by (|dh|, low word signed like dh):
             // only points whose |dh| is the element's largest can hold it
             ll = -FLT_MAX;
             if (lh == LH) {
 #pragma unroll
-                for (int s = 0; s < 2; ++s)
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const f2 d = df_sub({uh[s][i], ul[s][i]}, {vh[s][i], vl[s][i]});
-                        if (fabsf(d.h) == LH)
-                            ll = fmaxf(ll, __uint_as_float(__float_as_uint(d.l) ^ (__float_as_uint(d.h) & 0x80000000u)));
-                    }
+                for (int i = 0; i < 8; ++i) {
+                    const p2 d = df_sub2({uh[i], ul[i]}, {vh[i], vl[i]});
+                    if (fabsf(d.h.x) == LH)
+                        ll = fmaxf(ll, __uint_as_float(__float_as_uint(d.l.x) ^ (__float_as_uint(d.h.x) & 0x80000000u)));
+                    if (fabsf(d.h.y) == LH)
+                        ll = fmaxf(ll, __uint_as_float(__float_as_uint(d.l.y) ^ (__float_as_uint(d.h.y) & 0x80000000u)));
+                }
             }
             // largest low word among the lanes holding LH: order-preserving integer key of a float
             const uint32_t kb_ = (lh == LH) ? (__float_as_uint(ll) ^ ((__float_as_uint(ll) >> 31) ? 0xffffffffu : 0x80000000u)) : 0u;
@@ -954,16 +984,15 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
             ll = __uint_as_float((kmax >> 31) ? (kmax ^ 0x80000000u) : ~kmax);
             if (LH == 0.0f) ll = 0.0f;
         } else {
-            float ep = 0.0f, dm = 0.0f;
+            float2 ep = make_float2(0.0f, 0.0f);
+            float dm = 0.0f;
 #pragma unroll
-            for (int s = 0; s < 2; ++s)
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const float d = uh[s][i] - vh[s][i];
-                    ep = fmaf(w3f[s][i] * d, d, ep);
-                    dm = fmaxf(dm, fabsf(d));
-                }
-            e2 = {warp_sum_f(ep), 0.0f};
+            for (int i = 0; i < 8; ++i) {
+                const float2 d = f2sub(uh[i], vh[i]);
+                ep = f2fma(f2mul(w3f[i], d), d, ep);
+                dm = fmaxf(dm, fmaxf(fabsf(d.x), fabsf(d.y)));
+            }
+            e2 = {warp_sum_f(ep.x + ep.y), 0.0f};
             lh = warp_max_nonneg(dm);
         }
         if (p.write_recon && p.recon[f]) {
@@ -971,9 +1000,12 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
             for (int s = 0; s < 2; ++s) {
                 double2* dst = reinterpret_cast<double2*>(p.recon[f] + static_cast<uint64_t>(e) * WN3 + (lane + 32 * s) * 8);
 #pragma unroll
-                for (int i = 0; i < 8; i += 2)
-                    dst[i / 2] = make_double2(static_cast<double>(vh[s][i]) + static_cast<double>(vl[s][i]),
-                                              static_cast<double>(vh[s][i + 1]) + static_cast<double>(vl[s][i + 1]));
+                for (int i = 0; i < 8; i += 2) {
+                    const float h0 = s ? vh[i].y : vh[i].x, l0 = s ? vl[i].y : vl[i].x;
+                    const float h1 = s ? vh[i + 1].y : vh[i + 1].x, l1 = s ? vl[i + 1].y : vl[i + 1].x;
+                    dst[i / 2] = make_double2(static_cast<double>(h0) + static_cast<double>(l0),
+                                              static_cast<double>(h1) + static_cast<double>(l1));
+                }
             }
         }
 
@@ -1192,6 +1224,7 @@ WTables make_wtables() {
     double Am[64], Phi[64], w[8];
     basis_tables(8, Am, Phi, w);
     for (int i = 0; i < 64; ++i) {
+        t.A2[i] = make_float2(static_cast<float>(Am[i]), static_cast<float>(Am[i]));
         t.Ah[i] = static_cast<float>(Am[i]);
         t.Al[i] = static_cast<float>(Am[i] - static_cast<double>(t.Ah[i]));
         t.Ph[i] = static_cast<float>(Phi[i]);
