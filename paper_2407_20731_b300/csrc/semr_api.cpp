@@ -32,16 +32,20 @@ uint64_t tiles_per_field(int lx, int64_t n_elem) {
     return (uint64_t(n_elem) + t - 1) / t;
 }
 
-// Scratch of one reduction: the CTA kernels' layout, and at lx = 8 also the
-// warp kernel's (whichever of the two runs, the buffer holds it).
-uint64_t scratch_need(int lx, int64_t n_elem, int32_t n_fields) {
-    const uint64_t cta = scratch_bytes(uint64_t(n_fields) * tiles_per_field(lx, n_elem));
-    return lx == 8 ? std::max(cta, warp_scratch_bytes(n_elem, n_fields)) : cta;
-}
-
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 }  // namespace
+
+// Scratch of one reduction: the CTA kernels' layout, and at lx = 8 also the
+// warp kernel's (whichever of the two runs, the buffer holds it).
+uint64_t semr::scratch_need(int lx, int64_t n_elem, int32_t n_fields) {
+    const uint64_t cta = scratch_bytes(uint64_t(n_fields) * tiles_per_field(lx, n_elem));
+    return lx == 8 ? std::max(cta, warp_scratch_bytes(n_elem, n_fields)) : cta;
+}
+uint64_t semr::scratch_min(int lx, int64_t n_elem, int32_t n_fields) {
+    const uint64_t cta = scratch_bytes(uint64_t(n_fields) * tiles_per_field(lx, n_elem));
+    return lx == 8 ? std::max(cta, warp_scratch_min(n_elem, n_fields)) : cta;
+}
 
 extern "C" int semr_sizes_for(int32_t lx, int64_t n_elem, int32_t n_fields, double tau, semr_sizes* out) {
     if (!out) return SEMR_EINVAL;
@@ -88,7 +92,8 @@ extern "C" int semr_reduce_async_timed(const semr_fieldset* fs, const semr_mesh*
     if (reinterpret_cast<uintptr_t>(mesh->jac) & 7u) return SEMR_EINVAL;
     semr_sizes sz;
     semr_sizes_for(mesh->lx, mesh->n_elem, fs->n_fields, fs->tau, &sz);
-    if (out->scratch_bytes < sz.scratch_bytes || out->payload_cap < sz.code_base) return SEMR_EINVAL;
+    if (out->scratch_bytes < scratch_min(mesh->lx, mesh->n_elem, fs->n_fields) || out->payload_cap < sz.code_base)
+        return SEMR_EINVAL;
 
     LaunchParams p;
     std::memset(&p, 0, sizeof(p));
@@ -121,7 +126,7 @@ extern "C" int semr_reduce_async_timed(const semr_fieldset* fs, const semr_mesh*
     const bool warp = warp_applicable(p);
     uint64_t zero = scratch_zero_bytes(tiles);
     if (warp) {
-        split_scratch_warp(p, static_cast<uint8_t*>(out->scratch), mesh->n_elem, fs->n_fields);
+        split_scratch_warp(p, static_cast<uint8_t*>(out->scratch), out->scratch_bytes, mesh->n_elem, fs->n_fields);
         p.tile = kWarpTile;
         p.tiles_per_field = (int32_t)((uint64_t(mesh->n_elem) + kWarpTile - 1) / kWarpTile);
         zero = scratch_zero_bytes(warp_tiles(mesh->n_elem, fs->n_fields));

@@ -45,23 +45,34 @@ SEMR_HD inline uint64_t scratch_bytes(uint64_t tiles) {
 }
 
 // Warp-per-element kernel (lx = 8): look-back tiles of kWarpTile elements of one
-// field.  Scratch: [control][tile_state][tile_part][umax_elem f32 x n_fields *
-// n_elem][staging per resident CTA (at most kWarpStageCtas): for two tiles, codes in
-// kWarpSlot-code slots per element and the within-tile prefixes].  An element with
-// more codes writes them directly.
+// field, CTAs of kWarpCtaWarps warps.  Scratch: [control][tile_state][tile_part]
+// [umax_elem f32 x n_fields * n_elem][staging per resident CTA (at most
+// kWarpStageCtas): for two tiles, each warp's codes in an arena of kWarpArena int16,
+// the within-tile prefixes and the elements' arena offsets].  An element whose
+// codes do not fit its warp's arena writes them at their final place directly.
 constexpr int kWarpTile = 128;
-constexpr int kWarpSlot = 32;
+constexpr int kWarpCtaWarps = 4;
+constexpr int kWarpArena = 4096;
 constexpr uint64_t kWarpStageCtas = 1024;
 constexpr uint64_t kWarpStageBytes =
-    (2ull * kWarpTile * kWarpSlot * 2 + 2ull * (kWarpTile + 1) * 4 + 255) & ~255ull;  // per CTA
+    (2ull * kWarpCtaWarps * kWarpArena * 2 + 2ull * (kWarpTile + 1) * 4 + 2ull * kWarpTile * 4 + 255) & ~255ull;
 SEMR_HD inline uint64_t warp_tiles(int64_t n_elem, int32_t n_fields) {
     return uint64_t(n_fields) * ((uint64_t(n_elem) + kWarpTile - 1) / kWarpTile);
 }
-SEMR_HD inline uint64_t warp_stage_ctas(uint64_t tiles) { return tiles < kWarpStageCtas ? tiles : kWarpStageCtas; }
+// Bytes of the warp kernel's scratch before the staging (256-aligned).
+SEMR_HD inline uint64_t warp_scratch_head(int64_t n_elem, int32_t n_fields) {
+    const uint64_t t = warp_tiles(n_elem, n_fields);
+    return (scratch_bytes(t) + pad16(4ull * uint64_t(n_fields) * uint64_t(n_elem)) + 255) & ~uint64_t(255);
+}
+// Full warp-kernel scratch: staging for as many CTAs as may be resident (recommended size).
 SEMR_HD inline uint64_t warp_scratch_bytes(int64_t n_elem, int32_t n_fields) {
     const uint64_t t = warp_tiles(n_elem, n_fields);
-    const uint64_t head = (scratch_bytes(t) + pad16(4ull * uint64_t(n_fields) * uint64_t(n_elem)) + 255) & ~uint64_t(255);
-    return head + warp_stage_ctas(t) * kWarpStageBytes;
+    return warp_scratch_head(n_elem, n_fields) + (t < kWarpStageCtas ? t : kWarpStageCtas) * kWarpStageBytes;
+}
+// Smallest usable warp-kernel scratch: staging for one CTA (a smaller scratch buffer
+// limits the kernel's grid to the CTAs it can stage for).
+SEMR_HD inline uint64_t warp_scratch_min(int64_t n_elem, int32_t n_fields) {
+    return warp_scratch_head(n_elem, n_fields) + kWarpStageBytes;
 }
 // bytes that must be zero before each launch (control + tile states)
 SEMR_HD inline uint64_t scratch_zero_bytes(uint64_t tiles) { return kScratchControlBytes + pad16(8 * tiles); }
@@ -117,15 +128,24 @@ inline void split_scratch(LaunchParams& p, uint8_t* scratch, uint64_t tiles) {
     p.tile_part = reinterpret_cast<double*>(scratch + kScratchControlBytes + pad16(8 * tiles));
 }
 
-// Scratch split of the warp kernel (layout of warp_scratch_bytes).
-inline void split_scratch_warp(LaunchParams& p, uint8_t* scratch, int64_t n_elem, int32_t n_fields) {
+// Scratch split of the warp kernel (layout of warp_scratch_bytes) for a buffer of
+// `bytes` (at least warp_scratch_min): staging for as many CTAs as it holds.
+inline void split_scratch_warp(LaunchParams& p, uint8_t* scratch, uint64_t bytes, int64_t n_elem, int32_t n_fields) {
     const uint64_t t = warp_tiles(n_elem, n_fields);
     split_scratch(p, scratch, t);
     p.umax_elem = reinterpret_cast<float*>(scratch + scratch_bytes(t));
-    const uint64_t head = (scratch_bytes(t) + pad16(4ull * uint64_t(n_fields) * uint64_t(n_elem)) + 255) & ~uint64_t(255);
+    const uint64_t head = warp_scratch_head(n_elem, n_fields);
     p.code_stage = reinterpret_cast<int16_t*>(scratch + head);
-    p.stage_ctas = (int32_t)warp_stage_ctas(t);
+    uint64_t ctas = (bytes - head) / kWarpStageBytes;
+    if (ctas > kWarpStageCtas) ctas = kWarpStageCtas;
+    if (ctas > t) ctas = t;
+    p.stage_ctas = (int32_t)ctas;
 }
+
+// Scratch sizes of one reduction: recommended (every kernel at full occupancy) and
+// the smallest accepted (semr_api.cpp).
+uint64_t scratch_need(int lx, int64_t n_elem, int32_t n_fields);
+uint64_t scratch_min(int lx, int64_t n_elem, int32_t n_fields);
 
 // Work queue of a batched launch: items of one (lx, precision) group; item i
 // owns global tiles [tile_base[i], tile_base[i+1]) and fields

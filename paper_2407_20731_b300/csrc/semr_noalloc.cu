@@ -43,7 +43,9 @@ extern "C" int semr_reduce_async_noalloc(const semr_fieldset* fs, const semr_mes
     semr_sizes sz;
     int rc = semr_sizes_for(mesh->lx, mesh->n_elem, fs->n_fields, fs->tau, &sz);
     if (rc) return rc;
-    if (sz.scratch_bytes > SEMR_NOALLOC_SCRATCH_BYTES) return SEMR_EINVAL;  // beyond the fixed scratch
+    // beyond the fixed scratch (it may hold less than the recommended size: the lx = 8 kernel
+    // then runs on as many CTAs as the array can stage codes for)
+    if (semr::scratch_min(mesh->lx, mesh->n_elem, fs->n_fields) > SEMR_NOALLOC_SCRATCH_BYTES) return SEMR_EINVAL;
     void* scratch = nullptr;
     rc = scratch_address(&scratch);
     if (rc) return rc;

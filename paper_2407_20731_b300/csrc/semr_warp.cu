@@ -41,7 +41,7 @@ namespace semr {
 namespace {
 
 constexpr int WLX = 8, WNP = 64, WN3 = 512;
-constexpr int WPB = 4;               // warps per CTA
+constexpr int WPB = kWarpCtaWarps;   // warps per CTA
 constexpr int TSK = 104, TSJ = 12;   // FP32 transpose strides (plane, row) in floats
 constexpr int TSK2 = 72, TSJ2 = 9;   // float-pair transpose strides (dense inverse, FP64 mode)
 constexpr int WSPARSE = 10;          // sparse reconstruction up to this many kept modes
@@ -483,21 +483,26 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
     const uint32_t E = A.n_elem, tpf = A.tiles_per_field, total_tiles = A.total_tiles;
     unsigned* counter = &p.ctl->tile_counter;
     unsigned* status = &p.ctl->status;
-    // this CTA's staging: codes [2 tile parities][kWarpTile][kWarpSlot], then the within-tile
-    // prefixes [2][kWarpTile + 1] (a tile's codes are placed one tile later)
+    // this CTA's staging (a tile's codes are placed one tile later): codes [2 tile parities][warp]
+    // [kWarpArena], within-tile prefixes [2][kWarpTile + 1], arena offsets [2][kWarpTile]
     uint8_t* stage_cta = reinterpret_cast<uint8_t*>(p.code_stage) + static_cast<uint64_t>(blockIdx.x) * kWarpStageBytes;
     int16_t* stage_codes = reinterpret_cast<int16_t*>(stage_cta);
-    uint32_t* stage_pre = reinterpret_cast<uint32_t*>(stage_cta + 2ull * kWarpTile * kWarpSlot * 2);
+    uint32_t* stage_pre = reinterpret_cast<uint32_t*>(stage_cta + 2ull * WPB * kWarpArena * 2);
+    uint32_t* stage_off = stage_pre + 2 * (kWarpTile + 1);
+    constexpr uint32_t kDirect = 0xffffffffu;  // arena offset of an element written directly
 
     // tiles: kWarpTile consecutive elements of one field; warp w takes elements w, w + 4, ...
     __shared__ uint32_t s_tile[2];  // current tile; the next one, claimed when the current one is computed
     __shared__ uint32_t s_cnt[kWarpTile];  // tile tag << 16 | code count; tag 0xffff: nothing yet
     __shared__ unsigned long long s_excl;
+    __shared__ unsigned long long s_peek;  // a tile's exclusive prefix for directly written codes
+    __shared__ uint32_t s_peek_tag;        // that tile + 1 (0: none)
     __shared__ double s_wpart[WPB][4];  // per-warp partials of the tile
     __shared__ int s_abort;
     if (threadIdx.x == 0) {
         s_tile[0] = atomicAdd(counter, 1u);
         s_abort = 0;
+        s_peek_tag = 0;
     }
     for (int i = threadIdx.x; i < kWarpTile; i += WPB * 32) s_cnt[i] = 0xffff0000u;
     __syncthreads();
@@ -520,13 +525,14 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
     // Copy the staged codes of a tile (staging parity pp, nhp elements) to code_base + 2 (excl + prefix).
     auto place_codes = [&](int pp, int nhp, uint64_t excl) {
         const uint32_t* pre = stage_pre + pp * (kWarpTile + 1);
+        const int16_t* arena = stage_codes + (pp * WPB + wid) * kWarpArena;
         for (int il = wid; il < nhp; il += WPB) {
-            const uint32_t b = pre[il], n = pre[il + 1] - b;
-            if (n > static_cast<uint32_t>(kWarpSlot)) continue;  // written directly
+            const uint32_t b = pre[il], n = pre[il + 1] - b, off = stage_off[pp * kWarpTile + il];
+            if (off == kDirect) continue;  // written directly
             const uint64_t gbyte = p.code_base + 2ull * (excl + b);
             if (gbyte + 2ull * n <= p.payload_cap) {
                 int16_t* dst = reinterpret_cast<int16_t*>(p.payload + gbyte);
-                const int16_t* src = stage_codes + (pp * kWarpTile + il) * kWarpSlot;
+                const int16_t* src = arena + off;
                 for (uint32_t k = lane; k < n; k += 32) dst[k] = src[k];
             } else if (lane == 0 && n > 0) {
                 atomicOr(status, static_cast<unsigned>(SEMR_STATUS_OVERFLOW));
@@ -541,6 +547,8 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
     uint32_t f, e0;
     int nh;
     geom(tcur, f, e0, nh);
+    int16_t* arena = stage_codes + (par * WPB + wid) * kWarpArena;  // this warp's codes of the tile
+    uint32_t atop = 0;                                             // its fill (warp-uniform)
     for (int il = wid; il < nh; il += WPB) {
         const uint32_t e = e0 + static_cast<uint32_t>(il);
         if (!inflight && lane == 0) issue(f, e);
@@ -555,7 +563,6 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
         }
         parity ^= 1u;
         inflight = false;
-        int16_t* scodes = stage_codes + (par * kWarpTile + il) * kWarpSlot;  // first codes (global, L2-resident)
 
         // ---- the lane's two pencils, split into floats with integer instructions
         float2 uh[8], ul[8];  // (pencil lane, pencil lane + 32) at point i
@@ -765,6 +772,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
         }
         __syncwarp();
         uint32_t n_e;
+        bool staged;  // the element's codes fit the warp's arena (else they are written directly)
         {
             const uint32_t mw = (lane < 16) ? smask[lane] : 0u;
             const uint32_t c = __popc(mw);
@@ -787,6 +795,8 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
                 cdst[e] = static_cast<uint16_t>(n_e);
                 s_cnt[il] = (tag << 16) | n_e;
             }
+            staged = atop + n_e <= static_cast<uint32_t>(kWarpArena);
+            if (lane == 0) stage_off[par * kWarpTile + il] = staged ? atop : kDirect;
             if (e + 1 == E && lane < 16) {  // zero the padding after the step and count sections
                 const uint64_t se = 2ull * E;
                 if (se + lane < pad16(se)) {
@@ -809,15 +819,27 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
                 const float yh = pick(a2, wi) * qd;
                 const float c = (yh + 12582912.0f) - 12582912.0f;  // round half to even (|y| < 2^22)
                 const int rank = static_cast<int>(swpre[wi]) + __popc(wd & lt_mask);
-                if (rank < kWarpSlot) scodes[rank] = static_cast<int16_t>(c);
+                if (staged) arena[atop + rank] = static_cast<int16_t>(c);
                 if (rank < WSPARSE) skl[rank] = make_int2(lane + 32 * wi, __float_as_int(c));
             }
         }
-        if (n_e > static_cast<uint32_t>(kWarpSlot)) {
-            // more codes than the slot holds (rare): write them at their final place, which needs
-            // the tile's exclusive prefix and the counts of the tile's earlier elements; every such
-            // wait points to smaller element indices, so it ends
-            uint64_t before = lookback_peek(p.tile_state, tcur, status);
+        if (staged) {
+            atop += n_e;
+        } else {
+            // the warp's arena is full (extreme inputs only): write the codes at their final place,
+            // which needs the tile's exclusive prefix (computed once per tile) and the counts of the
+            // tile's earlier elements; every such wait points to smaller element indices, so it ends
+            uint64_t before;
+            if (s_peek_tag == tcur + 1u) {
+                before = s_peek;
+            } else {
+                before = lookback_peek(p.tile_state, tcur, status);
+                if (lane == 0) {
+                    s_peek = before;
+                    __threadfence_block();
+                    s_peek_tag = tcur + 1u;
+                }
+            }
             uint32_t part = 0;
             for (int jj = lane; jj < il; jj += 32) {
                 uint32_t v = 0;
