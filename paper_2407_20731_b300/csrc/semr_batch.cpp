@@ -21,16 +21,20 @@ using namespace semr;
 
 namespace {
 
+// Variant tile = kWarpTile: the warp-per-element kernel (lx = 8); others: the CTA kernel.
 struct Group {
     int lx = 0, precision = 0, tile = 0;
     std::vector<int> items;       // indices into the caller's item array
     float tuned_ms[4] = {0, 0, 0, 0};
     int variants[4] = {0, 0, 0, 0};
     int n_variants = 0;
+    bool warp_ok = false;         // every item fits the warp kernel
     // workspace offsets
     uint64_t off_desc = 0, off_tile_base = 0, off_field_base = 0, off_zero = 0, zero_bytes = 0;
+    uint64_t off_maps = 0, off_stage = 0, stage_ctas = 0;  // warp kernel
     uint64_t total_tiles = 0;
     uint32_t total_fields = 0;
+    bool warp() const { return tile == kWarpTile; }
 };
 
 uint64_t align256(uint64_t b) { return (b + 255) & ~uint64_t(255); }
@@ -105,10 +109,18 @@ int build_workspace(semr_batch* b, cudaStream_t st) {
         off = align256(off + 8 * (n + 1));
         G.off_field_base = off;
         off = align256(off + 4 * (n + 1));
-        G.off_zero = off;  // [counter 256][per item: control 256 + states]
-        off += 256;
         G.total_tiles = 0;
         G.total_fields = 0;
+        for (int idx : G.items) {
+            G.total_tiles += item_tiles(b->items[idx], G.tile);
+            G.total_fields += (uint32_t)b->items[idx].fs.n_fields;
+        }
+        if (G.warp()) {  // tensor maps, one per (item, field)
+            G.off_maps = off;
+            off = align256(off + kTensorMapBytes * G.total_fields);
+        }
+        G.off_zero = off;  // [counter 256][per item: control 256 + states]
+        off += 256;
         for (int idx : G.items) {
             const uint64_t t = item_tiles(b->items[idx], G.tile);
             off += kScratchControlBytes + pad16(8 * t);
@@ -116,6 +128,13 @@ int build_workspace(semr_batch* b, cudaStream_t st) {
         G.zero_bytes = off - G.off_zero;
         off = align256(off);
         for (int idx : G.items) off = align256(off + 32 * item_tiles(b->items[idx], G.tile));  // partials
+        if (G.warp()) {  // per-item element maxima, then one code staging for the group
+            for (int idx : G.items)
+                off = align256(off + 4ull * uint64_t(b->items[idx].mesh.n_elem) * b->items[idx].fs.n_fields);
+            G.stage_ctas = std::min<uint64_t>(G.total_tiles, kWarpStageCtas);
+            G.off_stage = off;
+            off = align256(off + G.stage_ctas * kWarpStageBytes);
+        }
     }
     b->ws_bytes = std::max<uint64_t>(off, 256);
     if (cudaMalloc(reinterpret_cast<void**>(&b->ws), b->ws_bytes) != cudaSuccess) return SEMR_ENOMEM;
@@ -127,6 +146,10 @@ int build_workspace(semr_batch* b, cudaStream_t st) {
         std::vector<uint32_t> fb(n + 1, 0);
         uint64_t zoff = G.off_zero + 256;
         uint64_t poff = align256(G.off_zero + G.zero_bytes);
+        uint64_t uoff = poff;  // warp kernel: element maxima after the partials
+        if (G.warp())
+            for (int idx : G.items) uoff = align256(uoff + 32 * item_tiles(b->items[idx], G.tile));
+        std::vector<uint8_t> maps(G.warp() ? kTensorMapBytes * G.total_fields : 0);
         descs[g].resize(n);
         for (size_t i = 0; i < n; ++i) {
             const semr_batch_item& it = b->items[G.items[i]];
@@ -138,6 +161,13 @@ int build_workspace(semr_batch* b, cudaStream_t st) {
             p.ctl = reinterpret_cast<ScratchControl*>(b->ws + zoff);
             p.tile_state = reinterpret_cast<uint64_t*>(b->ws + zoff + kScratchControlBytes);
             p.tile_part = reinterpret_cast<double*>(b->ws + poff);
+            if (G.warp()) {
+                p.umax_elem = reinterpret_cast<float*>(b->ws + uoff);
+                uoff = align256(uoff + 4ull * uint64_t(it.mesh.n_elem) * it.fs.n_fields);
+                p.code_stage = reinterpret_cast<int16_t*>(b->ws + G.off_stage);
+                p.stage_ctas = (int32_t)G.stage_ctas;
+                if (warp_encode_maps(p, maps.data() + kTensorMapBytes * fb[i]) != 0) return SEMR_EUNSUPPORTED;
+            }
             zoff += kScratchControlBytes + pad16(8 * t);
             poff = align256(poff + 32 * t);
             tb[i + 1] = tb[i] + t;
@@ -152,6 +182,9 @@ int build_workspace(semr_batch* b, cudaStream_t st) {
             cudaMemcpyAsync(b->ws + G.off_field_base, fb.data(), 4 * (n + 1), cudaMemcpyHostToDevice, st) !=
                 cudaSuccess)
             return SEMR_ECUDA;
+        if (G.warp() && cudaMemcpyAsync(b->ws + G.off_maps, maps.data(), maps.size(), cudaMemcpyHostToDevice, st) !=
+                            cudaSuccess)
+            return SEMR_ECUDA;
     }
     return cudaStreamSynchronize(st) == cudaSuccess ? SEMR_OK : SEMR_ECUDA;
 }
@@ -164,6 +197,7 @@ BatchQueue queue_of(const semr_batch* b, const Group& G) {
     q.counter = reinterpret_cast<unsigned*>(b->ws + G.off_zero);
     q.n_items = (int32_t)G.items.size();
     q.total_tiles = G.total_tiles;
+    q.tmaps = G.warp() ? b->ws + G.off_maps : nullptr;
     return q;
 }
 
@@ -171,9 +205,69 @@ int launch_all(semr_batch* b, cudaStream_t st) {
     for (const Group& G : b->groups) {
         if (cudaMemsetAsync(b->ws + G.off_zero, 0, G.zero_bytes, st) != cudaSuccess) return SEMR_ECUDA;
         const BatchQueue q = queue_of(b, G);
-        if (launch_reduce_fast_batch(q, G.lx, G.precision, G.tile, st) != cudaSuccess) return SEMR_ECUDA;
-        if (launch_finalize_batch(q, G.total_fields, st) != cudaSuccess) return SEMR_ECUDA;
+        if (G.warp()) {
+            if (launch_reduce_warp_batch(q, G.precision, G.stage_ctas, st) != cudaSuccess) return SEMR_ECUDA;
+            if (launch_finalize_warp_batch(q, G.total_fields, st) != cudaSuccess) return SEMR_ECUDA;
+        } else {
+            if (launch_reduce_fast_batch(q, G.lx, G.precision, G.tile, st) != cudaSuccess) return SEMR_ECUDA;
+            if (launch_finalize_batch(q, G.total_fields, st) != cudaSuccess) return SEMR_ECUDA;
+        }
     }
+    return SEMR_OK;
+}
+
+// Time the warp kernel on one snapshot as a one-item batch (one warm-up, three
+// timed launches); ms < 0 when it cannot run.
+int probe_warp(const semr_batch_item& it, int precision, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+    *ms = -1.0f;
+    LaunchParams p;
+    if (fill_params(it, kWarpTile, p)) return SEMR_OK;
+    const uint64_t t = item_tiles(it, kWarpTile), nf = (uint64_t)it.fs.n_fields;
+    const uint64_t stage_ctas = std::min<uint64_t>(t, kWarpStageCtas);
+    // [desc 1 KB][bases 512][maps][counter 256 + control + states][partials][maxima][staging]
+    const uint64_t o_maps = 2048, o_zero = align256(o_maps + kTensorMapBytes * nf);
+    const uint64_t zero = 256 + kScratchControlBytes + pad16(8 * t);
+    const uint64_t o_part = align256(o_zero + zero), o_umax = align256(o_part + 32 * t);
+    const uint64_t o_stage = align256(o_umax + 4ull * uint64_t(it.mesh.n_elem) * nf);
+    const uint64_t bytes = o_stage + stage_ctas * kWarpStageBytes;
+    uint8_t* w = nullptr;
+    if (cudaMalloc(reinterpret_cast<void**>(&w), bytes) != cudaSuccess) return SEMR_ENOMEM;
+    p.scratch = w + o_zero + 256;
+    p.ctl = reinterpret_cast<ScratchControl*>(w + o_zero + 256);
+    p.tile_state = reinterpret_cast<uint64_t*>(w + o_zero + 256 + kScratchControlBytes);
+    p.tile_part = reinterpret_cast<double*>(w + o_part);
+    p.umax_elem = reinterpret_cast<float*>(w + o_umax);
+    p.code_stage = reinterpret_cast<int16_t*>(w + o_stage);
+    p.stage_ctas = (int32_t)stage_ctas;
+    std::vector<uint8_t> maps(kTensorMapBytes * nf);
+    const uint64_t tb[2] = {0, t};
+    const uint32_t fb[2] = {0, (uint32_t)nf};
+    bool ok = warp_encode_maps(p, maps.data()) == 0 &&
+              cudaMemcpy(w, &p, sizeof(p), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(w + 1024, tb, sizeof(tb), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(w + 1536, fb, sizeof(fb), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(w + o_maps, maps.data(), maps.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    BatchQueue q{};
+    q.items = reinterpret_cast<const LaunchParams*>(w);
+    q.tile_base = reinterpret_cast<const uint64_t*>(w + 1024);
+    q.field_base = reinterpret_cast<const uint32_t*>(w + 1536);
+    q.counter = reinterpret_cast<unsigned*>(w + o_zero);
+    q.n_items = 1;
+    q.total_tiles = t;
+    q.tmaps = w + o_maps;
+    float total = 0.0f;
+    for (int rep = 0; rep < 4 && ok; ++rep) {
+        cudaMemsetAsync(w + o_zero, 0, zero, st);
+        cudaEventRecord(e0, st);
+        ok = launch_reduce_warp_batch(q, precision, stage_ctas, st) == cudaSuccess;
+        cudaEventRecord(e1, st);
+        if (ok) ok = cudaEventSynchronize(e1) == cudaSuccess;
+        float m = 0.0f;
+        if (ok && rep > 0 && cudaEventElapsedTime(&m, e0, e1) == cudaSuccess) total += m;
+    }
+    if (ok) *ms = total / 3.0f;
+    else cudaGetLastError();
+    cudaFree(w);
     return SEMR_OK;
 }
 
@@ -187,7 +281,8 @@ int autotune(semr_batch* b, Group& G, cudaStream_t st) {
             probe = idx;
     const semr_batch_item& it = b->items[probe];
     uint64_t max_tiles = 0;
-    for (int v = 0; v < G.n_variants; ++v) max_tiles = std::max(max_tiles, item_tiles(it, G.variants[v]));
+    for (int v = 0; v < G.n_variants; ++v)
+        if (G.variants[v] != kWarpTile) max_tiles = std::max(max_tiles, item_tiles(it, G.variants[v]));
     // probe workspace: descriptor, bases, counter + control + states, partials
     const uint64_t zero = 256 + kScratchControlBytes + pad16(8 * max_tiles);
     const uint64_t bytes = 4096 + zero + 32 * max_tiles + 256;
@@ -199,6 +294,22 @@ int autotune(semr_batch* b, Group& G, cudaStream_t st) {
     float best = 1e30f;
     int best_tile = G.variants[0];
     for (int v = 0; v < G.n_variants; ++v) {
+        if (G.variants[v] == kWarpTile) {
+            float ms = -1.0f;
+            const int rc = probe_warp(it, G.precision, st, e0, e1, &ms);
+            if (rc) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                cudaFree(w);
+                return rc;
+            }
+            G.tuned_ms[v] = ms;
+            if (ms >= 0.0f && ms < best) {
+                best = ms;
+                best_tile = kWarpTile;
+            }
+            continue;
+        }
         LaunchParams p;
         if (fill_params(it, G.variants[v], p)) continue;
         const uint64_t t = item_tiles(it, G.variants[v]);
@@ -279,6 +390,20 @@ extern "C" int semr_batch_create(semr_batch** out, const semr_batch_item* items,
             f = gid.find(key);
         }
         b->groups[f->second].items.push_back(i);
+    }
+    for (Group& G : b->groups) {  // lx = 8: the warp kernel first (the default) when every item fits it
+        if (G.lx != 8) continue;
+        G.warp_ok = true;
+        for (int idx : G.items) {
+            LaunchParams p;
+            G.warp_ok = G.warp_ok && fill_params(items[idx], kWarpTile, p) == SEMR_OK && warp_applicable(p);
+        }
+        if (G.warp_ok && G.n_variants < 4) {
+            for (int v = G.n_variants; v > 0; --v) G.variants[v] = G.variants[v - 1];
+            G.variants[0] = kWarpTile;
+            ++G.n_variants;
+            G.tile = kWarpTile;
+        }
     }
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (flags & SEMR_BATCH_AUTOTUNE) {

@@ -158,6 +158,7 @@ struct BatchQueue {
     int32_t n_items;
     int32_t pad_;
     uint64_t total_tiles;
+    const void* tmaps;           // warp kernel: device, 64-byte aligned tensor maps, one per field (field_base order)
 };
 
 // Kernel variants (elements per tile) available for a given lx; the first is the default.
@@ -173,6 +174,13 @@ int launch_finalize_batch(const BatchQueue& q, uint32_t total_fields, void* stre
 bool warp_applicable(const LaunchParams& p);
 int launch_reduce_warp(const LaunchParams& p, void* stream);
 int launch_finalize_warp(const LaunchParams& p, void* stream);
+// Batched form: items of one precision, each laid out as split_scratch_warp does
+// except that they share one code staging (stage_ctas CTAs).  warp_encode_maps
+// writes an item's n_fields tensor maps (128 bytes each) to host memory.
+constexpr uint64_t kTensorMapBytes = 128;
+int warp_encode_maps(const LaunchParams& p, void* maps);
+int launch_reduce_warp_batch(const BatchQueue& q, int precision, uint64_t stage_ctas, void* stream);
+int launch_finalize_warp_batch(const BatchQueue& q, uint32_t total_fields, void* stream);
 
 // Kernel launchers (semr_kernels.cu).  Return a cudaError_t value.
 int launch_reduce(const LaunchParams& p, int lx, void* stream);

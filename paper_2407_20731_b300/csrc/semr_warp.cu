@@ -414,14 +414,17 @@ __device__ __noinline__ void dense_inverse_pairs(float2* buf, const float* Ph, c
     __syncwarp();
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(const __grid_constant__ WArgs A) {
+// BATCH = false: one reduction, parameters and tensor maps in A.  BATCH = true: the
+// work queue q of several lx = 8 reductions (each with its own descriptor, payload
+// and scratch; their tensor maps in global memory at q.tmaps, field_base order).
+template <int MODE, bool BATCH>
+__global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
+    reduce_warp_kernel(const __grid_constant__ WArgs A, const BatchQueue q) {
     constexpr bool DF = MODE != 0;
     using SM = WSmem<DF>;
     extern __shared__ uint8_t smem_raw[];
     // the stages start 512-byte aligned: the 64-byte swizzle permutes 16-byte chunks by address bits 7-8
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 511) & ~uintptr_t(511));
-    const LaunchParams& p = A.p;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 
     float* sPTh = reinterpret_cast<float*>(smem + SM::off_tab);  // [p][i] = Phi[i][p]
@@ -480,12 +483,14 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
     const float4* sWq4 = reinterpret_cast<const float4*>(smem + SM::off_wq);
     if constexpr (!DF) __syncthreads();  // the weight table is overlaid by the results table
 
-    const uint32_t E = A.n_elem, tpf = A.tiles_per_field, total_tiles = A.total_tiles;
-    unsigned* counter = &p.ctl->tile_counter;
-    unsigned* status = &p.ctl->status;
+    const uint32_t total_tiles = BATCH ? static_cast<uint32_t>(q.total_tiles) : A.total_tiles;
+    unsigned* counter = BATCH ? q.counter : &A.p.ctl->tile_counter;
+    const CUtensorMap* qmaps = reinterpret_cast<const CUtensorMap*>(q.tmaps);
     // this CTA's staging (a tile's codes are placed one tile later): codes [2 tile parities][warp]
-    // [kWarpArena], within-tile prefixes [2][kWarpTile + 1], arena offsets [2][kWarpTile]
-    uint8_t* stage_cta = reinterpret_cast<uint8_t*>(p.code_stage) + static_cast<uint64_t>(blockIdx.x) * kWarpStageBytes;
+    // [kWarpArena], within-tile prefixes [2][kWarpTile + 1], arena offsets [2][kWarpTile]; a batched
+    // launch's items share it
+    uint8_t* stage_cta = reinterpret_cast<uint8_t*>(BATCH ? q.items[0].code_stage : A.p.code_stage) +
+                         static_cast<uint64_t>(blockIdx.x) * kWarpStageBytes;
     int16_t* stage_codes = reinterpret_cast<int16_t*>(stage_cta);
     uint32_t* stage_pre = reinterpret_cast<uint32_t*>(stage_cta + 2ull * WPB * kWarpArena * 2);
     uint32_t* stage_off = stage_pre + 2 * (kWarpTile + 1);
@@ -493,6 +498,23 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
 
     // tiles: kWarpTile consecutive elements of one field; warp w takes elements w, w + 4, ...
     __shared__ uint32_t s_tile[2];  // current tile; the next one, claimed when the current one is computed
+    __shared__ uint32_t s_titem[2], s_tloc[2];    // their item and tile index within the item (BATCH)
+    __shared__ LaunchParams s_par[BATCH ? 2 : 1];  // BATCH: descriptors of the current and previous tile
+    // item and local tile of a claimed global tile (thread 0)
+    auto resolve = [&](uint32_t g, int slot) {
+        uint32_t item = 0, loc = g;
+        if (BATCH && g < total_tiles) {  // last item whose first tile is <= g
+            int lo = 0, hi = q.n_items - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) / 2;
+                if (q.tile_base[mid] <= g) lo = mid; else hi = mid - 1;
+            }
+            item = static_cast<uint32_t>(lo);
+            loc = g - static_cast<uint32_t>(q.tile_base[lo]);
+        }
+        s_titem[slot] = item;
+        s_tloc[slot] = loc;
+    };
     __shared__ uint32_t s_cnt[kWarpTile];  // tile tag << 16 | code count; tag 0xffff: nothing yet
     __shared__ unsigned long long s_excl;
     __shared__ unsigned long long s_peek;  // a tile's exclusive prefix for directly written codes
@@ -501,29 +523,32 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
     __shared__ int s_abort;
     if (threadIdx.x == 0) {
         s_tile[0] = atomicAdd(counter, 1u);
+        resolve(s_tile[0], 0);
         s_abort = 0;
         s_peek_tag = 0;
     }
     for (int i = threadIdx.x; i < kWarpTile; i += WPB * 32) s_cnt[i] = 0xffff0000u;
     __syncthreads();
-    auto geom = [&](uint32_t tt, uint32_t& f, uint32_t& e0, int& nh) {
-        f = tt / tpf;
-        e0 = (tt - f * tpf) * kWarpTile;
-        nh = static_cast<int>(min(static_cast<uint32_t>(kWarpTile), E - e0));
+    // field, first element and element count of local tile tt of an item with tpf tiles per field
+    auto geom = [&](uint32_t tt, uint32_t tpf_, uint32_t E_, uint32_t& f, uint32_t& e0, int& nh) {
+        f = tt / tpf_;
+        e0 = (tt - f * tpf_) * kWarpTile;
+        nh = static_cast<int>(min(static_cast<uint32_t>(kWarpTile), E_ - e0));
     };
-    auto issue = [&](uint32_t f, uint32_t e) {  // lane 0: element block (f, e) into the stage
-        tma_load_2d(stage, &A.tm[f], 0, static_cast<int>(e * WNP), bar, SM::stage);
+    auto issue = [&](const CUtensorMap* tm, uint32_t e) {  // lane 0: element block e of map tm into the stage
+        tma_load_2d(stage, tm, 0, static_cast<int>(e * WNP), bar, SM::stage);
     };
     uint32_t parity = 0;
     uint32_t tag = 0;       // tags the counts of the current tile (0 .. 0xfffe, then wraps)
     bool inflight = false;  // a block is on its way into this warp's stage
     unsigned recomputed = 0;
-    uint32_t t_prev = 0xffffffffu;  // this CTA's previous tile, whose codes are still staged
+    uint32_t t_prev = 0xffffffffu;  // this CTA's previous tile (local index), whose codes are still staged
     int nh_prev = 0, par = 0;       // its element count; staging parity of the current tile
     uint32_t tot_prev = 0;          // warp 0: its code count
 
     // Copy the staged codes of a tile (staging parity pp, nhp elements) to code_base + 2 (excl + prefix).
-    auto place_codes = [&](int pp, int nhp, uint64_t excl) {
+    auto place_codes = [&](const LaunchParams& p, int pp, int nhp, uint64_t excl) {
+        unsigned* status = &p.ctl->status;
         const uint32_t* pre = stage_pre + pp * (kWarpTile + 1);
         const int16_t* arena = stage_codes + (pp * WPB + wid) * kWarpArena;
         for (int il = wid; il < nhp; il += WPB) {
@@ -542,16 +567,35 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
     for (;;) {
     // Tiles are claimed only once the previous one is computed, so they start in about
     // the order of their claims and a look-back never waits for a tile not yet begun.
-    const uint32_t tcur = s_tile[0];
-    if (tcur >= total_tiles) break;
+    if (s_tile[0] >= total_tiles) break;
+    const uint32_t gtile = s_tile[0];
+    const uint32_t item = s_titem[0], tcur = s_tloc[0];  // tcur: the tile's index within its item
+    if constexpr (BATCH) {  // the item's descriptor into this tile's slot (the other holds the previous one's)
+        __syncthreads();  // the slot's last reader (the placement of two tiles ago) is done
+        constexpr int PW = sizeof(LaunchParams) / 4;
+        static_assert(sizeof(LaunchParams) % 4 == 0, "descriptor copy by words");
+        for (int i = threadIdx.x; i < PW; i += WPB * 32)
+            reinterpret_cast<int*>(&s_par[par])[i] = reinterpret_cast<const int*>(&q.items[item])[i];
+        __syncthreads();
+    }
+    const LaunchParams& p = BATCH ? s_par[par] : A.p;
+    const LaunchParams& pprev = BATCH ? s_par[par ^ 1] : A.p;
+    const uint32_t E = static_cast<uint32_t>(p.n_elem), tpf = static_cast<uint32_t>(p.tiles_per_field);
+    const CUtensorMap* tmaps = BATCH ? qmaps + q.field_base[item] : A.tm;
+    unsigned* status = &p.ctl->status;
+    float tau_h = A.tau_h, tau_l = A.tau_l;
+    if constexpr (BATCH) {
+        tau_h = static_cast<float>(p.tau);
+        tau_l = static_cast<float>(p.tau - static_cast<double>(tau_h));
+    }
     uint32_t f, e0;
     int nh;
-    geom(tcur, f, e0, nh);
+    geom(tcur, tpf, E, f, e0, nh);
     int16_t* arena = stage_codes + (par * WPB + wid) * kWarpArena;  // this warp's codes of the tile
     uint32_t atop = 0;                                             // its fill (warp-uniform)
     for (int il = wid; il < nh; il += WPB) {
         const uint32_t e = e0 + static_cast<uint32_t>(il);
-        if (!inflight && lane == 0) issue(f, e);
+        if (!inflight && lane == 0) issue(&tmaps[f], e);
         if (!mbar_wait_bounded(bar, parity)) {
             if (lane == 0) {
                 atomicOr(status, static_cast<unsigned>(SEMR_STATUS_TIMEOUT));
@@ -598,7 +642,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
             if (il + WPB < nh) {
                 if (lane == 0) {
                     fence_proxy_async();
-                    issue(f, e + WPB);
+                    issue(&tmaps[f], e + WPB);
                 }
                 inflight = true;
             }
@@ -670,7 +714,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
         if (bad || !isfinite(S.h)) {
             if (lane == 0) atomicOr(status, static_cast<unsigned>(SEMR_STATUS_NONFINITE));
         } else {
-            t = df_norm(df_mul({A.tau_h, A.tau_l}, S));
+            t = df_norm(df_mul({tau_h, tau_l}, S));
             if (t.h >= 1.0e-30f && t.h <= 1.0e37f) {
                 const uint32_t tb_ = __float_as_uint(t.h);
                 int ex = static_cast<int>(tb_ >> 23) - 126;
@@ -830,14 +874,14 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
             // which needs the tile's exclusive prefix (computed once per tile) and the counts of the
             // tile's earlier elements; every such wait points to smaller element indices, so it ends
             uint64_t before;
-            if (s_peek_tag == tcur + 1u) {
+            if (s_peek_tag == gtile + 1u) {
                 before = s_peek;
             } else {
                 before = lookback_peek(p.tile_state, tcur, status);
                 if (lane == 0) {
                     s_peek = before;
                     __threadfence_block();
-                    s_peek_tag = tcur + 1u;
+                    s_peek_tag = gtile + 1u;
                 }
             }
             uint32_t part = 0;
@@ -1045,18 +1089,22 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
         }
         __syncwarp();  // the kept list and mask words are reused by the next element
     }
-    if (threadIdx.x == 0) s_tile[1] = atomicAdd(counter, 1u);
+    if (threadIdx.x == 0) {
+        s_tile[1] = atomicAdd(counter, 1u);
+        resolve(s_tile[1], 1);
+    }
     __syncthreads();  // every element of the tile is done
     {  // this warp's first block of the next tile streams in during the tile's bookkeeping
-        const uint32_t tn = s_tile[1];
-        if (tn < total_tiles && !s_abort) {
+        if (s_tile[1] < total_tiles && !s_abort) {
+            const uint32_t itn = s_titem[1], tn = s_tloc[1];
+            const LaunchParams* pn = BATCH ? &q.items[itn] : &A.p;
             uint32_t fn, e0n;
             int nhn;
-            geom(tn, fn, e0n, nhn);
+            geom(tn, static_cast<uint32_t>(pn->tiles_per_field), static_cast<uint32_t>(pn->n_elem), fn, e0n, nhn);
             if (wid < nhn) {
                 if (lane == 0) {
                     fence_proxy_async();
-                    issue(fn, e0n + static_cast<uint32_t>(wid));
+                    issue(BATCH ? &qmaps[q.field_base[itn] + fn] : &A.tm[fn], e0n + static_cast<uint32_t>(wid));
                 }
                 inflight = true;
             }
@@ -1094,12 +1142,14 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
             st_release_u64(&p.tile_state[tcur], (tcur == 0 ? kFlagPrefix : kFlagAggregate) | tot);
         }
         if (t_prev != 0xffffffffu) {
-            const uint64_t excl = lookback_warp(p.tile_state, t_prev, tot_prev, status);
+            const uint64_t excl = lookback_warp(pprev.tile_state, t_prev, tot_prev, &pprev.ctl->status);
             if (lane == 0) s_excl = excl;
         }
         tot_prev = tot;
     } else if (wid == 2 && lane == 0) {
         s_tile[0] = s_tile[1];
+        s_titem[0] = s_titem[1];
+        s_tloc[0] = s_tloc[1];
     }
     {
         // every warp: FP64 partials and element report of its own elements (lane k: element
@@ -1149,7 +1199,9 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
         tp[2] = fmax(fmax(s_wpart[0][2], s_wpart[1][2]), fmax(s_wpart[2][2], s_wpart[3][2]));
         tp[3] = fmax(fmax(s_wpart[0][3], s_wpart[1][3]), fmax(s_wpart[2][3], s_wpart[3][3]));
     }
-    if (t_prev != 0xffffffffu) place_codes(par ^ 1, nh_prev, s_excl);  // the previous tile's codes
+    if (t_prev != 0xffffffffu) place_codes(pprev, par ^ 1, nh_prev, s_excl);  // the previous tile's codes
+    if (recomputed && lane == 0) atomicAdd(&p.ctl->recomputed, recomputed);
+    recomputed = 0;
     t_prev = tcur;
     nh_prev = nh;
     par ^= 1;
@@ -1159,27 +1211,27 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6) reduce_warp_kernel(con
     }
     // the last tile: its look-back, then its codes
     if (t_prev != 0xffffffffu && !s_abort) {
+        const LaunchParams& pl = BATCH ? s_par[par ^ 1] : A.p;
         if (wid == 0) {
-            const uint64_t excl = lookback_warp(p.tile_state, t_prev, tot_prev, status);
+            const uint64_t excl = lookback_warp(pl.tile_state, t_prev, tot_prev, &pl.ctl->status);
             if (lane == 0) s_excl = excl;
         }
         __syncthreads();
-        place_codes(par ^ 1, nh_prev, s_excl);
+        place_codes(pl, par ^ 1, nh_prev, s_excl);
     }
     if (inflight) mbar_wait_bounded(bar, parity);  // after an abort: let a requested block land
-    if (lane == 0 && recomputed) atomicAdd(&p.ctl->recomputed, recomputed);
 }
 
 // Finalize of field f: tree over its tile partials, then the exact maximum of
 // |u|.  The kernel records each element's maximum rounded toward zero to
 // float, which keeps their order, so the elements whose rounded maximum is
 // the field's hold the exact one: those few blocks are reread.  256 threads.
-__global__ void __launch_bounds__(256) finalize_warp_kernel(const LaunchParams p) {
+__device__ void finalize_warp_field(const LaunchParams& p, int f) {
     __shared__ double red[4][256];
     __shared__ int s_list[64];
     __shared__ int s_cnt;
     __shared__ unsigned long long s_umax;
-    const int tid = threadIdx.x, f = blockIdx.x;
+    const int tid = threadIdx.x;
     finalize_tree(p.tile_part, f, static_cast<uint64_t>(p.tiles_per_field), red);
     const double M = red[3][0];
     if (tid == 0) {
@@ -1221,6 +1273,24 @@ __global__ void __launch_bounds__(256) finalize_warp_kernel(const LaunchParams p
         finalize_report(p, f, WLX, red[0][0], red[1][0], red[2][0], __longlong_as_double(static_cast<long long>(s_umax)));
 }
 
+__global__ void __launch_bounds__(256) finalize_warp_kernel(const LaunchParams p) { finalize_warp_field(p, blockIdx.x); }
+
+// One block per (item, field) of a batched launch.
+__global__ void __launch_bounds__(256) finalize_warp_batch_kernel(const BatchQueue q) {
+    __shared__ int s_item;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = q.n_items - 1;  // last item with field_base <= blockIdx.x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (q.field_base[mid] <= blockIdx.x) lo = mid; else hi = mid - 1;
+        }
+        s_item = lo;
+    }
+    __syncthreads();
+    const LaunchParams& p = q.items[s_item];
+    finalize_warp_field(p, static_cast<int>(blockIdx.x - q.field_base[s_item]));
+}
+
 // ------------------------------------------------------------ host side
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -1259,11 +1329,11 @@ WTables make_wtables() {
     return t;
 }
 
-template <int MODE>
-int launch_mode(const WArgs& a, void* stream) {
+template <int MODE, bool BATCH>
+int launch_mode(const WArgs& a, const BatchQueue& q, uint64_t total_tiles, uint64_t stage_ctas, void* stream) {
     using SM = WSmem<MODE != 0>;
     cudaError_t err;
-    auto kern = reduce_warp_kernel<MODE>;
+    auto kern = reduce_warp_kernel<MODE, BATCH>;
     if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes)) != cudaSuccess)
         return (int)err;
     int dev = 0, sms = 0, per_sm = 0;
@@ -1273,9 +1343,10 @@ int launch_mode(const WArgs& a, void* stream) {
         return (int)err;
     if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
     // persistent: as many CTAs as fit at once, never more than tiles or staging slots
-    const uint64_t want = std::min<uint64_t>(a.total_tiles, static_cast<uint64_t>(a.p.stage_ctas));
+    const uint64_t want = std::min<uint64_t>(total_tiles, stage_ctas);
     const unsigned grid = (unsigned)std::min<uint64_t>(want, static_cast<uint64_t>(sms) * per_sm);
-    kern<<<grid, WPB * 32, SM::bytes, static_cast<cudaStream_t>(stream)>>>(a);
+    if (grid == 0) return (int)cudaErrorInvalidConfiguration;
+    kern<<<grid, WPB * 32, SM::bytes, static_cast<cudaStream_t>(stream)>>>(a, q);
     return (int)cudaGetLastError();
 }
 
@@ -1312,7 +1383,39 @@ int launch_reduce_warp(const LaunchParams& p, void* stream) {
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return (int)cudaErrorInvalidValue;
     }
-    return p.precision == SEMR_FP32 ? launch_mode<0>(a, stream) : launch_mode<1>(a, stream);
+    BatchQueue q{};
+    return p.precision == SEMR_FP32 ? launch_mode<0, false>(a, q, a.total_tiles, p.stage_ctas, stream)
+                                    : launch_mode<1, false>(a, q, a.total_tiles, p.stage_ctas, stream);
+}
+
+int warp_encode_maps(const LaunchParams& p, void* maps) {
+    EncodeTiledFn enc = encoder();
+    if (!enc) return (int)cudaErrorNotSupported;
+    for (int f = 0; f < p.n_fields; ++f) {
+        const cuuint64_t dims[2] = {8, static_cast<cuuint64_t>(p.n_elem) * WNP};
+        const cuuint64_t strides[1] = {64};
+        const cuuint32_t box[2] = {8, WNP};
+        const cuuint32_t estr[2] = {1, 1};
+        CUtensorMap* tm = reinterpret_cast<CUtensorMap*>(static_cast<uint8_t*>(maps) + kTensorMapBytes * f);
+        if (enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(p.fields[f]), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return (int)cudaErrorInvalidValue;
+    }
+    return 0;
+}
+
+int launch_reduce_warp_batch(const BatchQueue& q, int precision, uint64_t stage_ctas, void* stream) {
+    WArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.tab = make_wtables();
+    return precision == SEMR_FP32 ? launch_mode<0, true>(a, q, q.total_tiles, stage_ctas, stream)
+                                  : launch_mode<1, true>(a, q, q.total_tiles, stage_ctas, stream);
+}
+
+int launch_finalize_warp_batch(const BatchQueue& q, uint32_t total_fields, void* stream) {
+    finalize_warp_batch_kernel<<<total_fields, 256, 0, static_cast<cudaStream_t>(stream)>>>(q);
+    return (int)cudaGetLastError();
 }
 
 int launch_finalize_warp(const LaunchParams& p, void* stream) {
