@@ -154,10 +154,13 @@ typedef struct {
     uint64_t header_bytes;       /* payload header */
     uint64_t code_base;          /* header + fixed sections: minimum payload capacity */
     uint64_t payload_worst;      /* code_base + every mode kept: always sufficient */
-    uint64_t scratch_bytes;      /* device scratch for semr_reduce_async */
+    uint64_t scratch_bytes;      /* device scratch for semr_reduce_async (recommended size) */
     uint64_t elem_report_bytes;  /* n_fields * n_elem * 3 doubles */
     uint32_t code_width;         /* 2, 4 or 8 bytes */
     uint32_t tiles;              /* work tiles of the CTA-per-tile kernels (saturates at 2^32-1) */
+    uint64_t scratch_min_bytes;  /* smallest scratch semr_reduce_async accepts (<= scratch_bytes);
+                                    at lx = 8 a scratch between the two runs the kernel on fewer
+                                    CTAs, with the same results */
 } semr_sizes;
 
 /* Device buffers of one reduction (all caller-owned device memory). */
@@ -270,11 +273,16 @@ int semr_gll(int32_t lx, double* nodes, double* weights);
  * array of SEMR_NOALLOC_SCRATCH_BYTES (64 MiB) that every GPU loading the
  * library holds until the process exits; nothing is allocated or freed
  * (no cudaMalloc, cudaFree or allocating library routine).  A snapshot
- * whose scratch (semr_sizes.scratch_bytes) exceeds that size is rejected
- * with SEMR_EINVAL.  At lx = 8 the scratch is about 10 bytes per
- * element-field (at least 24 MiB once a snapshot has 768 x 32 element-fields),
- * so snapshots up to about 6.7 million element-fields fit (e.g. 128^3 elements
- * x 3 fields).
+ * whose smallest usable scratch (semr_sizes.scratch_min_bytes) exceeds the
+ * array is rejected with SEMR_EBUDGET, before any pointer is looked at.
+ * At lx = 8 that is about 10 bytes per element-field (the CTA-per-tile
+ * kernel's 40 bytes per 4-element tile, which also covers the warp kernel's
+ * 4.3 bytes per element-field plus one CTA's 67,840-byte code staging), so
+ * snapshots up to about 6.7 million element-fields are accepted (e.g. 128^3
+ * elements x 3 fields).  The array holds code staging for every CTA the warp
+ * kernel can keep resident up to about 6.2 million (SEMR_FP64) or 1.6 million
+ * (SEMR_FP32) element-fields; beyond that it runs on the CTAs it can stage
+ * for (same results, less throughput).
  *
  * The first call on a device looks up the array's device address (with that
  * device current) and caches it: make that first call before any stream
@@ -282,8 +290,8 @@ int semr_gll(int32_t lx, double* nodes, double* weights);
  * persist between calls; each call clears the part that must start at zero.
  * Calls that overlap on the GPU (on different streams, or not yet finished
  * on another stream) race on the array and corrupt each other's results:
- * order them on one stream.  Errors as semr_reduce_async, plus SEMR_ECUDA if
- * the address lookup fails.
+ * order them on one stream.  Errors as semr_reduce_async, plus SEMR_EBUDGET
+ * (above) and SEMR_ECUDA if the address lookup fails.
  */
 #define SEMR_NOALLOC_SCRATCH_BYTES (64ull << 20)
 int semr_reduce_async_noalloc(const semr_fieldset* fs, const semr_mesh* mesh, uint8_t* payload,

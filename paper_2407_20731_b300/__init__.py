@@ -61,7 +61,7 @@ class semr_sizes(ctypes.Structure):
     _fields_ = [("header_bytes", ctypes.c_uint64), ("code_base", ctypes.c_uint64),
                 ("payload_worst", ctypes.c_uint64), ("scratch_bytes", ctypes.c_uint64),
                 ("elem_report_bytes", ctypes.c_uint64), ("code_width", ctypes.c_uint32),
-                ("tiles", ctypes.c_uint32)]
+                ("tiles", ctypes.c_uint32), ("scratch_min_bytes", ctypes.c_uint64)]
 
 
 class semr_outputs(ctypes.Structure):

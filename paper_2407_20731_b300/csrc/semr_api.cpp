@@ -61,6 +61,7 @@ extern "C" int semr_sizes_for(int32_t lx, int64_t n_elem, int32_t n_fields, doub
     out->elem_report_bytes = 24ull * uint64_t(n_elem) * n_fields;
     out->code_width = (uint32_t)width;
     out->tiles = (uint32_t)std::min<uint64_t>(tiles, 0xffffffffull);
+    out->scratch_min_bytes = scratch_min(lx, n_elem, n_fields);
     return SEMR_OK;
 }
 

@@ -45,7 +45,7 @@ extern "C" int semr_reduce_async_noalloc(const semr_fieldset* fs, const semr_mes
     if (rc) return rc;
     // beyond the fixed scratch (it may hold less than the recommended size: the lx = 8 kernel
     // then runs on as many CTAs as the array can stage codes for)
-    if (semr::scratch_min(mesh->lx, mesh->n_elem, fs->n_fields) > SEMR_NOALLOC_SCRATCH_BYTES) return SEMR_EINVAL;
+    if (semr::scratch_min(mesh->lx, mesh->n_elem, fs->n_fields) > SEMR_NOALLOC_SCRATCH_BYTES) return SEMR_EBUDGET;
     void* scratch = nullptr;
     rc = scratch_address(&scratch);
     if (rc) return rc;

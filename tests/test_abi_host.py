@@ -36,6 +36,21 @@ def test_sizes_match_payload_format(lx, ne, nf, tau):
     assert s.payload_worst == s.code_base + width * lx ** 3 * ne * nf
 
 
+@pytest.mark.parametrize("lx,ne,nf", [(8, 262144, 4), (8, 1, 1), (8, 1000000, 16), (6, 1001, 3), (10, 7, 1)])
+def test_scratch_sizes(lx, ne, nf):
+    s = semr.semr_sizes_for(lx, ne, nf, 1e-3)
+    assert 0 < s.scratch_min_bytes <= s.scratch_bytes
+    if lx == 8:
+        # the lx = 8 kernel keeps one float per element-field (its rounded max |u|)
+        assert s.scratch_min_bytes > 4 * ne * nf
+    # the no-allocation entry point's array: the 64^3 x 4 snapshot fits its minimum,
+    # 16 million element-fields do not
+    if (lx, ne, nf) == (8, 262144, 4):
+        assert s.scratch_min_bytes <= semr.SEMR_NOALLOC_SCRATCH_BYTES
+    if (lx, ne, nf) == (8, 1000000, 16):
+        assert s.scratch_min_bytes > semr.SEMR_NOALLOC_SCRATCH_BYTES
+
+
 def test_argument_validation_needs_no_gpu():
     fs, mesh, out = semr.semr_fieldset(), semr.semr_mesh(), semr.semr_outputs()
     assert semr.semr_reduce_async(fs, mesh, out, 0) == semr.SEMR_EINVAL  # zero sizes, null pointers

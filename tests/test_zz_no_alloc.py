@@ -73,9 +73,12 @@ def _meaningful(raw: bytes, n_fields: int) -> bytes:
 
 
 def test_noalloc_rejects_snapshots_beyond_its_scratch():
-    lx, nf, n_elem = 8, 8, 1000000  # 8 million element-fields * ~10 B > 64 MiB
-    assert semr.semr_sizes_for(lx, n_elem, nf, 1e-3).scratch_bytes > semr.SEMR_NOALLOC_SCRATCH_BYTES
+    lx, nf, n_elem = 8, 16, 1000000  # 16 million element-fields * ~10 B > 64 MiB
+    assert semr.semr_sizes_for(lx, n_elem, nf, 1e-3).scratch_min_bytes > semr.SEMR_NOALLOC_SCRATCH_BYTES
+    stream = torch.cuda.current_stream().cuda_stream
     fs, mesh = semr.semr_fieldset(), semr.semr_mesh()
     fs.n_fields, fs.tau, mesh.lx, mesh.n_elem = nf, 1e-3, lx, n_elem
-    rc = semr.semr_reduce_async_noalloc(fs, mesh, None, 0, None, None, torch.cuda.current_stream().cuda_stream)
-    assert rc == semr.SEMR_EINVAL
+    # rejected on size alone (no pointer is set: a size that fits fails on them instead)
+    assert semr.semr_reduce_async_noalloc(fs, mesh, None, 0, None, None, stream) == semr.SEMR_EBUDGET
+    mesh.n_elem = 1000
+    assert semr.semr_reduce_async_noalloc(fs, mesh, None, 0, None, None, stream) == semr.SEMR_EINVAL
