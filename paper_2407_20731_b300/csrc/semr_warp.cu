@@ -284,20 +284,22 @@ __device__ __forceinline__ uint64_t lookback_peek(const uint64_t* tile_state, ui
     return excl;
 }
 
-// Exact (float-pair) coefficient a[r][q][p] of the element in `stage`: each lane
-// contracts its two pencils (k0 + 4s, j) with A[p][.], A[q][j], A[r][k] and the
-// warp sums them.  Rare (decisions the FP32 bound cannot settle): out of line.
-__device__ __noinline__ f2 exact_coef(const uint8_t* stage, int pp, int qq, int rr, const float* sAh,
+// Exact (float-pair) coefficient a[r][q][p] of the element block at `u` (global memory,
+// [pencil][8]): each lane contracts its two pencils (k0 + 4s, j) with A[p][.], A[q][j],
+// A[r][k] and the warp sums them.  Rare (decisions the FP32 bound cannot settle): out of
+// line, and the block is reread from global memory (it was just loaded, so L2 holds it)
+// rather than from the stage, which already receives the warp's next block.
+__device__ __noinline__ f2 exact_coef(const double* __restrict__ u, int pp, int qq, int rr, const float* sAh,
                                       const float* sAl) {
-    const int lane = threadIdx.x & 31, j = lane & 7, k0 = lane >> 3, sw = (lane >> 1) & 3;
+    const int lane = threadIdx.x & 31, j = lane & 7, k0 = lane >> 3;
     f2 c = {0.0f, 0.0f};
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-        const uint8_t* row = stage + (lane + 32 * s) * 64;
+        const uint4* row = reinterpret_cast<const uint4*>(u + (lane + 32 * s) * 8);
         f2 xs = {0.0f, 0.0f};
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
-            const uint4 v = *reinterpret_cast<const uint4*>(row + ((cc ^ sw) << 4));
+            const uint4 v = __ldg(row + cc);
             float h0, l0, h1, l1;
             w_split(v.x, v.y, h0, l0);
             w_split(v.z, v.w, h1, l1);
@@ -551,17 +553,33 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
         unsigned* status = &p.ctl->status;
         const uint32_t* pre = stage_pre + pp * (kWarpTile + 1);
         const int16_t* arena = stage_codes + (pp * WPB + wid) * kWarpArena;
-        for (int il = wid; il < nhp; il += WPB) {
-            const uint32_t b = pre[il], n = pre[il + 1] - b, off = stage_off[pp * kWarpTile + il];
-            if (off == kDirect) continue;  // written directly
-            const uint64_t gbyte = p.code_base + 2ull * (excl + b);
-            if (gbyte + 2ull * n <= p.payload_cap) {
-                int16_t* dst = reinterpret_cast<int16_t*>(p.payload + gbyte);
-                const int16_t* src = arena + off;
-                for (uint32_t k = lane; k < n; k += 32) dst[k] = src[k];
-            } else if (lane == 0 && n > 0) {
-                atomicOr(status, static_cast<unsigned>(SEMR_STATUS_OVERFLOW));
-            }
+        // lane L: element wid + WPB L, one of the warp's own (its codes are in this warp's arena),
+        // so the prefixes and offsets of all 32 elements are fetched at once and their (few) codes
+        // are copied side by side
+        const int il = wid + WPB * lane;
+        uint32_t b = 0, n = 0, off = kDirect;
+        if (il < nhp) {
+            b = pre[il];
+            n = pre[il + 1] - b;
+            off = stage_off[pp * kWarpTile + il];
+        }
+        const uint64_t gbyte = p.code_base + 2ull * (excl + b);
+        bool copy = off != kDirect && n > 0;  // (off == kDirect: written directly)
+        if (copy && gbyte + 2ull * n > p.payload_cap) {
+            atomicOr(status, static_cast<unsigned>(SEMR_STATUS_OVERFLOW));
+            copy = false;
+        }
+        if (copy && n <= 32u) {
+            int16_t* dst = reinterpret_cast<int16_t*>(p.payload + gbyte);
+            const int16_t* src = arena + off;
+            for (uint32_t k = 0; k < n; ++k) dst[k] = src[k];
+        }
+        // elements with more codes: the whole warp copies each
+        for (uint32_t big = __ballot_sync(FULL, copy && n > 32u); big; big &= big - 1) {
+            const int src_lane = __ffs(big) - 1;
+            const uint32_t nb = __shfl_sync(FULL, n, src_lane), ob = __shfl_sync(FULL, off, src_lane);
+            int16_t* dst = reinterpret_cast<int16_t*>(p.payload + __shfl_sync(FULL, gbyte, src_lane));
+            for (uint32_t k = lane; k < nb; k += 32) dst[k] = arena[ob + k];
         }
     };
     for (;;) {
@@ -635,19 +653,16 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
                 }
             }
         }
-        // once every lane has consumed its loads (and, in FP64 mode, the exact recomputation
-        // has reread the block), the stage may be refilled with this warp's next element
-        auto prefetch_next = [&]() {
-            __syncwarp();
-            if (il + WPB < nh) {
-                if (lane == 0) {
-                    fence_proxy_async();
-                    issue(&tmaps[f], e + WPB);
-                }
-                inflight = true;
+        // once every lane has consumed its loads, the stage may be refilled with this warp's
+        // next element (an exact recomputation below rereads the block from global memory)
+        __syncwarp();
+        if (il + WPB < nh) {
+            if (lane == 0) {
+                fence_proxy_async();
+                issue(&tmaps[f], e + WPB);
             }
-        };
-        if constexpr (!DF) prefetch_next();
+            inflight = true;
+        }
         const bool bad = __any_sync(FULL, hmax >= (static_cast<uint32_t>(1023 + 127) << 20));
         // max |u| of the element from its largest high word, rounded toward zero to float: it
         // keeps the order of |u| (the finalize rereads the blocks that attain the field maximum)
@@ -765,7 +780,8 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
                     const int src = __ffs(__ballot_sync(FULL, amb != 0u)) - 1;
                     const int bsel = __shfl_sync(FULL, __ffs(amb) - 1, src);
                     const int ms = bsel >> 3, mr = bsel & 7;
-                    const f2 c = exact_coef(stage, src & 7, (src >> 3) + 4 * ms, mr, sAh, sAl);
+                    const f2 c = exact_coef(p.fields[f] + static_cast<uint64_t>(e) * WN3, src & 7, (src >> 3) + 4 * ms,
+                                            mr, sAh, sAl);
                     ++recomputed;
                     if (lane == src) {
                         const bool keep = df_ge(df_mul(c, c), t);
@@ -794,30 +810,22 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
             }
         }
 
-        if constexpr (DF) prefetch_next();
-
-        // ---- mask words: ballot over (slot s, row r) is word s + 2r (bit = lane)
+        // ---- mask words: the ballot over (slot s, row r) is word w = s + 2r (bit = lane).  Each
+        // word's prefix goes to shared memory (with the word) for the quantisation below; nzw marks
+        // the words holding kept modes.  The FP32 form keeps all 16 words in registers and counts
+        // there; FP64 mode, short of registers, scans the words in shared memory
+        uint8_t* fsec = p.payload + p.header_bytes + static_cast<uint64_t>(f) * p.fixed_bytes;
+        uint4* mdst = reinterpret_cast<uint4*>(fsec + static_cast<uint64_t>(e) * 64);
+        uint32_t n_e = 0, nzw = 0;
+        if constexpr (DF) {
 #pragma unroll
-        for (int q4 = 0; q4 < 4; ++q4) {  // words 4 q4 .. 4 q4 + 3: (s, r) = (0, 2q4), (1, 2q4), (0, 2q4+1), (1, 2q4+1)
-            uint32_t w0, w1, w2, w3;
-            if constexpr (DF) {
-                w0 = __ballot_sync(FULL, (kb >> (2 * q4)) & 1u);
-                w1 = __ballot_sync(FULL, (kb >> (8 + 2 * q4)) & 1u);
-                w2 = __ballot_sync(FULL, (kb >> (2 * q4 + 1)) & 1u);
-                w3 = __ballot_sync(FULL, (kb >> (8 + 2 * q4 + 1)) & 1u);
-            } else {  // keep iff |a| >= g, the exact float threshold
-                const bool th = emode == 1;
-                w0 = __ballot_sync(FULL, th && fabsf(a2[2 * q4].x) >= g);
-                w1 = __ballot_sync(FULL, th && fabsf(a2[2 * q4].y) >= g);
-                w2 = __ballot_sync(FULL, th && fabsf(a2[2 * q4 + 1].x) >= g);
-                w3 = __ballot_sync(FULL, th && fabsf(a2[2 * q4 + 1].y) >= g);
+            for (int q4 = 0; q4 < 4; ++q4) {  // words 4 q4 .. 4 q4 + 3
+                uint32_t w4[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) w4[h] = __ballot_sync(FULL, (kb >> (8 * (h & 1) + 2 * q4 + (h >> 1))) & 1u);
+                if (lane == 0) reinterpret_cast<uint4*>(smask)[q4] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
             }
-            if (lane == 0) reinterpret_cast<uint4*>(smask)[q4] = make_uint4(w0, w1, w2, w3);
-        }
-        __syncwarp();
-        uint32_t n_e;
-        bool staged;  // the element's codes fit the warp's arena (else they are written directly)
-        {
+            __syncwarp();
             const uint32_t mw = (lane < 16) ? smask[lane] : 0u;
             const uint32_t c = __popc(mw);
             uint32_t incl = c;
@@ -826,50 +834,65 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
                 const uint32_t v = __shfl_up_sync(FULL, incl, o);
                 if (lane >= o) incl += v;
             }
-            if (lane < 16) swpre[lane] = incl - c;
-            n_e = __shfl_sync(FULL, incl, 15);
-            // payload: mask words, step, count
-            uint8_t* fsec = p.payload + p.header_bytes + static_cast<uint64_t>(f) * p.fixed_bytes;
-            if (lane < 16) reinterpret_cast<uint32_t*>(fsec)[static_cast<uint64_t>(e) * 16 + lane] = mw;
-            const uint64_t mb = static_cast<uint64_t>(E) * 64;  // mask section (a multiple of 16)
-            int16_t* sdst = reinterpret_cast<int16_t*>(fsec + mb);
-            uint16_t* cdst = reinterpret_cast<uint16_t*>(fsec + mb + pad16(2ull * E));
-            if (lane == 0) {
-                sdst[e] = static_cast<int16_t>(step);
-                cdst[e] = static_cast<uint16_t>(n_e);
-                s_cnt[il] = (tag << 16) | n_e;
+            if (lane < 16) {
+                swpre[lane] = incl - c;
+                reinterpret_cast<uint32_t*>(mdst)[lane] = mw;
             }
-            staged = atop + n_e <= static_cast<uint32_t>(kWarpArena);
-            if (lane == 0) stage_off[par * kWarpTile + il] = staged ? atop : kDirect;
-            if (e + 1 == E && lane < 16) {  // zero the padding after the step and count sections
-                const uint64_t se = 2ull * E;
-                if (se + lane < pad16(se)) {
-                    reinterpret_cast<uint8_t*>(sdst)[se + lane] = 0;
-                    reinterpret_cast<uint8_t*>(cdst)[se + lane] = 0;
+            n_e = __shfl_sync(FULL, incl, 15);
+            nzw = __ballot_sync(FULL, mw != 0u);
+        } else {
+            uint32_t wv[16];
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int s = 0; s < 2; ++s)  // keep iff |a| >= g, the exact float threshold
+                    wv[s + 2 * r] = __ballot_sync(FULL, emode == 1 && fabsf(s ? a2[r].y : a2[r].x) >= g);
+#pragma unroll
+            for (int w = 0; w < 16; ++w) {
+                nzw |= (wv[w] != 0u ? 1u : 0u) << w;
+                n_e += __popc(wv[w]);
+            }
+            if (lane == 0) {
+                uint32_t run = 0;
+#pragma unroll
+                for (int q4 = 0; q4 < 4; ++q4) {
+                    const uint4 v = make_uint4(wv[4 * q4], wv[4 * q4 + 1], wv[4 * q4 + 2], wv[4 * q4 + 3]);
+                    mdst[q4] = v;
+                    reinterpret_cast<uint4*>(smask)[q4] = v;
+                    uint4 pr;
+                    pr.x = run; run += __popc(v.x);
+                    pr.y = run; run += __popc(v.y);
+                    pr.z = run; run += __popc(v.z);
+                    pr.w = run; run += __popc(v.w);
+                    reinterpret_cast<uint4*>(swpre)[q4] = pr;
                 }
             }
         }
-        __syncwarp();
-
-        // ---- quantise: code = rint(a 2^-s), ties to even (exact: a 2^-s is a power-of-two scaling)
-        const uint32_t lt_mask = (1u << lane) - 1u;
-        // words holding kept modes (bit w = s + 2r), the same in every lane
-        uint32_t nzw = __ballot_sync(FULL, lane < 16 && smask[lane] != 0u);
-        while (nzw) {
-            const int wi = __ffs(nzw) - 1;
-            nzw &= nzw - 1;
-            const uint32_t wd = smask[wi];
-            if ((wd >> lane) & 1u) {
-                const float yh = pick(a2, wi) * qd;
-                const float c = (yh + 12582912.0f) - 12582912.0f;  // round half to even (|y| < 2^22)
-                const int rank = static_cast<int>(swpre[wi]) + __popc(wd & lt_mask);
-                if (staged) arena[atop + rank] = static_cast<int16_t>(c);
-                if (rank < WSPARSE) skl[rank] = make_int2(lane + 32 * wi, __float_as_int(c));
+        // payload: step and count (lane 0)
+        const uint64_t mb = static_cast<uint64_t>(E) * 64;  // mask section (a multiple of 16)
+        int16_t* sdst = reinterpret_cast<int16_t*>(fsec + mb);
+        uint16_t* cdst = reinterpret_cast<uint16_t*>(fsec + mb + pad16(2ull * E));
+        // the element's codes fit the warp's arena (else they are written directly)
+        const bool staged = atop + n_e <= static_cast<uint32_t>(kWarpArena);
+        if (lane == 0) {
+            sdst[e] = static_cast<int16_t>(step);
+            cdst[e] = static_cast<uint16_t>(n_e);
+            s_cnt[il] = (tag << 16) | n_e;
+            stage_off[par * kWarpTile + il] = staged ? atop : kDirect;
+        }
+        if (e + 1 == E && lane < 16) {  // zero the padding after the step and count sections
+            const uint64_t se = 2ull * E;
+            if (se + lane < pad16(se)) {
+                reinterpret_cast<uint8_t*>(sdst)[se + lane] = 0;
+                reinterpret_cast<uint8_t*>(cdst)[se + lane] = 0;
             }
         }
-        if (staged) {
-            atop += n_e;
-        } else {
+
+        // ---- quantise: code = rint(a 2^-s), ties to even (exact: a 2^-s is a power-of-two scaling),
+        // to the warp's arena, or straight to the payload when the arena is full
+        int16_t* qdst = arena + atop;
+        bool qwrite = true;
+        if (!staged) {
             // the warp's arena is full (extreme inputs only): write the codes at their final place,
             // which needs the tile's exclusive prefix (computed once per tile) and the counts of the
             // tile's earlier elements; every such wait points to smaller element indices, so it ends
@@ -897,20 +920,26 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
             }
             before += __reduce_add_sync(FULL, part);
             const uint64_t gbyte = p.code_base + 2ull * before;
-            const bool fits = gbyte + 2ull * n_e <= p.payload_cap;
-            if (!fits && lane == 0) atomicOr(status, static_cast<unsigned>(SEMR_STATUS_OVERFLOW));
-            int16_t* dst = reinterpret_cast<int16_t*>(p.payload + gbyte);
-            uint32_t nz = __ballot_sync(FULL, lane < 16 && smask[lane] != 0u);
-            while (fits && nz) {
-                const int wi = __ffs(nz) - 1;
-                nz &= nz - 1;
-                if ((smask[wi] >> lane) & 1u) {
-                    const float yh = pick(a2, wi) * qd;
-                    const float c = (yh + 12582912.0f) - 12582912.0f;
-                    dst[swpre[wi] + __popc(smask[wi] & lt_mask)] = static_cast<int16_t>(c);
+            qwrite = gbyte + 2ull * n_e <= p.payload_cap;
+            if (!qwrite && lane == 0) atomicOr(status, static_cast<unsigned>(SEMR_STATUS_OVERFLOW));
+            qdst = reinterpret_cast<int16_t*>(p.payload + gbyte);
+        }
+        __syncwarp();
+        {
+            const uint32_t lt_mask = (1u << lane) - 1u;
+            while (nzw) {
+                const int wi = __ffs(nzw) - 1;
+                nzw &= nzw - 1;
+                const uint32_t wd = smask[wi];
+                if ((wd >> lane) & 1u) {
+                    const float c = (pick(a2, wi) * qd + 12582912.0f) - 12582912.0f;  // round half to even (|y| < 2^22)
+                    const uint32_t rank = swpre[wi] + __popc(wd & lt_mask);
+                    if (qwrite) qdst[rank] = static_cast<int16_t>(c);
+                    if (rank < static_cast<uint32_t>(WSPARSE)) skl[rank] = make_int2(lane + 32 * wi, __float_as_int(c));
                 }
             }
         }
+        if (staged) atop += n_e;
         __syncwarp();
 
         // ---- reconstruction u~ of the lane's nodal pencils (both packed; pairs in FP64 mode)
