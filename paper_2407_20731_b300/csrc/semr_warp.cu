@@ -44,7 +44,8 @@ constexpr int WLX = 8, WNP = 64, WN3 = 512;
 constexpr int WPB = kWarpCtaWarps;   // warps per CTA
 constexpr int TSK = 104, TSJ = 12;   // FP32 transpose strides (plane, row) in floats
 constexpr int TSK2 = 72, TSJ2 = 9;   // float-pair transpose strides (dense inverse, FP64 mode)
-constexpr int WSPARSE = 10;          // sparse reconstruction up to this many kept modes
+// sparse reconstruction up to this many kept modes (the capacity of the kept list)
+template <bool DF> __host__ __device__ constexpr int wsparse() { return DF ? 24 : 16; }
 constexpr uint32_t kWaitPolls = 1000;      // bounded mbarrier polls, each suspending up to kWaitHintNs
 constexpr uint32_t kWaitHintNs = 1000000;
 constexpr unsigned FULL = 0xffffffffu;
@@ -92,7 +93,7 @@ struct WSmem {
     static constexpr size_t o_mask = o_tb + tb_bytes;     // 16 mask words
     static constexpr size_t o_wpre = o_mask + 64;         // 16 word prefixes
     static constexpr size_t o_kl = o_wpre + 64;           // kept list (mode, code)
-    static constexpr size_t o_bar = o_kl + 96;
+    static constexpr size_t o_bar = o_kl + 8 * wsparse<DF>();
     static constexpr size_t wbytes = o_bar + 16;
     static constexpr size_t bytes = off_warp + WPB * wbytes + 512;  // + alignment slack
 };
@@ -147,18 +148,6 @@ __device__ __forceinline__ void w_split(uint32_t lo, uint32_t hi, float& uh, flo
     // their unit is 2^(E - 46) for uh = 1.x 2^E: exponent field of uh minus 46 (clamped at 0)
     const int ex = static_cast<int>(__float_as_uint(uh) & 0x7f800000u) - (46 << 23);
     ul = m * __uint_as_float(static_cast<uint32_t>(max(ex, 0)) | (hi & 0x80000000u));
-}
-
-// 8-point even-odd folded inverse transform (FP32, tables from the constant bank).
-__device__ __forceinline__ void w_inv(const float* __restrict__ Ph, const float (&x)[8], float (&y)[8]) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float e = fmaf(Ph[i * 8 + 6], x[6], fmaf(Ph[i * 8 + 4], x[4], fmaf(Ph[i * 8 + 2], x[2], Ph[i * 8] * x[0])));
-        const float o =
-            fmaf(Ph[i * 8 + 7], x[7], fmaf(Ph[i * 8 + 5], x[5], fmaf(Ph[i * 8 + 3], x[3], Ph[i * 8 + 1] * x[1])));
-        y[i] = e + o;
-        y[7 - i] = e - o;
-    }
 }
 
 // ---- packed FP32x2 arithmetic: the two pencils of a lane travel together as (s = 0, s = 1)
@@ -313,106 +302,138 @@ __device__ __noinline__ f2 exact_coef(const double* __restrict__ u, int pp, int 
     return warp_sum_pair(c);
 }
 
+// 8-point even-odd folded inverse in FP32, both pencils packed (tables from the constant bank).
+__device__ __forceinline__ void w_inv2(const float* __restrict__ Ph, const float2 (&x)[8], float2 (&y)[8]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 e = f2fma(f2dup(Ph[i * 8 + 6]), x[6], f2fma(f2dup(Ph[i * 8 + 4]), x[4],
+                         f2fma(f2dup(Ph[i * 8 + 2]), x[2], f2mul(f2dup(Ph[i * 8]), x[0]))));
+        const float2 o = f2fma(f2dup(Ph[i * 8 + 7]), x[7], f2fma(f2dup(Ph[i * 8 + 5]), x[5],
+                         f2fma(f2dup(Ph[i * 8 + 3]), x[3], f2mul(f2dup(Ph[i * 8 + 1]), x[1]))));
+        y[i] = f2add(e, o);
+        y[7 - i] = f2sub(e, o);
+    }
+}
+
 // Dense folded inverse in FP32 for an element that keeps many modes (rare, out of
-// line): r (registers) -> k, q -> j, p -> i through the warp's buffer.  Input: the
-// kept values (code x 2^s, else 0) of the lane's coefficients (s, r) at
-// buf[(lane + 32 s) * 9 + r]; result: its nodal pencils (k0 + 4s, j) at
-// buf[(lane + 32 s) * 9 + i].
+// line): r (registers) -> k, q -> j, p -> i through the warp's buffer, the lane's two
+// pencils packed.  Input: the kept values (code x 2^s, else 0) of the lane's
+// coefficients (s, r) at buf[(lane + 32 s) * 9 + r]; result: its nodal pencils
+// (k0 + 4s, j) at buf[(lane + 32 s) * 9 + i].
 __device__ __noinline__ void dense_inverse_f32(float* buf, const float* Ph) {
     const int lane = threadIdx.x & 31, j = lane & 7, k0 = lane >> 3;
-    float x[8], y[2][8];
+    float2 x[8], y[8];
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-#pragma unroll
-        for (int r = 0; r < 8; ++r) x[r] = buf[(lane + 32 * s) * 9 + r];
-        w_inv(Ph, x, y[s]);  // lane (q = k0 + 4s, p = j): values over k
+    for (int r = 0; r < 8; ++r) x[r] = make_float2(buf[lane * 9 + r], buf[(lane + 32) * 9 + r]);
+    w_inv2(Ph, x, y);  // lane (q = k0 + 4s, p = j): values over k
+    __syncwarp();
+    {
+        float4* d0 = reinterpret_cast<float4*>(buf + k0 * TSK + j * TSJ);
+        float4* d1 = reinterpret_cast<float4*>(buf + (k0 + 4) * TSK + j * TSJ);
+        d0[0] = make_float4(y[0].x, y[1].x, y[2].x, y[3].x);
+        d0[1] = make_float4(y[4].x, y[5].x, y[6].x, y[7].x);
+        d1[0] = make_float4(y[0].y, y[1].y, y[2].y, y[3].y);
+        d1[1] = make_float4(y[4].y, y[5].y, y[6].y, y[7].y);
     }
     __syncwarp();
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        float4* d = reinterpret_cast<float4*>(buf + (k0 + 4 * s) * TSK + j * TSJ);
-        d[0] = make_float4(y[s][0], y[s][1], y[s][2], y[s][3]);
-        d[1] = make_float4(y[s][4], y[s][5], y[s][6], y[s][7]);
+    for (int q = 0; q < 8; ++q)  // lane (k = k0 + 4s, p = j): values over q
+        x[q] = make_float2(buf[q * TSK + j * TSJ + k0], buf[q * TSK + j * TSJ + k0 + 4]);
+    w_inv2(Ph, x, y);
+    __syncwarp();
+    {
+        float4* d0 = reinterpret_cast<float4*>(buf + k0 * TSK + j * TSJ);
+        float4* d1 = reinterpret_cast<float4*>(buf + (k0 + 4) * TSK + j * TSJ);
+        d0[0] = make_float4(y[0].x, y[1].x, y[2].x, y[3].x);
+        d0[1] = make_float4(y[4].x, y[5].x, y[6].x, y[7].x);
+        d1[0] = make_float4(y[0].y, y[1].y, y[2].y, y[3].y);
+        d1[1] = make_float4(y[4].y, y[5].y, y[6].y, y[7].y);
     }
     __syncwarp();
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {  // lane (k = k0 + 4s, p = j): values over q
+    for (int pp = 0; pp < 8; ++pp)  // lane (k = k0 + 4s, j): values over p
+        x[pp] = make_float2(buf[k0 * TSK + pp * TSJ + j], buf[(k0 + 4) * TSK + pp * TSJ + j]);
+    w_inv2(Ph, x, y);
+    __syncwarp();
 #pragma unroll
-        for (int q = 0; q < 8; ++q) x[q] = buf[q * TSK + j * TSJ + k0 + 4 * s];
-        w_inv(Ph, x, y[s]);
+    for (int i = 0; i < 8; ++i) {
+        buf[lane * 9 + i] = y[i].x;
+        buf[(lane + 32) * 9 + i] = y[i].y;
     }
     __syncwarp();
+}
+
+// Packed pair sum a + b of both pencils.
+__device__ __forceinline__ p2 df_add2(p2 a, p2 b) {
+    const p2 s = two_sum2(a.h, b.h);
+    return fast_two_sum2(s.h, f2add(s.l, f2add(a.l, b.l)));
+}
+
+// 8-point even-odd folded inverse in float pairs, both pencils packed (tables from the
+// constant bank): y[i] = sum_p Phi[i][p] x[p].
+__device__ __forceinline__ void w_inv_df2(const float* __restrict__ Ph, const float* __restrict__ Pl,
+                                          const p2 (&x)[8], p2 (&y)[8]) {
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        float4* d = reinterpret_cast<float4*>(buf + (k0 + 4 * s) * TSK + j * TSJ);
-        d[0] = make_float4(y[s][0], y[s][1], y[s][2], y[s][3]);
-        d[1] = make_float4(y[s][4], y[s][5], y[s][6], y[s][7]);
+    for (int i = 0; i < 4; ++i) {
+        p2 e = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)}, o = e;
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+            const p2 c = {f2dup(Ph[i * 8 + p]), f2dup(Pl[i * 8 + p])};
+            if ((p & 1) == 0) df_fma_acc2(e, c, x[p]);
+            else df_fma_acc2(o, c, x[p]);
+        }
+        e = df_norm2(e);
+        o = df_norm2(o);
+        y[i] = df_add2(e, o);
+        y[7 - i] = df_sub2(e, o);
     }
-    __syncwarp();
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {  // lane (k = k0 + 4s, j): values over p
-#pragma unroll
-        for (int pp = 0; pp < 8; ++pp) x[pp] = buf[(k0 + 4 * s) * TSK + pp * TSJ + j];
-        w_inv(Ph, x, y[s]);
-    }
-    __syncwarp();
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-        for (int i = 0; i < 8; ++i) buf[(lane + 32 * s) * 9 + i] = y[s][i];
-    __syncwarp();
 }
 
 // Dense folded inverse in float pairs for an element that keeps many modes (a
 // rare path, kept out of line so that its registers do not weigh on the
-// common one): r (registers) -> k, q -> j, p -> i through the warp's buffer.
-// Input as dense_inverse_f32 (floats); result: the lane's nodal pencils
-// (k0 + 4s, j) at buf[(lane + 32 s) * 9 + i] (pairs).
+// common one): r (registers) -> k, q -> j, p -> i through the warp's buffer,
+// the lane's two pencils packed.  Input as dense_inverse_f32 (floats); result:
+// the lane's nodal pencils (k0 + 4s, j) at buf[(lane + 32 s) * 9 + i] (pairs).
 __device__ __noinline__ void dense_inverse_pairs(float2* buf, const float* Ph, const float* Pl) {
     const int lane = threadIdx.x & 31, j = lane & 7, k0 = lane >> 3;
     const float* vin = reinterpret_cast<const float*>(buf);
-    f2 x[8], y[2][8];
+    p2 x[8], y[8];
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-#pragma unroll
-        for (int r = 0; r < 8; ++r) x[r] = {vin[(lane + 32 * s) * 9 + r], 0.0f};
-        inv1d_df<8>(Ph, Pl, x, y[s]);  // lane (q = k0 + 4s, p = j): values over k
-    }
+    for (int r = 0; r < 8; ++r)
+        x[r] = {make_float2(vin[lane * 9 + r], vin[(lane + 32) * 9 + r]), make_float2(0.0f, 0.0f)};
+    w_inv_df2(Ph, Pl, x, y);  // lane (q = k0 + 4s, p = j): values over k
     __syncwarp();
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) buf[(k0 + 4 * s) * TSK2 + j * TSJ2 + kk] = make_float2(y[s][kk].h, y[s][kk].l);
+        for (int kk = 0; kk < 8; ++kk)
+            buf[(k0 + 4 * s) * TSK2 + j * TSJ2 + kk] = s ? make_float2(y[kk].h.y, y[kk].l.y) : make_float2(y[kk].h.x, y[kk].l.x);
     __syncwarp();
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {  // lane (k = k0 + 4s, p = j): values over q
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const float2 v = buf[q * TSK2 + j * TSJ2 + k0 + 4 * s];
-            x[q] = {v.x, v.y};
-        }
-        inv1d_df<8>(Ph, Pl, x, y[s]);
+    for (int q = 0; q < 8; ++q) {  // lane (k = k0 + 4s, p = j): values over q
+        const float2 v0 = buf[q * TSK2 + j * TSJ2 + k0], v1 = buf[q * TSK2 + j * TSJ2 + k0 + 4];
+        x[q] = {make_float2(v0.x, v1.x), make_float2(v0.y, v1.y)};
     }
+    w_inv_df2(Ph, Pl, x, y);
     __syncwarp();
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) buf[(k0 + 4 * s) * TSK2 + j * TSJ2 + jj] = make_float2(y[s][jj].h, y[s][jj].l);
+        for (int jj = 0; jj < 8; ++jj)
+            buf[(k0 + 4 * s) * TSK2 + j * TSJ2 + jj] = s ? make_float2(y[jj].h.y, y[jj].l.y) : make_float2(y[jj].h.x, y[jj].l.x);
     __syncwarp();
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {  // lane (k = k0 + 4s, j): values over p
-#pragma unroll
-        for (int pp = 0; pp < 8; ++pp) {
-            const float2 v = buf[(k0 + 4 * s) * TSK2 + pp * TSJ2 + j];
-            x[pp] = {v.x, v.y};
-        }
-        inv1d_df<8>(Ph, Pl, x, y[s]);
+    for (int pp = 0; pp < 8; ++pp) {  // lane (k = k0 + 4s, j): values over p
+        const float2 v0 = buf[k0 * TSK2 + pp * TSJ2 + j], v1 = buf[(k0 + 4) * TSK2 + pp * TSJ2 + j];
+        x[pp] = {make_float2(v0.x, v1.x), make_float2(v0.y, v1.y)};
     }
+    w_inv_df2(Ph, Pl, x, y);
     __syncwarp();
 #pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-        for (int i = 0; i < 8; ++i) buf[(lane + 32 * s) * 9 + i] = make_float2(y[s][i].h, y[s][i].l);
+    for (int i = 0; i < 8; ++i) {
+        buf[lane * 9 + i] = make_float2(y[i].h.x, y[i].l.x);
+        buf[(lane + 32) * 9 + i] = make_float2(y[i].h.y, y[i].l.y);
+    }
     __syncwarp();
 }
 
@@ -935,7 +956,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
                     const float c = (pick(a2, wi) * qd + 12582912.0f) - 12582912.0f;  // round half to even (|y| < 2^22)
                     const uint32_t rank = swpre[wi] + __popc(wd & lt_mask);
                     if (qwrite) qdst[rank] = static_cast<int16_t>(c);
-                    if (rank < static_cast<uint32_t>(WSPARSE)) skl[rank] = make_int2(lane + 32 * wi, __float_as_int(c));
+                    if (rank < static_cast<uint32_t>(wsparse<DF>())) skl[rank] = make_int2(lane + 32 * wi, __float_as_int(c));
                 }
             }
         }
@@ -949,47 +970,58 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
             vh[i] = make_float2(0.0f, 0.0f);
             vl[i] = make_float2(0.0f, 0.0f);
         }
-        if (n_e <= static_cast<uint32_t>(WSPARSE)) {
+        if (n_e <= static_cast<uint32_t>(wsparse<DF>())) {
             if constexpr (DF) {
-                // kept modes grouped by their index p along i: u~(i) = sum_p B_p phi_p(x_i), with
-                // B_p = sum over the group of c 2^s phi_q(x_j) phi_r(x_k) for each pencil; phi_0 is
-                // constant, so the p = 0 group sets the pencil and costs nothing per point
-                uint32_t pmask = 0;
-                for (uint32_t tk = 0; tk < n_e; ++tk) pmask |= 1u << (skl[tk].x & 7);
-                for (uint32_t pm = pmask; pm; pm &= pm - 1) {
-                    const int pp = __ffs(pm) - 1;
-                    f2 B0 = {0.0f, 0.0f}, B1 = {0.0f, 0.0f};
-                    for (uint32_t tk = 0; tk < n_e; ++tk) {
-                        const int2 kv = skl[tk];
-                        if ((kv.x & 7) != pp) continue;
-                        const int qq = (kv.x >> 3) & 7, rr = kv.x >> 6;
-                        const float cs = __int_as_float(kv.y) * qu;  // c 2^s, exact
-                        const f2 fj = {sPTh[qq * 8 + j], sPTl[qq * 8 + j]};
-                        B0 = df_add(B0, df_mulf(df_mul(fj, {sPTh[rr * 8 + k0], sPTl[rr * 8 + k0]}), cs));
-                        B1 = df_add(B1, df_mulf(df_mul(fj, {sPTh[rr * 8 + k0 + 4], sPTl[rr * 8 + k0 + 4]}), cs));
+                // u~(i) = sum over kept modes of B phi_p(x_i), B = c 2^s phi_q(x_j) phi_r(x_k) per pencil,
+                // both pencils packed.  Two passes over the kept list: the modes with p = 0 (phi_0 is
+                // constant along the pencil) give one pair per pencil that starts every point; each
+                // other mode adds B phi_p(x_i) at the eight points
+                auto coef = [&](int2 kv) -> p2 {  // B of both pencils (k0, k0 + 4) as packed pairs
+                    const int qq = (kv.x >> 3) & 7, rr = kv.x >> 6;
+                    const float2 cs = f2dup(__int_as_float(kv.y) * qu);  // c 2^s, exact
+                    const float2 fjh = f2dup(sPTh[qq * 8 + j]), fjl = f2dup(sPTl[qq * 8 + j]);
+                    const float2 frh = make_float2(sPTh[rr * 8 + k0], sPTh[rr * 8 + k0 + 4]);
+                    const float2 frl = make_float2(sPTl[rr * 8 + k0], sPTl[rr * 8 + k0 + 4]);
+                    const float2 ph = f2mul(fjh, frh);
+                    const float2 pl = f2add(f2fma(fjh, frh, f2neg(ph)), f2fma(fjh, frl, f2mul(fjl, frh)));
+                    const float2 bh = f2mul(ph, cs);
+                    return {bh, f2fma(pl, cs, f2fma(ph, cs, f2neg(bh)))};
+                };
+                p2 c0 = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+                for (uint32_t tk = 0; tk < n_e; ++tk) {
+                    const int2 kv = skl[tk];
+                    if ((kv.x & 7) != 0) continue;
+                    const p2 B = coef(kv);
+                    const p2 sm = two_sum2(c0.h, B.h);
+                    c0 = fast_two_sum2(sm.h, f2add(sm.l, f2add(c0.l, B.l)));
+                }
+                {  // times phi_0, the same at every point
+                    const p2 ph0 = {f2dup(sPTh[0]), f2dup(sPTl[0])};
+                    p2 v0 = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+                    df_fma_acc2(v0, c0, ph0);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        vh[i] = v0.h;
+                        vl[i] = v0.l;
                     }
-                    if (pp == 0) {  // the first group: u~ = B_0 phi_0 at every point of the pencil
-                        const f2 c0 = df_mul(B0, {sPTh[0], sPTl[0]}), c1 = df_mul(B1, {sPTh[0], sPTl[0]});
+                }
+                for (uint32_t tk = 0; tk < n_e; ++tk) {
+                    const int2 kv = skl[tk];
+                    const int pp = kv.x & 7;
+                    if (pp == 0) continue;
+                    const p2 Bp = coef(kv);
+                    const float4* ch4 = reinterpret_cast<const float4*>(sPT2h + pp * 8);
+                    const float4* cl4 = reinterpret_cast<const float4*>(sPT2l + pp * 8);
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            vh[i] = make_float2(c0.h, c1.h);
-                            vl[i] = make_float2(c0.l, c1.l);
-                        }
-                    } else {
-                        const p2 Bp = {make_float2(B0.h, B1.h), make_float2(B0.l, B1.l)};
-                        const float4* ch4 = reinterpret_cast<const float4*>(sPT2h + pp * 8);
-                        const float4* cl4 = reinterpret_cast<const float4*>(sPT2l + pp * 8);
-#pragma unroll
-                        for (int i2 = 0; i2 < 4; ++i2) {
-                            const float4 ch = ch4[i2], cl = cl4[i2];  // points 2 i2, 2 i2 + 1 (duplicated)
-                            p2 acc0 = {vh[2 * i2], vl[2 * i2]}, acc1 = {vh[2 * i2 + 1], vl[2 * i2 + 1]};
-                            df_fma_acc2(acc0, Bp, {make_float2(ch.x, ch.y), make_float2(cl.x, cl.y)});
-                            df_fma_acc2(acc1, Bp, {make_float2(ch.z, ch.w), make_float2(cl.z, cl.w)});
-                            vh[2 * i2] = acc0.h;
-                            vl[2 * i2] = acc0.l;
-                            vh[2 * i2 + 1] = acc1.h;
-                            vl[2 * i2 + 1] = acc1.l;
-                        }
+                    for (int i2 = 0; i2 < 4; ++i2) {
+                        const float4 ch = ch4[i2], cl = cl4[i2];  // points 2 i2, 2 i2 + 1 (duplicated)
+                        p2 acc0 = {vh[2 * i2], vl[2 * i2]}, acc1 = {vh[2 * i2 + 1], vl[2 * i2 + 1]};
+                        df_fma_acc2(acc0, Bp, {make_float2(ch.x, ch.y), make_float2(cl.x, cl.y)});
+                        df_fma_acc2(acc1, Bp, {make_float2(ch.z, ch.w), make_float2(cl.z, cl.w)});
+                        vh[2 * i2] = acc0.h;
+                        vl[2 * i2] = acc0.l;
+                        vh[2 * i2 + 1] = acc1.h;
+                        vl[2 * i2 + 1] = acc1.l;
                     }
                 }
 #pragma unroll
