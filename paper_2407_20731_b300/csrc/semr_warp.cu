@@ -302,6 +302,40 @@ __device__ __noinline__ f2 exact_coef(const double* __restrict__ u, int pp, int 
     return warp_sum_pair(c);
 }
 
+// Settles every ambiguous keep or rounding decision of an element exactly (a rare path,
+// out of line): the lane's coefficients (s, r) are at buf[lane * 17 + 8 s + r]; each mode
+// with its bit set in the lane's amb is recomputed exactly, one at a time over the warp, and
+// a kept one becomes its code times 2^s (exact), so the quantisation reproduces the code of
+// the exact value.  Returns the lane's updated keep bits.
+__device__ __noinline__ uint32_t resolve_ambiguous(float* buf, uint32_t amb, uint32_t kb, const double* __restrict__ u,
+                                                   const float* sAh, const float* sAl, f2 t, float qd, float qu,
+                                                   unsigned& recomputed) {
+    const int lane = threadIdx.x & 31;
+    while (__any_sync(FULL, amb != 0u)) {
+        const int src = __ffs(__ballot_sync(FULL, amb != 0u)) - 1;
+        const int bsel = __shfl_sync(FULL, __ffs(amb) - 1, src);
+        const int ms = bsel >> 3, mr = bsel & 7;
+        const f2 c = exact_coef(u, src & 7, (src >> 3) + 4 * ms, mr, sAh, sAl);
+        ++recomputed;
+        if (lane == src) {
+            const bool keep = df_ge(df_mul(c, c), t);
+            float v = c.h;
+            if (keep) {
+                const float yh = c.h * qd, yl = c.l * qd;
+                float cc = (yh + 12582912.0f) - 12582912.0f;
+                const float diff = (yh - cc) + yl;
+                cc += (diff > 0.5f) ? 1.0f : ((diff < -0.5f) ? -1.0f : 0.0f);
+                v = cc * qu;
+            }
+            buf[lane * 17 + bsel] = v;
+            kb = keep ? (kb | (1u << bsel)) : (kb & ~(1u << bsel));
+            amb &= ~(1u << bsel);
+        }
+    }
+    __syncwarp();
+    return kb;
+}
+
 // 8-point even-odd folded inverse in FP32, both pencils packed (tables from the constant bank).
 __device__ __forceinline__ void w_inv2(const float* __restrict__ Ph, const float2 (&x)[8], float2 (&y)[8]) {
 #pragma unroll
@@ -796,37 +830,18 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
                             amb |= 1u << b;
                         }
                     }
-                // exact (float-pair) coefficient of each ambiguous mode, one at a time over the warp
-                while (__any_sync(FULL, amb != 0u)) {
-                    const int src = __ffs(__ballot_sync(FULL, amb != 0u)) - 1;
-                    const int bsel = __shfl_sync(FULL, __ffs(amb) - 1, src);
-                    const int ms = bsel >> 3, mr = bsel & 7;
-                    const f2 c = exact_coef(p.fields[f] + static_cast<uint64_t>(e) * WN3, src & 7, (src >> 3) + 4 * ms,
-                                            mr, sAh, sAl);
-                    ++recomputed;
-                    if (lane == src) {
-                        const bool keep = df_ge(df_mul(c, c), t);
-                        // a kept coefficient becomes its code times 2^s (exact), so the
-                        // quantisation below reproduces the code of the exact value
-                        float v = c.h;
-                        if (keep) {
-                            const float yh = c.h * qd, yl = c.l * qd;
-                            float cc = (yh + 12582912.0f) - 12582912.0f;
-                            const float diff = (yh - cc) + yl;
-                            cc += (diff > 0.5f) ? 1.0f : ((diff < -0.5f) ? -1.0f : 0.0f);
-                            v = cc * qu;
-                        }
+                // exact (float-pair) coefficient of each ambiguous mode (rare): out of line, with
+                // the lane's coefficients passed through the warp's transpose buffer (free here)
+                if (__any_sync(FULL, amb != 0u)) {
 #pragma unroll
-                        for (int s = 0; s < 2; ++s)
-#pragma unroll
-                            for (int r = 0; r < 8; ++r)
-                                if (8 * s + r == bsel) {
-                                    if (s == 0) a2[r].x = v;
-                                    else a2[r].y = v;
-                                }
-                        kb = keep ? (kb | (1u << bsel)) : (kb & ~(1u << bsel));
-                        amb &= ~(1u << bsel);
+                    for (int r = 0; r < 8; ++r) {
+                        tb[lane * 17 + r] = a2[r].x;
+                        tb[lane * 17 + 8 + r] = a2[r].y;
                     }
+                    kb = resolve_ambiguous(tb, amb, kb, p.fields[f] + static_cast<uint64_t>(e) * WN3, sAh, sAl, t, qd, qu,
+                                           recomputed);
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) a2[r] = make_float2(tb[lane * 17 + r], tb[lane * 17 + 8 + r]);
                 }
             }
         }
