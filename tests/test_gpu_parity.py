@@ -160,3 +160,45 @@ def test_fp32_form_many_codes_decode():
     dec = semr.semr_decode(res.payload)
     umax = np.abs(fields.cpu().numpy()).reshape(2, -1).max(axis=1)
     assert np.all(np.abs(dec - rec).reshape(2, -1).max(axis=1) <= 1e-5 * umax)
+
+
+def _kept_exactly(counts, n_fields, seed):
+    """lx = 8 blocks with a chosen number of kept modes: k coefficients of size
+    1..1.5 at random modes, the rest below 1e-7 (built through the oracle's
+    inverse transform).  At tau = 1e-2 exactly the k large ones are kept while
+    k <= 44 (the smallest share, 1 / (2.25 k), stays above tau)."""
+    rng = np.random.default_rng(seed)
+    E = len(counts)
+    f = np.empty((n_fields, E, 512))
+    for fi in range(n_fields):
+        for e, k in enumerate(counts):
+            a = rng.uniform(-1e-7, 1e-7, 512)
+            m = rng.choice(512, k, replace=False)
+            a[m] = rng.choice([-1.0, 1.0], k) * rng.uniform(1.0, 1.5, k)
+            f[fi, e] = oracle.inverse(8, a).reshape(-1)
+    j = rng.uniform(0.5, 2.0, E)
+    return torch.from_numpy(f).cuda().contiguous(), torch.from_numpy(j).cuda().contiguous()
+
+
+def test_sparse_and_dense_reconstruction_limits():
+    """Elements that keep just below and just above each sparse-path limit of the
+    lx = 8 kernel (10, 16 and 24 kept modes; past the limit the dense inverse
+    runs): FP64 mode bit-exact with the oracle and its reconstruction within
+    1e-12 max|u|; the FP32 form's counts as the oracle's and its codes within
+    one unit of the FP64 ones."""
+    counts = [1, 2, 9, 10, 11, 15, 16, 17, 23, 24, 25, 26, 40] * 19
+    fields, jac = _kept_exactly(counts, 2, seed=77)
+    f_np, j_np = fields.cpu().numpy(), jac.cpu().numpy()
+    o = oracle.reduce(f_np, j_np, 1e-2, fragile_cap=100000)
+    assert np.array_equal(oracle.sections(o.payload)["counts"][0], np.array(counts))
+    res, rec = run_gpu(fields, jac, 8, 1e-2)
+    assert res.summary.status == 0
+    compare_payloads(res.payload, o.payload, o.fragile)
+    compare_reports(f_np, j_np, rec, o, res.elem_report, res.summary, 8)
+    r32, rec32 = run_gpu(fields, jac, 8, 1e-2, precision=semr.SEMR_FP32)
+    g, s = oracle.sections(r32.payload), oracle.sections(o.payload)
+    assert np.array_equal(g["counts"], s["counts"]) and np.array_equal(g["masks"], s["masks"])
+    assert np.array_equal(g["steps"], s["steps"])
+    assert np.abs(g["codes"].astype(np.int32) - s["codes"].astype(np.int32)).max() <= 1
+    umax = np.abs(f_np).reshape(2, -1).max(axis=1)
+    assert np.abs(rec32 - o.recon).reshape(2, -1).max(axis=1).max() <= 2e-5 * umax.max()
