@@ -38,8 +38,11 @@ sys.path.insert(0, ROOT)
 N_SIDE, LX, N_FIELDS = 64, 8, 4
 SEEDS = [10, 11, 12, 13]
 METRIC = "snapshot GB/s reduced (FP64 input ingested per second)"
-KERNEL_SOURCES = ["paper_2407_20731_b300/csrc/semr_warp.cu", "paper_2407_20731_b300/csrc/semr_fast.cu",
-                  "paper_2407_20731_b300/csrc/semr_device.cuh", "paper_2407_20731_b300/csrc/semr_internal.h"]
+# sources of the kernel a profile summary covers: the warp kernel (threshold truncation at lx = 8)
+# and the CTA kernel (the cumulative variant)
+_CSRC = "paper_2407_20731_b300/csrc/"
+KERNEL_SOURCES = [_CSRC + "semr_warp.cu", _CSRC + "semr_device.cuh", _CSRC + "semr_internal.h"]
+CUMULATIVE_SOURCES = [_CSRC + "semr_fast.cu", _CSRC + "semr_device.cuh", _CSRC + "semr_internal.h"]
 # FP64 pipe of B300, nominal (the FP32 pipes run ~50x faster; FP64 mode runs on them)
 FP64_PIPE_TFLOPS_NOMINAL = 1.25
 
@@ -66,9 +69,9 @@ def parse_args():
     return ap.parse_args()
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(cumulative: bool = False) -> str:
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in (CUMULATIVE_SOURCES if cumulative else KERNEL_SOURCES):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -94,7 +97,7 @@ def profiled_traffic(precision: str, cumulative: bool = False):
     text = open(path).read()
     m_hash = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
     m_traf = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
-    if not (m_hash and m_traf) or m_hash.group(1) != kernel_source_hash():
+    if not (m_hash and m_traf) or m_hash.group(1) != kernel_source_hash(cumulative):
         return None
     return float(m_traf.group(1))
 
