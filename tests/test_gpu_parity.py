@@ -202,3 +202,25 @@ def test_sparse_and_dense_reconstruction_limits():
     assert np.abs(g["codes"].astype(np.int32) - s["codes"].astype(np.int32)).max() <= 1
     umax = np.abs(f_np).reshape(2, -1).max(axis=1)
     assert np.abs(rec32 - o.recon).reshape(2, -1).max(axis=1).max() <= 2e-5 * umax.max()
+
+
+@pytest.mark.parametrize("precision", [semr.SEMR_FP64, semr.SEMR_FP32])
+def test_lx8_nonfinite_and_out_of_range_flagged(precision):
+    """lx = 8 (the warp-per-element kernel): a NaN, an infinity and a value past
+    the float-pair range (|u| >= 2^127) each flag SEMR_STATUS_NONFINITE, and
+    their elements keep nothing.  Every other byte of the payload equals the
+    payload of the same snapshot with those three blocks set to zero (a zero
+    block also keeps nothing and stores the sentinel step)."""
+    fields, jac = make_case(300, 8, 2, seed=13)
+    zeroed = fields.clone()
+    bad = [(0, 5, 17, float("nan")), (0, 130, 0, float("inf")), (1, 200, 511, 1e39)]
+    for f, e, i, v in bad:
+        fields[f, e, i] = v
+        zeroed[f, e] = 0.0
+    res, _ = run_gpu(fields, jac, 8, 1e-3, precision=precision)
+    ref, _ = run_gpu(zeroed, jac, 8, 1e-3, precision=precision)
+    assert res.summary.status & semr.SEMR_STATUS_NONFINITE
+    assert ref.summary.status == 0
+    counts = oracle.sections(res.payload)["counts"]
+    assert all(counts[f, e] == 0 for f, e, _, _ in bad)
+    assert res.payload.size == ref.payload.size and np.array_equal(res.payload, ref.payload)
