@@ -298,6 +298,18 @@ int semr_reduce_async_noalloc(const semr_fieldset* fs, const semr_mesh* mesh, ui
                               uint64_t payload_cap, double* elem_report, semr_summary* summary,
                               void* cuda_stream);
 
+/* Self-test of the bounded device-side waits, with no fault and no hang: one
+ * warp runs (0) the decoupled look-back of a tile whose predecessor never
+ * publishes its state, and (1) the wait for a phase of an mbarrier that never
+ * completes, the two waits every reduction kernel bounds.  Each gives up at
+ * its bound (the look-back after 2^22 polls, about 2-3 s; the barrier after
+ * 1000 polls of at most 1 ms each) and records SEMR_STATUS_TIMEOUT; the
+ * kernel then returns and the context stays usable.  status_out: host
+ * uint32_t[2], receives the status word of each wait.  Blocks until done
+ * (current device, legacy default stream).  Returns SEMR_OK, SEMR_EINVAL
+ * (null status_out), SEMR_ENOMEM or SEMR_ECUDA. */
+int semr_selftest_waits(uint32_t* status_out);
+
 /* ------------------------------------------------------ batched launches */
 
 /* One snapshot of a batch: as for semr_reduce_async; out.scratch is ignored

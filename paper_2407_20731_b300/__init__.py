@@ -140,6 +140,7 @@ EXPORTS = [
                                                  ctypes.c_uint64, _P, _P, _P]),
     ("semr_slice_rgba", ctypes.c_int, [ctypes.POINTER(semr_lattice), ctypes.POINTER(_P), ctypes.POINTER(semr_slice),
                                        _P, _P, _P]),
+    ("semr_selftest_waits", ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32)]),
 ]
 SEMR_NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -237,6 +238,14 @@ def semr_decode(payload: np.ndarray) -> np.ndarray:
     _check(_lib.semr_decode(payload.ctypes.data_as(_P), payload.nbytes, out.ctypes.data_as(_P), out.size,
                             None, None, None), "semr_decode")
     return out
+
+
+def semr_selftest_waits() -> tuple[int, int]:
+    """Status words of the look-back and mbarrier waits made to run out (both
+    should be SEMR_STATUS_TIMEOUT)."""
+    out = (ctypes.c_uint32 * 2)()
+    _check(_lib.semr_selftest_waits(out), "semr_selftest_waits")
+    return int(out[0]), int(out[1])
 
 
 def semr_gll(lx: int) -> tuple[np.ndarray, np.ndarray]:

@@ -1426,6 +1426,21 @@ int launch_mode(const WArgs& a, const BatchQueue& q, uint64_t total_tiles, uint6
     return (int)cudaGetLastError();
 }
 
+// Self-test of the bounded waits: the look-back of tile 1, whose predecessor never
+// publishes, and phase 0 of an mbarrier that expects one arrival that never comes.
+// Each wait gives up at its bound and records SEMR_STATUS_TIMEOUT; nothing faults or hangs.
+__global__ void selftest_waits_kernel(uint64_t* tile_state, unsigned* status) {
+    __shared__ uint64_t bar;
+    const int lane = threadIdx.x & 31;
+    lookback_warp(tile_state, 1, 0, &status[0]);
+    if (lane == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (!mbar_wait_bounded(&bar, 0) && lane == 0) atomicOr(&status[1], static_cast<unsigned>(SEMR_STATUS_TIMEOUT));
+}
+
 }  // namespace
 
 bool warp_applicable(const LaunchParams& p) {
@@ -1500,3 +1515,21 @@ int launch_finalize_warp(const LaunchParams& p, void* stream) {
 }
 
 }  // namespace semr
+
+extern "C" int semr_selftest_waits(uint32_t* status_out) {
+    if (!status_out) return SEMR_EINVAL;
+    void* buf = nullptr;
+    if (cudaMalloc(&buf, 32) != cudaSuccess) return SEMR_ENOMEM;
+    int rc = SEMR_OK;
+    uint64_t* tile_state = static_cast<uint64_t*>(buf);            // 2 states, never published
+    unsigned* status = reinterpret_cast<unsigned*>(tile_state + 2);  // 2 status words
+    if (cudaMemset(buf, 0, 32) != cudaSuccess) rc = SEMR_ECUDA;
+    if (rc == SEMR_OK) {
+        semr::selftest_waits_kernel<<<1, 32>>>(tile_state, status);
+        if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+            cudaMemcpy(status_out, status, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = SEMR_ECUDA;
+    }
+    cudaFree(buf);
+    return rc;
+}
