@@ -91,8 +91,7 @@ struct WSmem {
     static constexpr size_t o_tb = 0;
     static constexpr size_t tb_bytes = DF ? 8 * 8 * TSK2 : 4 * 8 * TSK;
     static constexpr size_t o_mask = o_tb + tb_bytes;     // 16 mask words
-    static constexpr size_t o_wpre = o_mask + 64;         // 16 word prefixes
-    static constexpr size_t o_kl = o_wpre + 64;           // kept list (mode, code)
+    static constexpr size_t o_kl = o_mask + 64;           // kept list (mode, code)
     static constexpr size_t o_bar = o_kl + 8 * wsparse<DF>();
     static constexpr size_t wbytes = o_bar + 16;
     static constexpr size_t bytes = off_warp + WPB * wbytes + 512;  // + alignment slack
@@ -519,7 +518,6 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
     float* tb = reinterpret_cast<float*>(wb + SM::o_tb);
     float2* tb2 = reinterpret_cast<float2*>(wb + SM::o_tb);
     uint32_t* smask = reinterpret_cast<uint32_t*>(wb + SM::o_mask);
-    uint32_t* swpre = reinterpret_cast<uint32_t*>(wb + SM::o_wpre);
     int2* skl = reinterpret_cast<int2*>(wb + SM::o_kl);
     uint64_t* bar = reinterpret_cast<uint64_t*>(wb + SM::o_bar);
     if (lane == 0) {
@@ -846,10 +844,10 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
             }
         }
 
-        // ---- mask words: the ballot over (slot s, row r) is word w = s + 2r (bit = lane).  Each
-        // word's prefix goes to shared memory (with the word) for the quantisation below; nzw marks
-        // the words holding kept modes.  The FP32 form keeps all 16 words in registers and counts
-        // there; FP64 mode, short of registers, scans the words in shared memory
+        // ---- mask words: the ballot over (slot s, row r) is word w = s + 2r (bit = lane).  The
+        // words go to shared memory for the quantisation below; nzw marks the words holding kept
+        // modes.  The FP32 form keeps all 16 words in registers and counts there; FP64 mode, short
+        // of registers, counts them from shared memory
         uint8_t* fsec = p.payload + p.header_bytes + static_cast<uint64_t>(f) * p.fixed_bytes;
         uint4* mdst = reinterpret_cast<uint4*>(fsec + static_cast<uint64_t>(e) * 64);
         uint32_t n_e = 0, nzw = 0;
@@ -863,18 +861,8 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
             }
             __syncwarp();
             const uint32_t mw = (lane < 16) ? smask[lane] : 0u;
-            const uint32_t c = __popc(mw);
-            uint32_t incl = c;
-#pragma unroll
-            for (int o = 1; o < 16; o <<= 1) {
-                const uint32_t v = __shfl_up_sync(FULL, incl, o);
-                if (lane >= o) incl += v;
-            }
-            if (lane < 16) {
-                swpre[lane] = incl - c;
-                reinterpret_cast<uint32_t*>(mdst)[lane] = mw;
-            }
-            n_e = __shfl_sync(FULL, incl, 15);
+            if (lane < 16) reinterpret_cast<uint32_t*>(mdst)[lane] = mw;
+            n_e = __reduce_add_sync(FULL, static_cast<unsigned>(__popc(mw)));
             nzw = __ballot_sync(FULL, mw != 0u);
         } else {
             uint32_t wv[16];
@@ -889,18 +877,11 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
                 n_e += __popc(wv[w]);
             }
             if (lane == 0) {
-                uint32_t run = 0;
 #pragma unroll
                 for (int q4 = 0; q4 < 4; ++q4) {
                     const uint4 v = make_uint4(wv[4 * q4], wv[4 * q4 + 1], wv[4 * q4 + 2], wv[4 * q4 + 3]);
                     mdst[q4] = v;
                     reinterpret_cast<uint4*>(smask)[q4] = v;
-                    uint4 pr;
-                    pr.x = run; run += __popc(v.x);
-                    pr.y = run; run += __popc(v.y);
-                    pr.z = run; run += __popc(v.z);
-                    pr.w = run; run += __popc(v.w);
-                    reinterpret_cast<uint4*>(swpre)[q4] = pr;
                 }
             }
         }
@@ -963,16 +944,18 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
         __syncwarp();
         {
             const uint32_t lt_mask = (1u << lane) - 1u;
+            uint32_t run = 0;  // codes of the words before wi (the words come in increasing order)
             while (nzw) {
                 const int wi = __ffs(nzw) - 1;
                 nzw &= nzw - 1;
                 const uint32_t wd = smask[wi];
                 if ((wd >> lane) & 1u) {
                     const float c = (pick(a2, wi) * qd + 12582912.0f) - 12582912.0f;  // round half to even (|y| < 2^22)
-                    const uint32_t rank = swpre[wi] + __popc(wd & lt_mask);
+                    const uint32_t rank = run + __popc(wd & lt_mask);
                     if (qwrite) qdst[rank] = static_cast<int16_t>(c);
                     if (rank < static_cast<uint32_t>(wsparse<DF>())) skl[rank] = make_int2(lane + 32 * wi, __float_as_int(c));
                 }
+                run += __popc(wd);
             }
         }
         if (staged) atop += n_e;
