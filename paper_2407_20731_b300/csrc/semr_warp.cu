@@ -844,10 +844,10 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
             }
         }
 
-        // ---- mask words: the ballot over (slot s, row r) is word w = s + 2r (bit = lane).  The
-        // words go to shared memory for the quantisation below; nzw marks the words holding kept
-        // modes.  The FP32 form keeps all 16 words in registers and counts there; FP64 mode, short
-        // of registers, counts them from shared memory
+        // ---- mask words: the ballot over (slot s, row r) is word w = s + 2r (bit = lane).  Lane 0
+        // stores the 16 words to shared memory (and the payload); lane w < 16 then reads word w, so
+        // the count is one warp reduction and nzw (the words holding kept modes) one ballot.  The
+        // FP32 form ballots its threshold test directly; FP64 mode ballots its settled keep bits
         uint8_t* fsec = p.payload + p.header_bytes + static_cast<uint64_t>(f) * p.fixed_bytes;
         uint4* mdst = reinterpret_cast<uint4*>(fsec + static_cast<uint64_t>(e) * 64);
         uint32_t n_e = 0, nzw = 0;
@@ -871,11 +871,6 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
 #pragma unroll
                 for (int s = 0; s < 2; ++s)  // keep iff |a| >= g, the exact float threshold
                     wv[s + 2 * r] = __ballot_sync(FULL, emode == 1 && fabsf(s ? a2[r].y : a2[r].x) >= g);
-#pragma unroll
-            for (int w = 0; w < 16; ++w) {
-                nzw |= (wv[w] != 0u ? 1u : 0u) << w;
-                n_e += __popc(wv[w]);
-            }
             if (lane == 0) {
 #pragma unroll
                 for (int q4 = 0; q4 < 4; ++q4) {
@@ -884,6 +879,10 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
                     reinterpret_cast<uint4*>(smask)[q4] = v;
                 }
             }
+            __syncwarp();
+            const uint32_t mw = (lane < 16) ? smask[lane] : 0u;
+            n_e = __reduce_add_sync(FULL, static_cast<unsigned>(__popc(mw)));
+            nzw = __ballot_sync(FULL, mw != 0u);
         }
         // payload: step and count (lane 0)
         const uint64_t mb = static_cast<uint64_t>(E) * 64;  // mask section (a multiple of 16)
