@@ -942,6 +942,13 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
         }
         __syncwarp();
         {
+            if constexpr (DF) {  // the lane's coefficients by word index w = s + 2r, in the warp's
+                // transpose buffer (free here; rows of 20 floats, conflict-free 16-byte stores)
+                float4* arow = reinterpret_cast<float4*>(tb + lane * 20);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    arow[q] = make_float4(a2[2 * q].x, a2[2 * q].y, a2[2 * q + 1].x, a2[2 * q + 1].y);
+            }
             const uint32_t lt_mask = (1u << lane) - 1u;
             uint32_t run = 0;  // codes of the words before wi (the words come in increasing order)
             while (nzw) {
@@ -949,7 +956,8 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
                 nzw &= nzw - 1;
                 const uint32_t wd = smask[wi];
                 if ((wd >> lane) & 1u) {
-                    const float c = (pick(a2, wi) * qd + 12582912.0f) - 12582912.0f;  // round half to even (|y| < 2^22)
+                    const float a = DF ? tb[lane * 20 + wi] : pick(a2, wi);
+                    const float c = (a * qd + 12582912.0f) - 12582912.0f;  // round half to even (|y| < 2^22)
                     const uint32_t rank = run + __popc(wd & lt_mask);
                     if (qwrite) qdst[rank] = static_cast<int16_t>(c);
                     if (rank < static_cast<uint32_t>(wsparse<DF>())) skl[rank] = make_int2(lane + 32 * wi, __float_as_int(c));
