@@ -2,26 +2,29 @@
 // JPEG-like truncation of the modal Legendre coefficients of SEM element
 // blocks, keeping the most energetic modes; Eq. 1 for the compression ratio).
 //
-// One warp reduces one element-field (an 8^3 block, 4 KB of FP64) at a time
-// and claims the next one from a global counter, so nothing in the loop waits
-// on the rest of the CTA:
+// One warp reduces one element-field (an 8^3 block, 4 KB of FP64) at a time.
+// A CTA of four warps claims look-back tiles of 128 consecutive elements of one
+// field from a global counter (warp w takes elements w, w + 4, ...), and no CTA
+// barrier runs per element:
 //   * TMA: the block arrives in the warp's shared-memory stage as a 2-D tile
 //     (64 pencils x 8 doubles, 64-byte swizzle), so every lane reads its two
-//     pencils with conflict-free 16-byte loads; the next element is requested
-//     as soon as these values are in registers and streams in meanwhile;
-//   * lane L owns the pencils P = L and L + 32 (P = j + 8k) in every phase:
-//     the forward transform contracts i in registers, then j and k after two
-//     padded transposes in shared memory private to the warp; the inverse
-//     runs the other way round, so each lane ends with the pencils it loaded;
+//     pencils with conflict-free 16-byte loads; the warp's next block is
+//     requested as soon as these values are in registers and streams in meanwhile;
+//   * lane L owns the pencils P = L and L + 32 (P = j + 8k) in every phase, the
+//     two packed as FP32x2: the forward transform contracts i in registers, then
+//     j and k after two padded transposes in shared memory private to the warp;
+//     the inverse runs the other way round, so each lane ends with the pencils
+//     it loaded;
 //   * coefficient a[r][q][p] of mode m = p + 8q + 64r lands in lane m & 31,
 //     slot (m >> 5) & 1, register r: each of the 16 ballots over (slot, r) is
 //     exactly mask word m >> 5 of the payload;
-//   * element sums are warp shuffles; the code count is published for the
-//     decoupled look-back right after the mask, the predecessors' states are
-//     read before the reconstruction and consumed after it;
-//   * per-element norm partials are collected for 32 elements and converted
-//     to FP64 by all lanes at once: B300's FP64 pipe runs at ~1/64 of the
-//     FP32 rate, so no FP64 instruction runs per point or per element.
+//   * element sums are warp shuffles; each warp stages its codes in its own
+//     arena; at the end of a tile the CTA publishes the tile's code count, then
+//     resolves the previous tile's prefix (decoupled look-back, one tile late,
+//     so it rarely waits) and copies that tile's staged codes to their place;
+//   * the elements' norm partials are kept per tile and converted to FP64 by all
+//     lanes at once: B300's FP64 pipe runs at ~1/64 of the FP32 rate, so no FP64
+//     instruction runs per point or per element.
 // Precision modes as in semr_fast.cu: SEMR_FP32 runs FP32 transforms with an
 // exact float-pair threshold test; SEMR_FP64 runs the forward transform in
 // FP32 under a proven error bound, recomputes exactly (float pairs) every
