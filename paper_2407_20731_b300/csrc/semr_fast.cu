@@ -188,9 +188,12 @@ __device__ __forceinline__ void elem_reduce(float* red, double* out, f2 s, unsig
 
 // Resident threads per SM the register budget aims at: enough warps to hide
 // the latency of the tile's barrier phases, without spilling the larger orders.
+// FP64 mode with 2-element tiles (lx >= 9), measured: 768 threads (3 CTAs at lx
+// 9-10, 2 at lx 12) beat 512; at lx = 11 the third CTA's register cap spills.
 constexpr int min_ctas_per_sm(int lx, int mode, int block) {
     const int target = (mode & MODE_CUM) ? (!(mode & MODE_DF64) ? 768 : 512)
-                       : !(mode & MODE_DF64) ? (lx <= 10 ? 1024 : 768) : (lx <= 8 ? 1024 : 512);
+                       : !(mode & MODE_DF64) ? (lx <= 10 ? 1024 : 768)
+                                             : (lx <= 8 ? 1024 : lx == 11 ? 512 : 768);
     return target / block > 0 ? target / block : 1;
 }
 
@@ -1194,7 +1197,7 @@ int batch_mode(const BatchQueue& q, int lx, int tile, void* stream) {
     SEMR_BATCH_CASE(8, 8)
     SEMR_BATCH_CASE(9, tile_elems(9))
     SEMR_BATCH_CASE(10, tile_elems(10))
-    SEMR_BATCH_CASE(10, 2)
+    SEMR_BATCH_CASE(10, 4)
     SEMR_BATCH_CASE(11, tile_elems(11))
     SEMR_BATCH_CASE(12, tile_elems(12))
 #undef SEMR_BATCH_CASE
@@ -1208,7 +1211,7 @@ int tile_variants(int lx, int* out, int cap) {
     int n = 1;
     if (lx == 6) v[n++] = 16;
     if (lx == 8) v[n++] = 8;
-    if (lx == 10) v[n++] = 2;
+    if (lx == 10) v[n++] = 4;
     for (int i = 0; i < n && i < cap; ++i) out[i] = v[i];
     return n;
 }
