@@ -79,7 +79,7 @@ SEMR_HD inline uint64_t scratch_zero_bytes(uint64_t tiles) { return kScratchCont
 
 // Elements per tile (one CTA per tile) for a given lx.
 SEMR_HD constexpr int tile_elems(int lx) {
-    return lx <= 2 ? 64 : lx <= 3 ? 32 : lx <= 5 ? 16 : lx <= 6 ? 8 : lx <= 8 ? 4 : 2;
+    return lx <= 2 ? 32 : lx <= 3 ? 16 : lx <= 6 ? 8 : lx <= 8 ? 4 : 2;
 }
 
 struct ScratchControl {
