@@ -190,10 +190,10 @@ __device__ __forceinline__ void elem_reduce(float* red, double* out, f2 s, unsig
 // the latency of the tile's barrier phases, without spilling the larger orders.
 // FP64 mode with 2-element tiles (lx >= 9), measured: 768 threads (3 CTAs at lx
 // 9-10, 2 at lx 12) beat 512; at lx = 11 the third CTA's register cap spills.
-// The cumulative variant in FP64 mode: 1024 threads up to lx = 6, 768 above
-// (measured at lx = 6, 8 and 10 against 512).
+// The cumulative variant: 1024 threads in the FP32 form; in FP64 mode 1024 up to
+// lx = 6 and 768 above (measured at lx = 6, 8 and 10 against 512 and 768).
 constexpr int min_ctas_per_sm(int lx, int mode, int block) {
-    const int target = (mode & MODE_CUM) ? (!(mode & MODE_DF64) ? 768 : (lx <= 6 ? 1024 : 768))
+    const int target = (mode & MODE_CUM) ? (!(mode & MODE_DF64) ? 1024 : (lx <= 6 ? 1024 : 768))
                        : !(mode & MODE_DF64) ? (lx <= 10 ? 1024 : 768)
                                              : (lx <= 8 ? 1024 : lx == 11 ? 512 : 768);
     return target / block > 0 ? target / block : 1;
