@@ -46,6 +46,11 @@
  *   code = rint(a_m * 2^{-s_e}), ties to even.  Codes are int16 when
  *   tau * 32767^2 > 4 (then |code| <= 2 / sqrt(tau) < 32767), else int32.
  *   An element with t below the smallest normal double keeps nothing.
+ *   The result depends on the field's magnitude only through exact powers of
+ *   two: every element is read as u * 2^-k, k the binary exponent of its
+ *   largest |u|, so scaling a field by 2^j leaves masks, counts and codes
+ *   unchanged and shifts every step by j (for magnitudes 2^-1022 <= |u| <
+ *   2^500; the status bits below flag elements outside that range).
  */
 #ifndef SEMR_H
 #define SEMR_H
@@ -104,7 +109,13 @@ extern "C" {
 /* summary.status bits (device-written) */
 #define SEMR_STATUS_OVERFLOW 1    /* payload_cap too small: codes not written */
 #define SEMR_STATUS_TIMEOUT 2     /* look-back wait gave up */
-#define SEMR_STATUS_NONFINITE 4   /* some element energy was NaN/Inf */
+#define SEMR_STATUS_NONFINITE 4   /* an element held a NaN, an infinity or a magnitude of 2^500 or more
+                                     (its energy would overflow FP64 arithmetic): that element keeps
+                                     nothing */
+#define SEMR_STATUS_TINY 8        /* informational, not an error: an element held only subnormal values
+                                     (every |u| < 2^-1022).  It keeps nothing, as an FP64 evaluation
+                                     does (its t = tau S_e underflows), and its e2_e, E_e and Linf_e
+                                     are reported as 0 where FP64 gives values below 2^-1022 */
 
 typedef struct {
     int32_t lx;            /* GLL points per direction, SEMR_LX_MIN..SEMR_LX_MAX */
@@ -116,7 +127,8 @@ typedef struct {
 typedef struct {
     int32_t n_fields;                 /* 1..SEMR_MAX_FIELDS */
     int32_t precision;                /* SEMR_FP64 or SEMR_FP32 */
-    double tau;                       /* threshold, finite, >= 0; 0 = lossless mode */
+    double tau;                       /* threshold: 0 (lossless mode) or 2^-60 < tau <= 2^64 (for smaller
+                                         tau a code 2/sqrt(tau) would not fit int32) */
     int32_t flags;                    /* SEMR_WRITE_RECON | SEMR_CUMULATIVE, or 0 */
     int32_t pad_;
     const double* fields[SEMR_MAX_FIELDS];  /* device, n_elem*lx^3 FP64 each */
@@ -209,11 +221,23 @@ int semr_reduce_async_timed(const semr_fieldset* fs, const semr_mesh* mesh, cons
                             void* cuda_stream, void* ev_begin, void* ev_end);
 
 /*
- * semr_open: a reduction stream with library-owned buffers.
+ * semr_open: a reduction stream with library-owned buffers (the hand-over of
+ * a snapshot from the simulation to the in-situ reduction, Sec. III-A: the
+ * producer submits and goes on; results are fetched when ready).
  *   device: CUDA device ordinal.  cuda_stream: cudaStream_t to order work on
  *   (NULL: the library creates its own non-blocking stream).
- *   mem_budget_bytes: upper bound on device memory that in-flight tickets may
- *   hold (payload worst case + scratch + reports); 0 = no bound.
+ *   mem_budget_bytes: upper bound on device memory that unfetched tickets may
+ *   hold (payload + scratch + reports); 0 = no bound.
+ * A ticket's payload is sized for an estimate of its codes: twice the
+ * largest share of modes kept by the stream's completed tickets (1/16 of all
+ * modes before the first completes), plus 4096 codes, at most every mode.  A
+ * ticket whose codes do not fit is re-run once, at the exact size its first
+ * run reports, when its completion is next observed (semr_query or
+ * semr_fetch); the field and Jacobian buffers must therefore stay valid
+ * until semr_query returns SEMR_OK or semr_fetch succeeds.  The stream's
+ * calls are thread-safe with respect to each other, except semr_close,
+ * which must not overlap any other call on the stream.  No call holds the
+ * stream's lock while it waits for the device or copies.
  * Errors: SEMR_EINVAL, SEMR_ECUDA, SEMR_ENOMEM.
  */
 int semr_open(semr_stream** s, int device, void* cuda_stream, uint64_t mem_budget_bytes);
@@ -228,18 +252,26 @@ int semr_open(semr_stream** s, int device, void* cuda_stream, uint64_t mem_budge
  */
 int semr_submit(semr_stream* s, const semr_fieldset* fs, const semr_mesh* mesh, uint64_t* ticket);
 
-/* semr_query: SEMR_OK when the ticket's work is complete, SEMR_EAGAIN if not,
- * SEMR_EINVAL for an unknown ticket. */
+/* semr_query: SEMR_OK when the ticket's results are final, SEMR_EAGAIN if
+ * its work (or its exact-size re-run, started by this call) is still running,
+ * SEMR_EBUDGET if that re-run does not fit the budget next to the other
+ * unfetched tickets (fetch some, then query again), SEMR_EINVAL for an unknown
+ * ticket, SEMR_ENOMEM / SEMR_ECUDA if the re-run could not be started. */
 int semr_query(semr_stream* s, uint64_t ticket);
 
 /*
  * semr_fetch: copy a ticket's results to host memory and release the ticket.
- *   wait: nonzero blocks until complete; zero returns SEMR_EAGAIN if not.
+ *   wait: nonzero blocks until the results are final (through a re-run, if
+ *   one is needed); zero returns SEMR_EAGAIN if they are not.
  *   payload (host, cap bytes) or NULL; *payload_bytes gets the size.
  *   reports (host, n_fields entries) or NULL; elem_report (host, n_fields *
  *   n_elem * 3 doubles) or NULL.
- * Errors: SEMR_EAGAIN, SEMR_EINVAL, SEMR_ENOSPACE (cap too small: nothing
- * copied, ticket kept), SEMR_ETIMEDOUT / SEMR_ENONFINITE (device status;
+ * The copies run on a copy stream of the library's, ordered after this
+ * ticket's work only.
+ * Errors: SEMR_EAGAIN (not final, or another fetch of the ticket is in
+ * progress), SEMR_EINVAL (unknown ticket), SEMR_EBUDGET (as semr_query),
+ * SEMR_ENOSPACE (cap too small: nothing copied, ticket kept; *payload_bytes
+ * holds the size needed), SEMR_ETIMEDOUT / SEMR_ENONFINITE (device status;
  * results copied, ticket released), SEMR_ECUDA.
  */
 int semr_fetch(semr_stream* s, uint64_t ticket, int wait, void* payload, uint64_t cap,

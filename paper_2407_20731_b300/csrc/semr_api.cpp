@@ -24,6 +24,9 @@ int check_common(int32_t lx, int64_t n_elem, int32_t n_fields, double tau) {
     const uint64_t n3 = uint64_t(lx) * lx * lx;
     if (uint64_t(n_elem) * n3 >= (1ull << 40)) return SEMR_EINVAL;
     if (!(tau >= 0.0) || std::isinf(tau)) return SEMR_EINVAL;
+    // a kept code is at most 2/sqrt(tau) in magnitude: below 2^-60 it would not fit int32;
+    // above 2^64 nothing can be kept (a_m^2 <= S_e) and t = tau S_e may leave the range
+    if (tau != 0.0 && (tau <= 0x1p-60 || tau > 0x1p64)) return SEMR_EINVAL;
     return SEMR_OK;
 }
 
@@ -143,39 +146,150 @@ extern "C" int semr_reduce_async_timed(const semr_fieldset* fs, const semr_mesh*
 }
 
 // ------------------------------------------------------------ stream API
+//
+// A ticket owns one stream-ordered device allocation (payload | scratch |
+// summary | element report).  The payload is sized for an estimate of the
+// snapshot's codes, not for every mode kept (which would be about 14 times
+// the payload of a 64^3 x 4 snapshot at tau = 1e-3): the estimate is twice
+// the largest share of modes kept by the stream's completed tickets (1/16 of
+// all modes before the first one), plus 4096 codes.  A ticket whose codes
+// do not fit is re-run once at its exact size, which the first run reports
+// (its counts and steps are complete; only the codes were not written).
+// Each ticket's summary is copied to pinned host memory behind the kernels,
+// so completion and its status are known without a device round trip.  No
+// call holds the stream's lock across a device wait or a copy.
+
+namespace {
+
+uint64_t align256(uint64_t b) { return (b + 255) & ~uint64_t(255); }
+
+constexpr int kPinnedChunk = 64;  // pinned summaries allocated together
+
+}  // namespace
 
 struct Ticket {
-    uint8_t* dev = nullptr;       // one allocation: payload | scratch | summary | elem report
-    uint64_t bytes = 0;
+    uint8_t* dev = nullptr;   // payload | scratch | summary | elem report
+    uint64_t bytes = 0;       // of dev (what the budget counts)
     uint64_t payload_cap = 0;
-    uint64_t off_scratch = 0, off_summary = 0, off_elem = 0;
-    int32_t n_fields = 0;
-    int64_t n_elem = 0;
+    uint64_t off_scratch = 0, off_summary = 0, off_elem = 0, scratch_bytes = 0;
     cudaEvent_t done = nullptr;
+    semr_summary* host_sum = nullptr;  // pinned, written by the stream before `done`
+    semr_fieldset fs{};        // the request, kept for a re-run at the exact size
+    semr_mesh mesh{};
+    uint64_t modes = 0;        // n_fields * n_elem * lx^3
+    bool rerun = false;        // already re-run once
+    bool busy = false;         // a fetch is waiting for or copying this ticket
 };
 
 struct semr_stream {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t copy_stream = nullptr;  // device-to-host copies of fetched results
     uint64_t budget = 0;
     uint64_t in_flight = 0;
     uint64_t next_ticket = 1;
+    double fill = 1.0 / 16;  // largest share of modes kept so far (payload estimate)
+    bool fill_seen = false;
     std::unordered_map<uint64_t, Ticket> tickets;
-    semr_summary* host_summary = nullptr;  // pinned
+    std::vector<semr_summary*> pinned_free;
+    std::vector<semr_summary*> pinned_chunks;
     std::mutex mu;
 };
 
 namespace {
 
-uint64_t align256(uint64_t b) { return (b + 255) & ~uint64_t(255); }
+semr_summary* pinned_get(semr_stream* s) {  // with s->mu held
+    if (s->pinned_free.empty()) {
+        semr_summary* c = nullptr;
+        if (cudaMallocHost(reinterpret_cast<void**>(&c), sizeof(semr_summary) * kPinnedChunk) != cudaSuccess)
+            return nullptr;
+        s->pinned_chunks.push_back(c);
+        for (int k = kPinnedChunk - 1; k >= 0; --k) s->pinned_free.push_back(c + k);
+    }
+    semr_summary* p = s->pinned_free.back();
+    s->pinned_free.pop_back();
+    return p;
+}
 
-void release(semr_stream* s, Ticket& t) {
+// Allocate a ticket's device block for a payload of `payload_cap` bytes and
+// launch its reduction, the summary copy and the completion event (s->mu held).
+int ticket_launch(semr_stream* s, Ticket& t, const semr_sizes& sz, uint64_t payload_cap) {
+    t.payload_cap = payload_cap;
+    t.off_scratch = align256(payload_cap);
+    t.off_summary = align256(t.off_scratch + sz.scratch_bytes);
+    t.off_elem = align256(t.off_summary + sizeof(semr_summary));
+    t.bytes = align256(t.off_elem + sz.elem_report_bytes);
+    t.scratch_bytes = sz.scratch_bytes;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&t.dev), t.bytes, s->stream) != cudaSuccess) {
+        t.dev = nullptr;
+        return SEMR_ENOMEM;
+    }
+    semr_outputs o;
+    o.payload = t.dev;
+    o.payload_cap = t.payload_cap;
+    o.elem_report = reinterpret_cast<double*>(t.dev + t.off_elem);
+    o.summary = reinterpret_cast<semr_summary*>(t.dev + t.off_summary);
+    o.scratch = t.dev + t.off_scratch;
+    o.scratch_bytes = t.scratch_bytes;
+    int rc = semr_reduce_async(&t.fs, &t.mesh, &o, s->stream);
+    if (rc == SEMR_OK && cudaMemcpyAsync(t.host_sum, o.summary, sizeof(semr_summary), cudaMemcpyDeviceToHost,
+                                         s->stream) != cudaSuccess)
+        rc = SEMR_ECUDA;
+    if (rc == SEMR_OK && cudaEventRecord(t.done, s->stream) != cudaSuccess) rc = SEMR_ECUDA;
+    if (rc != SEMR_OK) {
+        cudaFreeAsync(t.dev, s->stream);
+        t.dev = nullptr;
+    }
+    return rc;
+}
+
+void release(semr_stream* s, Ticket& t) {  // s->mu held
     if (t.dev) cudaFreeAsync(t.dev, s->stream);
     if (t.done) cudaEventDestroy(t.done);
+    if (t.host_sum) s->pinned_free.push_back(t.host_sum);
     s->in_flight -= t.bytes;
     t.dev = nullptr;
     t.done = nullptr;
+    t.host_sum = nullptr;
+}
+
+// State of a ticket (s->mu held): SEMR_OK when its results are final,
+// SEMR_EAGAIN while its work runs (a ticket whose codes overflowed its first
+// payload is re-run here at the exact size), SEMR_EBUDGET when that re-run
+// does not fit the budget next to the other tickets in flight (their memory
+// is freed only when they are fetched), or an error.
+int ticket_state(semr_stream* s, Ticket& t) {
+    const cudaError_t e = cudaEventQuery(t.done);
+    if (e == cudaErrorNotReady) return SEMR_EAGAIN;
+    if (e != cudaSuccess) return SEMR_ECUDA;
+    const semr_summary& sm = *t.host_sum;
+    if (!(sm.status & SEMR_STATUS_OVERFLOW)) {
+        if (t.modes) {
+            const double share = double(sm.code_total) / double(t.modes);
+            if (!s->fill_seen || share > s->fill) s->fill = share;
+            s->fill_seen = true;
+        }
+        return SEMR_OK;
+    }
+    if (t.rerun || (sm.status & ~uint32_t(SEMR_STATUS_OVERFLOW))) return SEMR_OK;  // reported as it stands
+    semr_sizes sz;
+    if (semr_sizes_for(t.mesh.lx, t.mesh.n_elem, t.fs.n_fields, t.fs.tau, &sz) != SEMR_OK) return SEMR_EINVAL;
+    const uint64_t need = std::max<uint64_t>(sm.payload_bytes, sz.code_base);
+    const uint64_t grow = align256(align256(need) + sz.scratch_bytes + sizeof(semr_summary) + 512 +
+                                   sz.elem_report_bytes);
+    if (s->budget && s->in_flight - t.bytes + grow > s->budget) return SEMR_EBUDGET;
+    Ticket old = t;
+    t.rerun = true;
+    const int rc = ticket_launch(s, t, sz, need);
+    if (rc != SEMR_OK) {
+        t = old;
+        t.rerun = true;
+        return rc;
+    }
+    cudaFreeAsync(old.dev, s->stream);
+    s->in_flight = s->in_flight - old.bytes + t.bytes;
+    return SEMR_EAGAIN;
 }
 
 }  // namespace
@@ -200,10 +314,10 @@ extern "C" int semr_open(semr_stream** out, int device, void* cuda_stream, uint6
         }
         s->own_stream = true;
     }
-    if (cudaMallocHost(&s->host_summary, sizeof(semr_summary)) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
         if (s->own_stream) cudaStreamDestroy(s->stream);
         delete s;
-        return SEMR_ENOMEM;
+        return SEMR_ECUDA;
     }
     *out = s;
     return SEMR_OK;
@@ -215,33 +329,26 @@ extern "C" int semr_submit(semr_stream* s, const semr_fieldset* fs, const semr_m
     int rc = semr_sizes_for(mesh->lx, mesh->n_elem, fs->n_fields, fs->tau, &sz);
     if (rc) return rc;
     Ticket t;
-    t.n_fields = fs->n_fields;
-    t.n_elem = mesh->n_elem;
-    t.payload_cap = sz.payload_worst;
-    t.off_scratch = align256(sz.payload_worst);
-    t.off_summary = align256(t.off_scratch + sz.scratch_bytes);
-    t.off_elem = align256(t.off_summary + sizeof(semr_summary));
-    t.bytes = align256(t.off_elem + sz.elem_report_bytes);
+    t.fs = *fs;
+    t.mesh = *mesh;
+    t.modes = uint64_t(fs->n_fields) * uint64_t(mesh->n_elem) * uint64_t(mesh->lx) * mesh->lx * mesh->lx;
     std::lock_guard<std::mutex> lk(s->mu);
-    if (s->budget && s->in_flight + t.bytes > s->budget) return SEMR_EBUDGET;
+    const double est = std::min(1.0, 2.0 * s->fill) * double(t.modes) + 4096.0;
+    const uint64_t cap = std::min<uint64_t>(sz.payload_worst, sz.code_base + sz.code_width * uint64_t(est));
+    const uint64_t bytes = align256(align256(cap) + sz.scratch_bytes + sizeof(semr_summary) + 512 +
+                                    sz.elem_report_bytes);
+    if (s->budget && s->in_flight + bytes > s->budget) return SEMR_EBUDGET;
     if (cudaSetDevice(s->device) != cudaSuccess) return SEMR_ECUDA;
-    if (cudaMallocAsync(reinterpret_cast<void**>(&t.dev), t.bytes, s->stream) != cudaSuccess) return SEMR_ENOMEM;
+    t.host_sum = pinned_get(s);
+    if (!t.host_sum) return SEMR_ENOMEM;
     if (cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming) != cudaSuccess) {
-        cudaFreeAsync(t.dev, s->stream);
+        s->pinned_free.push_back(t.host_sum);
         return SEMR_ECUDA;
     }
-    semr_outputs o;
-    o.payload = t.dev;
-    o.payload_cap = t.payload_cap;
-    o.elem_report = reinterpret_cast<double*>(t.dev + t.off_elem);
-    o.summary = reinterpret_cast<semr_summary*>(t.dev + t.off_summary);
-    o.scratch = t.dev + t.off_scratch;
-    o.scratch_bytes = sz.scratch_bytes;
-    rc = semr_reduce_async(fs, mesh, &o, s->stream);
-    if (rc == SEMR_OK && cudaEventRecord(t.done, s->stream) != cudaSuccess) rc = SEMR_ECUDA;
+    rc = ticket_launch(s, t, sz, cap);
     if (rc != SEMR_OK) {
-        cudaFreeAsync(t.dev, s->stream);
         cudaEventDestroy(t.done);
+        s->pinned_free.push_back(t.host_sum);
         return rc;
     }
     s->in_flight += t.bytes;
@@ -255,46 +362,64 @@ extern "C" int semr_query(semr_stream* s, uint64_t ticket) {
     std::lock_guard<std::mutex> lk(s->mu);
     auto it = s->tickets.find(ticket);
     if (it == s->tickets.end()) return SEMR_EINVAL;
-    cudaError_t e = cudaEventQuery(it->second.done);
-    if (e == cudaSuccess) return SEMR_OK;
-    if (e == cudaErrorNotReady) return SEMR_EAGAIN;
-    return SEMR_ECUDA;
+    if (cudaSetDevice(s->device) != cudaSuccess) return SEMR_ECUDA;
+    return ticket_state(s, it->second);
 }
 
 extern "C" int semr_fetch(semr_stream* s, uint64_t ticket, int wait, void* payload, uint64_t cap,
                           uint64_t* payload_bytes, semr_field_report* reports, double* elem_report) {
     if (!s) return SEMR_EINVAL;
-    std::lock_guard<std::mutex> lk(s->mu);
+    std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->tickets.find(ticket);
     if (it == s->tickets.end()) return SEMR_EINVAL;
-    Ticket& t = it->second;
-    if (!wait) {
-        cudaError_t e = cudaEventQuery(t.done);
-        if (e == cudaErrorNotReady) return SEMR_EAGAIN;
-        if (e != cudaSuccess) return SEMR_ECUDA;
-    } else if (cudaEventSynchronize(t.done) != cudaSuccess) {
-        return SEMR_ECUDA;
-    }
+    if (it->second.busy) return SEMR_EAGAIN;  // another fetch of this ticket is in progress
     if (cudaSetDevice(s->device) != cudaSuccess) return SEMR_ECUDA;
-    if (cudaMemcpy(s->host_summary, t.dev + t.off_summary, sizeof(semr_summary), cudaMemcpyDeviceToHost) !=
-        cudaSuccess)
-        return SEMR_ECUDA;
-    const semr_summary& sm = *s->host_summary;
+    for (;;) {  // until the results are final; waits run without the lock
+        const int st = ticket_state(s, it->second);
+        if (st == SEMR_OK) break;
+        if (st != SEMR_EAGAIN || !wait) return st;
+        const cudaEvent_t ev = it->second.done;
+        it->second.busy = true;
+        lk.unlock();
+        const cudaError_t e = cudaEventSynchronize(ev);
+        lk.lock();
+        it = s->tickets.find(ticket);
+        if (it == s->tickets.end()) return SEMR_EINVAL;  // closed meanwhile
+        it->second.busy = false;
+        if (e != cudaSuccess) return SEMR_ECUDA;
+    }
+    Ticket& t = it->second;
+    const semr_summary sm = *t.host_sum;
     if (payload_bytes) *payload_bytes = sm.payload_bytes;
-    if (payload && cap < sm.payload_bytes) return SEMR_ENOSPACE;
-    if (payload && cudaMemcpy(payload, t.dev, sm.payload_bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
-        return SEMR_ECUDA;
-    if (reports) std::memcpy(reports, sm.field, sizeof(semr_field_report) * t.n_fields);
-    if (elem_report &&
-        cudaMemcpy(elem_report, t.dev + t.off_elem, 24ull * t.n_elem * t.n_fields, cudaMemcpyDeviceToHost) !=
+    if (payload && cap < sm.payload_bytes) return SEMR_ENOSPACE;  // nothing copied, ticket kept
+    if (reports) std::memcpy(reports, sm.field, sizeof(semr_field_report) * t.fs.n_fields);
+    const uint8_t* dev = t.dev;
+    const uint64_t off_elem = t.off_elem;
+    const uint64_t elem_bytes = 24ull * uint64_t(t.mesh.n_elem) * t.fs.n_fields;
+    const cudaEvent_t done = t.done;
+    t.busy = true;
+    lk.unlock();
+    // copies on the stream's copy stream, ordered after the ticket's work only
+    int rc = SEMR_OK;
+    if (cudaStreamWaitEvent(s->copy_stream, done, 0) != cudaSuccess) rc = SEMR_ECUDA;
+    if (rc == SEMR_OK && payload && sm.payload_bytes &&
+        cudaMemcpyAsync(payload, dev, sm.payload_bytes, cudaMemcpyDeviceToHost, s->copy_stream) != cudaSuccess)
+        rc = SEMR_ECUDA;
+    if (rc == SEMR_OK && elem_report &&
+        cudaMemcpyAsync(elem_report, dev + off_elem, elem_bytes, cudaMemcpyDeviceToHost, s->copy_stream) !=
             cudaSuccess)
-        return SEMR_ECUDA;
-    const uint32_t status = sm.status;
-    release(s, t);
+        rc = SEMR_ECUDA;
+    if (cudaStreamSynchronize(s->copy_stream) != cudaSuccess) rc = SEMR_ECUDA;
+    lk.lock();
+    it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) return SEMR_EINVAL;  // closed meanwhile
+    it->second.busy = false;
+    if (rc != SEMR_OK) return rc;
+    release(s, it->second);
     s->tickets.erase(it);
-    if (status & SEMR_STATUS_TIMEOUT) return SEMR_ETIMEDOUT;
-    if (status & SEMR_STATUS_OVERFLOW) return SEMR_ENOSPACE;
-    if (status & SEMR_STATUS_NONFINITE) return SEMR_ENONFINITE;
+    if (sm.status & SEMR_STATUS_TIMEOUT) return SEMR_ETIMEDOUT;
+    if (sm.status & SEMR_STATUS_OVERFLOW) return SEMR_ENOSPACE;
+    if (sm.status & SEMR_STATUS_NONFINITE) return SEMR_ENONFINITE;
     return SEMR_OK;
 }
 
@@ -304,10 +429,12 @@ extern "C" void semr_close(semr_stream* s) {
         std::lock_guard<std::mutex> lk(s->mu);
         cudaSetDevice(s->device);
         cudaStreamSynchronize(s->stream);
+        cudaStreamSynchronize(s->copy_stream);
         for (auto& kv : s->tickets) release(s, kv.second);
         s->tickets.clear();
         cudaStreamSynchronize(s->stream);
-        if (s->host_summary) cudaFreeHost(s->host_summary);
+        for (semr_summary* c : s->pinned_chunks) cudaFreeHost(c);
+        cudaStreamDestroy(s->copy_stream);
         if (s->own_stream) cudaStreamDestroy(s->stream);
     }
     delete s;

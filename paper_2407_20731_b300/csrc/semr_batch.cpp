@@ -162,7 +162,7 @@ int build_workspace(semr_batch* b, cudaStream_t st) {
             p.tile_state = reinterpret_cast<uint64_t*>(b->ws + zoff + kScratchControlBytes);
             p.tile_part = reinterpret_cast<double*>(b->ws + poff);
             if (G.warp()) {
-                p.umax_elem = reinterpret_cast<float*>(b->ws + uoff);
+                p.hmax_elem = reinterpret_cast<uint32_t*>(b->ws + uoff);
                 uoff = align256(uoff + 4ull * uint64_t(it.mesh.n_elem) * it.fs.n_fields);
                 p.code_stage = reinterpret_cast<int16_t*>(b->ws + G.off_stage);
                 p.stage_ctas = (int32_t)G.stage_ctas;
@@ -236,7 +236,7 @@ int probe_warp(const semr_batch_item& it, int precision, cudaStream_t st, cudaEv
     p.ctl = reinterpret_cast<ScratchControl*>(w + o_zero + 256);
     p.tile_state = reinterpret_cast<uint64_t*>(w + o_zero + 256 + kScratchControlBytes);
     p.tile_part = reinterpret_cast<double*>(w + o_part);
-    p.umax_elem = reinterpret_cast<float*>(w + o_umax);
+    p.hmax_elem = reinterpret_cast<uint32_t*>(w + o_umax);
     p.code_stage = reinterpret_cast<int16_t*>(w + o_stage);
     p.stage_ctas = (int32_t)stage_ctas;
     std::vector<uint8_t> maps(kTensorMapBytes * nf);

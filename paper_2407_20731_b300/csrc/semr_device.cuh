@@ -154,21 +154,40 @@ __device__ __forceinline__ float threshold_abs32_fast(double t) {
 
 // Round-toward-zero conversion of a double with |u| in the normal float
 // range (or zero) using integer instructions only (B300 runs F2F on its
-// slow FP64 pipe).  Magnitudes below 2^-126 come out as (near) zero.
+// slow FP64 pipe).  Magnitudes below 2^-126 come out as zero.
 __device__ __forceinline__ float d2f_rz(double u) {
     const int lo = __double2loint(u), hi = __double2hiint(u);
     const int t = (hi & 0x7fffffff) - 0x38000000;  // rebias the exponent: 1023 -> 127
     const int f = t > 0 ? __funnelshift_l(lo, t, 3) : 0;  // (t << 3) | (lo >> 29)
     return __int_as_float(f | (hi & 0x80000000));
 }
-
-// Split u into uh + ul: uh = u rounded toward zero to 24 bits, ul the
-// remaining 29 mantissa bits rounded to a float (so |u - uh - ul| <= 2^-48
-// |u|).  Integer instructions plus one I2F and one FMUL.
-__device__ __forceinline__ void d2f_split(double u, float& uh, float& ul) {
+// d2f_rz of u 2^-ke, for an exact power-of-two prescale given as kb = ke << 20.
+__device__ __forceinline__ float d2f_rz_scaled(double u, int kb) {
     const int lo = __double2loint(u), hi = __double2hiint(u);
-    const int e = (hi >> 20) & 0x7ff;
-    const int t = (hi & 0x7fffffff) - 0x38000000;
+    const int t = (hi & 0x7fffffff) - 0x38000000 - kb;
+    const int f = t > 0 ? __funnelshift_l(lo, t, 3) : 0;
+    return __int_as_float(f | (hi & 0x80000000));
+}
+// Prescale exponent of an element from its largest high word of |u| (sign
+// cleared): ke with max |u| 2^-ke in [1, 2); 0 for an element of zeros and
+// subnormals (hmax < 2^20), at most 1023.
+__device__ __forceinline__ int prescale_exponent(uint32_t hmax) {
+    return hmax < 0x00100000u ? 0 : min((int)(hmax >> 20) - 1023, 1023);
+}
+// Element flags from the same word: NaN, infinity or |u| >= 2^500 (energies
+// beyond FP64); only subnormal values (|u| < 2^-1022).
+__device__ __forceinline__ bool hmax_bad(uint32_t hmax) { return hmax >= ((uint32_t)(1023 + 500) << 20); }
+__device__ __forceinline__ bool hmax_tiny(uint32_t hmax) { return hmax < 0x00100000u; }
+
+// Split u 2^-ke into uh + ul, for an exact power-of-two prescale given as
+// kb = ke << 20: uh = u 2^-ke rounded toward zero to 24 bits, ul the
+// remaining 29 mantissa bits rounded to a float (so |u 2^-ke - uh - ul| <=
+// 2^-48 |u 2^-ke|); both exactly 0 when |u 2^-ke| < 2^-126.  Integer
+// instructions plus one I2F and one FMUL.
+__device__ __forceinline__ void d2f_split(double u, int kb, float& uh, float& ul) {
+    const int lo = __double2loint(u), hi = __double2hiint(u);
+    const int e = ((hi >> 20) & 0x7ff) - (kb >> 20);
+    const int t = (hi & 0x7fffffff) - 0x38000000 - kb;  // rebias the exponent: 1023 + ke -> 127
     uh = __int_as_float((t > 0 ? __funnelshift_l(lo, t, 3) : 0) | (hi & 0x80000000));
     // remainder: (lo & 0x1fffffff) * 2^(e - 1075)
     const float rem = __uint2float_rn((unsigned)lo & 0x1fffffffu);
@@ -179,11 +198,6 @@ __device__ __forceinline__ void d2f_split(double u, float& uh, float& ul) {
     ul = (t > 0) ? __int_as_float(__float_as_int(r) | (hi & 0x80000000)) : 0.0f;
 }
 
-// True when a double cannot go through the float-pair path: NaN, infinity,
-// or a magnitude of 2^127 or more.
-__device__ __forceinline__ bool out_of_float_range(double u) {
-    return ((__double2hiint(u) >> 20) & 0x7ff) >= 1023 + 127;
-}
 
 // ------------------------------------------------- FP32-pair arithmetic
 

@@ -244,8 +244,8 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
     int* s_epre = s_cnt + TILE;          // [TILE + 1]
     int* s_step = s_epre + TILE + 1;     // [TILE]
     int* s_mode = s_step + TILE;         // [TILE]
-    int* s_bad = s_mode + TILE;          // [TILE]
-    int* s_flag = s_bad + TILE;          // [2]: dense inverse needed
+    uint32_t* s_hx = reinterpret_cast<uint32_t*>(s_mode + TILE);  // [TILE] largest high word of |u|
+    int* s_flag = reinterpret_cast<int*>(s_hx + TILE);  // [2]: dense inverse needed
     float* s_g = reinterpret_cast<float*>(s_flag + 2);  // [2 * TILE]: threshold (hi, lo)
     float* s_marg = s_g + 2 * TILE;                       // [TILE]: bound on |a_fp32 - a|
     // cumulative variant
@@ -329,7 +329,7 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
     if constexpr (!C::BALLOT) {
         for (int i = tid; i < TILE * MW; i += C::BLOCK) smask[i] = 0u;
     }
-    if (tid < TILE) s_bad[tid] = 0;
+    if (tid < TILE) s_hx[tid] = 0u;
     __syncthreads();
     const uint64_t tile = s_tile[0];
     if (tile == ~0ull) break;
@@ -351,9 +351,12 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
     const bool active = (tid < C::NT) && (lt < n_here);
     const int64_t e = e0 + lt;
 
-    // ---- load the pencil u[k=pa][j=pb][0..LX-1], split to floats with integer ops
+    // ---- load the pencil u[k=pa][j=pb][0..LX-1], split to floats with integer ops.  The
+    // element is read as u 2^-ke, ke the binary exponent of its largest |u| (an exact
+    // power-of-two prescale: masks and codes do not change under it, steps and norms are
+    // scaled back exactly), so every value formed below lies near 1 whatever the field's units.
     float uh[LX], ul[LX];
-    unsigned long long umax_bits = 0;  // max |u|: exact double pattern (FP64 mode) or float pattern
+    unsigned long long umax_bits = 0;  // max |u|: exact double pattern
     {
         double u[LX];
         if (active) {
@@ -373,20 +376,31 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
 #pragma unroll
             for (int i = 0; i < LX; ++i) u[i] = 0.0;
         }
-        bool bad = false;
+        uint32_t hm = 0;  // largest high word of |u| in the pencil, then in the element
 #pragma unroll
         for (int i = 0; i < LX; ++i) {
-            bad |= out_of_float_range(u[i]);
+            umax_bits = max(umax_bits, (unsigned long long)__double_as_longlong(u[i]) & 0x7fffffffffffffffull);
+            hm = max(hm, (uint32_t)__double2hiint(u[i]) & 0x7fffffffu);
+        }
+        if constexpr (C::ALIGNED) {  // the element's lanes of this warp first
+            const unsigned seg_mask =
+                (C::SEG == 32) ? 0xffffffffu : (((1u << C::SEG) - 1u) << (lane & ~(C::SEG - 1)));
+            hm = __reduce_max_sync(seg_mask, hm);
+            if ((lane & (C::SEG - 1)) == 0 && in_tile) atomicMax(&s_hx[lt], hm);
+        } else if (in_tile) {
+            atomicMax(&s_hx[lt], hm);
+        }
+        __syncthreads();
+        const int kb = prescale_exponent(in_tile ? s_hx[lts] : 0u) << 20;
+#pragma unroll
+        for (int i = 0; i < LX; ++i) {
             if constexpr (DF) {
-                umax_bits = max(umax_bits, (unsigned long long)__double_as_longlong(u[i]) & 0x7fffffffffffffffull);
-                d2f_split(u[i], uh[i], ul[i]);
+                d2f_split(u[i], kb, uh[i], ul[i]);
             } else {
-                uh[i] = d2f_rz(u[i]);
+                uh[i] = d2f_rz_scaled(u[i], kb);
                 ul[i] = 0.0f;
-                umax_bits = max(umax_bits, (unsigned long long)__float_as_uint(fabsf(uh[i])));
             }
         }
-        if (bad) s_bad[lt] = 1;  // read after the next barrier
     }
 
     // ---- forward transform in FP32 along i (registers), j, k (shared-memory
@@ -486,7 +500,7 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
         }
         if (tid < TILE) s_ncand[tid] = 0;
     }
-    elem_reduce<LX, TILE_, DF>(red, selem, sp, umax_bits, DF, 0, 2, n_here);  // S -> [0], max|u| -> [2]
+    elem_reduce<LX, TILE_, DF>(red, selem, sp, umax_bits, true, 0, 2, n_here);  // S' -> [0], max|u| -> [2]
 
     // ---- per element (one thread each): t = tau S, step s, magnitude threshold g
     if (tid < TILE) {
@@ -498,22 +512,34 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
             s_cK[l] = 0;
             s_tint[l] = 0ull;
         }
+        const uint32_t hx = s_hx[l];
+        const int ke = prescale_exponent(hx);
         if (l < n_here) {
-            if (!isfinite(Se) || s_bad[l]) {
+            if (!isfinite(Se) || hmax_bad(hx)) {
                 atomicOr(&ctl->status, (unsigned)SEMR_STATUS_NONFINITE);
             } else if (p.lossless) {
                 mode = 2;
+                if (hmax_tiny(hx)) atomicOr(&ctl->status, (unsigned)SEMR_STATUS_TINY);
+            } else if (hmax_tiny(hx)) {  // zeros and subnormals only: keeps nothing, norms 0
+                if (hx != 0u) atomicOr(&ctl->status, (unsigned)SEMR_STATUS_TINY);
             } else {
+                // t' = tau S' of the prescaled block (S' >= min w_i w_j w_k > 3e-6 and tau > 2^-60:
+                // normal); the element's t = t' 2^2ke, so ex = ex' + 2 ke and s_e = s' + ke with
+                // s' = floor((ex' - 1) / 2).  s_step holds s', which the codes and the
+                // reconstruction use; the payload gets s' + ke
                 const double t = p.tau * Se;
-                if (t >= DBL_MIN && isfinite(t)) {
-                    const long long bits = __double_as_longlong(t);
-                    const int ex = (int)((bits >> 52) & 0x7ff) - 1022;
-                    const int st = (ex - 1) >> 1;
-                    if (st >= -250 && st <= 250) {  // 2^-s as a product of two normal floats
+                const long long bits = __double_as_longlong(t);
+                const int exs = (int)((bits >> 52) & 0x7ff) - 1022;
+                const int ex = exs + 2 * ke;
+                if (!isfinite(t) || !(t >= DBL_MIN) || ex > 1024) {  // t overflows FP64
+                    atomicOr(&ctl->status, (unsigned)SEMR_STATUS_NONFINITE);
+                } else if (ex >= -1021) {  // t >= 2^-1022, the smallest normal double
+                    const int st = (exs - 1) >> 1;
+                    if (st >= -250 && st <= 250) {  // 2^-s' as a product of two normal floats
                         step = st;
                         mode = 1;
-                        if constexpr (CUM) {  // t in [2^(ex-1), 2^ex): K = 48 - ex, floor(t 2^K) = M >> 5
-                            s_cK[l] = 48 - ex;
+                        if constexpr (CUM) {  // t' in [2^(ex'-1), 2^ex'): K = 48 - ex', floor(t' 2^K) = M >> 5
+                            s_cK[l] = 48 - exs;
                             s_tint[l] = (((unsigned long long)bits & 0xfffffffffffffull) | (1ull << 52)) >> 5;
                         }
                         // FP64 mode refines g to the exact double threshold only for elements
@@ -522,8 +548,6 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
                     } else {
                         atomicOr(&ctl->status, (unsigned)SEMR_STATUS_NONFINITE);
                     }
-                } else if (!isfinite(t)) {
-                    atomicOr(&ctl->status, (unsigned)SEMR_STATUS_NONFINITE);
                 }
             }
         }
@@ -535,8 +559,10 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
         // bound on |a_fp32 - a|: (H + 2) roundings per folded contraction (H terms, the fold,
         // the table), 3 contractions, 2 more for the input split; (|A|^3 |u|)_m <= 2^1.5 max|u|
         // because every row of A has sum |A_pi| <= sqrt(2); a factor 2 of safety on top.
+        // max |u 2^-ke| rounded toward zero (the top 20 mantissa bits of hx, in [1, 2)).
         constexpr float kMarg = (3.0f * ((LX + 1) / 2 + 2) + 2.0f) * 5.9604645e-8f * 2.8285f * 2.0f;
-        s_marg[l] = kMarg * (float)selem[l * 8 + 2] * 1.0000002f;
+        const float umx = hmax_tiny(hx) ? 0.0f : __uint_as_float(0x3f800000u | ((hx & 0xfffffu) << 3));
+        s_marg[l] = kMarg * umx * 1.000002f;
     }
     __syncthreads();
     const int emode = in_tile ? s_mode[lt] : 0;
@@ -810,7 +836,8 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
                 const int rank = (int)swpre[lt * MW + (m >> 5)] +
                                  __popc(smask[lt * MW + (m >> 5)] & ((1u << (m & 31)) - 1u));
                 if constexpr (S::code_b == 8)  // the launcher sends lossless work only to kernels with 8-B staging
-                    reinterpret_cast<double*>(scodes)[s_epre[lt] + rank] = (double)ah[r] + (double)al[r];
+                    reinterpret_cast<double*>(scodes)[s_epre[lt] + rank] =
+                        ((double)ah[r] + (double)al[r]) * pow2d(prescale_exponent(s_hx[lt]));
             }
         }
     } else {
@@ -1000,10 +1027,11 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
             }
             linf_bits = dm;
         }
-        if (p.write_recon && p.recon[f]) {
+        if (p.write_recon && p.recon[f]) {  // u~ = u~' 2^ke (exact)
             double* dst = p.recon[f] + e * N3 + P * LX;
+            const double sc = pow2d(prescale_exponent(s_hx[lt]));
 #pragma unroll
-            for (int i = 0; i < LX; ++i) dst[i] = (double)vh[i] + (double)vl[i];
+            for (int i = 0; i < LX; ++i) dst[i] = ((double)vh[i] + (double)vl[i]) * sc;
         }
     }
     elem_reduce<LX, TILE_, DF>(red, selem, e2p, linf_bits, DF, 1, 3, n_here);  // e2/J -> [1], Linf -> [3]
@@ -1015,11 +1043,12 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
     }
     if (tid == 32 % C::BLOCK) {  // another warp, when there is one
         double s0 = 0.0, s1 = 0.0, m2 = 0.0, m3 = 0.0;
-        for (int l = 0; l < n_here; ++l) {
+        for (int l = 0; l < n_here; ++l) {  // back from the prescaled block: 2^2ke, 2^ke
             const double J = p.jac[e0 + l];
-            s0 += J * selem[l * 8 + 1];
-            s1 += J * selem[l * 8 + 0];
-            m2 = fmax(m2, selem[l * 8 + 3]);
+            const double sc = pow2d(prescale_exponent(s_hx[l]));
+            s0 += J * ((selem[l * 8 + 1] * sc) * sc);
+            s1 += J * ((selem[l * 8 + 0] * sc) * sc);
+            m2 = fmax(m2, selem[l * 8 + 3] * sc);
             m3 = fmax(m3, selem[l * 8 + 2]);
         }
         double* tp = tile_part + 4 * tile;
@@ -1071,7 +1100,7 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
         int16_t* sdst = reinterpret_cast<int16_t*>(fsec + pad16((uint64_t)p.n_elem * mb));
         uint16_t* cdst = reinterpret_cast<uint16_t*>(fsec + pad16((uint64_t)p.n_elem * mb) + pad16(2ull * p.n_elem));
         if (tid < n_here) {
-            sdst[e0 + tid] = (int16_t)s_step[tid];
+            sdst[e0 + tid] = (int16_t)(s_mode[tid] == 1 ? s_step[tid] + prescale_exponent(s_hx[tid]) : INT16_MIN);
             cdst[e0 + tid] = (uint16_t)s_cnt[tid];
         }
         if (e0 + n_here == p.n_elem && tid < 16) {
@@ -1088,7 +1117,9 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
         if (p.elem_report && tid < 3 * n_here) {
             const int l = tid / 3, c = tid % 3;
             const double J = p.jac[e0 + l];
-            const double v = (c == 0) ? J * selem[l * 8 + 1] : (c == 1) ? J * selem[l * 8 + 0] : selem[l * 8 + 3];
+            const double sc = pow2d(prescale_exponent(s_hx[l]));
+            const double v = (c == 0) ? J * ((selem[l * 8 + 1] * sc) * sc)
+                                      : (c == 1) ? J * ((selem[l * 8 + 0] * sc) * sc) : selem[l * 8 + 3] * sc;
             p.elem_report[((uint64_t)f * p.n_elem + e0) * 3 + tid] = v;
         }
     }

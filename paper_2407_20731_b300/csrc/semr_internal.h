@@ -46,7 +46,7 @@ SEMR_HD inline uint64_t scratch_bytes(uint64_t tiles) {
 
 // Warp-per-element kernel (lx = 8): look-back tiles of kWarpTile elements of one
 // field, CTAs of kWarpCtaWarps warps.  Scratch: [control][tile_state][tile_part]
-// [umax_elem f32 x n_fields * n_elem][staging per resident CTA (at most
+// [hmax_elem u32 x n_fields * n_elem][staging per resident CTA (at most
 // kWarpStageCtas): for two tiles, each warp's codes in an arena of kWarpArena int16,
 // the within-tile prefixes and the elements' arena offsets].  An element whose
 // codes do not fit its warp's arena writes them at their final place directly.
@@ -116,7 +116,7 @@ struct LaunchParams {
     int32_t tile;   // elements per tile of the kernel variant that runs this item
     int32_t cumulative;  // cumulative-energy truncation (never together with lossless)
     int32_t stage_ctas;  // warp kernel: CTAs the code staging holds (its grid is at most this)
-    float* umax_elem;    // warp kernel: max |u| per element-field, rounded toward zero to float
+    uint32_t* hmax_elem; // warp kernel: per element-field, the largest high word of |u| (orders like max |u|)
     int16_t* code_stage; // warp kernel: kWarpTile x 512 staged codes per CTA
 };
 
@@ -133,7 +133,7 @@ inline void split_scratch(LaunchParams& p, uint8_t* scratch, uint64_t tiles) {
 inline void split_scratch_warp(LaunchParams& p, uint8_t* scratch, uint64_t bytes, int64_t n_elem, int32_t n_fields) {
     const uint64_t t = warp_tiles(n_elem, n_fields);
     split_scratch(p, scratch, t);
-    p.umax_elem = reinterpret_cast<float*>(scratch + scratch_bytes(t));
+    p.hmax_elem = reinterpret_cast<uint32_t*>(scratch + scratch_bytes(t));
     const uint64_t head = warp_scratch_head(n_elem, n_fields);
     p.code_stage = reinterpret_cast<int16_t*>(scratch + head);
     uint64_t ctas = (bytes - head) / kWarpStageBytes;

@@ -58,14 +58,15 @@ struct WTables {         // lx = 8 tables, as kernel parameters (constant bank)
     float Ah[64], Al[64];  // analysis A[p][i] (hi, lo)
     float Ph[64], Pl[64];  // synthesis Phi[i][p] (hi, lo)
     float wh[8], wl[8];    // GLL weights (hi, lo)
+    float2 w2[8];          // GLL weights (hi), duplicated for the packed FP32 error sums
 };
 
 struct WStash {    // one element's results, kept until the end of its tile
-    uint32_t pad;
-    float umax;    // max |u| rounded toward zero to float
-    float sh, sl;  // S = sum w u^2 (pair; FP32 form: sl = 0)
-    float eh, el;  // e2 = sum w (u - u~)^2 (pair)
-    float lh, ll;  // Linf = max |u - u~| (pair)
+    int32_t ke;     // the element's prescale exponent: the values below are those of u 2^-ke
+    uint32_t hmax;  // largest high word of |u| (orders the elements like max |u|)
+    float sh, sl;   // S = sum w u^2 (pair; FP32 form: sl = 0)
+    float eh, el;   // e2 = sum w (u - u~)^2 (pair)
+    float lh, ll;   // Linf = max |u - u~| (pair)
 };
 static_assert(sizeof(WStash) == 32, "stash entry");
 
@@ -136,15 +137,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     for (uint32_t it = 0; it < kWaitPolls && !ok; ++it) ok = mbar_try_wait(bar, parity);
     return __all_sync(FULL, ok);
 }
-// Round-toward-zero float of a double (integer instructions; |u| >= 2^-126 or it comes out ~0).
-__device__ __forceinline__ float w_d2f_rz(uint32_t lo, uint32_t hi) {
-    const int t = max(static_cast<int>(hi & 0x7fffffffu) - 0x38000000, 0);  // rebias 1023 -> 127
+// Round-toward-zero float of u 2^-ke for a double u = (lo, hi), with bias = 0x38000000 + (ke << 20)
+// (integer instructions; the exponent is rebiased from 1023 + ke to 127, so the scaling is exact;
+// values with |u 2^-ke| < 2^-126 come out ~0).
+__device__ __forceinline__ float w_d2f_rz(uint32_t lo, uint32_t hi, int bias) {
+    const int t = max(static_cast<int>(hi & 0x7fffffffu) - bias, 0);
     return __uint_as_float(__funnelshift_l(lo, static_cast<uint32_t>(t), 3) | (hi & 0x80000000u));
 }
-// u = uh + ul: uh rounded toward zero to 24 bits, ul the next 23 bits (|u - uh - ul| < 2^-46 |u|);
-// both zero-ish below 2^-80.
-__device__ __forceinline__ void w_split(uint32_t lo, uint32_t hi, float& uh, float& ul) {
-    uh = w_d2f_rz(lo, hi);
+// u 2^-ke = uh + ul: uh rounded toward zero to 24 bits, ul the next 23 bits (|u 2^-ke - uh - ul| <
+// 2^-46 |u 2^-ke|); both zero-ish below 2^-80.
+__device__ __forceinline__ void w_split(uint32_t lo, uint32_t hi, int bias, float& uh, float& ul) {
+    uh = w_d2f_rz(lo, hi, bias);
     // mantissa bits 28..6 of the low word, an exact float integer via the 2^23 magic number
     const float m = __uint_as_float(((lo >> 6) & 0x7fffffu) | 0x4b000000u) - 8388608.0f;
     // their unit is 2^(E - 46) for uh = 1.x 2^E: exponent field of uh minus 46 (clamped at 0)
@@ -281,7 +284,7 @@ __device__ __forceinline__ uint64_t lookback_peek(const uint64_t* tile_state, ui
 // line, and the block is reread from global memory (it was just loaded, so L2 holds it)
 // rather than from the stage, which already receives the warp's next block.
 __device__ __noinline__ f2 exact_coef(const double* __restrict__ u, int pp, int qq, int rr, const float* sAh,
-                                      const float* sAl) {
+                                      const float* sAl, int bias) {
     const int lane = threadIdx.x & 31, j = lane & 7, k0 = lane >> 3;
     f2 c = {0.0f, 0.0f};
 #pragma unroll
@@ -292,8 +295,8 @@ __device__ __noinline__ f2 exact_coef(const double* __restrict__ u, int pp, int 
         for (int cc = 0; cc < 4; ++cc) {
             const uint4 v = __ldg(row + cc);
             float h0, l0, h1, l1;
-            w_split(v.x, v.y, h0, l0);
-            w_split(v.z, v.w, h1, l1);
+            w_split(v.x, v.y, bias, h0, l0);
+            w_split(v.z, v.w, bias, h1, l1);
             df_fma_acc(xs, {sAh[pp * 8 + 2 * cc], sAl[pp * 8 + 2 * cc]}, {h0, l0});
             df_fma_acc(xs, {sAh[pp * 8 + 2 * cc + 1], sAl[pp * 8 + 2 * cc + 1]}, {h1, l1});
         }
@@ -310,14 +313,14 @@ __device__ __noinline__ f2 exact_coef(const double* __restrict__ u, int pp, int 
 // a kept one becomes its code times 2^s (exact), so the quantisation reproduces the code of
 // the exact value.  Returns the lane's updated keep bits.
 __device__ __noinline__ uint32_t resolve_ambiguous(float* buf, uint32_t amb, uint32_t kb, const double* __restrict__ u,
-                                                   const float* sAh, const float* sAl, f2 t, float qd, float qu,
-                                                   unsigned& recomputed) {
+                                                   const float* sAh, const float* sAl, int bias, f2 t, float qd,
+                                                   float qu, unsigned& recomputed) {
     const int lane = threadIdx.x & 31;
     while (__any_sync(FULL, amb != 0u)) {
         const int src = __ffs(__ballot_sync(FULL, amb != 0u)) - 1;
         const int bsel = __shfl_sync(FULL, __ffs(amb) - 1, src);
         const int ms = bsel >> 3, mr = bsel & 7;
-        const f2 c = exact_coef(u, src & 7, (src >> 3) + 4 * ms, mr, sAh, sAl);
+        const f2 c = exact_coef(u, src & 7, (src >> 3) + 4 * ms, mr, sAh, sAl, bias);
         ++recomputed;
         if (lane == src) {
             const bool keep = df_ge(df_mul(c, c), t);
@@ -502,18 +505,15 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
         if constexpr (DF) sPT2l[c * 8 + i] = f2dup(A.tab.Pl[t]);
     }
     // quadrature weight products w_i w_j w_k of point i of pencils P = lane and lane + 32 (P = j + 8k):
-    // FP64 mode [i][lane] = (hi0, hi1, lo0, lo1), FP32 form [i][P] (hi)
-    for (int t = threadIdx.x; t < 512; t += WPB * 32) {
+    // FP64 mode [i][lane] = (hi0, hi1, lo0, lo1); the FP32 form forms its error sums as
+    // sum_i w_i (w_j w_k d_i^2) with the w_j w_k of its two pencils in a register pair
+    for (int t = threadIdx.x; DF && t < 512; t += WPB * 32) {
         const int i = t >> 6, P = t & 63, jj = P & 7, kk = P >> 3;
         const f2 w3 = df_mul({A.tab.wh[i], A.tab.wl[i]},
                              df_mul({A.tab.wh[jj], A.tab.wl[jj]}, {A.tab.wh[kk], A.tab.wl[kk]}));
-        if constexpr (DF) {
-            float* wt = reinterpret_cast<float*>(smem + SM::off_wq) + (i * 32 + (P & 31)) * 4;
-            wt[P >> 5] = w3.h;
-            wt[2 + (P >> 5)] = w3.l;
-        } else {
-            reinterpret_cast<float*>(smem + SM::off_wq)[t] = w3.h;
-        }
+        float* wt = reinterpret_cast<float*>(smem + SM::off_wq) + (i * 32 + (P & 31)) * 4;
+        wt[P >> 5] = w3.h;
+        wt[2 + (P >> 5)] = w3.l;
     }
     uint8_t* wb = smem + SM::off_warp + wid * SM::wbytes;
     uint8_t* stage = smem + wid * SM::stage;
@@ -532,14 +532,10 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
     // this lane's pencils: (k, j) = (k0 + 4s, j) in nodal phases, (k0 + 4s, j) -> (q, p) in modal ones
     const int j = lane & 7, k0 = lane >> 3;
     const int sw = (lane >> 1) & 3;  // 64-byte swizzle of rows lane and lane + 32
-    float2 w3f[8];                   // FP32 form: weight products of this lane's points (s = 0, 1)
-    if constexpr (!DF) {
-        const float* wt = reinterpret_cast<const float*>(smem + SM::off_wq);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) w3f[i] = make_float2(wt[i * 64 + lane], wt[i * 64 + lane + 32]);
-    }
+    // FP32 form: w_j w_k of this lane's pencils (k0, j) and (k0 + 4, j)
+    const float2 wjk = make_float2(df_mul({A.tab.wh[j], A.tab.wl[j]}, {A.tab.wh[k0], A.tab.wl[k0]}).h,
+                                   df_mul({A.tab.wh[j], A.tab.wl[j]}, {A.tab.wh[k0 + 4], A.tab.wl[k0 + 4]}).h);
     const float4* sWq4 = reinterpret_cast<const float4*>(smem + SM::off_wq);
-    if constexpr (!DF) __syncthreads();  // the weight table is overlaid by the results table
 
     const uint32_t total_tiles = BATCH ? static_cast<uint32_t>(q.total_tiles) : A.total_tiles;
     unsigned* counter = BATCH ? q.counter : &A.p.ctl->tile_counter;
@@ -682,12 +678,31 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
         parity ^= 1u;
         inflight = false;
 
+        // ---- the element's largest high word of |u| (a first pass over the stage's high words)
+        uint32_t hm = 0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const uint4 v = *reinterpret_cast<const uint4*>(stage + (lane + 32 * (c >> 2)) * 64 + (((c & 3) ^ sw) << 4));
+            hm = max(hm, max(v.y & 0x7fffffffu, v.w & 0x7fffffffu));
+        }
+        const uint32_t hmax0 = __reduce_max_sync(FULL, hm);
+        const bool bad = __any_sync(FULL, hm >= (static_cast<uint32_t>(1023 + 500) << 20));
+        const bool tiny = __all_sync(FULL, hm < 0x00100000u);
+        // exact power-of-two prescale: the element is read as u 2^-ke with ke the binary exponent
+        // of its largest |u|, so every value formed below lies near 1 whatever the field's units
+        // (masks and codes do not change under it; steps and norms are scaled back exactly).
+        // NaN, infinity or |u| >= 2^500 (energies beyond FP64): flagged, keeps nothing; zeros and
+        // subnormals only (|u| < 2^-1022): a zero block, keeps nothing
+        const int bias = 0x38000000 + ((hmax0 < 0x00100000u ? 0 : min(static_cast<int>(hmax0 >> 20) - 1023, 1023)) << 20);
+        if (lane == 0) {  // the element's stash entry keeps these (read back below, not held in registers)
+            s_res[il].ke = (bias - 0x38000000) >> 20;
+            s_res[il].hmax = hmax0;
+        }
         // ---- the lane's two pencils, split into floats with integer instructions
         float2 uh[8], ul[8];  // (pencil lane, pencil lane + 32) at point i
-        uint32_t hmax = 0;    // largest high word of |u|
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            const uint8_t* row = stage + (lane + 32 * s) * 64;
+        for (int pen = 0; pen < 2; ++pen) {
+            const uint8_t* row = stage + (lane + 32 * pen) * 64;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const uint4 v = *reinterpret_cast<const uint4*>(row + ((c ^ sw) << 4));
@@ -695,11 +710,10 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int i = 2 * c + h;
-                    hmax = max(hmax, hi[h] & 0x7fffffffu);
                     float vh_, vl_ = 0.0f;
-                    if constexpr (DF) w_split(lo[h], hi[h], vh_, vl_);
-                    else vh_ = w_d2f_rz(lo[h], hi[h]);
-                    if (s == 0) {
+                    if constexpr (DF) w_split(lo[h], hi[h], bias, vh_, vl_);
+                    else vh_ = w_d2f_rz(lo[h], hi[h], bias);
+                    if (pen == 0) {
                         uh[i].x = vh_;
                         ul[i].x = vl_;
                     } else {
@@ -719,11 +733,6 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
             }
             inflight = true;
         }
-        const bool bad = __any_sync(FULL, hmax >= (static_cast<uint32_t>(1023 + 127) << 20));
-        // max |u| of the element from its largest high word, rounded toward zero to float: it
-        // keeps the order of |u| (the finalize rereads the blocks that attain the field maximum)
-        // and is within a factor 1 + 2^-20 of it
-        const float umax_e = w_d2f_rz(0u, __reduce_max_sync(FULL, hmax));
 
         // ---- forward transform (FP32, both pencils packed): i in registers, then j and k through
         // the warp's buffer.  Layout A [k0][j][p][s] (plane 176, row 20 floats) lets a lane read its
@@ -777,20 +786,32 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
         }
 
         // ---- per element (warp-uniform): t = tau S, step s_e = floor((ex - 1) / 2) for
-        // t = mu 2^ex, and g = the smallest float with g^2 >= t
+        // t = mu 2^ex, and g = the smallest float with g^2 >= t.  All of it for the prescaled
+        // block: t' = t 2^-2ke, so ex = ex' + 2 ke and s_e = s' + ke with s' = floor((ex' - 1) / 2);
+        // the codes rint(a' 2^-s') equal rint(a 2^-s_e)
         int emode = 0;  // 0: keep none, 1: threshold
-        int step = INT16_MIN;
+        int step = INT16_MIN, sps = 0;  // s_e and s'
         f2 t = {0.0f, 0.0f};
         float g = 0.0f;
+        const uint32_t hmax = s_res[il].hmax;
+        const int ke = s_res[il].ke;
         if (bad || !isfinite(S.h)) {
             if (lane == 0) atomicOr(status, static_cast<unsigned>(SEMR_STATUS_NONFINITE));
+        } else if (tiny) {  // zeros and subnormals only: keeps nothing, norms 0
+            if (lane == 0 && hmax != 0u) atomicOr(status, static_cast<unsigned>(SEMR_STATUS_TINY));
         } else {
+            // S' >= min w_i w_j w_k > 4e-5 (|u'| reaches 1) and 3.7e-9 < tau <= 2^64 (int16 codes),
+            // so t' is a normal float
             t = df_norm(df_mul({tau_h, tau_l}, S));
-            if (t.h >= 1.0e-30f && t.h <= 1.0e37f) {
-                const uint32_t tb_ = __float_as_uint(t.h);
-                int ex = static_cast<int>(tb_ >> 23) - 126;
-                if ((tb_ & 0x7fffffu) == 0u && t.l < 0.0f) --ex;  // t just below a power of two
-                step = (ex - 1) >> 1;
+            const uint32_t tb_ = __float_as_uint(t.h);
+            int exs = static_cast<int>(tb_ >> 23) - 126;
+            if ((tb_ & 0x7fffffu) == 0u && t.l < 0.0f) --exs;  // t just below a power of two
+            const int ex = exs + 2 * ke;
+            if (ex > 1024) {  // t = tau S_e overflows FP64
+                if (lane == 0) atomicOr(status, static_cast<unsigned>(SEMR_STATUS_NONFINITE));
+            } else if (ex >= -1021) {  // t >= 2^-1022, the smallest normal double
+                sps = (exs - 1) >> 1;
+                step = sps + ke;
                 emode = 1;
                 asm("sqrt.approx.f32 %0, %1;" : "=f"(g) : "f"(t.h));
 #pragma unroll 1
@@ -802,8 +823,8 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
                 }
             }
         }
-        // t in [1e-30, 1e37] keeps s in [-50, 61]: 2^-s and 2^s are normal floats (exact scalings)
-        const float qd = pow2f(emode ? -step : 0), qu = pow2f(emode ? step : 0);
+        // t' in [1e-13, 2^70] keeps s' in [-22, 35]: 2^-s' and 2^s' are normal floats (exact scalings)
+        const float qd = pow2f(-sps), qu = pow2f(sps);
 
         // ---- keep decisions; FP64 mode recomputes exactly what FP32 cannot settle
         uint32_t kb = 0;  // keep bit (8 s + r)
@@ -813,6 +834,8 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
                 // the table), 3 contractions, 2 more for the input split; every row of A has
                 // sum |A_pi| <= sqrt(2), so (|A|^3 |u|)_m <= 2^1.5 max|u|; a factor 2 of safety
                 constexpr float kMarg = (3.0f * (4 + 2) + 2.0f) * 5.9604645e-8f * 2.8285f * 2.0f;
+                // max |u 2^-ke| rounded toward zero to float: the top 20 mantissa bits of hmax, in [1, 2)
+                const float umax_e = __uint_as_float(0x3f800000u | ((hmax & 0xfffffu) << 3));
                 const float M = kMarg * umax_e * 1.000002f;
                 const float Mg = M + g * 2.4e-7f;  // plus the float rounding of g +- M
                 const float Mq = Mg * qd;
@@ -839,8 +862,8 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
                         tb[lane * 17 + r] = a2[r].x;
                         tb[lane * 17 + 8 + r] = a2[r].y;
                     }
-                    kb = resolve_ambiguous(tb, amb, kb, p.fields[f] + static_cast<uint64_t>(e) * WN3, sAh, sAl, t, qd, qu,
-                                           recomputed);
+                    kb = resolve_ambiguous(tb, amb, kb, p.fields[f] + static_cast<uint64_t>(e) * WN3, sAh, sAl,
+                                           0x38000000 + (ke << 20), t, qd, qu, recomputed);
 #pragma unroll
                     for (int r = 0; r < 8; ++r) a2[r] = make_float2(tb[lane * 17 + r], tb[lane * 17 + 8 + r]);
                 }
@@ -1124,13 +1147,14 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const float2 d = f2sub(uh[i], vh[i]);
-                ep = f2fma(f2mul(w3f[i], d), d, ep);
+                ep = f2fma(f2mul(A.tab.w2[i], d), d, ep);
                 dm = fmaxf(dm, fmaxf(fabsf(d.x), fabsf(d.y)));
             }
-            e2 = {warp_sum_f(ep.x + ep.y), 0.0f};
+            e2 = {warp_sum_f(fmaf(ep.x, wjk.x, ep.y * wjk.y)), 0.0f};
             lh = warp_max_nonneg(dm);
         }
-        if (p.write_recon && p.recon[f]) {
+        if (p.write_recon && p.recon[f]) {  // u~ = u~' 2^ke (exact)
+            const double sc = pow2d(s_res[il].ke);
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
                 double2* dst = reinterpret_cast<double2*>(p.recon[f] + static_cast<uint64_t>(e) * WN3 + (lane + 32 * s) * 8);
@@ -1138,23 +1162,21 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
                 for (int i = 0; i < 8; i += 2) {
                     const float h0 = s ? vh[i].y : vh[i].x, l0 = s ? vl[i].y : vl[i].x;
                     const float h1 = s ? vh[i + 1].y : vh[i + 1].x, l1 = s ? vl[i + 1].y : vl[i + 1].x;
-                    dst[i / 2] = make_double2(static_cast<double>(h0) + static_cast<double>(l0),
-                                              static_cast<double>(h1) + static_cast<double>(l1));
+                    dst[i / 2] = make_double2((static_cast<double>(h0) + static_cast<double>(l0)) * sc,
+                                              (static_cast<double>(h1) + static_cast<double>(l1)) * sc);
                 }
             }
         }
 
         if (lane == 0) {
-            WStash st;
-            st.pad = 0;
-            st.umax = umax_e;
-            st.sh = S.h;
-            st.sl = S.l;
-            st.eh = e2.h;
-            st.el = e2.l;
-            st.lh = lh;
-            st.ll = ll;
-            s_res[il] = st;
+            WStash& st = s_res[il];
+            const bool zero = st.hmax < 0x00100000u;  // zeros and subnormals only: a zero block
+            st.sh = zero ? 0.0f : S.h;
+            st.sl = zero ? 0.0f : S.l;
+            st.eh = zero ? 0.0f : e2.h;
+            st.el = zero ? 0.0f : e2.l;
+            st.lh = zero ? 0.0f : lh;
+            st.ll = zero ? 0.0f : ll;
         }
         __syncwarp();  // the kept list and mask words are reused by the next element
     }
@@ -1231,14 +1253,16 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
             const WStash st = s_res[il];
             const uint64_t ge = static_cast<uint64_t>(f) * E + e0 + il;
             const double J = p.jac[e0 + il];
-            const double Sd = static_cast<double>(st.sh) + static_cast<double>(st.sl);
-            const double e2d = static_cast<double>(st.eh) + static_cast<double>(st.el);
+            // back from the prescaled block: energies times 2^2ke (two exact factors), Linf times 2^ke
+            const double sc = pow2d(st.ke);
+            const double Sd = ((static_cast<double>(st.sh) + static_cast<double>(st.sl)) * sc) * sc;
+            const double e2d = ((static_cast<double>(st.eh) + static_cast<double>(st.el)) * sc) * sc;
             v0 = J * e2d;
             v1 = J * Sd;
-            const double x2 = static_cast<double>(st.lh) + static_cast<double>(st.ll);
+            const double x2 = (static_cast<double>(st.lh) + static_cast<double>(st.ll)) * sc;
             m2 = static_cast<unsigned long long>(__double_as_longlong(x2));
-            m3 = static_cast<unsigned long long>(__double_as_longlong(static_cast<double>(st.umax)));
-            p.umax_elem[ge] = st.umax;
+            m3 = st.hmax;
+            p.hmax_elem[ge] = st.hmax;
             if (p.elem_report) {
                 double* er = p.elem_report + 3 * ge;
                 er[0] = v0;
@@ -1257,7 +1281,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
             s_wpart[wid][0] = v0;
             s_wpart[wid][1] = v1;
             s_wpart[wid][2] = __longlong_as_double(static_cast<long long>(m2));
-            s_wpart[wid][3] = __longlong_as_double(static_cast<long long>(m3));
+            s_wpart[wid][3] = static_cast<double>(m3);  // the largest high word, as a number
         }
     }
     __syncthreads();
@@ -1292,9 +1316,11 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
 }
 
 // Finalize of field f: tree over its tile partials, then the exact maximum of
-// |u|.  The kernel records each element's maximum rounded toward zero to
-// float, which keeps their order, so the elements whose rounded maximum is
-// the field's hold the exact one: those few blocks are reread.  256 threads.
+// |u|.  The kernel records each element's largest high word of |u| (sign
+// cleared, exponent and top 20 mantissa bits), which orders the elements like
+// their maxima, so the elements whose high word is the field's hold the exact
+// maximum: those few blocks are reread.  A field whose every high word is 0
+// (zeros and subnormals only) reports 0 without a reread.  256 threads.
 __device__ void finalize_warp_field(const LaunchParams& p, int f) {
     __shared__ double red[4][256];
     __shared__ int s_list[64];
@@ -1309,9 +1335,9 @@ __device__ void finalize_warp_field(const LaunchParams& p, int f) {
     }
     __syncthreads();
     const uint64_t E = static_cast<uint64_t>(p.n_elem);
-    const float* um = p.umax_elem + static_cast<uint64_t>(f) * E;
+    const uint32_t* um = p.hmax_elem + static_cast<uint64_t>(f) * E;
     const double* src = p.fields[f];
-    for (uint64_t t = tid; t < static_cast<uint64_t>(p.tiles_per_field); t += 256) {
+    for (uint64_t t = tid; M > 0.0 && t < static_cast<uint64_t>(p.tiles_per_field); t += 256) {
         if (p.tile_part[4 * (static_cast<uint64_t>(f) * p.tiles_per_field + t) + 3] != M) continue;
         const uint64_t ee = min(E, (t + 1) * kWarpTile);
         for (uint64_t e = t * kWarpTile; e < ee; ++e) {
@@ -1394,6 +1420,7 @@ WTables make_wtables() {
     for (int i = 0; i < 8; ++i) {
         t.wh[i] = static_cast<float>(w[i]);
         t.wl[i] = static_cast<float>(w[i] - static_cast<double>(t.wh[i]));
+        t.w2[i] = make_float2(t.wh[i], t.wh[i]);
     }
     return t;
 }

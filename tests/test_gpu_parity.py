@@ -206,14 +206,14 @@ def test_sparse_and_dense_reconstruction_limits():
 
 @pytest.mark.parametrize("precision", [semr.SEMR_FP64, semr.SEMR_FP32])
 def test_lx8_nonfinite_and_out_of_range_flagged(precision):
-    """lx = 8 (the warp-per-element kernel): a NaN, an infinity and a value past
-    the float-pair range (|u| >= 2^127) each flag SEMR_STATUS_NONFINITE, and
-    their elements keep nothing.  Every other byte of the payload equals the
+    """lx = 8 (the warp-per-element kernel): a NaN, an infinity and a value of
+    2^500 or more (whose element energy leaves the FP64 range) each flag
+    SEMR_STATUS_NONFINITE, and their elements keep nothing.  Every other byte of the payload equals the
     payload of the same snapshot with those three blocks set to zero (a zero
     block also keeps nothing and stores the sentinel step)."""
     fields, jac = make_case(300, 8, 2, seed=13)
     zeroed = fields.clone()
-    bad = [(0, 5, 17, float("nan")), (0, 130, 0, float("inf")), (1, 200, 511, 1e39)]
+    bad = [(0, 5, 17, float("nan")), (0, 130, 0, float("inf")), (1, 200, 511, 1e160)]
     for f, e, i, v in bad:
         fields[f, e, i] = v
         zeroed[f, e] = 0.0
