@@ -60,7 +60,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--n-side", type=int, default=64, help="elements per side (profiling a smaller case)")
-    ap.add_argument("--serving-requests", type=int, default=800, help="requests per serving run in the extras")
+    ap.add_argument("--serving-requests", type=int, default=10000, help="requests per serving run in the extras")
     ap.add_argument("--serving-only", action="store_true", help="print only the serving report (JSON)")
     ap.add_argument("--batched-only", action="store_true", help="print only the batched report (JSON)")
     ap.add_argument("--cumulative", action="store_true", help="cumulative-energy truncation on the device leg")
@@ -206,14 +206,34 @@ def calibrated_sample(fields_host, jac_host, tau, target_s):
     return n
 
 
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(fields_host, jac_host, tau, target_s):
+    """The oracle on every host core, and on one core, each on a sample sized
+    for about target_s seconds of work."""
     import oracle
     n = calibrated_sample(fields_host, jac_host, tau, target_s)
     dt = time_oracle(fields_host, jac_host, tau, n)
     nbytes = fields_host.shape[0] * n * LX ** 3 * 8
+    # one core: a sample sized from the all-core rate (about a third of target_s at one core)
+    n1 = int(max(256, min(fields_host.shape[1], n / max(oracle.max_threads(), 1) / 3)))
+    dt1 = time_oracle(fields_host, jac_host, tau, n1, n_threads=1)
+    nb1 = fields_host.shape[0] * n1 * LX ** 3 * 8
     return {"value": nbytes / dt / 1e9, "unit": "GB/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "cpu_model": cpu_model(),
             "sample": f"first {n} of {fields_host.shape[1]} elements of each of the {fields_host.shape[0]} fields "
-                      f"({100.0 * n / fields_host.shape[1]:.2f}% of the snapshot), {dt:.1f} s"}
+                      f"({100.0 * n / fields_host.shape[1]:.2f}% of the snapshot), {dt:.1f} s",
+            "single_core": {"value": round(nb1 / dt1 / 1e9, 4), "unit": "GB/s", "cores": 1,
+                            "sample": f"first {n1} elements of each field, {dt1:.1f} s"}}
 
 
 # ------------------------------------------------------------------ helpers
@@ -411,11 +431,62 @@ def run_extras(dev, flist, jac, E, snapshot_bytes, peaks):
         del b
         return res
 
+    prec_form = {}
+    for t in (1e-3, 1e-5):
+        prec_form[f"{t:g}"] = timed(t, semr.SEMR_FP32)
+        prec_form[f"{t:g}"]["vs_fp64_oracle"] = precision_vs_oracle(dev, flist, jac, E, t)
     return {"slice_image": slice_report(dev, flist[:3], peaks),
             "by_tau_fp64": {f"{t:g}": timed(t, semr.SEMR_FP64) for t in (1e-2, 1e-3, 1e-4)},
-            "precision_form_fp32": {f"{t:g}": timed(t, semr.SEMR_FP32) for t in (1e-3, 1e-5)},
+            "precision_form_fp32": prec_form,
             "cumulative_energy": {"fp64 tau=1e-3": timed(1e-3, semr.SEMR_FP64, cumulative=True),
                                   "fp32 tau=1e-3": timed(1e-3, semr.SEMR_FP32, cumulative=True)}}
+
+
+def precision_vs_oracle(dev, flist, jac, E, tau, n_sample=2048, seed=7):
+    """The precision form (FP32 transforms) against the FP64 oracle, per field,
+    on sampled elements of the full snapshot: the FP32 form's reconstruction
+    u~32 against the oracle's u~64 (relative L2 in the GLL mass norm and
+    relative Linf), its reported error against the oracle's (L2_rel of
+    u - u~), and the element-fields whose payload (mask, step, count, codes)
+    differs from the oracle's.  The sample: n_sample elements per field,
+    uniformly at random, plus the first and last tiles."""
+    import torch
+
+    import oracle
+    import paper_2407_20731_b300 as semr
+    F = len(flist)
+    rec = [torch.empty_like(flist[i]) for i in range(F)]
+    res = semr.reduce(flist, jac, LX, tau, precision=semr.SEMR_FP32, recon=rec, elem_report=False)
+    rng = np.random.default_rng(seed)
+    idx = np.unique(np.concatenate([rng.choice(E, size=min(n_sample, E), replace=False),
+                                    np.arange(min(128, E)), np.arange(max(0, E - 128), E)]))
+    it = torch.as_tensor(idx, device=dev)
+    u = torch.stack([flist[i].view(E, -1)[it] for i in range(F)]).cpu().numpy()
+    r32 = torch.stack([rec[i].view(E, -1)[it] for i in range(F)]).cpu().numpy()
+    J = jac[it].cpu().numpy()
+    o = oracle.reduce(u, J, tau)
+    g = oracle.sections(res.payload)
+    os_ = oracle.sections(o.payload)
+    gc = np.concatenate([[0], np.cumsum(g["counts"].reshape(-1).astype(np.int64))])
+    oc = np.concatenate([[0], np.cumsum(os_["counts"].reshape(-1).astype(np.int64))])
+    x, w = oracle.gll(LX)
+    w3 = (w[:, None, None] * w[None, :, None] * w[None, None, :]).reshape(-1)
+    out = []
+    for f in range(F):
+        mism = 0
+        for k, e in enumerate(idx):
+            gi, oi = f * E + e, f * len(idx) + k
+            same = (np.array_equal(g["masks"][f, e], os_["masks"][f, k]) and g["steps"][f, e] == os_["steps"][f, k]
+                    and np.array_equal(g["codes"][gc[gi]:gc[gi + 1]], os_["codes"][oc[oi]:oc[oi + 1]]))
+            mism += 0 if same else 1
+        d = r32[f] - o.recon[f]
+        den = np.sqrt(np.sum(J[:, None] * w3[None, :] * u[f] ** 2))
+        e32 = np.sqrt(np.sum(J[:, None] * w3[None, :] * (u[f] - r32[f]) ** 2)) / den
+        out.append({"recon_l2_rel_vs_oracle": float(f"{np.sqrt(np.sum(J[:, None] * w3[None, :] * d * d)) / den:.3e}"),
+                    "recon_linf_rel_vs_oracle": float(f"{np.abs(d).max() / np.abs(u[f]).max():.3e}"),
+                    "l2_rel_fp32": float(f"{e32:.6e}"), "l2_rel_oracle": float(f"{o.field_report[f, 1]:.6e}"),
+                    "payload_mismatch": int(mism), "sampled": int(len(idx))})
+    return out
 
 
 def slice_report(dev, uvw, peaks, W=2048, H=2048, z0=2.0, n=20):
@@ -488,6 +559,20 @@ def run_batched(dev, precision, reps=5, tau=1e-3):
     torch.cuda.synchronize()
     plain_ms = e[0].elapsed_time(e[1]) / reps
     graph_ms = e[2].elapsed_time(e[3]) / reps
+    # per-snapshot latency from the start of the batch: plain launches complete one after
+    # another (an event after each), the graph completes every snapshot at its end
+    pe = [torch.cuda.Event(enable_timing=True) for _ in range(len(snaps) + 1)]
+    ge = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    pe[0].record(stream)
+    for k, (sn, b) in enumerate(zip(snaps, plain_bufs)):
+        semr.reduce_async(sn[0], sn[1], sn[2], sn[3], b, sn[4])
+        pe[k + 1].record(stream)
+    ge[0].record(stream)
+    batch.replay()
+    ge[1].record(stream)
+    torch.cuda.synchronize()
+    plain_lat = np.array([pe[0].elapsed_time(pe[k + 1]) for k in range(len(snaps))])
+    graph_lat = np.full(len(snaps), ge[0].elapsed_time(ge[1]))
     res = batch.results()
     same = all(np.array_equal(p, b.payload[: sm.payload_bytes].cpu().numpy())
                for (p, _), b, sm in zip(res, plain_bufs, [semr.summary_from(b) for b in plain_bufs]))
@@ -495,6 +580,11 @@ def run_batched(dev, precision, reps=5, tau=1e-3):
            "plain_launches_ms": round(plain_ms, 3), "plain_GB_s": round(total_bytes / plain_ms / 1e6, 1),
            "graph_replay_ms": round(graph_ms, 3), "graph_GB_s": round(total_bytes / graph_ms / 1e6, 1),
            "speedup": round(plain_ms / graph_ms, 3), "plan_s": round(plan_s, 2), "payloads_identical": bool(same),
+           "latency_from_batch_start_ms": {
+               "plain": {"p50": round(float(np.percentile(plain_lat, 50)), 3),
+                         "p99": round(float(np.percentile(plain_lat, 99)), 3)},
+               "graph": {"p50": round(float(np.percentile(graph_lat, 50)), 3),
+                         "p99": round(float(np.percentile(graph_lat, 99)), 3)}},
            "schedule": [{"lx": g[0], "tile": g[2], "items": g[3], "tuned_ms": {str(k): round(v, 4) for k, v in g[4].items()}}
                         for g in batch.schedule()]}
     batch.close()
@@ -530,7 +620,87 @@ def calibrate_tau(pool, precision, target=1e-3):
     return out
 
 
-def run_serving(pool, taus, n_requests=800, producers=8, mean_ms=50.0, slots=8, budget=120 << 30,
+def make_traces(n_requests, producers, mean_ms, pool_size, seed):
+    """Per producer: seeded Poisson arrival times (s) and pool picks."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    per = n_requests // producers
+    traces = []
+    for _ in range(producers):
+        arrivals = np.cumsum(rng.exponential(mean_ms * 1e-3, size=per))
+        picks = rng.integers(0, pool_size, size=per)
+        traces.append(list(zip(arrivals, picks)))
+    return traces
+
+
+def latency_stats(lat_s):
+    lat_ms = np.asarray(lat_s) * 1e3
+    return {"p50_ms": round(float(np.percentile(lat_ms, 50)), 3), "p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
+            "mean_ms": round(float(lat_ms.mean()), 3)}
+
+
+def run_plain(pool, taus, n_requests=10000, producers=8, mean_ms=50.0, precision=1, seed=5):
+    """Plain per-snapshot launches: the same producers and trace as the served
+    run; one worker takes the snapshots in arrival order and launches each
+    reduction on one stream (buffers allocated beforehand, one set per pool
+    snapshot), waiting for it before the next.  Latency = completion -
+    submission."""
+    import queue
+    import threading
+
+    import torch
+
+    import paper_2407_20731_b300 as semr
+    traces = make_traces(n_requests, producers, mean_ms, len(pool), seed)
+    bufs = [semr.alloc_buffers(lx, jac.numel(), len(fields), taus[lx], fields[0].device) for fields, jac, lx, _ in pool]
+    stream = torch.cuda.Stream()
+    for (fields, jac, lx, _), b in zip(pool, bufs):  # warm-up, untimed: every pool snapshot once
+        with torch.cuda.stream(stream):
+            semr.reduce_async(fields, jac, lx, taus[lx], b, precision)
+    stream.synchronize()
+    q: queue.Queue = queue.Queue()
+    lat, span, bytes_done = [], [], [0]
+    t0 = time.perf_counter() + 0.05
+
+    def producer(trace):
+        for at, k in trace:
+            d = t0 + at - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            q.put((time.perf_counter(), k))
+        q.put(None)
+
+    def worker():
+        ends = 0
+        while ends < producers:
+            item = q.get()
+            if item is None:
+                ends += 1
+                continue
+            ts, k = item
+            fields, jac, lx, nb = pool[k]
+            with torch.cuda.stream(stream):
+                semr.reduce_async(fields, jac, lx, taus[lx], bufs[k], precision)
+            stream.synchronize()
+            te = time.perf_counter()
+            lat.append(te - ts)
+            span.append((ts, te))
+            bytes_done[0] += nb
+
+    th = [threading.Thread(target=producer, args=(t,)) for t in traces] + [threading.Thread(target=worker)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    del bufs
+    out = {"requests": len(lat), "launches": "one stream, in arrival order, each waited for", "producers": producers,
+           "mean_interarrival_ms": mean_ms}
+    out.update(latency_stats(lat))
+    out.update({"sustained_GB_s": round(bytes_done[0] / max(max(b for a, b in span) - min(a for a, b in span), 1e-9)
+                                        / 1e9, 2), "input_GB": round(bytes_done[0] / 1e9, 2)})
+    return out
+
+
+def run_serving(pool, taus, n_requests=10000, producers=8, mean_ms=50.0, slots=8, budget=120 << 30,
                 precision=1, seed=5):
     """Producers emit snapshots by seeded Poisson arrivals; a collector waits
     for each result and releases it.  Latency = completion - submission."""
@@ -538,20 +708,14 @@ def run_serving(pool, taus, n_requests=800, producers=8, mean_ms=50.0, slots=8, 
     import threading
 
     import paper_2407_20731_b300 as semr
-    rng = np.random.Generator(np.random.PCG64(seed))
-    per = n_requests // producers
-    traces = []
-    for _ in range(producers):
-        arrivals = np.cumsum(rng.exponential(mean_ms * 1e-3, size=per))
-        picks = rng.integers(0, len(pool), size=per)
-        traces.append(list(zip(arrivals, picks)))
+    traces = make_traces(n_requests, producers, mean_ms, len(pool), seed)
     srv = semr.Server(slots=slots, mem_budget_bytes=budget)
     # warm-up, untimed: every pool snapshot once (grows the memory pool, loads kernels)
     for fields, jac, lx, _ in pool:
         srv.release(srv.submit(fields, jac, lx, taus[lx], precision))
     srv_stats0 = srv.stats()
     done_q: queue.Queue = queue.Queue()
-    lat, errors, span = [], [], []
+    lat, errors, span, admit, service = [], [], [], [], []
     t0 = time.perf_counter() + 0.05
 
     def producer(trace):
@@ -574,6 +738,8 @@ def run_serving(pool, taus, n_requests=800, producers=8, mean_ms=50.0, slots=8, 
             if rc:
                 errors.append(rc)
             lat.append(info.t_done - info.t_submit)
+            admit.append(info.t_admit - info.t_submit)
+            service.append(info.t_done - info.t_admit)
             span.append((info.t_submit, info.t_done))
             srv.release(rid)
 
@@ -585,13 +751,15 @@ def run_serving(pool, taus, n_requests=800, producers=8, mean_ms=50.0, slots=8, 
     st = srv.stats()
     st["bytes_done"] -= srv_stats0["bytes_done"]
     srv.close()
-    lat_ms = np.array(lat) * 1e3
-    return {"requests": len(lat), "slots": slots, "producers": producers, "mean_interarrival_ms": mean_ms,
-            "p50_ms": round(float(np.percentile(lat_ms, 50)), 3), "p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
-            "mean_ms": round(float(lat_ms.mean()), 3), "errors": len(errors),
-            "sustained_GB_s": round(st["bytes_done"] / max(max(b for a, b in span) - min(a for a, b in span), 1e-9)
-                                    / 1e9, 2),
-            "input_GB": round(st["bytes_done"] / 1e9, 2)}
+    out = {"requests": len(lat), "slots": slots, "producers": producers, "mean_interarrival_ms": mean_ms}
+    out.update(latency_stats(lat))
+    out.update({"errors": len(errors),
+                "admission_delay_ms": {k.replace("_ms", ""): v for k, v in latency_stats(admit).items()},
+                "service_ms": {k.replace("_ms", ""): v for k, v in latency_stats(service).items()},
+                "sustained_GB_s": round(st["bytes_done"] / max(max(b for a, b in span) - min(a for a, b in span),
+                                                               1e-9) / 1e9, 2),
+                "input_GB": round(st["bytes_done"] / 1e9, 2)})
+    return out
 
 
 def serving_report(dev, n_requests, precision=1):
@@ -600,10 +768,12 @@ def serving_report(dev, n_requests, precision=1):
     progress(f"serving: tau per lx {taus}")
     served = run_serving(pool, taus, n_requests, slots=8, precision=precision)
     progress(f"serving: served run done ({served['p50_ms']} / {served['p99_ms']} ms)")
-    plain = run_serving(pool, taus, n_requests, slots=1, precision=precision)
-    # the same trace at ten times the arrival rate (a loaded server)
-    served_x10 = run_serving(pool, taus, max(n_requests // 2, 64), mean_ms=5.0, slots=8, precision=precision)
-    plain_x10 = run_serving(pool, taus, max(n_requests // 2, 64), mean_ms=5.0, slots=1, precision=precision)
+    plain = run_plain(pool, taus, n_requests, precision=precision)
+    progress(f"serving: plain run done ({plain['p50_ms']} / {plain['p99_ms']} ms)")
+    # ten times the arrival rate (a loaded server), a shorter trace
+    nx = max(min(n_requests // 5, 2000), 64)
+    served_x10 = run_serving(pool, taus, nx, mean_ms=5.0, slots=8, precision=precision)
+    plain_x10 = run_plain(pool, taus, nx, mean_ms=5.0, precision=precision)
     return {"precision": "fp32 transforms, FP64 in" if precision == 1 else "fp64", "budget_GB": 120,
             "tau_per_lx": {str(k): v for k, v in taus.items()}, "served": served, "plain": plain,
             "served_10x_load": served_x10, "plain_10x_load": plain_x10}

@@ -80,8 +80,10 @@ extern "C" {
 #define SEMR_LX_MAX 12
 
 /* precision of the transforms */
-#define SEMR_FP64 0          /* FP64 accuracy: every value a pair of floats (about 48 significant bits,
-                                ~1e-14 relative), run on the FP32 pipes; payloads match an FP64
+#define SEMR_FP64 0          /* FP64 accuracy on the FP32 pipes: an FP32 forward transform under a
+                                proven error bound settles most decisions, the few it cannot are
+                                recomputed in hardware FP64; energies, reconstruction and norms are
+                                float pairs (about 48 significant bits).  Payloads match an FP64
                                 computation bit for bit outside decisions within 1e-9 of a tie */
 #define SEMR_FP32 1          /* the precision form: transforms in FP32 with FP32 accumulation; the
                                 threshold test is exactly the FP64 comparison; element and field
@@ -112,6 +114,11 @@ extern "C" {
 #define SEMR_STATUS_NONFINITE 4   /* an element held a NaN, an infinity or a magnitude of 2^500 or more
                                      (its energy would overflow FP64 arithmetic): that element keeps
                                      nothing */
+#define SEMR_STATUS_STAGE 16      /* after a timed-out wait for an element block's TMA copy, a second
+                                     bounded wait for that copy gave up too: the copy may have landed in
+                                     shared memory after the kernel stopped using it (results invalid,
+                                     as with SEMR_STATUS_TIMEOUT, which is also set; treat the device as
+                                     suspect) */
 #define SEMR_STATUS_TINY 8        /* informational, not an error: an element held only subnormal values
                                      (every |u| < 2^-1022).  It keeps nothing, as an FP64 evaluation
                                      does (its t = tau S_e underflows), and its e2_e, E_e and Linf_e
@@ -333,13 +340,16 @@ int semr_reduce_async_noalloc(const semr_fieldset* fs, const semr_mesh* mesh, ui
 /* Self-test of the bounded device-side waits, with no fault and no hang: one
  * warp runs (0) the decoupled look-back of a tile whose predecessor never
  * publishes its state, and (1) the wait for a phase of an mbarrier that never
- * completes, the two waits every reduction kernel bounds.  Each gives up at
- * its bound (the look-back after 2^22 polls, about 2-3 s; the barrier after
- * 1000 polls of at most 1 ms each) and records SEMR_STATUS_TIMEOUT; the
- * kernel then returns and the context stays usable.  status_out: host
- * uint32_t[2], receives the status word of each wait.  Blocks until done
- * (current device, legacy default stream).  Returns SEMR_OK, SEMR_EINVAL
- * (null status_out), SEMR_ENOMEM or SEMR_ECUDA. */
+ * completes, the two waits every reduction kernel bounds, followed (as in the
+ * reduce kernel's abort path) by the second bounded wait for a copy that
+ * might still be in flight.  Each wait gives up at its bound (the look-back
+ * after 2^22 polls, about 2-3 s; the barrier after 1000 polls of at most 1 ms
+ * each, twice) and records what the kernel records: SEMR_STATUS_TIMEOUT for
+ * (0), SEMR_STATUS_TIMEOUT | SEMR_STATUS_STAGE for (1).  The kernel then
+ * returns and the context stays usable.  status_out: host uint32_t[2],
+ * receives the status word of each wait.  Blocks until done (current device,
+ * legacy default stream).  Returns SEMR_OK, SEMR_EINVAL (null status_out),
+ * SEMR_ENOMEM or SEMR_ECUDA. */
 int semr_selftest_waits(uint32_t* status_out);
 
 /* ------------------------------------------------------ batched launches */

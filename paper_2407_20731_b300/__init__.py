@@ -31,6 +31,7 @@ SEMR_FP64, SEMR_FP32, SEMR_FP64_NATIVE = 0, 1, 2
 SEMR_WRITE_RECON, SEMR_CUMULATIVE = 1, 2
 SEMR_PAYLOAD_LOSSLESS, SEMR_PAYLOAD_CODE32, SEMR_PAYLOAD_FP32, SEMR_PAYLOAD_CUMULATIVE = 1, 2, 4, 8
 SEMR_STATUS_OVERFLOW, SEMR_STATUS_TIMEOUT, SEMR_STATUS_NONFINITE, SEMR_STATUS_TINY = 1, 2, 4, 8
+SEMR_STATUS_STAGE = 16
 
 
 class semr_mesh(ctypes.Structure):

@@ -45,6 +45,7 @@ constexpr int MODE_CUM = 2;   // bit 1: cumulative-energy truncation
 template <int LX>
 struct FastTables {
     float Ah[LX * LX], Al[LX * LX];    // analysis A[p*LX + i] (hi, lo)
+    double A64[LX * LX];               // analysis A[p*LX + i] in FP64 (the exact recomputation)
     float Ph[LX * LX], Pl[LX * LX];    // synthesis Phi[i*LX + p] (hi, lo)
     float wh[LX], wl[LX];              // GLL weights (hi, lo)
 };
@@ -614,37 +615,34 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
                 s_g[2 * tid] = ge.h;
                 s_g[2 * tid + 1] = ge.l;
             }
+            // Each entry in hardware FP64 from the element's doubles (reread from global memory,
+            // where L2 still holds them): a kept coefficient can be as small as ~7e-6 max|u| at
+            // tau = 1e-6 in a spiky element, where float pairs would carry a relative error near
+            // the 1e-9 band of the decisions.  Rare, so the slow FP64 pipe costs little.
             const int n_amb = total < AMB_CAP ? total : AMB_CAP;
             for (int k = 0; k < n_amb; ++k) {
                 const int code = s_amb[k];
                 const int el = code >> 16, m = code & 0xffff;
-                f2 c = {0.0f, 0.0f};
+                double c = 0.0;
                 if (lt == el && active) {
                     const int pp = m % LX, qq = (m / LX) % LX, rr = m / NP;
-                    f2 xs = {0.0f, 0.0f};
+                    const double* src = p.fields[f] + e * N3 + P * LX;
+                    double xs = 0.0;
 #pragma unroll
-                    for (int i = 0; i < LX; ++i) df_fma_acc(xs, {sAh[pp * PT + i], sAl[pp * PT + i]}, {uh[i], ul[i]});
-                    xs = df_norm(xs);
-                    c = df_mul(df_mul(xs, {sAh[qq * PT + pb], sAl[qq * PT + pb]}), {sAh[rr * PT + pa], sAl[rr * PT + pa]});
+                    for (int i = 0; i < LX; ++i) xs = fma(tab.A64[pp * LX + i], __ldg(src + i), xs);
+                    c = (xs * tab.A64[qq * LX + pb]) * tab.A64[rr * LX + pa];
                 }
-                // CTA-wide pair sum (only element el contributes)
+                // CTA-wide sum (only element el contributes), in a fixed order
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float h = __shfl_xor_sync(0xffffffffu, c.h, o);
-                    const float l2 = __shfl_xor_sync(0xffffffffu, c.l, o);
-                    const f2 t = two_sum(c.h, h);
-                    c = {t.h, t.l + (c.l + l2)};
-                }
-                if (lane == 0) reinterpret_cast<float2*>(red)[tid >> 5] = make_float2(c.h, c.l);
+                for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+                if (lane == 0) reinterpret_cast<double*>(red)[tid >> 5] = c;
                 __syncthreads();
                 if (tid == 0) {
-                    f2 a = {0.0f, 0.0f};
-                    for (int w = 0; w < C::NW; ++w) {
-                        const float2 v = reinterpret_cast<float2*>(red)[w];
-                        a = df_add(a, {v.x, v.y});
-                    }
-                    s_ambv[2 * k] = a.h;
-                    s_ambv[2 * k + 1] = a.l;
+                    double a = 0.0;
+                    for (int w = 0; w < C::NW; ++w) a += reinterpret_cast<double*>(red)[w];
+                    const f2 ap = df_from_double(a * pow2d(-prescale_exponent(s_hx[el])));  // u 2^-ke
+                    s_ambv[2 * k] = ap.h;
+                    s_ambv[2 * k + 1] = ap.l;
                 }
                 __syncthreads();
             }
@@ -1140,6 +1138,7 @@ FastTables<LX> make_tables() {
     double A[LX * LX], Phi[LX * LX], w[LX];
     basis_tables(LX, A, Phi, w);
     for (int i = 0; i < LX * LX; ++i) {
+        tab.A64[i] = A[i];
         tab.Ah[i] = (float)A[i];
         tab.Al[i] = (float)(A[i] - (double)tab.Ah[i]);
         tab.Ph[i] = (float)Phi[i];

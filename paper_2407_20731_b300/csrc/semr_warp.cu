@@ -59,6 +59,7 @@ struct WTables {         // lx = 8 tables, as kernel parameters (constant bank)
     float Ph[64], Pl[64];  // synthesis Phi[i][p] (hi, lo)
     float wh[8], wl[8];    // GLL weights (hi, lo)
     float2 w2[8];          // GLL weights (hi), duplicated for the packed FP32 error sums
+    double A64[64];        // analysis A[p][i] in FP64 (the exact recomputation)
 };
 
 struct WStash {    // one element's results, kept until the end of its tile
@@ -246,6 +247,17 @@ __device__ __forceinline__ float pick(const float2 (&a)[8], int w) {
     }
 }
 
+// The second wait after a timed-out wait for a TMA block: the copy may still be in flight, and
+// the CTA must not stop using its stage while it can land.  Waits once more (bounded, all 32
+// lanes); if that wait gives up too, records SEMR_STATUS_STAGE: the copy may land after the
+// kernel is done with the stage.  Returns whether the copy landed.
+__device__ __noinline__ bool drain_stage(uint64_t* bar, uint32_t parity, unsigned* status) {
+    const bool ok = mbar_wait_bounded(bar, parity);
+    if (!ok && (threadIdx.x & 31) == 0)
+        atomicOr(status, static_cast<unsigned>(SEMR_STATUS_TIMEOUT | SEMR_STATUS_STAGE));
+    return ok;
+}
+
 // Exclusive prefix of tile `tile` from its predecessors' states, as lookback_warp
 // computes it, without publishing anything (bounded; all 32 lanes).
 __device__ __forceinline__ uint64_t lookback_peek(const uint64_t* tile_state, uint64_t tile, unsigned* status) {
@@ -278,33 +290,33 @@ __device__ __forceinline__ uint64_t lookback_peek(const uint64_t* tile_state, ui
     return excl;
 }
 
-// Exact (float-pair) coefficient a[r][q][p] of the element block at `u` (global memory,
-// [pencil][8]): each lane contracts its two pencils (k0 + 4s, j) with A[p][.], A[q][j],
-// A[r][k] and the warp sums them.  Rare (decisions the FP32 bound cannot settle): out of
-// line, and the block is reread from global memory (it was just loaded, so L2 holds it)
-// rather than from the stage, which already receives the warp's next block.
-__device__ __noinline__ f2 exact_coef(const double* __restrict__ u, int pp, int qq, int rr, const float* sAh,
-                                      const float* sAl, int bias) {
+// Exact coefficient a'[r][q][p] = 2^-ke sum A[r][k] A[q][j] A[p][i] u[k][j][i] of the element block
+// at `u` (global memory, [pencil][8]) in hardware FP64: each lane contracts its two pencils
+// (k0 + 4s, j) with A[p][.], A[q][j], A[r][k] and the warp sums them.  FP64 because the decisions
+// sent here can lie within 1e-8 of a tie in relative terms: a kept coefficient may be as small as
+// about 7e-6 max|u| at tau = 1e-6 in a spiky element, where float pairs (47 input bits) would
+// carry a relative error near 1e-8.  Rare (decisions the FP32 bound cannot settle), so the slow
+// FP64 pipe costs little: out of line, and the block is reread from global memory (it was just
+// loaded, so L2 holds it) rather than from the stage, which already receives the warp's next block.
+__device__ __noinline__ double exact_coef(const double* __restrict__ u, int pp, int qq, int rr,
+                                          const double* __restrict__ A64, double sc) {
     const int lane = threadIdx.x & 31, j = lane & 7, k0 = lane >> 3;
-    f2 c = {0.0f, 0.0f};
+    double c = 0.0;
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-        const uint4* row = reinterpret_cast<const uint4*>(u + (lane + 32 * s) * 8);
-        f2 xs = {0.0f, 0.0f};
+        const double2* row = reinterpret_cast<const double2*>(u + (lane + 32 * s) * 8);
+        double xs = 0.0;
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
-            const uint4 v = __ldg(row + cc);
-            float h0, l0, h1, l1;
-            w_split(v.x, v.y, bias, h0, l0);
-            w_split(v.z, v.w, bias, h1, l1);
-            df_fma_acc(xs, {sAh[pp * 8 + 2 * cc], sAl[pp * 8 + 2 * cc]}, {h0, l0});
-            df_fma_acc(xs, {sAh[pp * 8 + 2 * cc + 1], sAl[pp * 8 + 2 * cc + 1]}, {h1, l1});
+            const double2 v = __ldg(row + cc);
+            xs = fma(A64[pp * 8 + 2 * cc], v.x, xs);
+            xs = fma(A64[pp * 8 + 2 * cc + 1], v.y, xs);
         }
-        xs = df_norm(xs);
-        const int kk = k0 + 4 * s;
-        c = df_add(c, df_mul(df_mul(xs, {sAh[qq * 8 + j], sAl[qq * 8 + j]}), {sAh[rr * 8 + kk], sAl[rr * 8 + kk]}));
+        c = fma(xs * A64[qq * 8 + j], A64[rr * 8 + k0 + 4 * s], c);
     }
-    return warp_sum_pair(c);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+    return c * sc;
 }
 
 // Settles every ambiguous keep or rounding decision of an element exactly (a rare path,
@@ -313,25 +325,20 @@ __device__ __noinline__ f2 exact_coef(const double* __restrict__ u, int pp, int 
 // a kept one becomes its code times 2^s (exact), so the quantisation reproduces the code of
 // the exact value.  Returns the lane's updated keep bits.
 __device__ __noinline__ uint32_t resolve_ambiguous(float* buf, uint32_t amb, uint32_t kb, const double* __restrict__ u,
-                                                   const float* sAh, const float* sAl, int bias, f2 t, float qd,
+                                                   const double* __restrict__ A64, double sc, f2 t, float qd,
                                                    float qu, unsigned& recomputed) {
     const int lane = threadIdx.x & 31;
+    const double td = static_cast<double>(t.h) + static_cast<double>(t.l);
     while (__any_sync(FULL, amb != 0u)) {
         const int src = __ffs(__ballot_sync(FULL, amb != 0u)) - 1;
         const int bsel = __shfl_sync(FULL, __ffs(amb) - 1, src);
         const int ms = bsel >> 3, mr = bsel & 7;
-        const f2 c = exact_coef(u, src & 7, (src >> 3) + 4 * ms, mr, sAh, sAl, bias);
+        const double c = exact_coef(u, src & 7, (src >> 3) + 4 * ms, mr, A64, sc);
         ++recomputed;
         if (lane == src) {
-            const bool keep = df_ge(df_mul(c, c), t);
-            float v = c.h;
-            if (keep) {
-                const float yh = c.h * qd, yl = c.l * qd;
-                float cc = (yh + 12582912.0f) - 12582912.0f;
-                const float diff = (yh - cc) + yl;
-                cc += (diff > 0.5f) ? 1.0f : ((diff < -0.5f) ? -1.0f : 0.0f);
-                v = cc * qu;
-            }
+            const bool keep = c * c >= td;
+            float v = static_cast<float>(c);
+            if (keep) v = static_cast<float>(rint(c * static_cast<double>(qd))) * qu;  // ties to even; exact
             buf[lane * 17 + bsel] = v;
             kb = keep ? (kb | (1u << bsel)) : (kb & ~(1u << bsel));
             amb &= ~(1u << bsel);
@@ -491,16 +498,12 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
 
     float* sPTh = reinterpret_cast<float*>(smem + SM::off_tab);  // [p][i] = Phi[i][p]
     float* sPTl = sPTh + 64;
-    float* sAh = sPTl + 64;  // [p][i] = A[p][i]
-    float* sAl = sAh + 64;
     float2* sPT2h = reinterpret_cast<float2*>(smem + SM::off_dup);  // [p][i] = (Phi[i][p], Phi[i][p])
     float2* sPT2l = sPT2h + 64;                                        // FP64 mode: low words
     for (int t = threadIdx.x; t < 64; t += WPB * 32) {
         const int i = t >> 3, c = t & 7;  // Ph[t] = Phi[i][c]
         sPTh[c * 8 + i] = A.tab.Ph[t];
         sPTl[c * 8 + i] = A.tab.Pl[t];
-        sAh[t] = A.tab.Ah[t];
-        sAl[t] = A.tab.Al[t];
         sPT2h[c * 8 + i] = f2dup(A.tab.Ph[t]);
         if constexpr (DF) sPT2l[c * 8 + i] = f2dup(A.tab.Pl[t]);
     }
@@ -671,7 +674,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
                 atomicOr(status, static_cast<unsigned>(SEMR_STATUS_TIMEOUT));
                 s_abort = 1;
             }
-            mbar_wait_bounded(bar, parity);  // the copy may still land: wait once more, bounded
+            drain_stage(bar, parity, status);  // the copy may still land: wait once more, bounded
             inflight = false;
             break;
         }
@@ -862,8 +865,8 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
                         tb[lane * 17 + r] = a2[r].x;
                         tb[lane * 17 + 8 + r] = a2[r].y;
                     }
-                    kb = resolve_ambiguous(tb, amb, kb, p.fields[f] + static_cast<uint64_t>(e) * WN3, sAh, sAl,
-                                           0x38000000 + (ke << 20), t, qd, qu, recomputed);
+                    kb = resolve_ambiguous(tb, amb, kb, p.fields[f] + static_cast<uint64_t>(e) * WN3, A.tab.A64,
+                                           pow2d(-ke), t, qd, qu, recomputed);
 #pragma unroll
                     for (int r = 0; r < 8; ++r) a2[r] = make_float2(tb[lane * 17 + r], tb[lane * 17 + 8 + r]);
                 }
@@ -1312,7 +1315,8 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
         __syncthreads();
         place_codes(pl, par ^ 1, nh_prev, s_excl);
     }
-    if (inflight) mbar_wait_bounded(bar, parity);  // after an abort: let a requested block land
+    // after an abort: let a requested block land before the CTA exits
+    if (inflight && !mbar_wait_bounded(bar, parity)) drain_stage(bar, parity, &(BATCH ? s_par[par ^ 1] : A.p).ctl->status);
 }
 
 // Finalize of field f: tree over its tile partials, then the exact maximum of
@@ -1412,6 +1416,7 @@ WTables make_wtables() {
     basis_tables(8, Am, Phi, w);
     for (int i = 0; i < 64; ++i) {
         t.A2[i] = make_float2(static_cast<float>(Am[i]), static_cast<float>(Am[i]));
+        t.A64[i] = Am[i];
         t.Ah[i] = static_cast<float>(Am[i]);
         t.Al[i] = static_cast<float>(Am[i] - static_cast<double>(t.Ah[i]));
         t.Ph[i] = static_cast<float>(Phi[i]);
@@ -1458,7 +1463,10 @@ __global__ void selftest_waits_kernel(uint64_t* tile_state, unsigned* status) {
         fence_mbar_init();
     }
     __syncwarp();
-    if (!mbar_wait_bounded(&bar, 0) && lane == 0) atomicOr(&status[1], static_cast<unsigned>(SEMR_STATUS_TIMEOUT));
+    if (!mbar_wait_bounded(&bar, 0)) {  // as the reduce kernel's abort path: timeout, then the drain
+        if (lane == 0) atomicOr(&status[1], static_cast<unsigned>(SEMR_STATUS_TIMEOUT));
+        drain_stage(&bar, 0, &status[1]);
+    }
 }
 
 }  // namespace

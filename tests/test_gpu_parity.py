@@ -65,6 +65,17 @@ def test_int32_codes():
     assert oracle.parse_header(res.payload)["flags"] & semr.SEMR_PAYLOAD_CODE32
 
 
+@pytest.mark.parametrize("n_elem,lx,n_fields,tau,seed", [(4096, 8, 3, 1e-6, 80), (3000, 6, 2, 1e-6, 84),
+                                                          (5000, 8, 2, 1e-7, 87), (2500, 10, 2, 1e-6, 82)])
+def test_small_tau_decisions_in_fp64(n_elem, lx, n_fields, tau, seed):
+    """Small tau keeps coefficients down to ~1e-5 max|u| of their element,
+    and the quantisation then decides codes |a|/q near half-integers to
+    ~1e-8 relative: the exact recomputation must be FP64-accurate there (at
+    seed 80, element 2551 of field 0 has |a|/q = 4.500000017 for mode 81,
+    outside the 1e-9 fragile band; float pairs rounded it to 4)."""
+    _full_compare(n_elem, lx, n_fields, tau, seed=seed)
+
+
 def test_tau_above_one_keeps_nothing():
     res, o = _full_compare(100, 8, 1, 2.0)
     assert res.summary.code_total == 0

@@ -7,8 +7,9 @@ import threading
 import numpy as np
 import pytest
 
+import oracle
 import paper_2407_20731_b300 as semr
-from parity import make_case
+from parity import compare_payloads, make_case
 
 pytestmark = pytest.mark.gpu
 
@@ -81,3 +82,27 @@ def test_budget_queues_and_rejects():
         tiny.submit(*reqs[0])
     assert e.value.code == semr.SEMR_EBUDGET
     tiny.close()
+
+
+def test_served_results_equal_the_oracle():
+    """FP64 mode through the server, all eight requests in flight together on
+    four slots: every served payload equals the FP64 oracle's outside its
+    fragile list, and every field report matches it."""
+    reqs = _requests()
+    srv = semr.Server(slots=4)
+    ids = [srv.submit(*r, precision=semr.SEMR_FP64) for r in reqs]
+    for rid, (fields, jac, lx, tau) in zip(ids, reqs):
+        rc, info = srv.wait(rid)
+        assert rc == semr.SEMR_OK
+        buf = np.zeros(int(info.summary.payload_bytes), dtype=np.uint8)
+        rc, _ = srv.release(rid, buf)
+        assert rc == semr.SEMR_OK
+        f_np = np.stack([f.cpu().numpy() for f in fields])
+        o = oracle.reduce(f_np, jac.cpu().numpy(), tau, fragile_cap=100000)
+        compare_payloads(buf, o.payload, o.fragile)
+        for f in range(len(fields)):
+            assert info.summary.field[f].umax == o.field_report[f, 6]
+            np.testing.assert_allclose(info.summary.field[f].sum_energy, o.field_report[f, 5], rtol=1e-12)
+            # the 1e-12 max|u| reconstruction tolerance allows ~1e-8 relative on L2_rel at tau = 1e-7
+            np.testing.assert_allclose(info.summary.field[f].l2_rel, o.field_report[f, 1], rtol=1e-6)
+    srv.close()
