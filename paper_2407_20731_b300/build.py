@@ -8,8 +8,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libsemr.so")
-SOURCES = [os.path.join(HERE, "csrc", s) for s in ("semr_kernels.cu", "semr_fast.cu", "semr_api.cpp", "semr_tables.cpp", "semr_noalloc.cu", "semr_batch.cpp", "semr_server.cpp", "semr_slice.cu", "semr_warp.cu")]
-HEADERS = [os.path.join(HERE, "csrc", h) for h in ("semr_internal.h", "semr_device.cuh")] + [os.path.join(ROOT, "include", "semr.h")]
+SOURCES = [os.path.join(HERE, "csrc", s) for s in ("semr_kernels.cu", "semr_fast.cu", "semr_api.cpp", "semr_tables.cpp", "semr_noalloc.cu", "semr_batch.cpp", "semr_server.cpp", "semr_slice.cu", "semr_warp.cu", "semr_group.cu")]
+HEADERS = [os.path.join(HERE, "csrc", h) for h in ("semr_internal.h", "semr_device.cuh", "semr_warp_common.cuh")] + [os.path.join(ROOT, "include", "semr.h")]
 
 NVCC_FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", "-shared", "-cudart", "static"]

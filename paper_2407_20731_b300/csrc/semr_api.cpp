@@ -43,11 +43,15 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 // warp kernel's (whichever of the two runs, the buffer holds it).
 uint64_t semr::scratch_need(int lx, int64_t n_elem, int32_t n_fields) {
     const uint64_t cta = scratch_bytes(uint64_t(n_fields) * tiles_per_field(lx, n_elem));
-    return lx == 8 ? std::max(cta, warp_scratch_bytes(n_elem, n_fields)) : cta;
+    if (lx == 8) return std::max(cta, warp_scratch_bytes(n_elem, n_fields));
+    if (group_tile(lx)) return std::max(cta, warp_scratch_bytes(n_elem, n_fields, group_tile(lx)));
+    return cta;
 }
 uint64_t semr::scratch_min(int lx, int64_t n_elem, int32_t n_fields) {
     const uint64_t cta = scratch_bytes(uint64_t(n_fields) * tiles_per_field(lx, n_elem));
-    return lx == 8 ? std::max(cta, warp_scratch_min(n_elem, n_fields)) : cta;
+    if (lx == 8) return std::max(cta, warp_scratch_min(n_elem, n_fields));
+    if (group_tile(lx)) return std::max(cta, warp_scratch_min(n_elem, n_fields, group_tile(lx)));
+    return cta;
 }
 
 extern "C" int semr_sizes_for(int32_t lx, int64_t n_elem, int32_t n_fields, double tau, semr_sizes* out) {
@@ -126,22 +130,27 @@ extern "C" int semr_reduce_async_timed(const semr_fieldset* fs, const semr_mesh*
     p.header_bytes = sz.header_bytes;
     p.fixed_bytes = field_fixed_bytes(mesh->lx, mesh->n_elem);
     p.code_base = sz.code_base;
-    // lx = 8 threshold truncation runs on the warp-per-element kernel: one look-back unit per element
+    // threshold truncation with int16 codes runs on the warp-level kernels: lx = 8 on the
+    // warp-per-element kernel, lx = 6 and 10 on the warp-group kernel
     const bool warp = warp_applicable(p);
+    const bool group = !warp && group_applicable(p);
     uint64_t zero = scratch_zero_bytes(tiles);
-    if (warp) {
-        split_scratch_warp(p, static_cast<uint8_t*>(out->scratch), out->scratch_bytes, mesh->n_elem, fs->n_fields);
-        p.tile = kWarpTile;
-        p.tiles_per_field = (int32_t)((uint64_t(mesh->n_elem) + kWarpTile - 1) / kWarpTile);
-        zero = scratch_zero_bytes(warp_tiles(mesh->n_elem, fs->n_fields));
+    if (warp || group) {
+        const int tile = warp ? kWarpTile : group_tile(mesh->lx);
+        split_scratch_warp(p, static_cast<uint8_t*>(out->scratch), out->scratch_bytes, mesh->n_elem, fs->n_fields, tile);
+        p.tile = tile;
+        p.tiles_per_field = (int32_t)((uint64_t(mesh->n_elem) + tile - 1) / tile);
+        zero = scratch_zero_bytes(warp_tiles(mesh->n_elem, fs->n_fields, tile));
     }
 
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (cudaMemsetAsync(out->scratch, 0, zero, st) != cudaSuccess) return SEMR_ECUDA;
     if (ev_begin && cudaEventRecord(static_cast<cudaEvent_t>(ev_begin), st) != cudaSuccess) return SEMR_ECUDA;
-    if ((warp ? launch_reduce_warp(p, st) : launch_reduce(p, mesh->lx, st)) != cudaSuccess) return SEMR_ECUDA;
+    const int lr = warp ? launch_reduce_warp(p, st) : group ? launch_reduce_group(p, st) : launch_reduce(p, mesh->lx, st);
+    if (lr != cudaSuccess) return SEMR_ECUDA;
     if (ev_end && cudaEventRecord(static_cast<cudaEvent_t>(ev_end), st) != cudaSuccess) return SEMR_ECUDA;
-    if ((warp ? launch_finalize_warp(p, st) : launch_finalize(p, mesh->lx, st)) != cudaSuccess) return SEMR_ECUDA;
+    const int lf = warp ? launch_finalize_warp(p, st) : group ? launch_finalize_group(p, st) : launch_finalize(p, mesh->lx, st);
+    if (lf != cudaSuccess) return SEMR_ECUDA;
     return SEMR_OK;
 }
 

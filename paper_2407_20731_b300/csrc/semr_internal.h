@@ -56,23 +56,25 @@ constexpr int kWarpArena = 4096;
 constexpr uint64_t kWarpStageCtas = 1024;
 constexpr uint64_t kWarpStageBytes =
     (2ull * kWarpCtaWarps * kWarpArena * 2 + 2ull * (kWarpTile + 1) * 4 + 2ull * kWarpTile * 4 + 255) & ~255ull;
-SEMR_HD inline uint64_t warp_tiles(int64_t n_elem, int32_t n_fields) {
-    return uint64_t(n_fields) * ((uint64_t(n_elem) + kWarpTile - 1) / kWarpTile);
+// The warp-group kernel (lx = 6 and 10, semr_group.cu) uses the same scratch layout with
+// look-back tiles of `tile` elements (128 at lx = 6, 64 at lx = 10).
+SEMR_HD inline uint64_t warp_tiles(int64_t n_elem, int32_t n_fields, int tile = kWarpTile) {
+    return uint64_t(n_fields) * ((uint64_t(n_elem) + tile - 1) / tile);
 }
 // Bytes of the warp kernel's scratch before the staging (256-aligned).
-SEMR_HD inline uint64_t warp_scratch_head(int64_t n_elem, int32_t n_fields) {
-    const uint64_t t = warp_tiles(n_elem, n_fields);
+SEMR_HD inline uint64_t warp_scratch_head(int64_t n_elem, int32_t n_fields, int tile = kWarpTile) {
+    const uint64_t t = warp_tiles(n_elem, n_fields, tile);
     return (scratch_bytes(t) + pad16(4ull * uint64_t(n_fields) * uint64_t(n_elem)) + 255) & ~uint64_t(255);
 }
 // Full warp-kernel scratch: staging for as many CTAs as may be resident (recommended size).
-SEMR_HD inline uint64_t warp_scratch_bytes(int64_t n_elem, int32_t n_fields) {
-    const uint64_t t = warp_tiles(n_elem, n_fields);
-    return warp_scratch_head(n_elem, n_fields) + (t < kWarpStageCtas ? t : kWarpStageCtas) * kWarpStageBytes;
+SEMR_HD inline uint64_t warp_scratch_bytes(int64_t n_elem, int32_t n_fields, int tile = kWarpTile) {
+    const uint64_t t = warp_tiles(n_elem, n_fields, tile);
+    return warp_scratch_head(n_elem, n_fields, tile) + (t < kWarpStageCtas ? t : kWarpStageCtas) * kWarpStageBytes;
 }
 // Smallest usable warp-kernel scratch: staging for one CTA (a smaller scratch buffer
 // limits the kernel's grid to the CTAs it can stage for).
-SEMR_HD inline uint64_t warp_scratch_min(int64_t n_elem, int32_t n_fields) {
-    return warp_scratch_head(n_elem, n_fields) + kWarpStageBytes;
+SEMR_HD inline uint64_t warp_scratch_min(int64_t n_elem, int32_t n_fields, int tile = kWarpTile) {
+    return warp_scratch_head(n_elem, n_fields, tile) + kWarpStageBytes;
 }
 // bytes that must be zero before each launch (control + tile states)
 SEMR_HD inline uint64_t scratch_zero_bytes(uint64_t tiles) { return kScratchControlBytes + pad16(8 * tiles); }
@@ -130,11 +132,12 @@ inline void split_scratch(LaunchParams& p, uint8_t* scratch, uint64_t tiles) {
 
 // Scratch split of the warp kernel (layout of warp_scratch_bytes) for a buffer of
 // `bytes` (at least warp_scratch_min): staging for as many CTAs as it holds.
-inline void split_scratch_warp(LaunchParams& p, uint8_t* scratch, uint64_t bytes, int64_t n_elem, int32_t n_fields) {
-    const uint64_t t = warp_tiles(n_elem, n_fields);
+inline void split_scratch_warp(LaunchParams& p, uint8_t* scratch, uint64_t bytes, int64_t n_elem, int32_t n_fields,
+                               int tile = kWarpTile) {
+    const uint64_t t = warp_tiles(n_elem, n_fields, tile);
     split_scratch(p, scratch, t);
     p.hmax_elem = reinterpret_cast<uint32_t*>(scratch + scratch_bytes(t));
-    const uint64_t head = warp_scratch_head(n_elem, n_fields);
+    const uint64_t head = warp_scratch_head(n_elem, n_fields, tile);
     p.code_stage = reinterpret_cast<int16_t*>(scratch + head);
     uint64_t ctas = (bytes - head) / kWarpStageBytes;
     if (ctas > kWarpStageCtas) ctas = kWarpStageCtas;
@@ -181,6 +184,15 @@ constexpr uint64_t kTensorMapBytes = 128;
 int warp_encode_maps(const LaunchParams& p, void* maps);
 int launch_reduce_warp_batch(const BatchQueue& q, int precision, uint64_t stage_ctas, void* stream);
 int launch_finalize_warp_batch(const BatchQueue& q, uint32_t total_fields, void* stream);
+
+// Warp-group kernel (semr_group.cu): lx = 6 and 10 threshold truncation in
+// SEMR_FP64 / SEMR_FP32 with int16 codes, one element per group of one (lx = 6)
+// or two (lx = 10) warps; the warp kernel's scratch layout with tiles of
+// group_tile(lx) elements (0 for an lx it does not serve).
+int group_tile(int lx);
+bool group_applicable(const LaunchParams& p);
+int launch_reduce_group(const LaunchParams& p, void* stream);
+int launch_finalize_group(const LaunchParams& p, void* stream);
 
 // Kernel launchers (semr_kernels.cu).  Return a cudaError_t value.
 int launch_reduce(const LaunchParams& p, int lx, void* stream);
