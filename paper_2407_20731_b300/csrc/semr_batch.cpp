@@ -21,21 +21,27 @@ using namespace semr;
 
 namespace {
 
-// Variant tile = kWarpTile: the warp-per-element kernel (lx = 8); others: the CTA kernel.
+// Variants: at lx = 8, tile kWarpTile is the warp-per-element kernel; at lx = 6 and 10, tile
+// group_tile(lx) is the warp-group kernel; every other tile is the CTA kernel.
 struct Group {
     int lx = 0, precision = 0, tile = 0;
     std::vector<int> items;       // indices into the caller's item array
     float tuned_ms[4] = {0, 0, 0, 0};
     int variants[4] = {0, 0, 0, 0};
     int n_variants = 0;
-    bool warp_ok = false;         // every item fits the warp kernel
+    bool warp_ok = false;         // every item fits the warp (lx = 8) or warp-group kernel
     // workspace offsets
     uint64_t off_desc = 0, off_tile_base = 0, off_field_base = 0, off_zero = 0, zero_bytes = 0;
     uint64_t off_maps = 0, off_stage = 0, stage_ctas = 0;  // warp kernel
     uint64_t total_tiles = 0;
     uint32_t total_fields = 0;
-    bool warp() const { return tile == kWarpTile; }
+    bool warp() const { return lx == 8 && tile == kWarpTile; }               // warp-per-element kernel
+    bool grp() const { return group_tile(lx) != 0 && tile == group_tile(lx); }  // warp-group kernel
+    bool wl() const { return warp() || grp(); }  // either: element maxima and one shared code staging
 };
+
+// The warp-level kernel's tile of an lx (0: none).
+int wl_tile(int lx) { return lx == 8 ? kWarpTile : group_tile(lx); }
 
 uint64_t align256(uint64_t b) { return (b + 255) & ~uint64_t(255); }
 
@@ -128,7 +134,7 @@ int build_workspace(semr_batch* b, cudaStream_t st) {
         G.zero_bytes = off - G.off_zero;
         off = align256(off);
         for (int idx : G.items) off = align256(off + 32 * item_tiles(b->items[idx], G.tile));  // partials
-        if (G.warp()) {  // per-item element maxima, then one code staging for the group
+        if (G.wl()) {  // per-item element maxima, then one code staging for the group
             for (int idx : G.items)
                 off = align256(off + 4ull * uint64_t(b->items[idx].mesh.n_elem) * b->items[idx].fs.n_fields);
             G.stage_ctas = std::min<uint64_t>(G.total_tiles, kWarpStageCtas);
@@ -146,8 +152,8 @@ int build_workspace(semr_batch* b, cudaStream_t st) {
         std::vector<uint32_t> fb(n + 1, 0);
         uint64_t zoff = G.off_zero + 256;
         uint64_t poff = align256(G.off_zero + G.zero_bytes);
-        uint64_t uoff = poff;  // warp kernel: element maxima after the partials
-        if (G.warp())
+        uint64_t uoff = poff;  // warp-level kernels: element maxima after the partials
+        if (G.wl())
             for (int idx : G.items) uoff = align256(uoff + 32 * item_tiles(b->items[idx], G.tile));
         std::vector<uint8_t> maps(G.warp() ? kTensorMapBytes * G.total_fields : 0);
         descs[g].resize(n);
@@ -161,12 +167,13 @@ int build_workspace(semr_batch* b, cudaStream_t st) {
             p.ctl = reinterpret_cast<ScratchControl*>(b->ws + zoff);
             p.tile_state = reinterpret_cast<uint64_t*>(b->ws + zoff + kScratchControlBytes);
             p.tile_part = reinterpret_cast<double*>(b->ws + poff);
-            if (G.warp()) {
+            if (G.wl()) {
                 p.hmax_elem = reinterpret_cast<uint32_t*>(b->ws + uoff);
                 uoff = align256(uoff + 4ull * uint64_t(it.mesh.n_elem) * it.fs.n_fields);
                 p.code_stage = reinterpret_cast<int16_t*>(b->ws + G.off_stage);
                 p.stage_ctas = (int32_t)G.stage_ctas;
-                if (warp_encode_maps(p, maps.data() + kTensorMapBytes * fb[i]) != 0) return SEMR_EUNSUPPORTED;
+                if (G.warp() && warp_encode_maps(p, maps.data() + kTensorMapBytes * fb[i]) != 0)
+                    return SEMR_EUNSUPPORTED;
             }
             zoff += kScratchControlBytes + pad16(8 * t);
             poff = align256(poff + 32 * t);
@@ -208,6 +215,9 @@ int launch_all(semr_batch* b, cudaStream_t st) {
         if (G.warp()) {
             if (launch_reduce_warp_batch(q, G.precision, G.stage_ctas, st) != cudaSuccess) return SEMR_ECUDA;
             if (launch_finalize_warp_batch(q, G.total_fields, st) != cudaSuccess) return SEMR_ECUDA;
+        } else if (G.grp()) {
+            if (launch_reduce_group_batch(q, G.lx, G.precision, G.stage_ctas, st) != cudaSuccess) return SEMR_ECUDA;
+            if (launch_finalize_group_batch(q, G.lx, G.total_fields, st) != cudaSuccess) return SEMR_ECUDA;
         } else {
             if (launch_reduce_fast_batch(q, G.lx, G.precision, G.tile, st) != cudaSuccess) return SEMR_ECUDA;
             if (launch_finalize_batch(q, G.total_fields, st) != cudaSuccess) return SEMR_ECUDA;
@@ -216,13 +226,14 @@ int launch_all(semr_batch* b, cudaStream_t st) {
     return SEMR_OK;
 }
 
-// Time the warp kernel on one snapshot as a one-item batch (one warm-up, three
-// timed launches); ms < 0 when it cannot run.
+// Time the warp-level kernel of the snapshot's lx on it as a one-item batch (one
+// warm-up, three timed launches); ms < 0 when it cannot run.
 int probe_warp(const semr_batch_item& it, int precision, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, float* ms) {
     *ms = -1.0f;
+    const int lx = it.mesh.lx, tile = wl_tile(lx);
     LaunchParams p;
-    if (fill_params(it, kWarpTile, p)) return SEMR_OK;
-    const uint64_t t = item_tiles(it, kWarpTile), nf = (uint64_t)it.fs.n_fields;
+    if (tile == 0 || fill_params(it, tile, p)) return SEMR_OK;
+    const uint64_t t = item_tiles(it, tile), nf = (uint64_t)it.fs.n_fields;
     const uint64_t stage_ctas = std::min<uint64_t>(t, kWarpStageCtas);
     // [desc 1 KB][bases 512][maps][counter 256 + control + states][partials][maxima][staging]
     const uint64_t o_maps = 2048, o_zero = align256(o_maps + kTensorMapBytes * nf);
@@ -242,7 +253,7 @@ int probe_warp(const semr_batch_item& it, int precision, cudaStream_t st, cudaEv
     std::vector<uint8_t> maps(kTensorMapBytes * nf);
     const uint64_t tb[2] = {0, t};
     const uint32_t fb[2] = {0, (uint32_t)nf};
-    bool ok = warp_encode_maps(p, maps.data()) == 0 &&
+    bool ok = (lx != 8 || warp_encode_maps(p, maps.data()) == 0) &&
               cudaMemcpy(w, &p, sizeof(p), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(w + 1024, tb, sizeof(tb), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(w + 1536, fb, sizeof(fb), cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -259,7 +270,8 @@ int probe_warp(const semr_batch_item& it, int precision, cudaStream_t st, cudaEv
     for (int rep = 0; rep < 4 && ok; ++rep) {
         cudaMemsetAsync(w + o_zero, 0, zero, st);
         cudaEventRecord(e0, st);
-        ok = launch_reduce_warp_batch(q, precision, stage_ctas, st) == cudaSuccess;
+        ok = (lx == 8 ? launch_reduce_warp_batch(q, precision, stage_ctas, st)
+                      : launch_reduce_group_batch(q, lx, precision, stage_ctas, st)) == cudaSuccess;
         cudaEventRecord(e1, st);
         if (ok) ok = cudaEventSynchronize(e1) == cudaSuccess;
         float m = 0.0f;
@@ -282,7 +294,7 @@ int autotune(semr_batch* b, Group& G, cudaStream_t st) {
     const semr_batch_item& it = b->items[probe];
     uint64_t max_tiles = 0;
     for (int v = 0; v < G.n_variants; ++v)
-        if (G.variants[v] != kWarpTile) max_tiles = std::max(max_tiles, item_tiles(it, G.variants[v]));
+        if (G.variants[v] != wl_tile(G.lx)) max_tiles = std::max(max_tiles, item_tiles(it, G.variants[v]));
     // probe workspace: descriptor, bases, counter + control + states, partials
     const uint64_t zero = 256 + kScratchControlBytes + pad16(8 * max_tiles);
     const uint64_t bytes = 4096 + zero + 32 * max_tiles + 256;
@@ -294,7 +306,7 @@ int autotune(semr_batch* b, Group& G, cudaStream_t st) {
     float best = 1e30f;
     int best_tile = G.variants[0];
     for (int v = 0; v < G.n_variants; ++v) {
-        if (G.variants[v] == kWarpTile) {
+        if (G.variants[v] == wl_tile(G.lx)) {
             float ms = -1.0f;
             const int rc = probe_warp(it, G.precision, st, e0, e1, &ms);
             if (rc) {
@@ -306,7 +318,7 @@ int autotune(semr_batch* b, Group& G, cudaStream_t st) {
             G.tuned_ms[v] = ms;
             if (ms >= 0.0f && ms < best) {
                 best = ms;
-                best_tile = kWarpTile;
+                best_tile = G.variants[v];
             }
             continue;
         }
@@ -391,18 +403,20 @@ extern "C" int semr_batch_create(semr_batch** out, const semr_batch_item* items,
         }
         b->groups[f->second].items.push_back(i);
     }
-    for (Group& G : b->groups) {  // lx = 8: the warp kernel first (the default) when every item fits it
-        if (G.lx != 8) continue;
+    for (Group& G : b->groups) {  // the warp-level kernel first (the default) when every item fits it
+        const int wt = wl_tile(G.lx);
+        if (wt == 0) continue;
         G.warp_ok = true;
         for (int idx : G.items) {
             LaunchParams p;
-            G.warp_ok = G.warp_ok && fill_params(items[idx], kWarpTile, p) == SEMR_OK && warp_applicable(p);
+            G.warp_ok = G.warp_ok && fill_params(items[idx], wt, p) == SEMR_OK &&
+                        (G.lx == 8 ? warp_applicable(p) : group_applicable(p));
         }
         if (G.warp_ok && G.n_variants < 4) {
             for (int v = G.n_variants; v > 0; --v) G.variants[v] = G.variants[v - 1];
-            G.variants[0] = kWarpTile;
+            G.variants[0] = wt;
             ++G.n_variants;
-            G.tile = kWarpTile;
+            G.tile = wt;
         }
     }
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);

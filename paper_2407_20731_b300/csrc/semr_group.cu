@@ -247,12 +247,15 @@ __device__ __noinline__ uint32_t g_resolve(float* M, int w0, uint32_t amb, uint3
 
 template <int LX, int MODE>
 struct GOcc {  // CTAs per SM the register budget aims at
-    static constexpr int value = LX <= 6 ? (MODE ? 3 : 5) : 2;
+    static constexpr int value = LX <= 6 ? (MODE ? 3 : 5) : 3;
 };
 
-template <int LX, int MODE>
+// BATCH = false: one reduction, parameters in A.p.  BATCH = true: the work queue q of
+// several reductions of this lx (each with its own descriptor, payload and scratch; they
+// share one code staging).
+template <int LX, int MODE, bool BATCH>
 __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
-    reduce_group_kernel(const __grid_constant__ GArgs<LX> A) {
+    reduce_group_kernel(const __grid_constant__ GArgs<LX> A, const BatchQueue q) {
     using C = GCfg<LX>;
     constexpr bool DF = MODE != 0;
     using SM = GSmem<LX, DF>;
@@ -263,7 +266,6 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int gi = threadIdx.x / GT, g = threadIdx.x % GT, wg = g >> 5;  // group, thread in group, warp in group
-    const LaunchParams& p = A.p;
 
     // CTA tables: Phi [i][p] (hi, lo) and [p][i] (hi, lo)
     float* sPh = reinterpret_cast<float*>(smem + SM::off_tab);
@@ -302,10 +304,10 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
     const f2 wjk0 = df_mul({A.tab.wh[j0], A.tab.wl[j0]}, {A.tab.wh[k0], A.tab.wl[k0]});
     const f2 wjk1 = v1 ? df_mul({A.tab.wh[j1], A.tab.wl[j1]}, {A.tab.wh[k1], A.tab.wl[k1]}) : f2{0.0f, 0.0f};
 
-    const uint32_t total_tiles = A.total_tiles;
-    unsigned* counter = &p.ctl->tile_counter;
-    unsigned* status = &p.ctl->status;
-    uint8_t* stage_cta = reinterpret_cast<uint8_t*>(p.code_stage) + static_cast<uint64_t>(blockIdx.x) * kWarpStageBytes;
+    const uint32_t total_tiles = BATCH ? static_cast<uint32_t>(q.total_tiles) : A.total_tiles;
+    unsigned* counter = BATCH ? q.counter : &A.p.ctl->tile_counter;
+    uint8_t* stage_cta = reinterpret_cast<uint8_t*>(BATCH ? q.items[0].code_stage : A.p.code_stage) +
+                         static_cast<uint64_t>(blockIdx.x) * kWarpStageBytes;
     int16_t* stage_codes = reinterpret_cast<int16_t*>(stage_cta);
     uint32_t* stage_pre = reinterpret_cast<uint32_t*>(stage_cta + 2ull * kWarpCtaWarps * kWarpArena * 2);
     uint32_t* stage_off = stage_pre + 2 * (kWarpTile + 1);
@@ -313,6 +315,22 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
     constexpr int ARENA = WPE * kWarpArena;  // the group's codes per tile parity
 
     __shared__ uint32_t s_tile[2];
+    __shared__ uint32_t s_titem[2], s_tloc[2];    // their item and tile index within the item (BATCH)
+    __shared__ LaunchParams s_par[BATCH ? 2 : 1];  // BATCH: descriptors of the current and previous tile
+    auto resolve = [&](uint32_t gt, int slot) {    // item and local tile of a claimed tile (one thread)
+        uint32_t item = 0, loc = gt;
+        if (BATCH && gt < total_tiles) {           // last item whose first tile is <= gt
+            int lo = 0, hi = q.n_items - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) / 2;
+                if (q.tile_base[mid] <= gt) lo = mid; else hi = mid - 1;
+            }
+            item = static_cast<uint32_t>(lo);
+            loc = gt - static_cast<uint32_t>(q.tile_base[lo]);
+        }
+        s_titem[slot] = item;
+        s_tloc[slot] = loc;
+    };
     __shared__ uint32_t s_cnt[TILE];  // tile tag << 16 | code count
     __shared__ unsigned long long s_excl;
     __shared__ unsigned long long s_peek;
@@ -321,19 +339,20 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
     __shared__ int s_abort;
     if (threadIdx.x == 0) {
         s_tile[0] = atomicAdd(counter, 1u);
+        resolve(s_tile[0], 0);
         s_abort = 0;
         s_peek_tag = 0;
     }
     for (int i = threadIdx.x; i < TILE; i += GCTA) s_cnt[i] = 0xffff0000u;
     __syncthreads();
-    const uint32_t E = static_cast<uint32_t>(p.n_elem), tpf = static_cast<uint32_t>(p.tiles_per_field);
-    auto geom = [&](uint32_t tt, uint32_t& f, uint32_t& e0, int& nh) {
-        f = tt / tpf;
-        e0 = (tt - f * tpf) * TILE;
-        nh = static_cast<int>(min(static_cast<uint32_t>(TILE), E - e0));
+    // field, first element and element count of local tile tt of a reduction with tpf_ tiles per field
+    auto geom = [&](uint32_t tt, uint32_t tpf_, uint32_t E_, uint32_t& f, uint32_t& e0, int& nh) {
+        f = tt / tpf_;
+        e0 = (tt - f * tpf_) * TILE;
+        nh = static_cast<int>(min(static_cast<uint32_t>(TILE), E_ - e0));
     };
-    auto issue = [&](uint32_t f, uint32_t e) {  // thread g == 0: element block e of field f into the stage
-        bulk_load(stage, p.fields[f] + static_cast<uint64_t>(e) * N3, 8u * N3, bar);
+    auto issue = [&](const double* field, uint32_t e) {  // thread g == 0: element block e into the stage
+        bulk_load(stage, field + static_cast<uint64_t>(e) * N3, 8u * N3, bar);
     };
     uint32_t parity = 0;
     uint32_t tag = 0;
@@ -342,12 +361,12 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
     uint32_t t_prev = 0xffffffffu;
     int nh_prev = 0, par = 0;
     uint32_t tot_prev = 0;
-    const float tau_h = A.tau_h, tau_l = A.tau_l;
 
-    // Copy the staged codes of a tile (parity pp, nhp elements) to code_base + 2 (excl + prefix):
-    // warp 0 of each group, lane L: the group's element gi + GPC L.
-    auto place_codes = [&](int pp, int nhp, uint64_t excl) {
+    // Copy the staged codes of a tile (parity pp, nhp elements, descriptor pd) to code_base + 2
+    // (excl + prefix): warp 0 of each group, lane L: the group's element gi + GPC L.
+    auto place_codes = [&](const LaunchParams& pd, int pp, int nhp, uint64_t excl) {
         if (wg != 0) return;
+        unsigned* status = &pd.ctl->status;
         const uint32_t* pre = stage_pre + pp * (kWarpTile + 1);
         const int16_t* arena = stage_codes + (pp * kWarpCtaWarps + gi * WPE) * kWarpArena;
         const int il = gi + GPC * lane;
@@ -357,42 +376,61 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
             n = pre[il + 1] - b;
             off = stage_off[pp * kWarpTile + il];
         }
-        const uint64_t gbyte = p.code_base + 2ull * (excl + b);
+        const uint64_t gbyte = pd.code_base + 2ull * (excl + b);
         bool copy = off != kDirect && n > 0;
-        if (copy && gbyte + 2ull * n > p.payload_cap) {
+        if (copy && gbyte + 2ull * n > pd.payload_cap) {
             atomicOr(status, static_cast<unsigned>(SEMR_STATUS_OVERFLOW));
             copy = false;
         }
         if (copy && n <= 32u) {
-            int16_t* dst = reinterpret_cast<int16_t*>(p.payload + gbyte);
+            int16_t* dst = reinterpret_cast<int16_t*>(pd.payload + gbyte);
             const int16_t* src = arena + off;
             for (uint32_t k = 0; k < n; ++k) dst[k] = src[k];
         }
         for (uint32_t big = __ballot_sync(FULL, copy && n > 32u); big; big &= big - 1) {
             const int src_lane = __ffs(big) - 1;
             const uint32_t nb = __shfl_sync(FULL, n, src_lane), ob = __shfl_sync(FULL, off, src_lane);
-            int16_t* dst = reinterpret_cast<int16_t*>(p.payload + __shfl_sync(FULL, gbyte, src_lane));
+            int16_t* dst = reinterpret_cast<int16_t*>(pd.payload + __shfl_sync(FULL, gbyte, src_lane));
             for (uint32_t k = lane; k < nb; k += 32) dst[k] = arena[ob + k];
         }
     };
 
-    {  // the first block of each group's first tile
-        if (s_tile[0] < total_tiles) {
-            uint32_t f, e0;
-            int nh;
-            geom(s_tile[0], f, e0, nh);
-            if (gi < nh) {
-                if (g == 0) issue(f, e0 + gi);
-                inflight = true;
-            }
+    if (s_tile[0] < total_tiles) {  // the first block of each group's first tile
+        const LaunchParams* pn = BATCH ? &q.items[s_titem[0]] : &A.p;
+        uint32_t f, e0;
+        int nh;
+        geom(s_tloc[0], static_cast<uint32_t>(pn->tiles_per_field), static_cast<uint32_t>(pn->n_elem), f, e0, nh);
+        if (gi < nh) {
+            if (g == 0) issue(pn->fields[f], e0 + gi);
+            inflight = true;
         }
     }
     for (;;) {
+    // Tiles are claimed only once the previous one is computed, so they start in about the
+    // order of their claims and a look-back never waits for a tile not yet begun.
     if (s_tile[0] >= total_tiles) break;
-    const uint32_t tcur = s_tile[0];
+    const uint32_t gtile = s_tile[0];
+    const uint32_t item = s_titem[0], tcur = s_tloc[0];  // tcur: the tile's index within its reduction
+    if constexpr (BATCH) {  // the item's descriptor into this tile's slot (the other holds the previous one's)
+        __syncthreads();    // the slot's last reader (the placement of two tiles ago) is done
+        constexpr int PW = sizeof(LaunchParams) / 4;
+        static_assert(sizeof(LaunchParams) % 4 == 0, "descriptor copy by words");
+        for (int i = threadIdx.x; i < PW; i += GCTA)
+            reinterpret_cast<int*>(&s_par[par])[i] = reinterpret_cast<const int*>(&q.items[item])[i];
+        __syncthreads();
+    }
+    const LaunchParams& p = BATCH ? s_par[par] : A.p;
+    const LaunchParams& pprev = BATCH ? s_par[par ^ 1] : A.p;
+    unsigned* status = &p.ctl->status;
+    float tau_h = A.tau_h, tau_l = A.tau_l;
+    if constexpr (BATCH) {
+        tau_h = static_cast<float>(p.tau);
+        tau_l = static_cast<float>(p.tau - static_cast<double>(tau_h));
+    }
+    const uint32_t E = static_cast<uint32_t>(p.n_elem), tpf = static_cast<uint32_t>(p.tiles_per_field);
     uint32_t f, e0;
     int nh;
-    geom(tcur, f, e0, nh);
+    geom(tcur, tpf, E, f, e0, nh);
     int16_t* arena = stage_codes + (par * kWarpCtaWarps + gi * WPE) * kWarpArena;
     uint32_t atop = 0;
     uint8_t* fsec = p.payload + p.header_bytes + static_cast<uint64_t>(f) * p.fixed_bytes;
@@ -488,7 +526,7 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
             if (il + GPC < nh) {
                 if (g == 0) {
                     fence_proxy_async();
-                    issue(f, e + GPC);
+                    issue(p.fields[f], e + GPC);
                 }
                 inflight = true;
             }
@@ -678,14 +716,14 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
             // the group's arena is full (extreme inputs only): write at the final place, which needs
             // the tile's exclusive prefix and the counts of the tile's earlier elements
             uint64_t before;
-            if (s_peek_tag == tcur + 1u) {
+            if (s_peek_tag == gtile + 1u) {
                 before = s_peek;
             } else {
                 before = lookback_peek(p.tile_state, tcur, status);
                 if (g == 0) {
                     s_peek = before;
                     __threadfence_block();
-                    s_peek_tag = tcur + 1u;
+                    s_peek_tag = gtile + 1u;
                 }
             }
             uint32_t part = 0;
@@ -931,16 +969,20 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
         }
         gsync<WPE>(gi);  // the group's buffers and exchange slots are reused by the next element
     }
-    if (threadIdx.x == 0) s_tile[1] = atomicAdd(counter, 1u);
+    if (threadIdx.x == 0) {
+        s_tile[1] = atomicAdd(counter, 1u);
+        resolve(s_tile[1], 1);
+    }
     __syncthreads();  // every element of the tile is done
     if (s_tile[1] < total_tiles && !s_abort) {  // each group's first block of the next tile
+        const LaunchParams* pn = BATCH ? &q.items[s_titem[1]] : &A.p;
         uint32_t fn, e0n;
         int nhn;
-        geom(s_tile[1], fn, e0n, nhn);
+        geom(s_tloc[1], static_cast<uint32_t>(pn->tiles_per_field), static_cast<uint32_t>(pn->n_elem), fn, e0n, nhn);
         if (gi < nhn) {
             if (g == 0) {
                 fence_proxy_async();
-                issue(fn, e0n + gi);
+                issue(pn->fields[fn], e0n + gi);
             }
             inflight = true;
         }
@@ -973,12 +1015,14 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
             st_release_u64(&p.tile_state[tcur], (tcur == 0 ? kFlagPrefix : kFlagAggregate) | tot);
         }
         if (t_prev != 0xffffffffu) {
-            const uint64_t excl = lookback_warp(p.tile_state, t_prev, tot_prev, status);
+            const uint64_t excl = lookback_warp(pprev.tile_state, t_prev, tot_prev, &pprev.ctl->status);
             if (lane == 0) s_excl = excl;
         }
         tot_prev = tot;
     } else if (wid == 2 && lane == 0) {
         s_tile[0] = s_tile[1];
+        s_titem[0] = s_titem[1];
+        s_tloc[0] = s_tloc[1];
     }
     {  // every warp: FP64 partials and element report of the elements wid + 4 lane
         double v0 = 0.0, v1d = 0.0;
@@ -1026,7 +1070,7 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
         tp[2] = fmax(fmax(s_wpart[0][2], s_wpart[1][2]), fmax(s_wpart[2][2], s_wpart[3][2]));
         tp[3] = fmax(fmax(s_wpart[0][3], s_wpart[1][3]), fmax(s_wpart[2][3], s_wpart[3][3]));
     }
-    if (t_prev != 0xffffffffu) place_codes(par ^ 1, nh_prev, s_excl);
+    if (t_prev != 0xffffffffu) place_codes(pprev, par ^ 1, nh_prev, s_excl);
     if (recomputed && lane == 0) atomicAdd(&p.ctl->recomputed, recomputed);
     recomputed = 0;
     t_prev = tcur;
@@ -1037,27 +1081,28 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
     __syncthreads();
     }
     if (t_prev != 0xffffffffu && !s_abort) {  // the last tile: its look-back, then its codes
+        const LaunchParams& pl = BATCH ? s_par[par ^ 1] : A.p;
         if (wid == 0) {
-            const uint64_t excl = lookback_warp(p.tile_state, t_prev, tot_prev, status);
+            const uint64_t excl = lookback_warp(pl.tile_state, t_prev, tot_prev, &pl.ctl->status);
             if (lane == 0) s_excl = excl;
         }
         __syncthreads();
-        place_codes(par ^ 1, nh_prev, s_excl);
+        place_codes(pl, par ^ 1, nh_prev, s_excl);
     }
-    // after an abort: let a requested block land before the CTA exits
-    if (inflight && !mbar_wait_bounded(bar, parity)) drain_stage(bar, parity, status);
+    // after an abort: let a requested block land before the CTA exits (the second, bounded wait)
+    if (inflight) drain_stage(bar, parity, &(BATCH ? s_par[par ^ 1] : A.p).ctl->status);
 }
 
 // Finalize of field f: tree over its tile partials, then the exact maximum of |u| (the
 // elements whose largest high word is the field's hold it: those blocks are reread).
 template <int LX>
-__global__ void __launch_bounds__(256) finalize_group_kernel(const LaunchParams p) {
+__device__ void finalize_group_field(const LaunchParams& p, int f) {
     constexpr int N3 = LX * LX * LX, TILE = GCfg<LX>::TILE;
     __shared__ double red[4][256];
     __shared__ int s_list[64];
     __shared__ int s_cnt;
     __shared__ unsigned long long s_umax;
-    const int f = blockIdx.x, tid = threadIdx.x;
+    const int tid = threadIdx.x;
     finalize_tree(p.tile_part, f, static_cast<uint64_t>(p.tiles_per_field), red);
     const double M = red[3][0];
     if (tid == 0) {
@@ -1099,6 +1144,26 @@ __global__ void __launch_bounds__(256) finalize_group_kernel(const LaunchParams 
 }
 
 template <int LX>
+__global__ void __launch_bounds__(256) finalize_group_kernel(const LaunchParams p) { finalize_group_field<LX>(p, blockIdx.x); }
+
+// One block per (item, field) of a batched launch.
+template <int LX>
+__global__ void __launch_bounds__(256) finalize_group_batch_kernel(const BatchQueue q) {
+    __shared__ int s_item;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = q.n_items - 1;  // last item with field_base <= blockIdx.x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (q.field_base[mid] <= blockIdx.x) lo = mid; else hi = mid - 1;
+        }
+        s_item = lo;
+    }
+    __syncthreads();
+    const LaunchParams& p = q.items[s_item];
+    finalize_group_field<LX>(p, static_cast<int>(blockIdx.x - q.field_base[s_item]));
+}
+
+template <int LX>
 GTables<LX> make_gtables() {
     GTables<LX> t;
     double Am[LX * LX], Phi[LX * LX], w[LX];
@@ -1119,18 +1184,22 @@ GTables<LX> make_gtables() {
     return t;
 }
 
-template <int LX, int MODE>
-int launch_group_mode(const LaunchParams& p, void* stream) {
+// Launch of one reduction (q empty) or of a batch queue (BATCH; p unused but for stage_ctas).
+template <int LX, int MODE, bool BATCH>
+int launch_group_mode(const LaunchParams& p, const BatchQueue& q, uint64_t stage_ctas, void* stream) {
     using SM = GSmem<LX, MODE != 0>;
     GArgs<LX> a;
     std::memset(&a, 0, sizeof(a));
-    a.p = p;
     a.tab = make_gtables<LX>();
-    a.tau_h = static_cast<float>(p.tau);
-    a.tau_l = static_cast<float>(p.tau - static_cast<double>(a.tau_h));
-    a.total_tiles = static_cast<uint32_t>(static_cast<uint64_t>(p.n_fields) * p.tiles_per_field);
+    if (!BATCH) {
+        a.p = p;
+        a.tau_h = static_cast<float>(p.tau);
+        a.tau_l = static_cast<float>(p.tau - static_cast<double>(a.tau_h));
+        a.total_tiles = static_cast<uint32_t>(static_cast<uint64_t>(p.n_fields) * p.tiles_per_field);
+    }
+    const uint64_t total = BATCH ? q.total_tiles : a.total_tiles;
     cudaError_t err;
-    auto kern = reduce_group_kernel<LX, MODE>;
+    auto kern = reduce_group_kernel<LX, MODE, BATCH>;
     if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes)) != cudaSuccess)
         return (int)err;
     int dev = 0, sms = 0, per_sm = 0;
@@ -1139,10 +1208,11 @@ int launch_group_mode(const LaunchParams& p, void* stream) {
     if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, GCTA, SM::bytes)) != cudaSuccess)
         return (int)err;
     if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
-    const uint64_t want = std::min<uint64_t>(a.total_tiles, static_cast<uint64_t>(p.stage_ctas));
+    // persistent: as many CTAs as fit at once, never more than tiles or staging slots
+    const uint64_t want = std::min<uint64_t>(total, stage_ctas);
     const unsigned grid = (unsigned)std::min<uint64_t>(want, static_cast<uint64_t>(sms) * per_sm);
     if (grid == 0) return (int)cudaErrorInvalidConfiguration;
-    kern<<<grid, GCTA, SM::bytes, static_cast<cudaStream_t>(stream)>>>(a);
+    kern<<<grid, GCTA, SM::bytes, static_cast<cudaStream_t>(stream)>>>(a, q);
     return (int)cudaGetLastError();
 }
 
@@ -1166,11 +1236,33 @@ bool group_applicable(const LaunchParams& p) {
 
 int launch_reduce_group(const LaunchParams& p, void* stream) {
     const bool df = p.precision != SEMR_FP32;
+    const BatchQueue q{};
+    const uint64_t sc = static_cast<uint64_t>(p.stage_ctas);
     switch (p.lx) {
-        case 6: return df ? launch_group_mode<6, 1>(p, stream) : launch_group_mode<6, 0>(p, stream);
-        case 10: return df ? launch_group_mode<10, 1>(p, stream) : launch_group_mode<10, 0>(p, stream);
+        case 6: return df ? launch_group_mode<6, 1, false>(p, q, sc, stream) : launch_group_mode<6, 0, false>(p, q, sc, stream);
+        case 10: return df ? launch_group_mode<10, 1, false>(p, q, sc, stream) : launch_group_mode<10, 0, false>(p, q, sc, stream);
         default: return (int)cudaErrorInvalidValue;
     }
+}
+
+int launch_reduce_group_batch(const BatchQueue& q, int lx, int precision, uint64_t stage_ctas, void* stream) {
+    const bool df = precision != SEMR_FP32;
+    LaunchParams p;
+    std::memset(&p, 0, sizeof(p));
+    switch (lx) {
+        case 6: return df ? launch_group_mode<6, 1, true>(p, q, stage_ctas, stream) : launch_group_mode<6, 0, true>(p, q, stage_ctas, stream);
+        case 10: return df ? launch_group_mode<10, 1, true>(p, q, stage_ctas, stream) : launch_group_mode<10, 0, true>(p, q, stage_ctas, stream);
+        default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+int launch_finalize_group_batch(const BatchQueue& q, int lx, uint32_t total_fields, void* stream) {
+    switch (lx) {
+        case 6: finalize_group_batch_kernel<6><<<total_fields, 256, 0, static_cast<cudaStream_t>(stream)>>>(q); break;
+        case 10: finalize_group_batch_kernel<10><<<total_fields, 256, 0, static_cast<cudaStream_t>(stream)>>>(q); break;
+        default: return (int)cudaErrorInvalidValue;
+    }
+    return (int)cudaGetLastError();
 }
 
 int launch_finalize_group(const LaunchParams& p, void* stream) {

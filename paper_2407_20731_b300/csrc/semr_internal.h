@@ -193,6 +193,9 @@ int group_tile(int lx);
 bool group_applicable(const LaunchParams& p);
 int launch_reduce_group(const LaunchParams& p, void* stream);
 int launch_finalize_group(const LaunchParams& p, void* stream);
+// Batched form: items of one (lx, precision), laid out as for the warp kernel (no tensor maps).
+int launch_reduce_group_batch(const BatchQueue& q, int lx, int precision, uint64_t stage_ctas, void* stream);
+int launch_finalize_group_batch(const BatchQueue& q, int lx, uint32_t total_fields, void* stream);
 
 // Kernel launchers (semr_kernels.cu).  Return a cudaError_t value.
 int launch_reduce(const LaunchParams& p, int lx, void* stream);
