@@ -791,7 +791,9 @@ def emit(args, rank, world, value, ms_step, prec, roofline, cpu, e2e, clk, sm, e
                 "vs_baseline": None, "dtype": "f64" if prec == semr.SEMR_FP64 else "f32",
                 "data": "synthetic (seeded 16-mode |k|^-5/3 spectra + N(0,1e-6) noise, J~U[0.5,2])",
                 "config": workload_config(args, world), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": 2 * args.steps, "clocks": clk,
+                # one fused kernel per step (the warp kernel finalizes in its last CTA); the
+                # cumulative variant runs the CTA kernel and its finalize kernel
+                "gpu_launches": (2 if args.cumulative else 1) * args.steps, "clocks": clk,
                 "result": {"cr": round(sm.cr, 5), "payload_bytes": int(sm.payload_bytes),
                            "l2_rel": [round(sm.field[i].l2_rel, 6) for i in range(N_FIELDS)],
                            "linf_rel": [round(sm.field[i].linf_rel, 6) for i in range(N_FIELDS)]},

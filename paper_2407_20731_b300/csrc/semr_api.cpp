@@ -149,8 +149,8 @@ extern "C" int semr_reduce_async_timed(const semr_fieldset* fs, const semr_mesh*
     const int lr = warp ? launch_reduce_warp(p, st) : group ? launch_reduce_group(p, st) : launch_reduce(p, mesh->lx, st);
     if (lr != cudaSuccess) return SEMR_ECUDA;
     if (ev_end && cudaEventRecord(static_cast<cudaEvent_t>(ev_end), st) != cudaSuccess) return SEMR_ECUDA;
-    const int lf = warp ? launch_finalize_warp(p, st) : group ? launch_finalize_group(p, st) : launch_finalize(p, mesh->lx, st);
-    if (lf != cudaSuccess) return SEMR_ECUDA;
+    // the warp-level kernels finalize in their last CTA; the CTA kernels have a finalize kernel
+    if (!warp && !group && launch_finalize(p, mesh->lx, st) != cudaSuccess) return SEMR_ECUDA;
     return SEMR_OK;
 }
 

@@ -1091,6 +1091,12 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
     }
     // after an abort: let a requested block land before the CTA exits (the second, bounded wait)
     if (inflight) drain_stage(bar, parity, &(BATCH ? s_par[par ^ 1] : A.p).ctl->status);
+    // a single launch finalizes in the CTA that finishes last (no separate kernel, which could wait
+    // behind another launch's persistent CTAs), one field per warp
+    if constexpr (!BATCH) {
+        if (last_cta_done(&A.p.ctl->done_ctas))
+            for (int f = wid; f < A.p.n_fields; f += GCTA / 32) finalize_field_warp(A.p, f, LX, TILE);
+    }
 }
 
 // Finalize of field f: tree over its tile partials, then the exact maximum of |u| (the
@@ -1143,8 +1149,6 @@ __device__ void finalize_group_field(const LaunchParams& p, int f) {
         finalize_report(p, f, LX, red[0][0], red[1][0], red[2][0], __longlong_as_double(static_cast<long long>(s_umax)));
 }
 
-template <int LX>
-__global__ void __launch_bounds__(256) finalize_group_kernel(const LaunchParams p) { finalize_group_field<LX>(p, blockIdx.x); }
 
 // One block per (item, field) of a batched launch.
 template <int LX>
@@ -1265,13 +1269,5 @@ int launch_finalize_group_batch(const BatchQueue& q, int lx, uint32_t total_fiel
     return (int)cudaGetLastError();
 }
 
-int launch_finalize_group(const LaunchParams& p, void* stream) {
-    switch (p.lx) {
-        case 6: finalize_group_kernel<6><<<p.n_fields, 256, 0, static_cast<cudaStream_t>(stream)>>>(p); break;
-        case 10: finalize_group_kernel<10><<<p.n_fields, 256, 0, static_cast<cudaStream_t>(stream)>>>(p); break;
-        default: return (int)cudaErrorInvalidValue;
-    }
-    return (int)cudaGetLastError();
-}
 
 }  // namespace semr

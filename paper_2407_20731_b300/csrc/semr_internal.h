@@ -88,6 +88,7 @@ struct ScratchControl {
     uint32_t tile_counter;
     uint32_t status;
     uint32_t recomputed;  // coefficients recomputed exactly (FP64 mode)
+    uint32_t done_ctas;   // warp-level kernels: CTAs finished (the last one finalizes)
 };
 
 struct LaunchParams {
@@ -172,11 +173,10 @@ int launch_finalize_batch(const BatchQueue& q, uint32_t total_fields, void* stre
 
 // Warp-per-element kernel (semr_warp.cu): lx = 8 threshold truncation in
 // SEMR_FP64 / SEMR_FP32 with int16 codes.  warp_applicable() says whether it
-// takes a reduction; launch_reduce_warp / launch_finalize_warp run it and its
-// finalize (scratch split by split_scratch_warp, p.tile = kWarpTile).
+// takes a reduction; launch_reduce_warp runs it, its last CTA finalizing (scratch
+// split by split_scratch_warp, p.tile = kWarpTile).
 bool warp_applicable(const LaunchParams& p);
 int launch_reduce_warp(const LaunchParams& p, void* stream);
-int launch_finalize_warp(const LaunchParams& p, void* stream);
 // Batched form: items of one precision, each laid out as split_scratch_warp does
 // except that they share one code staging (stage_ctas CTAs).  warp_encode_maps
 // writes an item's n_fields tensor maps (128 bytes each) to host memory.
@@ -192,7 +192,6 @@ int launch_finalize_warp_batch(const BatchQueue& q, uint32_t total_fields, void*
 int group_tile(int lx);
 bool group_applicable(const LaunchParams& p);
 int launch_reduce_group(const LaunchParams& p, void* stream);
-int launch_finalize_group(const LaunchParams& p, void* stream);
 // Batched form: items of one (lx, precision), laid out as for the warp kernel (no tensor maps).
 int launch_reduce_group_batch(const BatchQueue& q, int lx, int precision, uint64_t stage_ctas, void* stream);
 int launch_finalize_group_batch(const BatchQueue& q, int lx, uint32_t total_fields, void* stream);

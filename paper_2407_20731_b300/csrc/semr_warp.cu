@@ -1167,6 +1167,12 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
     }
     // after an abort: let a requested block land before the CTA exits
     if (inflight && !mbar_wait_bounded(bar, parity)) drain_stage(bar, parity, &(BATCH ? s_par[par ^ 1] : A.p).ctl->status);
+    // a single launch finalizes in the CTA that finishes last (no separate kernel, which could wait
+    // behind another launch's persistent CTAs), one field per warp
+    if constexpr (!BATCH) {
+        if (last_cta_done(&A.p.ctl->done_ctas))
+            for (int f = wid; f < A.p.n_fields; f += WPB) finalize_field_warp(A.p, f, WLX, kWarpTile);
+    }
 }
 
 // Finalize of field f: tree over its tile partials, then the exact maximum of
@@ -1222,7 +1228,6 @@ __device__ void finalize_warp_field(const LaunchParams& p, int f) {
         finalize_report(p, f, WLX, red[0][0], red[1][0], red[2][0], __longlong_as_double(static_cast<long long>(s_umax)));
 }
 
-__global__ void __launch_bounds__(256) finalize_warp_kernel(const LaunchParams p) { finalize_warp_field(p, blockIdx.x); }
 
 // One block per (item, field) of a batched launch.
 __global__ void __launch_bounds__(256) finalize_warp_batch_kernel(const BatchQueue q) {
@@ -1387,10 +1392,6 @@ int launch_finalize_warp_batch(const BatchQueue& q, uint32_t total_fields, void*
     return (int)cudaGetLastError();
 }
 
-int launch_finalize_warp(const LaunchParams& p, void* stream) {
-    finalize_warp_kernel<<<p.n_fields, 256, 0, static_cast<cudaStream_t>(stream)>>>(p);
-    return (int)cudaGetLastError();
-}
 
 }  // namespace semr
 

@@ -160,6 +160,76 @@ __device__ __forceinline__ uint64_t lookback_peek(const uint64_t* tile_state, ui
     return excl;
 }
 
+// Finalize of field f by one warp of the CTA that finishes a single launch last (the CTA's
+// warps take fields w, w + warps, ...): the sums and maxima over the field's tile partials in a
+// fixed order (lane-strided sums, then a butterfly), then the exact maximum of |u| -- the kernel
+// records each element's largest high word of |u|, which orders the elements like their
+// maxima, so only the blocks whose high word is the field's are reread, each by the whole warp
+// -- then the field report and (field 0) the header and summary.  A field whose every high
+// word is 0 (zeros and subnormals) reports 0.  Every load is independent of the others, so the
+// warp keeps many in flight.
+__device__ inline void finalize_field_warp(const LaunchParams& p, int f, int lx, int tile) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t nper = static_cast<uint64_t>(p.tiles_per_field);
+    const uint64_t n3 = static_cast<uint64_t>(lx) * lx * lx;
+    const double* tp = p.tile_part + 4 * (static_cast<uint64_t>(f) * nper);
+    double s0 = 0.0, s1 = 0.0, m2 = 0.0, m3 = 0.0;
+#pragma unroll 4
+    for (uint64_t u = lane; u < nper; u += 32) {
+        const double2 a = *reinterpret_cast<const double2*>(tp + 4 * u);
+        const double2 b = *reinterpret_cast<const double2*>(tp + 4 * u + 2);
+        s0 += a.x;
+        s1 += a.y;
+        m2 = fmax(m2, b.x);
+        m3 = fmax(m3, b.y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(FULL, s0, o);
+        s1 += __shfl_xor_sync(FULL, s1, o);
+        m2 = fmax(m2, __shfl_xor_sync(FULL, m2, o));
+        m3 = fmax(m3, __shfl_xor_sync(FULL, m3, o));
+    }
+    const double M = m3;  // the field's largest high word, as a number
+    const uint64_t E = static_cast<uint64_t>(p.n_elem);
+    const uint32_t* um = p.hmax_elem + static_cast<uint64_t>(f) * E;
+    const double* src = p.fields[f];
+    unsigned long long umax = 0ull;
+    for (uint64_t u0 = 0; M > 0.0 && u0 < nper; u0 += 32) {
+        const uint64_t u = u0 + lane;
+        for (unsigned tb = __ballot_sync(FULL, u < nper && tp[4 * u + 3] == M); tb; tb &= tb - 1) {
+            const uint64_t t = u0 + (__ffs(tb) - 1);  // a tile that holds the maximum
+            const uint64_t ee = min(E, (t + 1) * static_cast<uint64_t>(tile));
+            for (uint64_t e0 = t * tile; e0 < ee; e0 += 32) {
+                const uint64_t e = e0 + lane;
+                for (unsigned eb = __ballot_sync(FULL, e < ee && static_cast<double>(um[e]) == M); eb; eb &= eb - 1) {
+                    const double* blk = src + (e0 + (__ffs(eb) - 1)) * n3;  // reread by the warp
+                    for (uint64_t i = lane; i < n3; i += 32)
+                        umax = max(umax, static_cast<unsigned long long>(__double_as_longlong(blk[i])) &
+                                             0x7fffffffffffffffull);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) umax = max(umax, __shfl_xor_sync(FULL, umax, o));
+    if (lane == 0) finalize_report(p, f, lx, s0, s1, m2, __longlong_as_double(static_cast<long long>(umax)));
+}
+
+// Whether this CTA is the last of the launch to finish (every thread gets the answer; call with
+// every thread after the CTA's last global write).  The counter lives in the control block.
+__device__ __forceinline__ bool last_cta_done(unsigned* done_ctas) {
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();  // this CTA's partials, states, codes and status before the count
+        s_last = atomicAdd(done_ctas, 1u) == gridDim.x - 1;
+        if (s_last) __threadfence();  // and the others' before the finalize reads them
+    }
+    __syncthreads();
+    return s_last != 0;
+}
+
 // Packed pair sum a + b of both pencils.
 __device__ __forceinline__ p2 df_add2(p2 a, p2 b) {
     const p2 s = two_sum2(a.h, b.h);
