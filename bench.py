@@ -41,7 +41,8 @@ METRIC = "snapshot GB/s reduced (FP64 input ingested per second)"
 # sources of the kernel a profile summary covers: the warp kernel (threshold truncation at lx = 8)
 # and the CTA kernel (the cumulative variant)
 _CSRC = "paper_2407_20731_b300/csrc/"
-KERNEL_SOURCES = [_CSRC + "semr_warp.cu", _CSRC + "semr_device.cuh", _CSRC + "semr_internal.h"]
+KERNEL_SOURCES = [_CSRC + "semr_warp.cu", _CSRC + "semr_warp_common.cuh", _CSRC + "semr_device.cuh",
+                  _CSRC + "semr_internal.h"]
 CUMULATIVE_SOURCES = [_CSRC + "semr_fast.cu", _CSRC + "semr_device.cuh", _CSRC + "semr_internal.h"]
 # FP64 pipe of B300, nominal (the FP32 pipes run ~50x faster; FP64 mode runs on them)
 FP64_PIPE_TFLOPS_NOMINAL = 1.25
@@ -60,6 +61,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--n-side", type=int, default=64, help="elements per side (profiling a smaller case)")
+    ap.add_argument("--lx", type=int, default=8, help="GLL points per direction (profiling another order)")
     ap.add_argument("--serving-requests", type=int, default=10000, help="requests per serving run in the extras")
     ap.add_argument("--serving-only", action="store_true", help="print only the serving report (JSON)")
     ap.add_argument("--batched-only", action="store_true", help="print only the batched report (JSON)")
@@ -326,12 +328,14 @@ def run_semr(args):
     algo = algorithmic_bytes(E, N_FIELDS, sm.code_total, int(bufs.sizes.code_width))
     peaks = measured_peaks()
     achieved = algo / (kernel_ms * 1e-3) / 1e9
-    traffic = profiled_traffic(args.precision, args.cumulative)
+    # the committed DRAM counts cover the benchmark's own workload only
+    traffic = profiled_traffic(args.precision, args.cumulative) if (LX, N_SIDE) == (8, 64) else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "peak_source": f"{peaks['source']} (MEASURED_PEAKS hbm_gbs, copy)",
-                "kernel": (f"reduce_fast_kernel<{LX}, " if args.cumulative else f"reduce_warp_kernel<{LX}, ")
-                          + ('float pairs (FP64 accuracy)' if prec == semr.SEMR_FP64 else 'FP32')
+                "kernel": (f"reduce_fast_kernel<{LX}, " if args.cumulative
+                           else "reduce_warp_kernel<" if LX == 8 else f"reduce_group_kernel<{LX}, ")
+                          + ('FP64 mode' if prec == semr.SEMR_FP64 else 'FP32')
                           + (", cumulative" if args.cumulative else "") + ">",
                 "kernel_ms": round(kernel_ms, 4), "algorithmic_bytes_per_launch": algo}
     flops = algorithmic_flops(E, N_FIELDS)
@@ -840,9 +844,10 @@ def run_reference(args):
 
 
 def main():
-    global N_SIDE
+    global N_SIDE, LX
     args = parse_args()
     N_SIDE = args.n_side
+    LX = args.lx
     if args.batched_only:
         import torch
         torch.cuda.set_device(0)
