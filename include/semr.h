@@ -123,6 +123,10 @@ extern "C" {
                                      (every |u| < 2^-1022).  It keeps nothing, as an FP64 evaluation
                                      does (its t = tau S_e underflows), and its e2_e, E_e and Linf_e
                                      are reported as 0 where FP64 gives values below 2^-1022 */
+#define SEMR_STATUS_BOUNDS 32     /* only in a library built with -DSEMR_BOUNDS (a checking build, see
+                                     semr_build_flags): a kernel computed an index or a byte range outside
+                                     the buffer it was about to read or write; that access was skipped
+                                     (results invalid) */
 
 typedef struct {
     int32_t lx;            /* GLL points per direction, SEMR_LX_MIN..SEMR_LX_MAX */
@@ -510,6 +514,21 @@ int semr_slice_rgba(const semr_lattice* mesh, const double* const* fields, const
 
 /* semr_strerror: static text for a status code. */
 const char* semr_strerror(int code);
+
+/* semr_build_flags: how this copy of the library was built.  SEMR_BUILD_BOUNDS:
+ * compiled with -DSEMR_BOUNDS, a checking build in which every kernel tests
+ * the index or byte range of each global access (payload, element report,
+ * reconstruction, scratch, slice image, staged codes) against its buffer
+ * before making it; an access outside is skipped and sets SEMR_STATUS_BOUNDS.
+ * The checks never trap.  Slower than the default build; for testing. */
+#define SEMR_BUILD_BOUNDS 1
+int semr_build_flags(void);
+
+/* semr_bounds_status: SEMR_STATUS_BOUNDS if, since the last reset, a kernel
+ * without a status word of its own (the slice kernels) skipped an access in
+ * a bounds build; 0 otherwise, and always 0 in the default build.  reset != 0
+ * clears it.  Synchronous (waits for the device); 0xffffffff on a CUDA error. */
+uint32_t semr_bounds_status(int reset);
 
 #ifdef __cplusplus
 }

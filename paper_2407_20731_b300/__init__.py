@@ -21,7 +21,10 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsemr.so")
+# SEMR_BOUNDS=1 in the environment loads the checking build libsemr_bounds.so
+# (compiled with -DSEMR_BOUNDS; the same ABI)
+BOUNDS_BUILD = os.environ.get("SEMR_BOUNDS", "") == "1"
+LIB_PATH = os.path.join(_HERE, "libsemr_bounds.so" if BOUNDS_BUILD else "libsemr.so")
 
 # status codes (include/semr.h)
 SEMR_OK, SEMR_EINVAL, SEMR_ENOMEM, SEMR_EBUDGET, SEMR_EAGAIN = 0, 1, 2, 3, 4
@@ -31,7 +34,8 @@ SEMR_FP64, SEMR_FP32, SEMR_FP64_NATIVE = 0, 1, 2
 SEMR_WRITE_RECON, SEMR_CUMULATIVE = 1, 2
 SEMR_PAYLOAD_LOSSLESS, SEMR_PAYLOAD_CODE32, SEMR_PAYLOAD_FP32, SEMR_PAYLOAD_CUMULATIVE = 1, 2, 4, 8
 SEMR_STATUS_OVERFLOW, SEMR_STATUS_TIMEOUT, SEMR_STATUS_NONFINITE, SEMR_STATUS_TINY = 1, 2, 4, 8
-SEMR_STATUS_STAGE = 16
+SEMR_STATUS_STAGE, SEMR_STATUS_BOUNDS = 16, 32
+SEMR_BUILD_BOUNDS = 1
 
 
 class semr_mesh(ctypes.Structure):
@@ -142,11 +146,13 @@ EXPORTS = [
     ("semr_slice_rgba", ctypes.c_int, [ctypes.POINTER(semr_lattice), ctypes.POINTER(_P), ctypes.POINTER(semr_slice),
                                        _P, _P, _P]),
     ("semr_selftest_waits", ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32)]),
+    ("semr_build_flags", ctypes.c_int, []),
+    ("semr_bounds_status", ctypes.c_uint32, [ctypes.c_int]),
 ]
 SEMR_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"libsemr.so is not built ({LIB_PATH}); run __graft_entry__.build() "
+    raise ImportError(f"{os.path.basename(LIB_PATH)} is not built ({LIB_PATH}); run __graft_entry__.build() "
                       "or python paper_2407_20731_b300/build.py")
 _lib = ctypes.CDLL(LIB_PATH)
 for _name, _res, _args in EXPORTS:
@@ -171,6 +177,14 @@ def _check(code: int, where: str) -> int:
 
 def semr_strerror(code: int) -> str:
     return _lib.semr_strerror(code).decode()
+
+
+def semr_build_flags() -> int:
+    return _lib.semr_build_flags()
+
+
+def semr_bounds_status(reset: bool = False) -> int:
+    return _lib.semr_bounds_status(1 if reset else 0)
 
 
 def semr_sizes_for(lx: int, n_elem: int, n_fields: int, tau: float) -> semr_sizes:

@@ -1,4 +1,7 @@
-"""Build libsemr.so in-tree with nvcc for sm_103a (B300)."""
+"""Build libsemr.so in-tree with nvcc for sm_103a (B300), and its checking
+variant libsemr_bounds.so (-DSEMR_BOUNDS: every kernel tests the index or byte
+range of each global access against its buffer and skips, flagging
+SEMR_STATUS_BOUNDS, any that falls outside)."""
 from __future__ import annotations
 
 import os
@@ -8,6 +11,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libsemr.so")
+LIB_BOUNDS = os.path.join(HERE, "libsemr_bounds.so")
 SOURCES = [os.path.join(HERE, "csrc", s) for s in ("semr_kernels.cu", "semr_fast.cu", "semr_api.cpp", "semr_tables.cpp", "semr_noalloc.cu", "semr_batch.cpp", "semr_server.cpp", "semr_slice.cu", "semr_warp.cu", "semr_group.cu")]
 HEADERS = [os.path.join(HERE, "csrc", h) for h in ("semr_internal.h", "semr_device.cuh", "semr_warp_common.cuh")] + [os.path.join(ROOT, "include", "semr.h")]
 
@@ -22,20 +26,46 @@ def nvcc() -> str:
     return "nvcc"
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+def stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(s) > t for s in SOURCES + HEADERS)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if force or stale():
-        cmd = [nvcc()] + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + SOURCES + ["-o", LIB]
-        subprocess.run(cmd, check=True)
-    return LIB
+def build(force: bool = False, verbose: bool = False, bounds: bool = False) -> str:
+    """Compile each source to an object under _build/ (in parallel), then link."""
+    lib = LIB_BOUNDS if bounds else LIB
+    if not (force or stale(lib)):
+        return lib
+    from concurrent.futures import ThreadPoolExecutor
+    odir = os.path.join(ROOT, "_build", "bounds" if bounds else "default")
+    os.makedirs(odir, exist_ok=True)
+    cflags = [f for f in NVCC_FLAGS if f not in ("-shared", "-cudart", "static")]
+    extra = (["-DSEMR_BOUNDS"] if bounds else []) + (["-Xptxas", "-v"] if verbose else [])
+
+    def obj(src: str) -> str:
+        o = os.path.join(odir, os.path.basename(src) + ".o")
+        subprocess.run([nvcc()] + cflags + extra + ["-c", src, "-o", o], check=True)
+        return o
+
+    with ThreadPoolExecutor(min(len(SOURCES), os.cpu_count() or 1)) as ex:
+        objs = list(ex.map(obj, SOURCES))
+    subprocess.run([nvcc(), "-shared", "-cudart", "static", "-gencode", "arch=compute_103a,code=sm_103a",
+                    "-Xcompiler", "-fPIC"] + objs + ["-o", lib], check=True)
+    return lib
+
+
+def build_all(force: bool = False) -> None:
+    """Both variants, compiled side by side."""
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(2) as ex:
+        for r in [ex.submit(build, force, False, b) for b in (False, True)]:
+            r.result()
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
-    print(LIB)
+    if "--bounds" in sys.argv:
+        print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, bounds=True))
+    else:
+        print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

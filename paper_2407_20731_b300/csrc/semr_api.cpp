@@ -562,3 +562,11 @@ extern "C" const char* semr_strerror(int code) {
         default: return "unknown status";
     }
 }
+
+extern "C" int semr_build_flags(void) {
+#ifdef SEMR_BOUNDS
+    return SEMR_BUILD_BOUNDS;
+#else
+    return 0;
+#endif
+}

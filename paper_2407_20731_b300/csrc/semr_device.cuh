@@ -14,6 +14,25 @@
 
 namespace semr {
 
+// ------------------------------------------------------ bounds build
+//
+// Built with -DSEMR_BOUNDS, every kernel passes the index or byte-range test
+// of each global access it makes to bchk() first: a test that fails sets
+// SEMR_STATUS_BOUNDS and the caller skips the access (nothing traps).  In
+// the default build bchk() is the constant true and the tests compile away.
+#ifdef SEMR_BOUNDS
+constexpr bool kBoundsBuild = true;
+#else
+constexpr bool kBoundsBuild = false;
+#endif
+__device__ __forceinline__ bool bchk(bool inside, unsigned* status) {
+    if constexpr (kBoundsBuild) {
+        if (!inside) atomicOr(status, static_cast<unsigned>(SEMR_STATUS_BOUNDS));
+        return inside;
+    }
+    return true;
+}
+
 // ------------------------------------------------------ memory ordering
 
 __device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
@@ -451,6 +470,16 @@ __device__ inline void finalize_tree(const double* part, int f, uint64_t nper, d
 // also writes the rest of the header and the summary.  One thread.
 __device__ inline void finalize_report(const LaunchParams& p, int f, int lx, double se2, double sen, double linf,
                                        double umax) {
+    // bounds build: the header, summary and state ranges follow from p alone, so field 0 (which
+    // writes the summary's status) tests them for every field
+    unsigned* status = &p.ctl->status;
+    if (!bchk(f >= 0 && f < p.n_fields && p.n_fields <= SEMR_MAX_FIELDS && p.tiles_per_field >= 1 &&
+                  kHeaderFixed + 8ull * p.n_fields <= p.header_bytes && p.header_bytes <= p.code_base &&
+                  p.code_base <= p.payload_cap,
+              status)) {
+        if (f == 0) p.summary->status = *reinterpret_cast<volatile unsigned*>(status);
+        return;
+    }
     const uint64_t* tile_state = p.tile_state;
     const uint64_t n_tiles = (uint64_t)p.n_fields * p.tiles_per_field;
     const uint64_t t0 = (uint64_t)f * p.tiles_per_field;

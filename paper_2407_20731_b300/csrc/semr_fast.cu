@@ -351,6 +351,13 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
     const int n_here = (p.n_elem - e0 < TILE) ? (int)(p.n_elem - e0) : TILE;
     const bool active = (tid < C::NT) && (lt < n_here);
     const int64_t e = e0 + lt;
+    // bounds build: the tile, its elements and its field's section of the payload (every write
+    // of the tile below is skipped if they fall outside their buffers)
+    const bool tok = bchk(tile < (uint64_t)p.n_fields * p.tiles_per_field && f < p.n_fields && n_here >= 1 &&
+                              pad16((uint64_t)p.n_elem * ((N3 + 7) / 8)) + 2 * pad16(2ull * p.n_elem) <= p.fixed_bytes &&
+                              p.header_bytes + (f + 1ull) * p.fixed_bytes <= p.code_base &&
+                              p.code_base <= p.payload_cap,
+                          &p.ctl->status);
 
     // ---- load the pencil u[k=pa][j=pb][0..LX-1], split to floats with integer ops.  The
     // element is read as u 2^-ke, ke the binary exponent of its largest |u| (an exact
@@ -813,7 +820,7 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
         }
         s_epre[TILE] = acc;
         s_flag[0] = big;
-        st_release_u64(&tile_state[tile], (tile == 0 ? kFlagPrefix : kFlagAggregate) | ((uint64_t)acc & kValueMask));
+        if (tok) st_release_u64(&tile_state[tile], (tile == 0 ? kFlagPrefix : kFlagAggregate) | ((uint64_t)acc & kValueMask));
     }
     __syncthreads();
     const bool dense = s_flag[0] != 0;
@@ -1025,7 +1032,7 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
             }
             linf_bits = dm;
         }
-        if (p.write_recon && p.recon[f]) {  // u~ = u~' 2^ke (exact)
+        if (p.write_recon && p.recon[f] && tok) {  // u~ = u~' 2^ke (exact)
             double* dst = p.recon[f] + e * N3 + P * LX;
             const double sc = pow2d(prescale_exponent(s_hx[lt]));
 #pragma unroll
@@ -1039,7 +1046,7 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
         const uint64_t ex = lookback_warp(tile_state, tile, (uint64_t)s_epre[TILE], &ctl->status);
         if (tid == 0) s_tile[1] = ex;
     }
-    if (tid == 32 % C::BLOCK) {  // another warp, when there is one
+    if (tid == 32 % C::BLOCK && tok) {  // another warp, when there is one
         double s0 = 0.0, s1 = 0.0, m2 = 0.0, m3 = 0.0;
         for (int l = 0; l < n_here; ++l) {  // back from the prescaled block: 2^2ke, 2^ke
             const double J = p.jac[e0 + l];
@@ -1063,7 +1070,9 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
         const uint64_t ncodes = (uint64_t)s_epre[TILE];
         const uint64_t gbyte = p.code_base + (uint64_t)width * tile_excl;
         const uint64_t nbytes = (uint64_t)width * ncodes;
-        if (gbyte + nbytes <= p.payload_cap) {
+        if (!tok) {
+            // (bounds build) nothing of this tile is written
+        } else if (gbyte + nbytes <= p.payload_cap) {
             uint8_t* dst = p.payload + gbyte;
             if (width == 8) {
                 if constexpr (S::code_b == 8) {
@@ -1081,7 +1090,7 @@ reduce_fast_kernel(const LaunchParams p0, const BatchQueue q, const FastTables<L
             atomicOr(&ctl->status, (unsigned)SEMR_STATUS_OVERFLOW);
         }
     }
-    {
+    if (tok) {
         constexpr int mb = (N3 + 7) / 8;
         uint8_t* fsec = p.payload + p.header_bytes + (uint64_t)f * p.fixed_bytes;
         if constexpr ((mb % 4) == 0) {  // whole words: element masks are word-aligned

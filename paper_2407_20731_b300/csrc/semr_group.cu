@@ -308,6 +308,9 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
     unsigned* counter = BATCH ? q.counter : &A.p.ctl->tile_counter;
     uint8_t* stage_cta = reinterpret_cast<uint8_t*>(BATCH ? q.items[0].code_stage : A.p.code_stage) +
                          static_cast<uint64_t>(blockIdx.x) * kWarpStageBytes;
+    if (!bchk(static_cast<int>(blockIdx.x) < (BATCH ? q.items[0].stage_ctas : A.p.stage_ctas),
+              BATCH ? &q.items[0].ctl->status : &A.p.ctl->status))
+        return;  // (before any barrier or copy) a grid larger than the code staging
     int16_t* stage_codes = reinterpret_cast<int16_t*>(stage_cta);
     uint32_t* stage_pre = reinterpret_cast<uint32_t*>(stage_cta + 2ull * kWarpCtaWarps * kWarpArena * 2);
     uint32_t* stage_off = stage_pre + 2 * (kWarpTile + 1);
@@ -351,8 +354,10 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
         e0 = (tt - f * tpf_) * TILE;
         nh = static_cast<int>(min(static_cast<uint32_t>(TILE), E_ - e0));
     };
-    auto issue = [&](const double* field, uint32_t e) {  // thread g == 0: element block e into the stage
-        bulk_load(stage, field + static_cast<uint64_t>(e) * N3, 8u * N3, bar);
+    // thread g == 0: element block e of field fi of reduction pi into the stage
+    auto issue = [&](const LaunchParams& pi, uint32_t fi, uint32_t e) {
+        if (bchk(fi < static_cast<uint32_t>(pi.n_fields) && e < static_cast<uint64_t>(pi.n_elem), &pi.ctl->status))
+            bulk_load(stage, pi.fields[fi] + static_cast<uint64_t>(e) * N3, 8u * N3, bar);
     };
     uint32_t parity = 0;
     uint32_t tag = 0;
@@ -382,6 +387,7 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
             atomicOr(status, static_cast<unsigned>(SEMR_STATUS_OVERFLOW));
             copy = false;
         }
+        copy = copy && bchk(off + n <= static_cast<uint32_t>(ARENA) && gbyte >= pd.code_base, status);
         if (copy && n <= 32u) {
             int16_t* dst = reinterpret_cast<int16_t*>(pd.payload + gbyte);
             const int16_t* src = arena + off;
@@ -401,7 +407,7 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
         int nh;
         geom(s_tloc[0], static_cast<uint32_t>(pn->tiles_per_field), static_cast<uint32_t>(pn->n_elem), f, e0, nh);
         if (gi < nh) {
-            if (g == 0) issue(pn->fields[f], e0 + gi);
+            if (g == 0) issue(*pn, f, e0 + gi);
             inflight = true;
         }
     }
@@ -437,8 +443,14 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
     const uint64_t mbytes = pad16(static_cast<uint64_t>(E) * MB);
     int16_t* sdst = reinterpret_cast<int16_t*>(fsec + mbytes);
     uint16_t* cdst = reinterpret_cast<uint16_t*>(fsec + mbytes + pad16(2ull * E));
+    // bounds build: the field section's layout within the payload (each element also tests e < E)
+    const bool fok = bchk(f < static_cast<uint32_t>(p.n_fields) && mbytes + 2 * pad16(2ull * E) <= p.fixed_bytes &&
+                              p.header_bytes + (f + 1ull) * p.fixed_bytes <= p.code_base &&
+                              p.code_base <= p.payload_cap,
+                          status);
     for (int il = gi; il < nh; il += GPC) {
         const uint32_t e = e0 + static_cast<uint32_t>(il);
+        const bool eok = fok && bchk(e < E, status);
         bool landed = mbar_wait_bounded(bar, parity);  // uniform over the warp
 
         // ---- the element's largest high word of |u| (first pass over the stage's high words; if the
@@ -526,7 +538,7 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
             if (il + GPC < nh) {
                 if (g == 0) {
                     fence_proxy_async();
-                    issue(p.fields[f], e + GPC);
+                    issue(p, f, e + GPC);
                 }
                 inflight = true;
             }
@@ -690,16 +702,18 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
         {
             const uint8_t* bmb = reinterpret_cast<const uint8_t*>(bm);
             uint8_t* mdst = fsec + static_cast<uint64_t>(e) * MB;
-            for (int b = g; b < MB; b += GT) mdst[b] = bmb[b];
+            for (int b = g; eok && b < MB; b += GT) mdst[b] = bmb[b];
         }
         const bool staged = atop + n_e <= static_cast<uint32_t>(ARENA);
         if (g == 0) {
-            sdst[e] = static_cast<int16_t>(step);
-            cdst[e] = static_cast<uint16_t>(n_e);
+            if (eok) {
+                sdst[e] = static_cast<int16_t>(step);
+                cdst[e] = static_cast<uint16_t>(n_e);
+            }
             s_cnt[il] = (tag << 16) | n_e;
             stage_off[par * kWarpTile + il] = staged ? atop : kDirect;
         }
-        if (e + 1 == E && g < 16) {  // zero the padding after the mask, step and count sections
+        if (e + 1 == E && g < 16 && eok) {  // zero the padding after the mask, step and count sections
             const uint64_t me = static_cast<uint64_t>(E) * MB;
             if (me + g < pad16(me)) fsec[me + g] = 0;
             const uint64_t se = 2ull * E;
@@ -741,6 +755,7 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
             const uint64_t gbyte = p.code_base + 2ull * before;
             qwrite = gbyte + 2ull * n_e <= p.payload_cap;
             if (!qwrite && g == 0) atomicOr(status, static_cast<unsigned>(SEMR_STATUS_OVERFLOW));
+            qwrite = qwrite && bchk(gbyte >= p.code_base, status);
             qdst = reinterpret_cast<int16_t*>(p.payload + gbyte);
         }
         {
@@ -945,7 +960,7 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
             lh = fmaxf(h0, h1);
             ll = (h0 > h1) ? l0 : (h1 > h0) ? l1 : fmaxf(l0, l1);
         }
-        if (p.write_recon && p.recon[f]) {  // u~ = u~' 2^ke (exact)
+        if (p.write_recon && p.recon[f] && eok) {  // u~ = u~' 2^ke (exact)
             const double sc = pow2d(ke);
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
@@ -982,7 +997,7 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
         if (gi < nhn) {
             if (g == 0) {
                 fence_proxy_async();
-                issue(pn->fields[fn], e0n + gi);
+                issue(*pn, fn, e0n + gi);
             }
             inflight = true;
         }
@@ -1010,7 +1025,7 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
             run += cl[h];
         }
         const uint32_t tot = __shfl_sync(FULL, incl, 31);
-        if (lane == 0) {
+        if (lane == 0 && bchk(tcur < static_cast<uint32_t>(p.n_fields) * tpf && nh <= kWarpTile, status)) {
             pre[nh] = tot;
             st_release_u64(&p.tile_state[tcur], (tcur == 0 ? kFlagPrefix : kFlagAggregate) | tot);
         }
@@ -1040,8 +1055,9 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
             const double x2 = (static_cast<double>(st.lh) + static_cast<double>(st.ll)) * sc;
             m2 = static_cast<unsigned long long>(__double_as_longlong(x2));
             m3 = st.hmax;
-            p.hmax_elem[ge] = st.hmax;
-            if (p.elem_report) {
+            const bool gok = bchk(ge < static_cast<uint64_t>(p.n_fields) * E, status);
+            if (gok) p.hmax_elem[ge] = st.hmax;
+            if (p.elem_report && gok) {
                 double* er = p.elem_report + 3 * ge;
                 er[0] = v0;
                 er[1] = v1d;
@@ -1063,7 +1079,7 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && bchk(tcur < static_cast<uint32_t>(p.n_fields) * tpf, status)) {
         double* tp = p.tile_part + 4ull * tcur;
         tp[0] = ((s_wpart[0][0] + s_wpart[1][0]) + s_wpart[2][0]) + s_wpart[3][0];
         tp[1] = ((s_wpart[0][1] + s_wpart[1][1]) + s_wpart[2][1]) + s_wpart[3][1];

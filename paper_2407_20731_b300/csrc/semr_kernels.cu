@@ -143,6 +143,13 @@ reduce_kernel(const LaunchParams p, const Tables<LX, T> tab) {
     const int f = (int)(tile / p.tiles_per_field);
     const int64_t e0 = (int64_t)(tile % p.tiles_per_field) * TILE;
     const int n_here = (p.n_elem - e0 < TILE) ? (int)(p.n_elem - e0) : TILE;
+    // bounds build: the tile's elements and its field's section of the payload (every write of
+    // the tile below is skipped if they fall outside their buffers)
+    const bool tok = bchk(f < p.n_fields && n_here >= 1 &&
+                              pad16((uint64_t)p.n_elem * ((N3 + 7) / 8)) + 2 * pad16(2ull * p.n_elem) <= p.fixed_bytes &&
+                              p.header_bytes + (f + 1ull) * p.fixed_bytes <= p.code_base &&
+                              p.code_base <= p.payload_cap,
+                          &p.ctl->status);
 
     const int lt = tid / NP;    // element within the tile
     const int P = tid % NP;     // pencil index
@@ -282,7 +289,7 @@ reduce_kernel(const LaunchParams p, const Tables<LX, T> tab) {
         s_epre[TILE] = acc;
         // publish the tile aggregate for the look-back
         const uint64_t v = (uint64_t)acc & kValueMask;
-        st_release_u64(&tile_state[tile], (tile == 0 ? kFlagPrefix : kFlagAggregate) | v);
+        if (tok) st_release_u64(&tile_state[tile], (tile == 0 ? kFlagPrefix : kFlagAggregate) | v);
     }
     __syncthreads();
 
@@ -359,7 +366,7 @@ reduce_kernel(const LaunchParams p, const Tables<LX, T> tab) {
             linf = fmax(linf, fabs(d));
             umax = fmax(umax, fabs(u[i]));
         }
-        if (p.write_recon && p.recon[f]) {
+        if (p.write_recon && p.recon[f] && tok) {
             double* dst = p.recon[f] + e * N3 + P * LX;
 #pragma unroll
             for (int i = 0; i < LX; ++i) dst[i] = (double)y[i];
@@ -391,7 +398,7 @@ reduce_kernel(const LaunchParams p, const Tables<LX, T> tab) {
                     __nanosleep(64);
                 }
             }
-            st_release_u64(&tile_state[tile], kFlagPrefix | ((excl + agg) & kValueMask));
+            if (tok) st_release_u64(&tile_state[tile], kFlagPrefix | ((excl + agg) & kValueMask));
         }
         s_tile[1] = excl;
         // per-tile partials for the field reductions
@@ -403,11 +410,13 @@ reduce_kernel(const LaunchParams p, const Tables<LX, T> tab) {
             m2 = fmax(m2, selem[l * 8 + 2]);
             m3 = fmax(m3, selem[l * 8 + 3]);
         }
-        double* tp = tile_part + 4 * tile;
-        tp[0] = s0;
-        tp[1] = s1;
-        tp[2] = m2;
-        tp[3] = m3;
+        if (tok) {
+            double* tp = tile_part + 4 * tile;
+            tp[0] = s0;
+            tp[1] = s1;
+            tp[2] = m2;
+            tp[3] = m3;
+        }
     }
     __syncthreads();
     const uint64_t tile_excl = s_tile[1];
@@ -417,7 +426,9 @@ reduce_kernel(const LaunchParams p, const Tables<LX, T> tab) {
         const uint64_t ncodes = (uint64_t)s_epre[TILE];
         const uint64_t gbyte = p.code_base + (uint64_t)width * tile_excl;
         const uint64_t nbytes = (uint64_t)width * ncodes;
-        if (gbyte + nbytes <= p.payload_cap) {
+        if (!tok) {
+            // (bounds build) nothing of this tile is written
+        } else if (gbyte + nbytes <= p.payload_cap) {
             uint8_t* dst = p.payload + gbyte;
             if (width == 8) {  // 8-byte aligned: code_base is 16-aligned
                 const double* sc = reinterpret_cast<const double*>(scodes);
@@ -433,7 +444,7 @@ reduce_kernel(const LaunchParams p, const Tables<LX, T> tab) {
             atomicOr(&ctl->status, (unsigned)SEMR_STATUS_OVERFLOW);
         }
     }
-    {
+    if (tok) {
         constexpr int mb = (N3 + 7) / 8;
         uint8_t* fsec = p.payload + p.header_bytes + (uint64_t)f * p.fixed_bytes;
         uint8_t* mdst = fsec + (uint64_t)e0 * mb;

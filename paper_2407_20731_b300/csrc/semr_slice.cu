@@ -129,8 +129,20 @@ __device__ __forceinline__ void basis(const SliceArgs& a, float x, float* L, int
     }
 }
 
+// Bounds build: the slice kernels have no status word of their own, so a skipped access is
+// recorded here (read and reset by semr_bounds_status).
+__device__ unsigned g_slice_bounds;
+
+__device__ __forceinline__ bool pixel_ok(const SliceArgs& a, int c, int r) {
+    return bchk(c >= 0 && c < a.W && r >= 0 && r < a.H, &g_slice_bounds);
+}
+__device__ __forceinline__ bool element_ok(const SliceArgs& a, int64_t e) {
+    return bchk(e >= 0 && e < (int64_t)a.n[0] * a.n[1] * a.n[2], &g_slice_bounds);
+}
+
 // Step 4 and the stores.  s: the coloured scalar (finite inside the mesh).
 __device__ __forceinline__ void put_pixel(const SliceArgs& a, int c, int r, float s) {
+    if (!pixel_ok(a, c, r)) return;
     float t = (s - a.vmin) * a.inv_range;
     t = fminf(fmaxf(t, 0.0f), 1.0f);
     int k = 0;
@@ -149,6 +161,7 @@ __device__ __forceinline__ void put_pixel(const SliceArgs& a, int c, int r, floa
 }
 
 __device__ __forceinline__ void put_background(const SliceArgs& a, int c, int r) {
+    if (!pixel_ok(a, c, r)) return;
     const size_t px = (size_t)r * a.W + c;
     reinterpret_cast<uint32_t*>(a.rgba)[px] = a.bg;
     if (a.values) a.values[px] = __int_as_float(0x7fc00000);  // NaN
@@ -213,6 +226,7 @@ __global__ void __launch_bounds__(kAxisThreads) slice_axis_kernel(const SliceArg
     // ---- load the element (all components) and contract along the normal
     auto coord = [&](int ax) { return ax == a.ax_a ? ea : (ax == a.ax_b ? eb : a.layer); };
     const int64_t e = coord(0) + (int64_t)a.n[0] * (coord(1) + (int64_t)a.n[1] * coord(2));
+    if (!element_ok(a, e)) return;  // uniform over the CTA
     for (int comp = 0; comp < a.nc; ++comp) {
         const double* src = a.f[comp] + e * N3;
 #pragma unroll 4
@@ -319,6 +333,7 @@ __global__ void __launch_bounds__(256) slice_generic_kernel(const SliceArgs a) {
         return;
     }
     const int64_t e = ei[0] + (int64_t)a.n[0] * (ei[1] + (int64_t)a.n[1] * ei[2]);
+    if (!element_ok(a, e)) return;
     float Lx[LX], Ly[LX], Lz[LX];
     basis<LX>(a, (float)xi[0], Lx);
     basis<LX>(a, (float)xi[1], Ly);
@@ -537,4 +552,14 @@ extern "C" int semr_slice_rgba(const semr_lattice* mesh, const double* const* fi
         case 12: return launch_slice<12>(a, axis, fill, st);
         default: return SEMR_EUNSUPPORTED;
     }
+}
+
+extern "C" uint32_t semr_bounds_status(int reset) {
+    unsigned v = 0;
+    if (cudaMemcpyFromSymbol(&v, semr::g_slice_bounds, sizeof(v)) != cudaSuccess) return 0xffffffffu;
+    if (reset) {
+        const unsigned z = 0;
+        if (cudaMemcpyToSymbol(semr::g_slice_bounds, &z, sizeof(z)) != cudaSuccess) return 0xffffffffu;
+    }
+    return v;
 }

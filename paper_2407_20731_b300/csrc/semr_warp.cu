@@ -398,6 +398,9 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
     // launch's items share it
     uint8_t* stage_cta = reinterpret_cast<uint8_t*>(BATCH ? q.items[0].code_stage : A.p.code_stage) +
                          static_cast<uint64_t>(blockIdx.x) * kWarpStageBytes;
+    if (!bchk(static_cast<int>(blockIdx.x) < (BATCH ? q.items[0].stage_ctas : A.p.stage_ctas),
+              BATCH ? &q.items[0].ctl->status : &A.p.ctl->status))
+        return;  // (before any barrier or copy) a grid larger than the code staging
     int16_t* stage_codes = reinterpret_cast<int16_t*>(stage_cta);
     uint32_t* stage_pre = reinterpret_cast<uint32_t*>(stage_cta + 2ull * WPB * kWarpArena * 2);
     uint32_t* stage_off = stage_pre + 2 * (kWarpTile + 1);
@@ -474,6 +477,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
             atomicOr(status, static_cast<unsigned>(SEMR_STATUS_OVERFLOW));
             copy = false;
         }
+        copy = copy && bchk(off + n <= static_cast<uint32_t>(kWarpArena) && gbyte >= p.code_base, status);
         if (copy && n <= 32u) {
             int16_t* dst = reinterpret_cast<int16_t*>(p.payload + gbyte);
             const int16_t* src = arena + off;
@@ -728,6 +732,12 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
         // the count is one warp reduction and nzw (the words holding kept modes) one ballot.  The
         // FP32 form ballots its threshold test directly; FP64 mode ballots its settled keep bits
         uint8_t* fsec = p.payload + p.header_bytes + static_cast<uint64_t>(f) * p.fixed_bytes;
+        // bounds build: the element, its field section and the section's layout within the payload
+        const bool eok = bchk(f < static_cast<uint32_t>(p.n_fields) && e < E &&
+                                  64ull * E + 2 * pad16(2ull * E) <= p.fixed_bytes &&
+                                  p.header_bytes + (f + 1ull) * p.fixed_bytes <= p.code_base &&
+                                  p.code_base <= p.payload_cap,
+                              status);
         uint4* mdst = reinterpret_cast<uint4*>(fsec + static_cast<uint64_t>(e) * 64);
         uint32_t n_e = 0, nzw = 0;
         if constexpr (DF) {
@@ -740,7 +750,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
             }
             __syncwarp();
             const uint32_t mw = (lane < 16) ? smask[lane] : 0u;
-            if (lane < 16) reinterpret_cast<uint32_t*>(mdst)[lane] = mw;
+            if (lane < 16 && eok) reinterpret_cast<uint32_t*>(mdst)[lane] = mw;
             n_e = __reduce_add_sync(FULL, static_cast<unsigned>(__popc(mw)));
             nzw = __ballot_sync(FULL, mw != 0u);
         } else {
@@ -754,7 +764,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
 #pragma unroll
                 for (int q4 = 0; q4 < 4; ++q4) {
                     const uint4 v = make_uint4(wv[4 * q4], wv[4 * q4 + 1], wv[4 * q4 + 2], wv[4 * q4 + 3]);
-                    mdst[q4] = v;
+                    if (eok) mdst[q4] = v;
                     reinterpret_cast<uint4*>(smask)[q4] = v;
                 }
             }
@@ -770,12 +780,14 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
         // the element's codes fit the warp's arena (else they are written directly)
         const bool staged = atop + n_e <= static_cast<uint32_t>(kWarpArena);
         if (lane == 0) {
-            sdst[e] = static_cast<int16_t>(step);
-            cdst[e] = static_cast<uint16_t>(n_e);
+            if (eok) {
+                sdst[e] = static_cast<int16_t>(step);
+                cdst[e] = static_cast<uint16_t>(n_e);
+            }
             s_cnt[il] = (tag << 16) | n_e;
             stage_off[par * kWarpTile + il] = staged ? atop : kDirect;
         }
-        if (e + 1 == E && lane < 16) {  // zero the padding after the step and count sections
+        if (e + 1 == E && lane < 16 && eok) {  // zero the padding after the step and count sections
             const uint64_t se = 2ull * E;
             if (se + lane < pad16(se)) {
                 reinterpret_cast<uint8_t*>(sdst)[se + lane] = 0;
@@ -817,6 +829,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
             const uint64_t gbyte = p.code_base + 2ull * before;
             qwrite = gbyte + 2ull * n_e <= p.payload_cap;
             if (!qwrite && lane == 0) atomicOr(status, static_cast<unsigned>(SEMR_STATUS_OVERFLOW));
+            qwrite = qwrite && bchk(gbyte >= p.code_base, status);
             qdst = reinterpret_cast<int16_t*>(p.payload + gbyte);
         }
         __syncwarp();
@@ -1006,7 +1019,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
             e2 = {warp_sum_f(fmaf(ep.x, wjk.x, ep.y * wjk.y)), 0.0f};
             lh = warp_max_nonneg(dm);
         }
-        if (p.write_recon && p.recon[f]) {  // u~ = u~' 2^ke (exact)
+        if (p.write_recon && p.recon[f] && eok) {  // u~ = u~' 2^ke (exact)
             const double sc = pow2d(s_res[il].ke);
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
@@ -1081,7 +1094,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
             run += cl[h];
         }
         const uint32_t tot = __shfl_sync(FULL, incl, 31);
-        if (lane == 0) {
+        if (lane == 0 && bchk(tcur < static_cast<uint32_t>(p.n_fields) * tpf, status)) {
             pre[kWarpTile] = tot;
             st_release_u64(&p.tile_state[tcur], (tcur == 0 ? kFlagPrefix : kFlagAggregate) | tot);
         }
@@ -1115,8 +1128,9 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
             const double x2 = (static_cast<double>(st.lh) + static_cast<double>(st.ll)) * sc;
             m2 = static_cast<unsigned long long>(__double_as_longlong(x2));
             m3 = st.hmax;
-            p.hmax_elem[ge] = st.hmax;
-            if (p.elem_report) {
+            const bool gok = bchk(ge < static_cast<uint64_t>(p.n_fields) * E, status);
+            if (gok) p.hmax_elem[ge] = st.hmax;
+            if (p.elem_report && gok) {
                 double* er = p.elem_report + 3 * ge;
                 er[0] = v0;
                 er[1] = v1;
@@ -1138,7 +1152,8 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {  // tile partials: the warps' partials in a fixed order
+    if (threadIdx.x == 0 && bchk(tcur < static_cast<uint32_t>(p.n_fields) * tpf, status)) {
+        // tile partials: the warps' partials in a fixed order
         double* tp = p.tile_part + 4ull * tcur;
         tp[0] = ((s_wpart[0][0] + s_wpart[1][0]) + s_wpart[2][0]) + s_wpart[3][0];
         tp[1] = ((s_wpart[0][1] + s_wpart[1][1]) + s_wpart[2][1]) + s_wpart[3][1];

@@ -18,12 +18,23 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_every_declared_symbol_is_exported():
     text = open(os.path.join(ROOT, "include", "semr.h")).read()
-    declared = set(re.findall(r"^\s*(?:int|void|const char\*)\s+(semr_\w+)\s*\(", text, re.M))
+    declared = set(re.findall(r"^\s*(?:int|void|uint32_t|const char\*)\s+(semr_\w+)\s*\(", text, re.M))
     assert declared, "no declarations parsed"
-    lib = ctypes.CDLL(semr.LIB_PATH)
-    for name in sorted(declared):
-        assert hasattr(lib, name), name
+    for path in (semr.LIB_PATH, os.path.join(os.path.dirname(semr.LIB_PATH), "libsemr_bounds.so")):
+        lib = ctypes.CDLL(path)
+        for name in sorted(declared):
+            assert hasattr(lib, name), (path, name)
     assert declared == {n for n, _, _ in semr.EXPORTS}
+
+
+def test_build_flags_name_the_checking_build():
+    """libsemr.so is the default build; libsemr_bounds.so (the same ABI) was
+    compiled with -DSEMR_BOUNDS and says so."""
+    here = os.path.dirname(semr.LIB_PATH)
+    for name, flags in (("libsemr.so", 0), ("libsemr_bounds.so", semr.SEMR_BUILD_BOUNDS)):
+        lib = ctypes.CDLL(os.path.join(here, name))
+        lib.semr_build_flags.restype = ctypes.c_int
+        assert lib.semr_build_flags() == flags, name
 
 
 @pytest.mark.parametrize("lx,ne,nf,tau", [(8, 262144, 4, 1e-3), (6, 1001, 3, 0.0), (10, 7, 1, 1e-9), (2, 5, 16, 0.5)])
