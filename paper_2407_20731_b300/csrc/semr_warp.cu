@@ -179,10 +179,11 @@ __device__ __noinline__ double exact_coef(const double* __restrict__ u, int pp, 
 // out of line): the lane's coefficients (s, r) are at buf[lane * 17 + 8 s + r]; each mode
 // with its bit set in the lane's amb is recomputed exactly, one at a time over the warp, and
 // a kept one becomes its code times 2^s (exact), so the quantisation reproduces the code of
-// the exact value.  Returns the lane's updated keep bits.
+// the exact value.  Returns the lane's updated keep bits.  keep_fixed: the keep bits are
+// already exact (cumulative truncation) and only the roundings are settled.
 __device__ __noinline__ uint32_t resolve_ambiguous(float* buf, uint32_t amb, uint32_t kb, const double* __restrict__ u,
                                                    const double* __restrict__ A64, double sc, f2 t, float qd,
-                                                   float qu, unsigned& recomputed) {
+                                                   float qu, unsigned& recomputed, bool keep_fixed) {
     const int lane = threadIdx.x & 31;
     const double td = static_cast<double>(t.h) + static_cast<double>(t.l);
     while (__any_sync(FULL, amb != 0u)) {
@@ -192,7 +193,7 @@ __device__ __noinline__ uint32_t resolve_ambiguous(float* buf, uint32_t amb, uin
         const double c = exact_coef(u, src & 7, (src >> 3) + 4 * ms, mr, A64, sc);
         ++recomputed;
         if (lane == src) {
-            const bool keep = c * c >= td;
+            const bool keep = keep_fixed ? ((kb >> bsel) & 1u) != 0u : c * c >= td;
             float v = static_cast<float>(c);
             if (keep) v = static_cast<float>(rint(c * static_cast<double>(qd))) * qu;  // ties to even; exact
             buf[lane * 17 + bsel] = v;
@@ -201,6 +202,122 @@ __device__ __noinline__ uint32_t resolve_ambiguous(float* buf, uint32_t amb, uin
         }
     }
     __syncwarp();
+    return kb;
+}
+
+// Cumulative-energy selection of an element that the fast path leaves open (a rare path,
+// out of line): the modes kept are those whose energy is at least T, the smallest energy
+// value v with sum_{a^2 <= v} a^2 > t.  FP64 mode recomputes the element's coefficients
+// a' = 2^-ke A x A x A u in hardware FP64 from its doubles (reread from L2); the FP32 form
+// takes its FP32 coefficients, passed at buf[lane * 17 + 8 s + r], as they are (their
+// squares are exact in FP64).  The energies become 64-bit fixed-point keys floor(a^2 2^K)
+// with t 2^K in [2^47, 2^48), so every sum is an exact integer sum whatever its order (the
+// floors move a sum by at most 512 units, 4e-12 t), and a bisection on the key value finds
+// T.  Returns the lane's keep bits (8 s + r); FP64 mode also leaves at buf[lane * 17 + b]
+// each kept coefficient's code times 2^s (exact, so the quantisation reproduces the code of
+// the FP64 value) and every other coefficient rounded to float.
+template <bool DF>
+__device__ __noinline__ uint32_t cum_general(float* buf, const double* __restrict__ u, const double* __restrict__ A64,
+                                             double sc, double td, float qd, float qu, unsigned& recomputed) {
+    const int lane = threadIdx.x & 31, j = lane & 7, k0 = lane >> 3;
+    double a[16];  // the lane's coefficients, b = 8 s + r: mode (p, q, r) = (j, k0 + 4 s, r)
+    if constexpr (DF) {
+        double* D = reinterpret_cast<double*>(buf);  // 512 doubles, the warp's buffer
+        double x[8], y[8];
+        __syncwarp();
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {  // along i: pencils (k, j) = (k0 + 4 s, j) -> D[k][j][p]
+            const double2* row = reinterpret_cast<const double2*>(u + (lane + 32 * s) * 8);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const double2 v = __ldg(row + c);
+                x[2 * c] = v.x * sc;
+                x[2 * c + 1] = v.y * sc;
+            }
+#pragma unroll
+            for (int pp = 0; pp < 8; ++pp) {
+                double acc = 0.0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc = fma(A64[pp * 8 + i], x[i], acc);
+                y[pp] = acc;
+            }
+#pragma unroll
+            for (int pp = 0; pp < 8; ++pp) D[((k0 + 4 * s) * 8 + j) * 8 + pp] = y[pp];
+        }
+        __syncwarp();
+        double z[2][8];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {  // along j: lane (k, p) = (k0 + 4 s, j) -> D[k][q][p]
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) x[jj] = D[((k0 + 4 * s) * 8 + jj) * 8 + j];
+#pragma unroll
+            for (int qq = 0; qq < 8; ++qq) {
+                double acc = 0.0;
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) acc = fma(A64[qq * 8 + jj], x[jj], acc);
+                z[s][qq] = acc;
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int qq = 0; qq < 8; ++qq) D[((k0 + 4 * s) * 8 + qq) * 8 + j] = z[s][qq];
+        __syncwarp();
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {  // along k: lane (q, p) = (k0 + 4 s, j) -> coefficient r
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) x[kk] = D[(kk * 8 + k0 + 4 * s) * 8 + j];
+#pragma unroll
+            for (int rr = 0; rr < 8; ++rr) {
+                double acc = 0.0;
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) acc = fma(A64[rr * 8 + kk], x[kk], acc);
+                a[8 * s + rr] = acc;
+            }
+        }
+        __syncwarp();
+        recomputed += 512;
+    } else {
+#pragma unroll
+        for (int b = 0; b < 16; ++b) a[b] = static_cast<double>(buf[lane * 17 + b]);
+    }
+    // keys and budget: t 2^K in [2^47, 2^48); energies of 2^50 / 2^K >= 4 t and more are clamped
+    // (always kept)
+    int ex;
+    frexp(td, &ex);  // td in [2^(ex - 1), 2^ex)
+    const double sK = ldexp(1.0, 48 - ex);
+    const unsigned long long tt = static_cast<unsigned long long>(td * sK);
+    constexpr unsigned long long kClamp = 1ull << 50;
+    unsigned long long key[16];
+    unsigned long long own = 0ull;
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+        const double v = a[b] * a[b] * sK;
+        key[b] = v >= static_cast<double>(kClamp) ? kClamp : static_cast<unsigned long long>(v);
+        own += key[b];
+    }
+    uint32_t kb = 0;
+    if (warp_sum_u62(own) > tt) {  // else every energy fits the budget: nothing kept
+        unsigned long long lo = 1, hi = kClamp;  // smallest v with sum_{key <= v} key > tt
+        while (lo < hi) {
+            const unsigned long long mid = lo + (hi - lo) / 2;
+            unsigned long long sm = 0ull;
+#pragma unroll
+            for (int b = 0; b < 16; ++b) sm += key[b] <= mid ? key[b] : 0ull;
+            if (warp_sum_u62(sm) > tt) hi = mid;
+            else lo = mid + 1;
+        }
+#pragma unroll
+        for (int b = 0; b < 16; ++b) kb |= (key[b] >= lo ? 1u : 0u) << b;
+    }
+    if constexpr (DF) {
+#pragma unroll
+        for (int b = 0; b < 16; ++b)
+            buf[lane * 17 + b] = ((kb >> b) & 1u) ? static_cast<float>(rint(a[b] * static_cast<double>(qd))) * qu
+                                                  : static_cast<float>(a[b]);
+        __syncwarp();
+    }
     return kb;
 }
 
@@ -336,7 +453,7 @@ __device__ __noinline__ void dense_inverse_pairs(float2* buf, const float* Ph, c
 // BATCH = false: one reduction, parameters and tensor maps in A.  BATCH = true: the
 // work queue q of several lx = 8 reductions (each with its own descriptor, payload
 // and scratch; their tensor maps in global memory at q.tmaps, field_base order).
-template <int MODE, bool BATCH>
+template <int MODE, bool BATCH, bool CUM = false>
 __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
     reduce_warp_kernel(const __grid_constant__ WArgs A, const BatchQueue q) {
     constexpr bool DF = MODE != 0;
@@ -685,7 +802,140 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
 
         // ---- keep decisions; FP64 mode recomputes exactly what FP32 cannot settle
         uint32_t kb = 0;  // keep bit (8 s + r)
-        if (emode == 1) {
+        if constexpr (CUM) {
+            if (emode == 1) {
+                // cumulative-energy truncation: keep the modes whose energy is at least T, the
+                // smallest energy value v with sum_{a^2 <= v} a^2 > t.  Every mode with a^2 > t is
+                // kept (the dropped ones fit the budget t); of the rest, extract the largest |a| one
+                // at a time, subtracting its square from R, the sum of the squares not extracted
+                // yet, until R <= t: the last one extracted is the smallest kept (ties with it are
+                // kept too).  FP64 mode takes the result only where the FP32 coefficients' bound M
+                // settles it -- t - R, R + (v - M)^2 - t and the gap between v and the largest
+                // coefficient left all clear of B = 2 M sum_{left} |a| + n M^2 plus the FP32 sums'
+                // rounding -- else (and beyond kCumIters extractions) the general path decides.
+                constexpr int kCumIters = 48;
+                float M = 0.0f, gb;  // gb: |a| >= gb surely has a^2 > t
+                if constexpr (DF) {
+                    constexpr float kMarg = (3.0f * (4 + 2) + 2.0f) * 5.9604645e-8f * 2.8285f * 2.0f;
+                    const float umax_e = __uint_as_float(0x3f800000u | ((hmax & 0xfffffu) << 3));
+                    M = kMarg * umax_e * 1.000002f;
+                    gb = g + (M + g * 2.4e-7f);
+                } else {
+                    gb = __uint_as_float(__float_as_uint(g) + 1u);  // |a| > g
+                }
+                auto absbits = [&](int b) -> uint32_t {
+                    return __float_as_uint(b & 8 ? a2[b & 7].y : a2[b & 7].x) & 0x7fffffffu;
+                };
+                uint32_t rem = 0;  // the lane's coefficients below gb, not extracted yet
+                float rs = 0.0f, sa = 0.0f;
+#pragma unroll
+                for (int b = 0; b < 16; ++b) {
+                    const float x = __uint_as_float(absbits(b));
+                    const bool low = x < gb;
+                    rem |= (low ? 1u : 0u) << b;
+                    rs = low ? fmaf(x, x, rs) : rs;
+                    sa = low ? sa + x : sa;
+                }
+                float R = warp_sum_f(rs);
+                float sabs = warp_sum_f(sa);
+                const float R0 = R;
+                int nrem = static_cast<int>(__reduce_add_sync(FULL, static_cast<unsigned>(__popc(rem))));
+                int it = 0;
+                float v = 0.0f;  // |a| of the last one extracted
+                uint32_t wm = 0;
+                bool done = R <= t.h, open = false;
+                for (;;) {
+                    uint32_t mk = 0;  // the largest coefficient left (the next to extract)
+#pragma unroll
+                    for (int b = 0; b < 16; ++b) mk = ((rem >> b) & 1u) ? max(mk, absbits(b)) : mk;
+                    wm = __reduce_max_sync(FULL, mk);
+                    if (done) break;
+                    if (it == kCumIters || wm == 0u) {  // (only zeros left with R > t: not settled)
+                        open = true;
+                        break;
+                    }
+                    if (lane == __ffs(__ballot_sync(FULL, mk == wm)) - 1) {  // one holder of it
+                        uint32_t hit = 0;
+#pragma unroll
+                        for (int b = 0; b < 16; ++b) hit |= (((rem >> b) & 1u) && absbits(b) == wm ? 1u : 0u) << b;
+                        rem &= ~(hit & (0u - hit));
+                    }
+                    v = __uint_as_float(wm);
+                    R = fmaf(-v, v, R);
+                    sabs -= v;
+                    --nrem;
+                    ++it;
+                    done = R <= t.h;
+                }
+                bool settled = !open;
+                if constexpr (DF) {
+                    if (settled) {
+                        // the smallest kept coefficient: the last extracted, else the smallest above gb
+                        float vk = v;
+                        if (it == 0) {
+                            uint32_t mn = 0x7f000000u;  // (2^127: nothing above gb)
+#pragma unroll
+                            for (int b = 0; b < 16; ++b) mn = ((rem >> b) & 1u) ? mn : min(mn, absbits(b));
+                            vk = __uint_as_float(__reduce_min_sync(FULL, mn));
+                        }
+                        const float wn = __uint_as_float(wm);  // the largest coefficient not kept
+                        const float rho = R0 * (6e-5f + 1.2e-7f * static_cast<float>(it)) + 2.4e-7f * t.h;
+                        const float B = 2.0f * M * sabs * 1.0001f + static_cast<float>(nrem) * M * M + rho;
+                        const float d1 = t.h - R;  // >= 0
+                        settled = d1 * 0.999999f > B;
+                        if (vk < 0x1p126f) {  // something is kept
+                            const float lv = fmaxf(vk - M, 0.0f);
+                            settled = settled && (lv * lv * 0.999999f - d1 * 1.000001f) > B &&
+                                      (vk - wn) > 2.0f * M * 1.000001f + vk * 1.2e-7f;
+                        }
+                    }
+                }
+                bool exactv = false;  // FP64 mode: a2 holds exact codes x 2^s where kept
+                if (!settled) {
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) {
+                        tb[lane * 17 + r] = a2[r].x;
+                        tb[lane * 17 + 8 + r] = a2[r].y;
+                    }
+                    kb = cum_general<DF>(tb, p.fields[f] + static_cast<uint64_t>(e) * WN3, A.tab.A64, pow2d(-ke),
+                                         static_cast<double>(t.h) + static_cast<double>(t.l), qd, qu, recomputed);
+                    if constexpr (DF) {
+#pragma unroll
+                        for (int r = 0; r < 8; ++r) a2[r] = make_float2(tb[lane * 17 + r], tb[lane * 17 + 8 + r]);
+                        exactv = true;
+                    }
+                    __syncwarp();
+                } else {
+                    // kept: everything at or above gb and every extracted coefficient, i.e. |a| >= v
+                    // (ties included), or |a| >= gb when nothing was extracted
+                    const uint32_t vb = __float_as_uint(it ? v : gb);
+#pragma unroll
+                    for (int b = 0; b < 16; ++b) kb |= (absbits(b) >= vb ? 1u : 0u) << b;
+                }
+                if constexpr (DF) {  // the rounding decisions of the kept coefficients
+                    if (!exactv) {
+                        const float Mq = M * qd * 1.000001f;
+                        uint32_t amb = 0;
+#pragma unroll
+                        for (int b = 0; b < 16; ++b) {
+                            const float y = __uint_as_float(absbits(b)) * qd;
+                            if (((kb >> b) & 1u) && fabsf((y - floorf(y)) - 0.5f) <= Mq + y * 1.2e-7f) amb |= 1u << b;
+                        }
+                        if (__any_sync(FULL, amb != 0u)) {
+#pragma unroll
+                            for (int r = 0; r < 8; ++r) {
+                                tb[lane * 17 + r] = a2[r].x;
+                                tb[lane * 17 + 8 + r] = a2[r].y;
+                            }
+                            kb = resolve_ambiguous(tb, amb, kb, p.fields[f] + static_cast<uint64_t>(e) * WN3,
+                                                   A.tab.A64, pow2d(-ke), t, qd, qu, recomputed, true);
+#pragma unroll
+                            for (int r = 0; r < 8; ++r) a2[r] = make_float2(tb[lane * 17 + r], tb[lane * 17 + 8 + r]);
+                        }
+                    }
+                }
+            }
+        } else if (emode == 1) {
             if constexpr (DF) {
                 // |a_fp32 - a| <= M: (H + 2) roundings per folded contraction (H = 4 terms, the fold,
                 // the table), 3 contractions, 2 more for the input split; every row of A has
@@ -720,7 +970,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
                         tb[lane * 17 + 8 + r] = a2[r].y;
                     }
                     kb = resolve_ambiguous(tb, amb, kb, p.fields[f] + static_cast<uint64_t>(e) * WN3, A.tab.A64,
-                                           pow2d(-ke), t, qd, qu, recomputed);
+                                           pow2d(-ke), t, qd, qu, recomputed, false);
 #pragma unroll
                     for (int r = 0; r < 8; ++r) a2[r] = make_float2(tb[lane * 17 + r], tb[lane * 17 + 8 + r]);
                 }
@@ -740,7 +990,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
                               status);
         uint4* mdst = reinterpret_cast<uint4*>(fsec + static_cast<uint64_t>(e) * 64);
         uint32_t n_e = 0, nzw = 0;
-        if constexpr (DF) {
+        if constexpr (DF || CUM) {
 #pragma unroll
             for (int q4 = 0; q4 < 4; ++q4) {  // words 4 q4 .. 4 q4 + 3
                 uint32_t w4[4];
@@ -1300,11 +1550,11 @@ WTables make_wtables() {
     return t;
 }
 
-template <int MODE, bool BATCH>
+template <int MODE, bool BATCH, bool CUM = false>
 int launch_mode(const WArgs& a, const BatchQueue& q, uint64_t total_tiles, uint64_t stage_ctas, void* stream) {
     using SM = WSmem<MODE != 0>;
     cudaError_t err;
-    auto kern = reduce_warp_kernel<MODE, BATCH>;
+    auto kern = reduce_warp_kernel<MODE, BATCH, CUM>;
     if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes)) != cudaSuccess)
         return (int)err;
     int dev = 0, sms = 0, per_sm = 0;
@@ -1342,7 +1592,7 @@ __global__ void selftest_waits_kernel(uint64_t* tile_state, unsigned* status) {
 }  // namespace
 
 bool warp_applicable(const LaunchParams& p) {
-    if (p.lx != 8 || p.cumulative || p.lossless || p.width != 2) return false;
+    if (p.lx != 8 || p.lossless || p.width != 2) return false;
     if (p.precision != SEMR_FP64 && p.precision != SEMR_FP32) return false;
     if (static_cast<uint64_t>(p.n_elem) * WNP >= (1ull << 31)) return false;  // TMA row coordinate
     for (int f = 0; f < p.n_fields; ++f)
@@ -1373,6 +1623,9 @@ int launch_reduce_warp(const LaunchParams& p, void* stream) {
             return (int)cudaErrorInvalidValue;
     }
     BatchQueue q{};
+    if (p.cumulative)  // cumulative-energy truncation (single launches only)
+        return p.precision == SEMR_FP32 ? launch_mode<0, false, true>(a, q, a.total_tiles, p.stage_ctas, stream)
+                                        : launch_mode<1, false, true>(a, q, a.total_tiles, p.stage_ctas, stream);
     return p.precision == SEMR_FP32 ? launch_mode<0, false>(a, q, a.total_tiles, p.stage_ctas, stream)
                                     : launch_mode<1, false>(a, q, a.total_tiles, p.stage_ctas, stream);
 }

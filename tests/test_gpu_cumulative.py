@@ -70,8 +70,14 @@ def test_flat_spectra_bisection(lx, tau):
 
 
 def test_many_tiles():
+    """40,000 element-fields at lx = 8: the warp kernel settles most boundaries
+    from its FP32 coefficients and sends the rest (boundary sums within the
+    coefficients' error bound of t, about one element in a hundred) to the
+    general path, which recomputes the element in FP64 (512 coefficients,
+    counted in the summary's recomputed)."""
     fields, jac = make_case(20000, 8, 2, seed=5)
-    _compare(fields, jac, 8, 1e-3)
+    res, _ = _compare(fields, jac, 8, 1e-3)
+    assert res.summary.recomputed >= 512
 
 
 def test_keeps_more_than_threshold_form():
@@ -118,13 +124,14 @@ def test_native_path_rejects_cumulative():
         semr.reduce([fields[0]], jac, 6, 1e-3, precision=semr.SEMR_FP64_NATIVE, cumulative=True)
 
 
-@pytest.mark.parametrize("lx,tau", [(8, 1e-3), (8, 1e-5), (6, 1e-2)])
-def test_fp32_form_budget(lx, tau):
+@pytest.mark.parametrize("lx,tau,white", [(8, 1e-3, False), (8, 1e-5, False), (6, 1e-2, False), (8, 0.05, True)])
+def test_fp32_form_budget(lx, tau, white):
     """FP32 precision form: with the oracle's FP64 coefficients a, the modes the
     GPU dropped fit the budget and the smallest kept one does not, up to the
     FP32 coefficient error delta <= 1e-5 max|u_e| (the forward transform's
     rounding bound with a wide margin)."""
-    fields, jac = make_case(2000, lx, 2, seed=33)
+    # white noise keeps hundreds of modes per element: the general (bisection) path
+    fields, jac = _white(300, lx, 2, seed=34) if white else make_case(2000, lx, 2, seed=33)
     res, rec = run_gpu(fields, jac, lx, tau, precision=semr.SEMR_FP32, cumulative=True)
     assert res.summary.status == 0
     f_np = fields.cpu().numpy()
@@ -145,7 +152,7 @@ def test_fp32_form_budget(lx, tau):
     err_k = err + 2 * delta * np.sqrt(np.where(has, kept_min, 0.0)) + delta ** 2
     assert np.all(~has | (dropped + kept_min > t - err_k))
     same = np.all(mask == s["masks"], axis=2).mean()
-    assert same >= 0.9, same
+    assert same >= (0.5 if white else 0.9), same
     for fi in range(f_np.shape[0]):
         fr, orr = res.summary.field[fi], o.field_report[fi]
         assert abs(fr.l2_rel - orr[1]) <= 2e-2 * orr[1] + 1e-7
