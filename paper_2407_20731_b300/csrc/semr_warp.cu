@@ -205,6 +205,27 @@ __device__ __noinline__ uint32_t resolve_ambiguous(float* buf, uint32_t amb, uin
     return kb;
 }
 
+// Settles the rounding of the kept coefficients of mask word w (slot w & 1, row w >> 1) that the
+// FP32 bound leaves undecided (a rare path, out of line): each flagged lane's coefficient is
+// recomputed exactly, one at a time over the warp, and becomes its code times 2^s (exact), also
+// at buf[lane * 20 + w] (the lane's row of coefficients by word).  Returns the lane's coefficient.
+__device__ __noinline__ float settle_rounding(float a, bool flag, int w, float* buf, const double* __restrict__ u,
+                                              const double* __restrict__ A64, double sc, float qd, float qu,
+                                              unsigned& recomputed) {
+    const int lane = threadIdx.x & 31;
+    for (uint32_t fl = __ballot_sync(FULL, flag); fl; fl &= fl - 1) {
+        const int src = __ffs(fl) - 1;
+        const double c = exact_coef(u, src & 7, (src >> 3) + 4 * (w & 1), w >> 1, A64, sc);
+        ++recomputed;
+        if (lane == src) {
+            a = static_cast<float>(rint(c * static_cast<double>(qd))) * qu;  // ties to even; exact
+            buf[lane * 20 + w] = a;
+        }
+    }
+    __syncwarp();
+    return a;
+}
+
 // Cumulative-energy selection of an element that the fast path leaves open (a rare path,
 // out of line): the modes kept are those whose energy is at least T, the smallest energy
 // value v with sum_{a^2 <= v} a^2 > t.  FP64 mode recomputes the element's coefficients
@@ -653,11 +674,13 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
         inflight = false;
 
         // ---- the element's largest high word of |u| (a first pass over the stage's high words)
+        // (the lane's 16 doubles stay in registers for the split below)
         uint32_t hm = 0;
+        uint4 raw[8];  // pencil lane + 32 (c >> 2), doubles 2 (c & 3) and 2 (c & 3) + 1
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const uint4 v = *reinterpret_cast<const uint4*>(stage + (lane + 32 * (c >> 2)) * 64 + (((c & 3) ^ sw) << 4));
-            hm = max(hm, max(v.y & 0x7fffffffu, v.w & 0x7fffffffu));
+            raw[c] = *reinterpret_cast<const uint4*>(stage + (lane + 32 * (c >> 2)) * 64 + (((c & 3) ^ sw) << 4));
+            hm = max(hm, max(raw[c].y & 0x7fffffffu, raw[c].w & 0x7fffffffu));
         }
         const uint32_t hmax0 = __reduce_max_sync(FULL, hm);
         const bool bad = __any_sync(FULL, hm >= (static_cast<uint32_t>(1023 + 500) << 20));
@@ -676,10 +699,9 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
         float2 uh[8], ul[8];  // (pencil lane, pencil lane + 32) at point i
 #pragma unroll
         for (int pen = 0; pen < 2; ++pen) {
-            const uint8_t* row = stage + (lane + 32 * pen) * 64;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const uint4 v = *reinterpret_cast<const uint4*>(row + ((c ^ sw) << 4));
+                const uint4 v = raw[4 * pen + c];
                 const uint32_t lo[2] = {v.x, v.z}, hi[2] = {v.y, v.w};
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -800,8 +822,10 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
         // t' in [1e-13, 2^70] keeps s' in [-22, 35]: 2^-s' and 2^s' are normal floats (exact scalings)
         const float qd = pow2f(-sps), qu = pow2f(sps);
 
-        // ---- keep decisions; FP64 mode recomputes exactly what FP32 cannot settle
+        // ---- keep decisions; FP64 mode recomputes exactly what FP32 cannot settle (the keep
+        // decisions here, the roundings of kept coefficients in the quantisation below)
         uint32_t kb = 0;  // keep bit (8 s + r)
+        float Mq = 0.0f;  // FP64 mode: the bound M in units of the step (the rounding screen)
         if constexpr (CUM) {
             if (emode == 1) {
                 // cumulative-energy truncation: keep the modes whose energy is at least T, the
@@ -912,28 +936,10 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
 #pragma unroll
                     for (int b = 0; b < 16; ++b) kb |= (absbits(b) >= vb ? 1u : 0u) << b;
                 }
-                if constexpr (DF) {  // the rounding decisions of the kept coefficients
-                    if (!exactv) {
-                        const float Mq = M * qd * 1.000001f;
-                        uint32_t amb = 0;
-#pragma unroll
-                        for (int b = 0; b < 16; ++b) {
-                            const float y = __uint_as_float(absbits(b)) * qd;
-                            if (((kb >> b) & 1u) && fabsf((y - floorf(y)) - 0.5f) <= Mq + y * 1.2e-7f) amb |= 1u << b;
-                        }
-                        if (__any_sync(FULL, amb != 0u)) {
-#pragma unroll
-                            for (int r = 0; r < 8; ++r) {
-                                tb[lane * 17 + r] = a2[r].x;
-                                tb[lane * 17 + 8 + r] = a2[r].y;
-                            }
-                            kb = resolve_ambiguous(tb, amb, kb, p.fields[f] + static_cast<uint64_t>(e) * WN3,
-                                                   A.tab.A64, pow2d(-ke), t, qd, qu, recomputed, true);
-#pragma unroll
-                            for (int r = 0; r < 8; ++r) a2[r] = make_float2(tb[lane * 17 + r], tb[lane * 17 + 8 + r]);
-                        }
-                    }
-                }
+                // FP64 mode: the roundings of the kept coefficients are screened in the quantisation
+                // (the general path's values are exact codes x 2^s, which the screen passes)
+                if constexpr (DF) Mq = M * qd * 1.000001f;
+                (void)exactv;
             }
         } else if (emode == 1) {
             if constexpr (DF) {
@@ -945,7 +951,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
                 const float umax_e = __uint_as_float(0x3f800000u | ((hmax & 0xfffffu) << 3));
                 const float M = kMarg * umax_e * 1.000002f;
                 const float Mg = M + g * 2.4e-7f;  // plus the float rounding of g +- M
-                const float Mq = Mg * qd;
+                Mq = Mg * qd;
                 uint32_t amb = 0;
 #pragma unroll
                 for (int s = 0; s < 2; ++s)
@@ -953,13 +959,8 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
                     for (int r = 0; r < 8; ++r) {
                         const float aa = fabsf(s ? a2[r].y : a2[r].x);
                         const int b = 8 * s + r;
-                        if (aa >= g + Mg) {  // surely kept: is its rounding decision sure too?
-                            const float y = aa * qd;
-                            kb |= 1u << b;
-                            if (fabsf((y - floorf(y)) - 0.5f) <= Mq + y * 1.2e-7f) amb |= 1u << b;
-                        } else if (!(aa < g - Mg)) {
-                            amb |= 1u << b;
-                        }
+                        if (aa >= g + Mg) kb |= 1u << b;            // surely kept
+                        else if (!(aa < g - Mg)) amb |= 1u << b;   // undecided
                     }
                 // exact (float-pair) coefficient of each ambiguous mode (rare): out of line, with
                 // the lane's coefficients passed through the warp's transpose buffer (free here)
@@ -1093,18 +1094,42 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
             }
             const uint32_t lt_mask = (1u << lane) - 1u;
             uint32_t run = 0;  // codes of the words before wi (the words come in increasing order)
+            bool settled_any = false;
             while (nzw) {
                 const int wi = __ffs(nzw) - 1;
                 nzw &= nzw - 1;
                 const uint32_t wd = smask[wi];
+                float a = 0.0f;
+                if constexpr (DF) {
+                    // a kept coefficient whose rounding the FP32 bound cannot settle is recomputed
+                    a = tb[lane * 20 + wi];
+                    const float y = fabsf(a) * qd;
+                    const bool ra = ((wd >> lane) & 1u) && fabsf((y - floorf(y)) - 0.5f) <= Mq + y * 1.2e-7f;
+                    if (__any_sync(FULL, ra)) {
+                        a = settle_rounding(a, ra, wi, tb, p.fields[f] + static_cast<uint64_t>(e) * WN3, A.tab.A64,
+                                            pow2d(-ke), qd, qu, recomputed);
+                        settled_any = true;
+                    }
+                }
                 if ((wd >> lane) & 1u) {
-                    const float a = DF ? tb[lane * 20 + wi] : pick(a2, wi);
+                    if constexpr (!DF) a = pick(a2, wi);
                     const float c = (a * qd + 12582912.0f) - 12582912.0f;  // round half to even (|y| < 2^22)
                     const uint32_t rank = run + __popc(wd & lt_mask);
                     if (qwrite) qdst[rank] = static_cast<int16_t>(c);
                     if (rank < static_cast<uint32_t>(wsparse<DF>())) skl[rank] = make_int2(lane + 32 * wi, __float_as_int(c));
                 }
                 run += __popc(wd);
+            }
+            if constexpr (DF) {
+                if (settled_any) {  // the dense reconstruction reads the kept coefficients from a2
+                    const float4* arow = reinterpret_cast<const float4*>(tb + lane * 20);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 v = arow[q];
+                        a2[2 * q] = make_float2(v.x, v.y);
+                        a2[2 * q + 1] = make_float2(v.z, v.w);
+                    }
+                }
             }
         }
         if (staged) atop += n_e;
