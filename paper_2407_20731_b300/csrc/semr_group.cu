@@ -245,6 +245,29 @@ __device__ __noinline__ uint32_t g_resolve(float* M, int w0, uint32_t amb, uint3
     return kb;
 }
 
+// Settles the rounding of this warp's kept modes of word w0 + kk that the FP32 bound leaves
+// undecided (bit set in flag: mode 32 (w0 + kk) + lane), one at a time over the warp: each
+// becomes its code times 2^s' (exact), also in M.  Returns the lane's value.
+template <int LX>
+__device__ __noinline__ float g_settle(float a, bool flag, float* M, int w0, int kk, const double* __restrict__ u,
+                                       const double* __restrict__ A64, double sc, float qd, float qu,
+                                       unsigned& recomputed) {
+    constexpr int NP = LX * LX;
+    const int lane = threadIdx.x & 31;
+    for (uint32_t fl = __ballot_sync(FULL, flag); fl; fl &= fl - 1) {
+        const int src = __ffs(fl) - 1;
+        const int m = 32 * (w0 + kk) + src;
+        const double c = g_exact_coef<LX>(u, m % LX, (m / LX) % LX, m / NP, A64, sc);
+        ++recomputed;
+        if (lane == src) {
+            a = static_cast<float>(rint(c * static_cast<double>(qd))) * qu;  // ties to even; exact
+            M[m] = a;
+        }
+    }
+    __syncwarp();
+    return a;
+}
+
 template <int LX, int MODE>
 struct GOcc {  // CTAs per SM the register budget aims at
     static constexpr int value = LX <= 6 ? (MODE ? 3 : 5) : 3;
@@ -455,18 +478,19 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
 
         // ---- the element's largest high word of |u| (first pass over the stage's high words; if the
         // block did not land the values are meaningless, but every read stays inside the stage)
+        // (the pencils' doubles stay in registers for the split below; an absent pencil is 0)
         const double* su = reinterpret_cast<const double*>(stage);
         uint32_t hm = 0;
+        uint4 raw[2][LX / 2];
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             const int P = s ? P1 : P0;
-            if (s == 0 || v1) {
-                const uint4* row = reinterpret_cast<const uint4*>(su + P * LX);
+            const bool ok = s == 0 || v1;
+            const uint4* row = reinterpret_cast<const uint4*>(su + P * LX);
 #pragma unroll
-                for (int c = 0; c < LX / 2; ++c) {
-                    const uint4 v = row[c];
-                    hm = max(hm, max(v.y & 0x7fffffffu, v.w & 0x7fffffffu));
-                }
+            for (int c = 0; c < LX / 2; ++c) {
+                raw[s][c] = ok ? row[c] : make_uint4(0u, 0u, 0u, 0u);
+                hm = max(hm, max(raw[s][c].y & 0x7fffffffu, raw[s][c].w & 0x7fffffffu));
             }
         }
         uint32_t hmax = __reduce_max_sync(FULL, hm);
@@ -500,12 +524,9 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
         float2 uh[LX], ul[LX];
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-            const int P = s ? P1 : P0;
-            const bool ok = s == 0 || v1;
-            const uint4* row = reinterpret_cast<const uint4*>(su + P * LX);
 #pragma unroll
             for (int c = 0; c < LX / 2; ++c) {
-                const uint4 v = ok ? row[c] : make_uint4(0u, 0u, 0u, 0u);
+                const uint4 v = raw[s][c];
                 const uint32_t lo[2] = {v.x, v.z}, hi[2] = {v.y, v.w};
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -646,24 +667,20 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
         for (int kk = 0; kk < WPW; ++kk)
             if (w0 + kk < MW && 32 * (w0 + kk) + lane < N3) vm |= 1u << kk;
         uint32_t kb = 0;
+        float Mq = 0.0f;  // FP64 mode: the bound in units of the step (the rounding screen, in the quantisation)
         if (emode == 1) {
             if constexpr (DF) {
                 constexpr float kMarg = (3.0f * (LX / 2 + 2) + 2.0f) * 5.9604645e-8f * 2.8285f * 2.0f;
                 const float umax_e = __uint_as_float(0x3f800000u | ((hmax & 0xfffffu) << 3));
                 const float Mm = kMarg * umax_e * 1.000002f;
                 const float Mg = Mm + gth * 2.4e-7f;
-                const float Mq = Mg * qd;
+                Mq = Mg * qd;
                 uint32_t amb = 0;
 #pragma unroll
                 for (int kk = 0; kk < WPW; ++kk) {
                     const float aa = fabsf(am[kk]);
-                    if (aa >= gth + Mg) {
-                        const float y = aa * qd;
-                        kb |= 1u << kk;
-                        if (fabsf((y - floorf(y)) - 0.5f) <= Mq + y * 1.2e-7f) amb |= 1u << kk;
-                    } else if (!(aa < gth - Mg)) {
-                        amb |= 1u << kk;
-                    }
+                    if (aa >= gth + Mg) kb |= 1u << kk;            // surely kept
+                    else if (!(aa < gth - Mg)) amb |= 1u << kk;   // undecided
                 }
                 kb &= vm;
                 amb &= vm;
@@ -765,9 +782,17 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
                 const int kk = __ffs(nzw) - 1;
                 nzw &= nzw - 1;
                 const uint32_t wd = bm[w0 + kk];
+                const int m = 32 * (w0 + kk) + lane;  // (within the buffer for every lane)
+                float a = M[m];
+                if constexpr (DF) {  // a kept mode whose rounding the FP32 bound cannot settle is recomputed
+                    const float y = fabsf(a) * qd;
+                    const bool ra = ((wd >> lane) & 1u) && fabsf((y - floorf(y)) - 0.5f) <= Mq + y * 1.2e-7f;
+                    if (__any_sync(FULL, ra))
+                        a = g_settle<LX>(a, ra, M, w0, kk, p.fields[f] + static_cast<uint64_t>(e) * N3, A.tab.A64,
+                                         pow2d(-ke), qd, qu, recomputed);
+                }
                 if ((wd >> lane) & 1u) {
-                    const int m = 32 * (w0 + kk) + lane;
-                    const float c = (M[m] * qd + 12582912.0f) - 12582912.0f;  // round half to even (|y| < 2^22)
+                    const float c = (a * qd + 12582912.0f) - 12582912.0f;  // round half to even (|y| < 2^22)
                     const uint32_t rank = run + __popc(wd & lt_mask);
                     if (qwrite) qdst[rank] = static_cast<int16_t>(c);
                     if (rank < static_cast<uint32_t>(KL)) skl[rank] = make_int2(m, __float_as_int(c));
