@@ -530,6 +530,16 @@ int semr_build_flags(void);
  * clears it.  Synchronous (waits for the device); 0xffffffff on a CUDA error. */
 uint32_t semr_bounds_status(int reset);
 
+/* semr_selftest_bounds: checking build only (SEMR_EUNSUPPORTED otherwise).
+ * Shows that the range tests fire: reduces a 300-element lx = 8 field (FP64
+ * mode, tau = 1e-3) into buffers of the full size while the kernels are told
+ * a payload capacity 64 bytes short of the fixed sections, so every element's
+ * payload range test fails and its writes are skipped (none leaves the
+ * buffers the call allocated).  *status_out gets the summary's status word,
+ * which must hold SEMR_STATUS_BOUNDS.  Synchronous; allocates and frees its
+ * own device memory. */
+int semr_selftest_bounds(uint32_t* status_out);
+
 #ifdef __cplusplus
 }
 #endif

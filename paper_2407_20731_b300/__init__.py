@@ -148,6 +148,7 @@ EXPORTS = [
     ("semr_selftest_waits", ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32)]),
     ("semr_build_flags", ctypes.c_int, []),
     ("semr_bounds_status", ctypes.c_uint32, [ctypes.c_int]),
+    ("semr_selftest_bounds", ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32)]),
 ]
 SEMR_NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -185,6 +186,14 @@ def semr_build_flags() -> int:
 
 def semr_bounds_status(reset: bool = False) -> int:
     return _lib.semr_bounds_status(1 if reset else 0)
+
+
+def semr_selftest_bounds() -> tuple[int, int]:
+    """(return code, status word) of the checking build's self-test, in which
+    every range test must fail (SEMR_EUNSUPPORTED in the default build)."""
+    st = ctypes.c_uint32(0)
+    rc = _lib.semr_selftest_bounds(ctypes.byref(st))
+    return rc, int(st.value)
 
 
 def semr_sizes_for(lx: int, n_elem: int, n_fields: int, tau: float) -> semr_sizes:

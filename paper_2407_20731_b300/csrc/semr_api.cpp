@@ -72,6 +72,12 @@ extern "C" int semr_sizes_for(int32_t lx, int64_t n_elem, int32_t n_fields, doub
     return SEMR_OK;
 }
 
+#ifdef SEMR_BOUNDS
+// semr_selftest_bounds only: launch with a payload capacity this many bytes short of the fixed
+// sections (inside a buffer that holds them all), so the kernels' range tests must fail
+static uint64_t g_bounds_cap_short = 0;
+#endif
+
 extern "C" int semr_reduce_async(const semr_fieldset* fs, const semr_mesh* mesh, const semr_outputs* out,
                                  void* cuda_stream) {
     return semr_reduce_async_timed(fs, mesh, out, cuda_stream, nullptr, nullptr);
@@ -130,6 +136,9 @@ extern "C" int semr_reduce_async_timed(const semr_fieldset* fs, const semr_mesh*
     p.header_bytes = sz.header_bytes;
     p.fixed_bytes = field_fixed_bytes(mesh->lx, mesh->n_elem);
     p.code_base = sz.code_base;
+#ifdef SEMR_BOUNDS
+    if (g_bounds_cap_short) p.payload_cap = p.code_base - g_bounds_cap_short;
+#endif
     // threshold truncation with int16 codes runs on the warp-level kernels: lx = 8 on the
     // warp-per-element kernel, lx = 6 and 10 on the warp-group kernel
     const bool warp = warp_applicable(p);
@@ -568,5 +577,63 @@ extern "C" int semr_build_flags(void) {
     return SEMR_BUILD_BOUNDS;
 #else
     return 0;
+#endif
+}
+
+extern "C" int semr_selftest_bounds(uint32_t* status_out) {
+#ifndef SEMR_BOUNDS
+    (void)status_out;
+    return SEMR_EUNSUPPORTED;
+#else
+    if (!status_out) return SEMR_EINVAL;
+    constexpr int lx = 8, n_elem = 300, n3 = lx * lx * lx;
+    semr_sizes sz;
+    if (semr_sizes_for(lx, n_elem, 1, 1e-3, &sz) != SEMR_OK) return SEMR_EINVAL;
+    const uint64_t field_bytes = 8ull * n3 * n_elem, jac_bytes = 8ull * n_elem;
+    const uint64_t total = field_bytes + jac_bytes + sz.payload_worst + sz.scratch_bytes + sizeof(semr_summary) + 1024;
+    uint8_t* buf = nullptr;
+    if (cudaMalloc(&buf, total) != cudaSuccess) return SEMR_ENOMEM;
+    int rc = SEMR_OK;
+    std::vector<double> host(static_cast<size_t>(n3) * n_elem);
+    for (size_t i = 0; i < host.size(); ++i) host[i] = static_cast<double>((i * 2654435761u) % 1000u) / 1000.0 - 0.5;
+    std::vector<double> jac(n_elem, 1.0);
+    uint8_t* f = buf;
+    uint8_t* j = f + field_bytes;
+    uint8_t* pay = j + jac_bytes;
+    uint8_t* scr = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(pay + sz.payload_worst) + 255) & ~uintptr_t(255));
+    uint8_t* sum = scr + ((sz.scratch_bytes + 255) & ~uint64_t(255));
+    if (cudaMemcpy(f, host.data(), field_bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(j, jac.data(), jac_bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        rc = SEMR_ECUDA;
+    } else {
+        semr_fieldset fs;
+        std::memset(&fs, 0, sizeof(fs));
+        fs.n_fields = 1;
+        fs.precision = SEMR_FP64;
+        fs.tau = 1e-3;
+        fs.fields[0] = reinterpret_cast<const double*>(f);
+        semr_mesh mesh;
+        std::memset(&mesh, 0, sizeof(mesh));
+        mesh.lx = lx;
+        mesh.n_elem = n_elem;
+        mesh.jac = reinterpret_cast<const double*>(j);
+        semr_outputs out;
+        std::memset(&out, 0, sizeof(out));
+        out.payload = pay;
+        out.payload_cap = sz.payload_worst;
+        out.summary = reinterpret_cast<semr_summary*>(sum);
+        out.scratch = scr;
+        out.scratch_bytes = sz.scratch_bytes;
+        g_bounds_cap_short = 64;  // the fixed sections no longer fit: every element's range test fails
+        rc = semr_reduce_async(&fs, &mesh, &out, nullptr);
+        g_bounds_cap_short = 0;
+        semr_summary h;
+        if (rc == SEMR_OK && (cudaDeviceSynchronize() != cudaSuccess ||
+                              cudaMemcpy(&h, sum, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess))
+            rc = SEMR_ECUDA;
+        if (rc == SEMR_OK) *status_out = h.status;
+    }
+    cudaFree(buf);
+    return rc;
 #endif
 }

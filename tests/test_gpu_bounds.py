@@ -16,7 +16,9 @@ lossless), the hardware-FP64 kernel, a payload too small for the codes, a
 batched launch over lx 6, 8 and 10, the no-allocation entry point, and both
 slice kernels.  For each it asserts SEMR_STATUS_BOUNDS clear and the canaries
 intact; the parent runs the same cases on the default build and requires the
-same bytes from both.
+same bytes from both.  A self-test of the checking build (a launch told a
+payload capacity short of its fixed sections, inside buffers of the full size)
+must report SEMR_STATUS_BOUNDS: the tests do fire.
 """
 import ctypes
 import hashlib
@@ -200,7 +202,10 @@ def run_cases(semr):
 def _child():
     import paper_2407_20731_b300 as semr
     assert semr.BOUNDS_BUILD and semr.semr_build_flags() == semr.SEMR_BUILD_BOUNDS
-    print("RESULT " + json.dumps(run_cases(semr)))
+    res = run_cases(semr)
+    # the range tests fire: a launch told a payload capacity short of its fixed sections
+    res["selftest"] = semr.semr_selftest_bounds()
+    print("RESULT " + json.dumps(res))
 
 
 @pytest.mark.gpu
@@ -213,6 +218,9 @@ def test_bounds_build_every_kernel_clean_and_identical():
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-3000:]
     line = [ln for ln in r.stdout.splitlines() if ln.startswith("RESULT ")][-1]
     checked = json.loads(line[len("RESULT "):])
+    rc, st = checked.pop("selftest")
+    assert rc == semr.SEMR_OK and st & semr.SEMR_STATUS_BOUNDS, (rc, st)
+    assert semr.semr_selftest_bounds()[0] == semr.SEMR_EUNSUPPORTED  # the default build has no tests
     plain = run_cases(semr)
     assert set(checked) == set(plain)
     for name, res in checked.items():
