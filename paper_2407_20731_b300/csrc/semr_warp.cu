@@ -205,27 +205,6 @@ __device__ __noinline__ uint32_t resolve_ambiguous(float* buf, uint32_t amb, uin
     return kb;
 }
 
-// Settles the rounding of the kept coefficients of mask word w (slot w & 1, row w >> 1) that the
-// FP32 bound leaves undecided (a rare path, out of line): each flagged lane's coefficient is
-// recomputed exactly, one at a time over the warp, and becomes its code times 2^s (exact), also
-// at buf[lane * 20 + w] (the lane's row of coefficients by word).  Returns the lane's coefficient.
-__device__ __noinline__ float settle_rounding(float a, bool flag, int w, float* buf, const double* __restrict__ u,
-                                              const double* __restrict__ A64, double sc, float qd, float qu,
-                                              unsigned& recomputed) {
-    const int lane = threadIdx.x & 31;
-    for (uint32_t fl = __ballot_sync(FULL, flag); fl; fl &= fl - 1) {
-        const int src = __ffs(fl) - 1;
-        const double c = exact_coef(u, src & 7, (src >> 3) + 4 * (w & 1), w >> 1, A64, sc);
-        ++recomputed;
-        if (lane == src) {
-            a = static_cast<float>(rint(c * static_cast<double>(qd))) * qu;  // ties to even; exact
-            buf[lane * 20 + w] = a;
-        }
-    }
-    __syncwarp();
-    return a;
-}
-
 // Cumulative-energy selection of an element that the fast path leaves open (a rare path,
 // out of line): the modes kept are those whose energy is at least T, the smallest energy
 // value v with sum_{a^2 <= v} a^2 > t.  FP64 mode recomputes the element's coefficients
@@ -822,10 +801,19 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
         // t' in [1e-13, 2^70] keeps s' in [-22, 35]: 2^-s' and 2^s' are normal floats (exact scalings)
         const float qd = pow2f(-sps), qu = pow2f(sps);
 
-        // ---- keep decisions; FP64 mode recomputes exactly what FP32 cannot settle (the keep
-        // decisions here, the roundings of kept coefficients in the quantisation below)
+        // ---- keep decisions; FP64 mode recomputes exactly what FP32 cannot settle
         uint32_t kb = 0;  // keep bit (8 s + r)
-        float Mq = 0.0f;  // FP64 mode: the bound M in units of the step (the rounding screen)
+        // FP64 mode: the rounding decisions of the lane's kept coefficients (a few per element,
+        // so a loop over the lane's keep bits), with Mq the bound in units of the step
+        auto screen_roundings = [&](uint32_t keep, float Mq) -> uint32_t {
+            uint32_t amb = 0;
+            for (uint32_t kk = keep; kk; kk &= kk - 1) {
+                const int b = __ffs(kk) - 1;
+                const float y = fabsf(pick(a2, 2 * (b & 7) + (b >> 3))) * qd;  // word s + 2 r of bit 8 s + r
+                if (fabsf((y - floorf(y)) - 0.5f) <= Mq + y * 1.2e-7f) amb |= 1u << b;
+            }
+            return amb;
+        };
         if constexpr (CUM) {
             if (emode == 1) {
                 // cumulative-energy truncation: keep the modes whose energy is at least T, the
@@ -936,10 +924,22 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
 #pragma unroll
                     for (int b = 0; b < 16; ++b) kb |= (absbits(b) >= vb ? 1u : 0u) << b;
                 }
-                // FP64 mode: the roundings of the kept coefficients are screened in the quantisation
-                // (the general path's values are exact codes x 2^s, which the screen passes)
-                if constexpr (DF) Mq = M * qd * 1.000001f;
-                (void)exactv;
+                if constexpr (DF) {  // the rounding decisions of the kept coefficients
+                    if (!exactv) {
+                        const uint32_t amb = screen_roundings(kb, M * qd * 1.000001f);
+                        if (__any_sync(FULL, amb != 0u)) {
+#pragma unroll
+                            for (int r = 0; r < 8; ++r) {
+                                tb[lane * 17 + r] = a2[r].x;
+                                tb[lane * 17 + 8 + r] = a2[r].y;
+                            }
+                            kb = resolve_ambiguous(tb, amb, kb, p.fields[f] + static_cast<uint64_t>(e) * WN3,
+                                                   A.tab.A64, pow2d(-ke), t, qd, qu, recomputed, true);
+#pragma unroll
+                            for (int r = 0; r < 8; ++r) a2[r] = make_float2(tb[lane * 17 + r], tb[lane * 17 + 8 + r]);
+                        }
+                    }
+                }
             }
         } else if (emode == 1) {
             if constexpr (DF) {
@@ -951,7 +951,6 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
                 const float umax_e = __uint_as_float(0x3f800000u | ((hmax & 0xfffffu) << 3));
                 const float M = kMarg * umax_e * 1.000002f;
                 const float Mg = M + g * 2.4e-7f;  // plus the float rounding of g +- M
-                Mq = Mg * qd;
                 uint32_t amb = 0;
 #pragma unroll
                 for (int s = 0; s < 2; ++s)
@@ -962,6 +961,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
                         if (aa >= g + Mg) kb |= 1u << b;            // surely kept
                         else if (!(aa < g - Mg)) amb |= 1u << b;   // undecided
                     }
+                amb |= screen_roundings(kb, Mg * qd);
                 // exact (float-pair) coefficient of each ambiguous mode (rare): out of line, with
                 // the lane's coefficients passed through the warp's transpose buffer (free here)
                 if (__any_sync(FULL, amb != 0u)) {
@@ -1094,42 +1094,18 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
             }
             const uint32_t lt_mask = (1u << lane) - 1u;
             uint32_t run = 0;  // codes of the words before wi (the words come in increasing order)
-            bool settled_any = false;
             while (nzw) {
                 const int wi = __ffs(nzw) - 1;
                 nzw &= nzw - 1;
                 const uint32_t wd = smask[wi];
-                float a = 0.0f;
-                if constexpr (DF) {
-                    // a kept coefficient whose rounding the FP32 bound cannot settle is recomputed
-                    a = tb[lane * 20 + wi];
-                    const float y = fabsf(a) * qd;
-                    const bool ra = ((wd >> lane) & 1u) && fabsf((y - floorf(y)) - 0.5f) <= Mq + y * 1.2e-7f;
-                    if (__any_sync(FULL, ra)) {
-                        a = settle_rounding(a, ra, wi, tb, p.fields[f] + static_cast<uint64_t>(e) * WN3, A.tab.A64,
-                                            pow2d(-ke), qd, qu, recomputed);
-                        settled_any = true;
-                    }
-                }
                 if ((wd >> lane) & 1u) {
-                    if constexpr (!DF) a = pick(a2, wi);
+                    const float a = DF ? tb[lane * 20 + wi] : pick(a2, wi);
                     const float c = (a * qd + 12582912.0f) - 12582912.0f;  // round half to even (|y| < 2^22)
                     const uint32_t rank = run + __popc(wd & lt_mask);
                     if (qwrite) qdst[rank] = static_cast<int16_t>(c);
                     if (rank < static_cast<uint32_t>(wsparse<DF>())) skl[rank] = make_int2(lane + 32 * wi, __float_as_int(c));
                 }
                 run += __popc(wd);
-            }
-            if constexpr (DF) {
-                if (settled_any) {  // the dense reconstruction reads the kept coefficients from a2
-                    const float4* arow = reinterpret_cast<const float4*>(tb + lane * 20);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float4 v = arow[q];
-                        a2[2 * q] = make_float2(v.x, v.y);
-                        a2[2 * q + 1] = make_float2(v.z, v.w);
-                    }
-                }
             }
         }
         if (staged) atop += n_e;
