@@ -107,6 +107,10 @@ struct GSmem {
 
 // exchange slots of a group (floats/words): each written by warp w at [slot + w]
 constexpr int XH = 0, XS = 2, XSL = 4, XC = 6, XE = 8, XEL = 10, XL = 12, XLL = 14, XA = 16;
+// cumulative truncation (before XC..XLL are used for the element): the sums R, sum |a| and the count
+// left, two alternating pairs for the per-extraction maxima, the smallest kept value; the general
+// path's 64-bit sums use the words XC .. XC + 7 (two alternating pairs of two-word values)
+constexpr int XR = 18, XB = 20, XN = 22, XM = 24, XV = 28;
 
 template <int WPE>
 __device__ __forceinline__ void gsync(int gi) {
@@ -268,6 +272,171 @@ __device__ __noinline__ float g_settle(float a, bool flag, float* M, int w0, int
     return a;
 }
 
+// Sum over the group of a per-warp value (both warps of an lx = 10 group call it; slot pair XS..
+// in the exchange words, alternating by `parity` so that one barrier per call suffices).
+template <int WPE>
+__device__ __forceinline__ unsigned long long group_sum_u62(unsigned long long v, uint32_t* xu, int wg, int gi,
+                                                           int parity) {
+    v = warp_sum_u62(v);
+    if constexpr (WPE == 1) {
+        return v;
+    } else {
+        uint32_t* slot = xu + XC + 4 * parity;
+        if ((threadIdx.x & 31) == 0) {
+            slot[2 * wg] = static_cast<uint32_t>(v);
+            slot[2 * wg + 1] = static_cast<uint32_t>(v >> 32);
+        }
+        gsync<WPE>(gi);
+        return (static_cast<unsigned long long>(slot[1]) << 32 | slot[0]) +
+               (static_cast<unsigned long long>(slot[3]) << 32 | slot[2]);
+    }
+}
+
+// Cumulative-energy selection of an element that the fast path leaves open (a rare path, out
+// of line; every thread of the group calls it): FP64 mode recomputes the element's coefficients
+// 2^-ke A x A x A u in hardware FP64 from its doubles (reread from L2) through the group's buffer
+// D (the transpose buffers, as doubles), the FP32 form takes its FP32 coefficients am as they
+// are.  Energies become 64-bit fixed-point keys floor(a^2 2^K), t 2^K in [2^47, 2^48) (exact
+// integer sums in any order), and a bisection on the key value finds T, the smallest key whose
+// sum of keys up to it exceeds floor(t 2^K).  Returns the lane's keep bits (bit kk: mode
+// 32 (w0 + kk) + lane); FP64 mode also rewrites the group's mode-ordered values M: each kept
+// mode its code times 2^s' (exact), every other mode its value rounded to float.
+template <int LX, int WPE, bool DF>
+__device__ __noinline__ uint32_t g_cum_general(float* M, const float* am, uint32_t vm, int w0, int wg, int gi, int g,
+                                               int P0, int P1, bool v1, uint32_t* xu,
+                                               const double* __restrict__ u, const double* __restrict__ A64,
+                                               double sc, double td, float qd, float qu, unsigned& recomputed) {
+    constexpr int N3 = LX * LX * LX, NP = LX * LX, MW = (N3 + 31) / 32, WPW = (MW + WPE - 1) / WPE;
+    const int lane = threadIdx.x & 31;
+    double a64[WPW];
+    if constexpr (DF) {
+        double* D = reinterpret_cast<double*>(M);  // N3 doubles (the transpose buffers)
+        double y[2][LX];
+        gsync<WPE>(gi);  // every read of M as floats is done
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {  // along i: pencils (k, j) -> D[k][j][p]
+            const int P = s ? P1 : P0;
+            if (s == 0 || v1) {
+                const double* row = u + static_cast<size_t>(P) * LX;
+                double x[LX];
+#pragma unroll
+                for (int i = 0; i < LX; ++i) x[i] = __ldg(row + i) * sc;
+#pragma unroll
+                for (int pp = 0; pp < LX; ++pp) {
+                    double acc = 0.0;
+#pragma unroll
+                    for (int i = 0; i < LX; ++i) acc = fma(A64[pp * LX + i], x[i], acc);
+                    y[s][pp] = acc;
+                }
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+            if (s == 0 || v1)
+#pragma unroll
+                for (int pp = 0; pp < LX; ++pp) D[(s ? P1 : P0) * LX + pp] = y[s][pp];
+        gsync<WPE>(gi);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {  // along j: pencils (k, p) -> D[k][q][p]
+            const int P = s ? P1 : P0;
+            if (s == 0 || v1) {
+                const int k = P / LX, pp = P % LX;
+                double x[LX];
+#pragma unroll
+                for (int jj = 0; jj < LX; ++jj) x[jj] = D[(k * LX + jj) * LX + pp];
+#pragma unroll
+                for (int q = 0; q < LX; ++q) {
+                    double acc = 0.0;
+#pragma unroll
+                    for (int jj = 0; jj < LX; ++jj) acc = fma(A64[q * LX + jj], x[jj], acc);
+                    y[s][q] = acc;
+                }
+            }
+        }
+        gsync<WPE>(gi);
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+            if (s == 0 || v1) {
+                const int P = s ? P1 : P0, k = P / LX, pp = P % LX;
+#pragma unroll
+                for (int q = 0; q < LX; ++q) D[(k * LX + q) * LX + pp] = y[s][q];
+            }
+        gsync<WPE>(gi);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {  // along k: pencils (q, p) -> coefficient r, mode P + NP r
+            const int P = s ? P1 : P0;
+            if (s == 0 || v1) {
+                const int q = P / LX, pp = P % LX;
+                double x[LX];
+#pragma unroll
+                for (int kk = 0; kk < LX; ++kk) x[kk] = D[(kk * LX + q) * LX + pp];
+#pragma unroll
+                for (int r = 0; r < LX; ++r) {
+                    double acc = 0.0;
+#pragma unroll
+                    for (int kk = 0; kk < LX; ++kk) acc = fma(A64[r * LX + kk], x[kk], acc);
+                    y[s][r] = acc;
+                }
+            }
+        }
+        gsync<WPE>(gi);
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+            if (s == 0 || v1)
+#pragma unroll
+                for (int r = 0; r < LX; ++r) D[(s ? P1 : P0) + NP * r] = y[s][r];
+        gsync<WPE>(gi);
+#pragma unroll
+        for (int kk = 0; kk < WPW; ++kk) a64[kk] = ((vm >> kk) & 1u) ? D[32 * (w0 + kk) + lane] : 0.0;
+        gsync<WPE>(gi);  // every double is read before M is rewritten as floats
+        recomputed += N3;
+    } else {
+#pragma unroll
+        for (int kk = 0; kk < WPW; ++kk) a64[kk] = ((vm >> kk) & 1u) ? static_cast<double>(am[kk]) : 0.0;
+    }
+    int ex;
+    frexp(td, &ex);  // td in [2^(ex - 1), 2^ex)
+    const double sK = ldexp(1.0, 48 - ex);
+    const unsigned long long tt = static_cast<unsigned long long>(td * sK);
+    constexpr unsigned long long kClamp = 1ull << 50;
+    unsigned long long key[WPW];
+    unsigned long long own = 0ull;
+#pragma unroll
+    for (int kk = 0; kk < WPW; ++kk) {
+        const double v = a64[kk] * a64[kk] * sK;
+        key[kk] = v >= static_cast<double>(kClamp) ? kClamp : static_cast<unsigned long long>(v);
+        own += key[kk];
+    }
+    int par = 0;
+    uint32_t kb = 0;
+    if (group_sum_u62<WPE>(own, xu, wg, gi, par) > tt) {  // else every energy fits the budget
+        unsigned long long lo = 1, hi = kClamp;  // smallest v with sum_{key <= v} key > tt
+        while (lo < hi) {
+            const unsigned long long mid = lo + (hi - lo) / 2;
+            unsigned long long sm = 0ull;
+#pragma unroll
+            for (int kk = 0; kk < WPW; ++kk) sm += key[kk] <= mid ? key[kk] : 0ull;
+            par ^= 1;
+            if (group_sum_u62<WPE>(sm, xu, wg, gi, par) > tt) hi = mid;
+            else lo = mid + 1;
+        }
+#pragma unroll
+        for (int kk = 0; kk < WPW; ++kk) kb |= (key[kk] >= lo ? 1u : 0u) << kk;
+    }
+    kb &= vm;
+    if constexpr (DF) {
+#pragma unroll
+        for (int kk = 0; kk < WPW; ++kk)
+            if ((vm >> kk) & 1u)
+                M[32 * (w0 + kk) + lane] = ((kb >> kk) & 1u)
+                                               ? static_cast<float>(rint(a64[kk] * static_cast<double>(qd))) * qu
+                                               : static_cast<float>(a64[kk]);
+    }
+    gsync<WPE>(gi);  // (M complete; the exchange words are free again)
+    (void)g;
+    return kb;
+}
+
 template <int LX, int MODE>
 struct GOcc {  // CTAs per SM the register budget aims at
     static constexpr int value = LX <= 6 ? (MODE ? 3 : 5) : 3;
@@ -276,7 +445,7 @@ struct GOcc {  // CTAs per SM the register budget aims at
 // BATCH = false: one reduction, parameters in A.p.  BATCH = true: the work queue q of
 // several reductions of this lx (each with its own descriptor, payload and scratch; they
 // share one code staging).
-template <int LX, int MODE, bool BATCH>
+template <int LX, int MODE, bool BATCH, bool CUM = false>
 __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
     reduce_group_kernel(const __grid_constant__ GArgs<LX> A, const BatchQueue q) {
     using C = GCfg<LX>;
@@ -668,7 +837,128 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
             if (w0 + kk < MW && 32 * (w0 + kk) + lane < N3) vm |= 1u << kk;
         uint32_t kb = 0;
         float Mq = 0.0f;  // FP64 mode: the bound in units of the step (the rounding screen, in the quantisation)
-        if (emode == 1) {
+        if constexpr (CUM) {
+            if (emode == 1) {
+                // cumulative-energy truncation, as the lx = 8 warp kernel: keep every mode above gb
+                // (surely a^2 > t), then extract the group's largest remaining |a| one at a time until
+                // the sum R of the squares left fits t; FP64 mode takes the result where the FP32 bound
+                // settles it, else (and beyond kCumIters extractions) the general path decides
+                constexpr int kCumIters = 48;
+                float M32 = 0.0f, gb;
+                if constexpr (DF) {
+                    constexpr float kMarg = (3.0f * (LX / 2 + 2) + 2.0f) * 5.9604645e-8f * 2.8285f * 2.0f;
+                    const float umax_e = __uint_as_float(0x3f800000u | ((hmax & 0xfffffu) << 3));
+                    M32 = kMarg * umax_e * 1.000002f;
+                    gb = gth + (M32 + gth * 2.4e-7f);
+                    Mq = M32 * qd * 1.000001f;
+                } else {
+                    gb = __uint_as_float(__float_as_uint(gth) + 1u);
+                }
+                uint32_t rem = 0;
+                float rs = 0.0f, sa = 0.0f;
+#pragma unroll
+                for (int kk = 0; kk < WPW; ++kk) {
+                    const float x = fabsf(am[kk]);
+                    const bool low = ((vm >> kk) & 1u) && x < gb;
+                    rem |= (low ? 1u : 0u) << kk;
+                    rs = low ? fmaf(x, x, rs) : rs;
+                    sa = low ? sa + x : sa;
+                }
+                float R = warp_sum_f(rs), sabs = warp_sum_f(sa);
+                int nrem = static_cast<int>(__reduce_add_sync(FULL, static_cast<unsigned>(__popc(rem))));
+                if constexpr (WPE > 1) {
+                    if (lane == 0) {
+                        xf[XR + wg] = R;
+                        xf[XB + wg] = sabs;
+                        xu[XN + wg] = static_cast<uint32_t>(nrem);
+                    }
+                    gsync<WPE>(gi);
+                    R = xf[XR] + xf[XR + 1];
+                    sabs = xf[XB] + xf[XB + 1];
+                    nrem = static_cast<int>(xu[XN] + xu[XN + 1]);
+                }
+                const float R0 = R;
+                int it = 0;
+                float v = 0.0f;
+                uint32_t gm = 0;
+                bool done = R <= t.h, open = false;
+                for (;;) {
+                    uint32_t mk = 0;
+#pragma unroll
+                    for (int kk = 0; kk < WPW; ++kk)
+                        mk = ((rem >> kk) & 1u) ? max(mk, __float_as_uint(am[kk]) & 0x7fffffffu) : mk;
+                    const uint32_t wm = __reduce_max_sync(FULL, mk);
+                    bool mine = true;  // this warp holds the one extracted
+                    gm = wm;
+                    if constexpr (WPE > 1) {
+                        if (lane == 0) xu[XM + 2 * (it & 1) + wg] = wm;
+                        gsync<WPE>(gi);
+                        const uint32_t m0 = xu[XM + 2 * (it & 1)], m1 = xu[XM + 2 * (it & 1) + 1];
+                        gm = max(m0, m1);
+                        mine = wg == 0 ? m0 == gm : m0 != gm;
+                    }
+                    if (done) break;
+                    if (it == kCumIters || gm == 0u) {
+                        open = true;
+                        break;
+                    }
+                    if (mine && lane == __ffs(__ballot_sync(FULL, mk == gm)) - 1) {
+                        uint32_t hit = 0;
+#pragma unroll
+                        for (int kk = 0; kk < WPW; ++kk)
+                            hit |= (((rem >> kk) & 1u) && (__float_as_uint(am[kk]) & 0x7fffffffu) == gm ? 1u : 0u) << kk;
+                        rem &= ~(hit & (0u - hit));
+                    }
+                    v = __uint_as_float(gm);
+                    R = fmaf(-v, v, R);
+                    sabs -= v;
+                    --nrem;
+                    ++it;
+                    done = R <= t.h;
+                }
+                bool settled = !open;
+                if constexpr (DF) {
+                    if (settled) {
+                        float vk = v;
+                        if (it == 0) {  // the smallest kept: the smallest above gb
+                            uint32_t mn = 0x7f000000u;
+#pragma unroll
+                            for (int kk = 0; kk < WPW; ++kk)
+                                mn = (((vm & ~rem) >> kk) & 1u) ? min(mn, __float_as_uint(am[kk]) & 0x7fffffffu) : mn;
+                            mn = __reduce_min_sync(FULL, mn);
+                            if constexpr (WPE > 1) {
+                                if (lane == 0) xu[XV + wg] = mn;
+                                gsync<WPE>(gi);
+                                mn = min(xu[XV], xu[XV + 1]);
+                            }
+                            vk = __uint_as_float(mn);
+                        }
+                        const float wn = __uint_as_float(gm);
+                        const float rho = R0 * (6e-5f + 1.2e-7f * static_cast<float>(it)) + 2.4e-7f * t.h;
+                        const float B = 2.0f * M32 * sabs * 1.0001f + static_cast<float>(nrem) * M32 * M32 + rho;
+                        const float d1 = t.h - R;
+                        settled = d1 * 0.999999f > B;
+                        if (vk < 0x1p126f) {
+                            const float lv = fmaxf(vk - M32, 0.0f);
+                            settled = settled && (lv * lv * 0.999999f - d1 * 1.000001f) > B &&
+                                      (vk - wn) > 2.0f * M32 * 1.000001f + vk * 1.2e-7f;
+                        }
+                    }
+                }
+                if (!settled) {
+                    kb = g_cum_general<LX, WPE, DF>(M, am, vm, w0, wg, gi, g, P0, P1, v1, xu,
+                                                    p.fields[f] + static_cast<uint64_t>(e) * N3, A.tab.A64,
+                                                    pow2d(-ke), static_cast<double>(t.h) + static_cast<double>(t.l),
+                                                    qd, qu, recomputed);
+                } else {
+                    const uint32_t vb = __float_as_uint(it ? v : gb);
+#pragma unroll
+                    for (int kk = 0; kk < WPW; ++kk)
+                        kb |= ((__float_as_uint(am[kk]) & 0x7fffffffu) >= vb ? 1u : 0u) << kk;
+                    kb &= vm;
+                }
+            }
+        } else if (emode == 1) {
             if constexpr (DF) {
                 constexpr float kMarg = (3.0f * (LX / 2 + 2) + 2.0f) * 5.9604645e-8f * 2.8285f * 2.0f;
                 const float umax_e = __uint_as_float(0x3f800000u | ((hmax & 0xfffffu) << 3));
@@ -1230,7 +1520,7 @@ GTables<LX> make_gtables() {
 }
 
 // Launch of one reduction (q empty) or of a batch queue (BATCH; p unused but for stage_ctas).
-template <int LX, int MODE, bool BATCH>
+template <int LX, int MODE, bool BATCH, bool CUM = false>
 int launch_group_mode(const LaunchParams& p, const BatchQueue& q, uint64_t stage_ctas, void* stream) {
     using SM = GSmem<LX, MODE != 0>;
     GArgs<LX> a;
@@ -1244,7 +1534,7 @@ int launch_group_mode(const LaunchParams& p, const BatchQueue& q, uint64_t stage
     }
     const uint64_t total = BATCH ? q.total_tiles : a.total_tiles;
     cudaError_t err;
-    auto kern = reduce_group_kernel<LX, MODE, BATCH>;
+    auto kern = reduce_group_kernel<LX, MODE, BATCH, CUM>;
     if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes)) != cudaSuccess)
         return (int)err;
     int dev = 0, sms = 0, per_sm = 0;
@@ -1272,7 +1562,7 @@ int group_tile(int lx) {
 }
 
 bool group_applicable(const LaunchParams& p) {
-    if (group_tile(p.lx) == 0 || p.cumulative || p.lossless || p.width != 2) return false;
+    if (group_tile(p.lx) == 0 || p.lossless || p.width != 2) return false;
     if (p.precision != SEMR_FP64 && p.precision != SEMR_FP32) return false;
     for (int f = 0; f < p.n_fields; ++f)
         if (reinterpret_cast<uintptr_t>(p.fields[f]) & 15u) return false;  // bulk copies need 16-byte aligned blocks
@@ -1283,6 +1573,15 @@ int launch_reduce_group(const LaunchParams& p, void* stream) {
     const bool df = p.precision != SEMR_FP32;
     const BatchQueue q{};
     const uint64_t sc = static_cast<uint64_t>(p.stage_ctas);
+    if (p.cumulative) {  // cumulative-energy truncation (single launches only)
+        switch (p.lx) {
+            case 6: return df ? launch_group_mode<6, 1, false, true>(p, q, sc, stream)
+                              : launch_group_mode<6, 0, false, true>(p, q, sc, stream);
+            case 10: return df ? launch_group_mode<10, 1, false, true>(p, q, sc, stream)
+                               : launch_group_mode<10, 0, false, true>(p, q, sc, stream);
+            default: return (int)cudaErrorInvalidValue;
+        }
+    }
     switch (p.lx) {
         case 6: return df ? launch_group_mode<6, 1, false>(p, q, sc, stream) : launch_group_mode<6, 0, false>(p, q, sc, stream);
         case 10: return df ? launch_group_mode<10, 1, false>(p, q, sc, stream) : launch_group_mode<10, 0, false>(p, q, sc, stream);

@@ -63,7 +63,7 @@ def test_thresholds_three_fields(tau):
     _compare(fields, jac, 8, tau)
 
 
-@pytest.mark.parametrize("lx,tau", [(8, 0.3), (8, 1e-2), (12, 0.1), (5, 0.2)])
+@pytest.mark.parametrize("lx,tau", [(8, 0.3), (8, 1e-2), (12, 0.1), (5, 0.2), (6, 0.3), (10, 1e-2)])
 def test_flat_spectra_bisection(lx, tau):
     fields, jac = _white(150, lx, 1, seed=80 + lx)
     _compare(fields, jac, lx, tau)
@@ -78,6 +78,15 @@ def test_many_tiles():
     fields, jac = make_case(20000, 8, 2, seed=5)
     res, _ = _compare(fields, jac, 8, 1e-3)
     assert res.summary.recomputed >= 512
+
+
+@pytest.mark.parametrize("lx,n_elem,tau", [(6, 6000, 1e-3), (10, 2500, 1e-4)])
+def test_many_tiles_warp_group(lx, n_elem, tau):
+    """The warp-group kernel (lx = 6: one warp per element, lx = 10: two) over
+    many look-back tiles: boundaries settled from the FP32 coefficients, the
+    rest through the general path, bit-exact with the oracle outside kind 4."""
+    fields, jac = make_case(n_elem, lx, 2, seed=40 + lx)
+    _compare(fields, jac, lx, tau)
 
 
 def test_keeps_more_than_threshold_form():
@@ -124,7 +133,8 @@ def test_native_path_rejects_cumulative():
         semr.reduce([fields[0]], jac, 6, 1e-3, precision=semr.SEMR_FP64_NATIVE, cumulative=True)
 
 
-@pytest.mark.parametrize("lx,tau,white", [(8, 1e-3, False), (8, 1e-5, False), (6, 1e-2, False), (8, 0.05, True)])
+@pytest.mark.parametrize("lx,tau,white", [(8, 1e-3, False), (8, 1e-5, False), (6, 1e-2, False), (8, 0.05, True),
+                                          (10, 1e-3, False), (6, 0.05, True)])
 def test_fp32_form_budget(lx, tau, white):
     """FP32 precision form: with the oracle's FP64 coefficients a, the modes the
     GPU dropped fit the budget and the smallest kept one does not, up to the
