@@ -205,8 +205,8 @@ __device__ __noinline__ uint32_t resolve_ambiguous(float* buf, uint32_t amb, uin
     return kb;
 }
 
-// Cumulative-energy selection of an element that the fast path leaves open (a rare path,
-// out of line): the modes kept are those whose energy is at least T, the smallest energy
+// Cumulative-energy selection of an element that the fast path leaves open (a rare path; inlined,
+// so that its call does not make the common path save registers around it): the modes kept are those whose energy is at least T, the smallest energy
 // value v with sum_{a^2 <= v} a^2 > t.  FP64 mode recomputes the element's coefficients
 // a' = 2^-ke A x A x A u in hardware FP64 from its doubles (reread from L2); the FP32 form
 // takes its FP32 coefficients, passed at buf[lane * 17 + 8 s + r], as they are (their
@@ -217,7 +217,7 @@ __device__ __noinline__ uint32_t resolve_ambiguous(float* buf, uint32_t amb, uin
 // each kept coefficient's code times 2^s (exact, so the quantisation reproduces the code of
 // the FP64 value) and every other coefficient rounded to float.
 template <bool DF>
-__device__ __noinline__ uint32_t cum_general(float* buf, const double* __restrict__ u, const double* __restrict__ A64,
+__device__ __forceinline__ uint32_t cum_general(float* buf, const double* __restrict__ u, const double* __restrict__ A64,
                                              double sc, double td, float qd, float qu, unsigned& recomputed) {
     const int lane = threadIdx.x & 31, j = lane & 7, k0 = lane >> 3;
     double a[16];  // the lane's coefficients, b = 8 s + r: mode (p, q, r) = (j, k0 + 4 s, r)
