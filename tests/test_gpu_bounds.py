@@ -10,11 +10,12 @@ summary, scratch, reconstruction, slice image and values -- is allocated
 with 4 KiB of canary bytes after its end.
 
 A child process loads the checking build (SEMR_BOUNDS=1) and runs the cases:
-the warp kernel (lx = 8, FP64 mode and FP32 form), the warp-group kernel
-(lx = 6 and 10), the CTA kernel (lx = 5 and 7, cumulative truncation,
-lossless), the hardware-FP64 kernel, a payload too small for the codes, a
-batched launch over lx 6, 8 and 10, the no-allocation entry point, and both
-slice kernels.  For each it asserts SEMR_STATUS_BOUNDS clear and the canaries
+the warp kernel (lx = 8, FP64 mode and FP32 form, threshold and cumulative
+truncation, the cumulative cases large enough to reach its general path), the
+warp-group kernel (lx = 6 and 10, both truncations), the CTA kernel (lx = 5
+and 7, cumulative truncation, lossless), the hardware-FP64 kernel, a payload
+too small for the codes, a batched launch over lx 6, 8 and 10, the
+no-allocation entry point, and both slice kernels.  For each it asserts SEMR_STATUS_BOUNDS clear and the canaries
 intact; the parent runs the same cases on the default build and requires the
 same bytes from both.  A self-test of the checking build (a launch told a
 payload capacity short of its fixed sections, inside buffers of the full size)
@@ -185,7 +186,11 @@ def run_cases(semr):
         "group_lx10_fp64": lambda: _reduce_case(semr, 10, 200, 2, 1e-4, P64, recon=True, seed=5),
         "cta_lx7_fp64": lambda: _reduce_case(semr, 7, 100, 1, 1e-3, P64, recon=True, seed=6),
         "cta_lx5_fp32": lambda: _reduce_case(semr, 5, 90, 2, 1e-4, P32, seed=7),
-        "cta_lx8_cumulative": lambda: _reduce_case(semr, 8, 300, 1, 1e-3, P64, cumulative=True, seed=8),
+        "warp_lx8_cumulative_fp64": lambda: _reduce_case(semr, 8, 3000, 1, 1e-4, P64, cumulative=True, recon=True, seed=8),
+        "warp_lx8_cumulative_fp32": lambda: _reduce_case(semr, 8, 300, 2, 1e-3, P32, cumulative=True, seed=18),
+        "group_lx6_cumulative": lambda: _reduce_case(semr, 6, 2000, 1, 1e-4, P64, cumulative=True, recon=True, seed=19),
+        "group_lx10_cumulative": lambda: _reduce_case(semr, 10, 600, 2, 1e-4, P64, cumulative=True, seed=20),
+        "cta_lx7_cumulative": lambda: _reduce_case(semr, 7, 200, 1, 1e-3, P64, cumulative=True, seed=22),
         "cta_lx8_lossless": lambda: _reduce_case(semr, 8, 50, 1, 0.0, P64, recon=True, seed=9),
         "native_lx8_fp64": lambda: _reduce_case(semr, 8, 200, 1, 1e-3, semr.SEMR_FP64_NATIVE, seed=10),
         "warp_lx8_overflow": lambda: _reduce_case(
