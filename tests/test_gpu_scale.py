@@ -8,9 +8,10 @@ exact power of two 2^k scales each coefficient by 2^k and each energy by
 barring under- or overflow) masks, counts and codes are unchanged and every
 step moves by exactly k.  The library reads each element as u 2^-ke (ke the
 binary exponent of its largest |u|), so its payloads must show the same
-invariance bit for bit, in both precisions and for the warp kernel (lx = 8)
-as well as the CTA kernels (lx = 6, 10).  Norms scale by exactly 2^2k (e2_e,
-E_e) and 2^k (Linf_e).
+invariance bit for bit, in both precisions, for the warp kernel (lx = 8) and
+the warp-group kernel (lx = 6, 10), and with either truncation (the
+cumulative budget t = tau S_e scales by 2^2k like every energy).  Norms scale
+by exactly 2^2k (e2_e, E_e) and 2^k (Linf_e).
 """
 import numpy as np
 import pytest
@@ -26,12 +27,13 @@ SCALES = [-120, -80, -40, 40, 80]
 NOSTEP = -32768
 
 
+@pytest.mark.parametrize("cumulative", [False, True])
 @pytest.mark.parametrize("precision", [semr.SEMR_FP64, semr.SEMR_FP32])
 @pytest.mark.parametrize("lx", [6, 8, 10])
-def test_power_of_two_scaling_invariance(lx, precision):
+def test_power_of_two_scaling_invariance(lx, precision, cumulative):
     tau = 1e-3
     fields, jac = make_case(301, lx, 2, seed=20 + lx)
-    base, _ = run_gpu(fields, jac, lx, tau, precision=precision, recon=False)
+    base, _ = run_gpu(fields, jac, lx, tau, precision=precision, recon=False, cumulative=cumulative)
     assert base.summary.status == 0
     b = oracle.sections(base.payload)
     kept = b["steps"] != NOSTEP
@@ -39,7 +41,7 @@ def test_power_of_two_scaling_invariance(lx, precision):
     j_np = jac.cpu().numpy()
     for k in SCALES:
         scaled = fields * (2.0 ** k)  # exact: no value under- or overflows
-        res, _ = run_gpu(scaled, jac, lx, tau, precision=precision, recon=False)
+        res, _ = run_gpu(scaled, jac, lx, tau, precision=precision, recon=False, cumulative=cumulative)
         assert res.summary.status == 0, (k, res.summary.status)
         g = oracle.sections(res.payload)
         assert np.array_equal(g["masks"], b["masks"]), k
@@ -56,7 +58,7 @@ def test_power_of_two_scaling_invariance(lx, precision):
         if precision == semr.SEMR_FP64:
             # FP64 mode against the oracle on the scaled snapshot itself
             f_np = scaled.cpu().numpy()
-            o = oracle.reduce(f_np, j_np, tau, fragile_cap=100000)
+            o = oracle.reduce(f_np, j_np, tau, fragile_cap=100000, cumulative=cumulative)
             compare_payloads(res.payload, o.payload, o.fragile)
 
 
