@@ -40,9 +40,9 @@ def snapshot():
     torch.cuda.empty_cache()
 
 
-def _run(fields, jac, precision):
+def _run(fields, jac, precision, cumulative=False):
     bufs = semr.alloc_buffers(LX, E, F, TAU, fields.device)
-    semr.reduce_async([fields[i] for i in range(F)], jac, LX, TAU, bufs, precision)
+    semr.reduce_async([fields[i] for i in range(F)], jac, LX, TAU, bufs, precision, cumulative=cumulative)
     torch.cuda.synchronize()
     sm = semr.summary_from(bufs)
     n = int(sm.payload_bytes)
@@ -78,7 +78,7 @@ def _sample(seed=7, n=1500):
     return np.unique(np.concatenate([rng.choice(E, n, replace=False), edges]))
 
 
-def _check_any_size(sm, payload, er, fields):
+def _check_any_size(sm, payload, er, fields, cumulative=False):
     h, masks, steps, counts, codes = _sections(payload)
     assert sm.status == 0
     # counts are the masks' popcounts; the code section holds exactly their sum
@@ -87,9 +87,11 @@ def _check_any_size(sm, payload, er, fields):
     total = int(counts.astype(np.int64).sum())
     assert h["code_total"] == total == sm.code_total
     assert sm.payload_bytes == h["code_base"] + 2 * total == payload.size
-    # every kept code is a nonzero integer within the quantisation's range
+    # every kept code is an integer within the quantisation's range, and nonzero under threshold
+    # truncation (a kept a^2 >= t >= q^2); the cumulative budget can keep modes below half a step
     assert codes.size == total
-    assert np.all(codes != 0)
+    if not cumulative:
+        assert np.all(codes != 0)
     assert np.abs(codes.astype(np.int32)).max() <= 2.0 / math.sqrt(TAU)
     # per field: kept codes, sums and maxima of the element reports
     umax = fields.reshape(F, -1).abs().amax(dim=1).cpu().numpy()
@@ -105,10 +107,11 @@ def _check_any_size(sm, payload, er, fields):
     return masks, steps, counts, codes
 
 
-def _oracle_sample(fields, jac, idx):
+def _oracle_sample(fields, jac, idx, cumulative=False):
     f_np = fields[:, torch.as_tensor(idx, device=fields.device)].cpu().numpy()
     j_np = jac[torch.as_tensor(idx, device=jac.device)].cpu().numpy()
-    o = oracle.reduce(f_np, j_np, TAU, want_recon=False, want_coeffs=False, fragile_cap=100000)
+    o = oracle.reduce(f_np, j_np, TAU, want_recon=False, want_coeffs=False, fragile_cap=100000,
+                      cumulative=cumulative)
     return f_np, j_np, o
 
 
@@ -126,14 +129,18 @@ def _per_element(idx, masks, steps, counts, codes, osec):
             yield f, k, same, codes[offs[i]:offs[i + 1]], osec["codes"][o_offs[j]:o_offs[j + 1]]
 
 
-def test_full_size_fp64_mode(snapshot):
-    """FP64 mode (the benchmark's): sampled element-fields bit-exact outside the
-    oracle's fragile entries; their reports within the parity tolerances."""
+@pytest.mark.parametrize("cumulative", [False, True])
+def test_full_size_fp64_mode(snapshot, cumulative):
+    """FP64 mode (the benchmark's), with threshold truncation and with the
+    cumulative-energy variant (the bench's cumulative leg): sampled
+    element-fields bit-exact outside the oracle's fragile entries; their
+    reports within the parity tolerances."""
     fields, jac = snapshot
-    sm, payload, er = _run(fields, jac, semr.SEMR_FP64)
-    masks, steps, counts, codes = _check_any_size(sm, payload, er, fields)
+    sm, payload, er = _run(fields, jac, semr.SEMR_FP64, cumulative)
+    assert bool(oracle.parse_header(payload)["flags"] & semr.SEMR_PAYLOAD_CUMULATIVE) == cumulative
+    masks, steps, counts, codes = _check_any_size(sm, payload, er, fields, cumulative)
     idx = _sample()
-    f_np, j_np, o = _oracle_sample(fields, jac, idx)
+    f_np, j_np, o = _oracle_sample(fields, jac, idx, cumulative)
     osec = oracle.sections(o.payload)
     fragile = {(int(f), int(k)) for f, k, _, _ in o.fragile}
     for f, k, same, gc, oc in _per_element(idx, masks, steps, counts, codes, osec):
