@@ -4,10 +4,14 @@
 // (DFMA, DADD, F2F conversions, DMNMX) shares a pipe of under 1 TFLOP/s.  So
 // no FP64 instruction runs per point:
 //   * MODE_F32  (the precision form): FP32 transforms with FP32 accumulation.
-//   * MODE_DF64 (FP64 accuracy): every value a pair of floats (hi + lo, about
-//     48 significant bits), error-free products via FMA; the result agrees
-//     with FP64 to ~1e-14 relative.
-// The input doubles are split into floats with integer instructions.  The
+//   * MODE_DF64 (FP64 accuracy): the forward transform in FP32 under a proven
+//     error bound, every coefficient whose keep or rounding decision that bound
+//     cannot settle recomputed in hardware FP64 (rare), and the energy,
+//     reconstruction and norms as pairs of floats (hi + lo, about 48
+//     significant bits, error-free products via FMA), which agree with FP64 to
+//     ~1e-14 relative.
+// The input doubles are split into floats with integer instructions, each
+// element read as u 2^-ke (an exact power-of-two prescale).  The
 // threshold test is an exact magnitude comparison, the sums over an element
 // are pair-of-float tree sums (deterministic), and only once per element do
 // a few FP64 instructions form t = tau S_e, the step and the threshold.

@@ -26,7 +26,8 @@
 // whose keep or rounding decision that bound cannot settle, and does the
 // energy, reconstruction and error norms in float pairs.  Every element is
 // read as u 2^-ke (an exact power-of-two prescale, ke the binary exponent of
-// its largest |u|).
+// its largest |u|).  CUM selects the cumulative-energy truncation, as in the
+// lx = 8 kernel, with the group's maxima and sums exchanged between its warps.
 #include <cuda_runtime.h>
 
 #include <cfloat>

@@ -25,11 +25,20 @@
 //   * the elements' norm partials are kept per tile and converted to FP64 by all
 //     lanes at once: B300's FP64 pipe runs at ~1/64 of the FP32 rate, so no FP64
 //     instruction runs per point or per element.
+//   * the CTA that finishes last (a counter in the scratch control block)
+//     computes the field reports, one field per warp, so a single reduction is
+//     one launch; a batched launch leaves them to a finalize kernel.
 // Precision modes as in semr_fast.cu: SEMR_FP32 runs FP32 transforms with an
 // exact float-pair threshold test; SEMR_FP64 runs the forward transform in
-// FP32 under a proven error bound, recomputes exactly (float pairs) every
+// FP32 under a proven error bound, recomputes in hardware FP64 every
 // coefficient whose keep or rounding decision that bound cannot settle, and
-// does the energy, reconstruction and error norms in float pairs.
+// does the energy, reconstruction and error norms in float pairs.  Every
+// element is read as u 2^-ke (an exact power-of-two prescale, ke the binary
+// exponent of its largest |u|).  CUM selects the cumulative-energy truncation:
+// the modes above sqrt(t) are kept and the largest remaining |a| extracted one
+// at a time until the squares left fit the budget t; FP64 mode keeps that
+// answer where the FP32 bound settles it and otherwise takes a general path
+// (the element in hardware FP64, a bisection on 64-bit fixed-point energies).
 #include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched at run time)
 #include <cuda_runtime.h>
 
