@@ -333,7 +333,7 @@ def run_semr(args):
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "peak_source": f"{peaks['source']} (MEASURED_PEAKS hbm_gbs, copy)",
                 "kernel": ("reduce_warp_kernel<" if LX == 8 else
-                           f"reduce_fast_kernel<{LX}, " if args.cumulative else f"reduce_group_kernel<{LX}, ")
+                           f"reduce_group_kernel<{LX}, " if LX in (6, 10) else f"reduce_fast_kernel<{LX}, ")
                           + ('FP64 mode' if prec == semr.SEMR_FP64 else 'FP32')
                           + (", cumulative" if args.cumulative else "") + ">",
                 "kernel_ms": round(kernel_ms, 4), "algorithmic_bytes_per_launch": algo}
@@ -794,10 +794,9 @@ def emit(args, rank, world, value, ms_step, prec, roofline, cpu, e2e, clk, sm, e
                 "vs_baseline": None, "dtype": "f64" if prec == semr.SEMR_FP64 else "f32",
                 "data": "synthetic (seeded 16-mode |k|^-5/3 spectra + N(0,1e-6) noise, J~U[0.5,2])",
                 "config": workload_config(args, world), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                # one fused kernel per step (the warp kernel finalizes in its last CTA, both
-                # truncations); the cumulative variant at other lx runs the CTA kernel and its
-                # finalize kernel
-                "gpu_launches": (2 if args.cumulative and LX != 8 else 1) * args.steps, "clocks": clk,
+                # one fused kernel per step at lx = 6, 8 and 10 (the warp-level kernels finalize in
+                # their last CTA, both truncations); other lx run the CTA kernel and its finalize
+                "gpu_launches": (1 if LX in (6, 8, 10) else 2) * args.steps, "clocks": clk,
                 "result": {"cr": round(sm.cr, 5), "payload_bytes": int(sm.payload_bytes),
                            "l2_rel": [round(sm.field[i].l2_rel, 6) for i in range(N_FIELDS)],
                            "linf_rel": [round(sm.field[i].linf_rel, 6) for i in range(N_FIELDS)]},
