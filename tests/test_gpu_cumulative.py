@@ -102,8 +102,10 @@ def test_keeps_more_than_threshold_form():
     assert cum.summary.field[0].l2_rel <= thr.summary.field[0].l2_rel
 
 
-def test_edge_cases():
-    lx = 8
+@pytest.mark.parametrize("lx", [6, 8, 10, 7])
+def test_edge_cases(lx):
+    """Zero and constant blocks, tau >= 1, lossless tau = 0 and a single element,
+    on each kernel that runs the variant (warp-group, warp, CTA)."""
     fields, jac = make_case(40, lx, 1)
     fields[0, :10] = 0.0
     fields[0, 10:20] = 3.25
@@ -120,10 +122,11 @@ def test_edge_cases():
     _compare(f1, j1, lx, 1e-2)
 
 
-def test_deterministic_repeat():
-    fields, jac = _white(500, 8, 2, seed=90)
-    a, ra = run_gpu(fields, jac, 8, 0.05, cumulative=True)
-    b, rb = run_gpu(fields, jac, 8, 0.05, cumulative=True)
+@pytest.mark.parametrize("lx", [6, 8, 10])
+def test_deterministic_repeat(lx):
+    fields, jac = _white(500, lx, 2, seed=90)
+    a, ra = run_gpu(fields, jac, lx, 0.05, cumulative=True)
+    b, rb = run_gpu(fields, jac, lx, 0.05, cumulative=True)
     assert np.array_equal(a.payload, b.payload) and np.array_equal(ra, rb)
 
 
