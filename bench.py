@@ -156,15 +156,21 @@ class ClockSampler:
 
 # -------------------------------------------------------------- distributed
 
-def dist_setup(args):
+def dist_setup(args=None):
+    """Ranks of a torchrun launch: one independent replica per GPU (NCCL for the
+    barrier and the max-over-ranks timing); gloo when no GPU is present, which
+    is how the multi-rank bookkeeping is tested on CPU."""
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
     elif torch.cuda.is_available():
         torch.cuda.set_device(0)
     return world, rank, local
@@ -181,7 +187,7 @@ def max_over_ranks(world, v: float) -> float:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -254,10 +260,15 @@ def algorithmic_bytes(n_elem, n_fields, code_total, width):
     return (n_fields * n_elem * (8 * n3 + mb + 4 + 24) + 8 * n_elem + width * code_total)
 
 
+def rank_seeds(rank):
+    """Field seeds of rank `rank`'s replica: rank 0 reduces the benchmark snapshot (seeds 10..13),
+    every other rank an independent one of the same shape."""
+    return [s + 100 * rank for s in SEEDS]
+
+
 def make_snapshot(rank, device):
     import synth
-    seeds = [s + 100 * rank for s in SEEDS]
-    f, j = synth.snapshot(N_SIDE ** 3, LX, seeds, device=device)
+    f, j = synth.snapshot(N_SIDE ** 3, LX, rank_seeds(rank), device=device)
     return f.reshape(N_FIELDS, N_SIDE ** 3, LX ** 3).contiguous(), j.contiguous()
 
 
