@@ -38,7 +38,7 @@ def _rank(rank, world, port, out):
 @pytest.mark.skipif(torch.cuda.is_available(), reason="the CPU (gloo) form of the multi-rank bookkeeping")
 def test_two_gloo_ranks_agree_on_the_slowest_step():
     world = 2
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork of a multi-threaded process
         out = m.dict()
         mp.spawn(_rank, args=(world, _free_port(), out), nprocs=world, join=True)
         res = dict(out)
