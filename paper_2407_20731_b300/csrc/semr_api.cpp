@@ -481,7 +481,9 @@ extern "C" int semr_decode(const void* payload_v, uint64_t bytes, double* out, u
     const uint64_t mb = mask_bytes_per_elem(lx);
     const uint64_t fixed = field_fixed_bytes(lx, (int64_t)ne);
     const int width = (flags & SEMR_PAYLOAD_LOSSLESS) ? 8 : ((flags & SEMR_PAYLOAD_CODE32) ? 4 : 2);
-    if (code_base != hdr + nf * fixed || code_base + code_total * width > bytes) return SEMR_EINVAL;
+    // (no product that can wrap: a corrupt code_total must not pass the size check)
+    if (code_base != hdr + nf * fixed || code_base > bytes || code_total > (bytes - code_base) / width)
+        return SEMR_EINVAL;
     if (lx_out) *lx_out = lx;
     if (nf_out) *nf_out = nf;
     if (ne_out) *ne_out = (int64_t)ne;

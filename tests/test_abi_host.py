@@ -119,6 +119,41 @@ def test_host_decoder_rejects_malformed():
         semr.semr_decode(r.payload[:-2])  # truncated code section
 
 
+def test_host_decoder_survives_corruption():
+    """Seeded corruptions of a valid payload -- header fields set to extreme
+    values (a code count whose size in bytes wraps around 2^64 among them),
+    random bytes flipped anywhere, truncations -- make the decoder return an
+    error or a finite-sized result; it never reads outside the buffer."""
+    import struct
+    f, j = synth.snapshot(20, 6, [5, 6])
+    r = oracle.reduce(f.numpy().reshape(2, 20, -1), j.numpy(), 1e-3)
+    good = r.payload
+    cases = []
+    for off, fmt, val in [(40, "<Q", 2 ** 63), (40, "<Q", 2 ** 62 + 1), (40, "<Q", 2 ** 64 - 1), (32, "<Q", 2 ** 63),
+                          (32, "<Q", 0), (16, "<Q", 2 ** 39), (16, "<Q", 0), (12, "<I", 0), (6, "<H", 13),
+                          (8, "<H", 17), (8, "<H", 0), (4, "<H", 7), (10, "<H", 0xffff)]:
+        bad = bytearray(good)
+        struct.pack_into(fmt, bad, off, val)
+        cases.append(np.frombuffer(bytes(bad), dtype=np.uint8))
+    rng = np.random.default_rng(11)
+    for _ in range(300):
+        bad = good.copy()
+        for pos in rng.integers(0, bad.size, size=rng.integers(1, 6)):
+            bad[pos] ^= np.uint8(1 << int(rng.integers(0, 8)))
+        cases.append(bad)
+    for cut in (1, 2, 17, good.size // 2, good.size - 1):
+        cases.append(good[:cut].copy())
+    ok = 0
+    for bad in cases:
+        try:
+            out = semr.semr_decode(bad)
+            assert out.ndim == 3
+            ok += 1
+        except semr.SemrError:
+            pass
+    assert ok < len(cases)  # most corruptions are caught
+
+
 def test_slice_argument_validation_needs_no_gpu():
     """Every case below is invalid, so the call returns before any CUDA work."""
     good_mesh = semr.make_lattice(8, (4, 4, 4))
