@@ -390,7 +390,7 @@ __device__ __noinline__ uint32_t g_cum_general(float* M, const float* am, uint32
 #pragma unroll
         for (int kk = 0; kk < WPW; ++kk) a64[kk] = ((vm >> kk) & 1u) ? D[32 * (w0 + kk) + lane] : 0.0;
         gsync<WPE>(gi);  // every double is read before M is rewritten as floats
-        recomputed += N3;
+        if (wg == 0) recomputed += N3;  // (counted once per element)
     } else {
 #pragma unroll
         for (int kk = 0; kk < WPW; ++kk) a64[kk] = ((vm >> kk) & 1u) ? static_cast<double>(am[kk]) : 0.0;
