@@ -412,11 +412,16 @@ void semr_batch_destroy(semr_batch* b);
  * Producers on any thread submit reductions of snapshots already in device
  * memory.  A dispatcher thread admits queued requests in arrival order into
  * `slots` device slots (one CUDA stream each) whenever a slot is free and the
- * request's device memory (worst-case payload + scratch + reports) fits
- * `mem_budget_bytes` (0: no bound) next to every admitted, unreleased request.
- * Admitted requests run concurrently and overlap on the GPU; results stay on
- * the device until released.  The input buffers must stay valid until the
- * request completes.
+ * request's device memory (payload + scratch + reports) fits `mem_budget_bytes`
+ * (0: no bound) next to every admitted, unreleased request.  The payload is
+ * sized for an estimate of the request's codes: twice the largest share of
+ * modes kept by the requests completed so far (1/16 of all modes before the
+ * first), plus 4096 codes, at most every mode kept.  A request whose codes do
+ * not fit is re-run once on its slot at the exact size its first run reports
+ * (when that fits the budget), so its completion comes later but its result is
+ * the same.  Admitted requests run concurrently and overlap on the GPU;
+ * results stay on the device until released.  The input buffers must stay
+ * valid until the request completes.
  */
 typedef struct semr_server semr_server;
 
@@ -424,7 +429,7 @@ typedef struct {
     double t_submit, t_admit, t_done;  /* host steady-clock seconds (completion from a stream callback) */
     int32_t slot;                      /* device slot that ran the request */
     int32_t status;                    /* SEMR_OK, or the error that stopped the launch */
-    uint64_t device_bytes;             /* device memory the request held */
+    uint64_t device_bytes;             /* device memory the request held (after a re-run: its exact size) */
     semr_summary summary;              /* as written by the reduction */
 } semr_request_info;
 

@@ -9,11 +9,16 @@
 // overlap on the GPU, and a request that arrives while others are running is
 // admitted as soon as a slot and memory free up.  Completion is signalled
 // from the stream by a host callback, which also timestamps it; results stay
-// on the device until the producer releases them.  This is the asynchronous
+// on the device until the producer releases them.  A request's payload is
+// sized for an estimate of its codes (twice the largest share of modes kept by
+// the requests completed so far, 1/16 of all modes before the first, plus 4096
+// codes) instead of every mode kept; a request whose codes outgrow it is re-run
+// once, on its slot, at the exact size its first run reports.  This is the asynchronous
 // in-situ approach of arXiv 2407.20731 (Sec. III-A: the application only
 // waits for the hand-over) realised with streams inside one process.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -38,10 +43,11 @@ struct Request {
     semr_fieldset fs{};
     semr_mesh mesh{};
     semr_sizes sz{};
-    uint64_t bytes = 0, off_scratch = 0, off_summary = 0, off_elem = 0;
+    uint64_t bytes = 0, off_scratch = 0, off_summary = 0, off_elem = 0, payload_cap = 0, modes = 0;
+    bool rerun = false;  // re-run at the exact payload size (the estimate was too small)
     double t_submit = 0, t_admit = 0, t_done = 0;
     int slot = -1;
-    int state = 0;  // 0 queued, 1 running, 2 done, 3 failed
+    int state = 0;  // 0 queued, 1 running, 2 done, 3 failed, 4 to be re-run at the exact size
     int status = SEMR_OK;
     uint8_t* dev = nullptr;
     semr_summary summary{};  // copied from the slot's pinned buffer when the request completes
@@ -49,6 +55,15 @@ struct Request {
 };
 
 uint64_t align256(uint64_t b) { return (b + 255) & ~uint64_t(255); }
+
+// Device block of a request for a payload of `cap` bytes: payload | scratch | summary | report.
+void layout(Request* r, uint64_t cap) {
+    r->payload_cap = cap;
+    r->off_scratch = align256(cap);
+    r->off_summary = align256(r->off_scratch + r->sz.scratch_bytes);
+    r->off_elem = align256(r->off_summary + sizeof(semr_summary));
+    r->bytes = align256(r->off_elem + r->sz.elem_report_bytes);
+}
 
 }  // namespace
 
@@ -72,6 +87,9 @@ struct semr_server {
     uint64_t admitted = 0, completed = 0;
     double busy_start = 0, busy_end = 0;
     uint64_t bytes_in_done = 0;
+    double fill = 0.0;  // largest share of modes kept by a completed request
+    bool fill_seen = false;
+    std::deque<uint64_t> reruns;  // requests whose codes outgrew the estimate (state 4)
 };
 
 namespace {
@@ -81,8 +99,21 @@ void CUDART_CB on_done(void* arg) {
     semr_server* s = r->owner;
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        r->t_done = now_s();
         std::memcpy(&r->summary, s->slot_summary[r->slot], sizeof(semr_summary));
+        if (r->summary.status == SEMR_STATUS_OVERFLOW && !r->rerun) {
+            // the codes outgrew the estimate: the dispatcher re-runs the request on its slot (which
+            // stays taken) at the exact size; no CUDA call may run in this callback
+            r->state = 4;
+            s->reruns.push_back(r->id);
+            s->cv.notify_all();
+            return;
+        }
+        if (r->modes && !(r->summary.status & SEMR_STATUS_OVERFLOW)) {
+            const double share = double(r->summary.code_total) / double(r->modes);
+            if (!s->fill_seen || share > s->fill) s->fill = share;
+            s->fill_seen = true;
+        }
+        r->t_done = now_s();
         r->state = 2;
         s->completed += 1;
         s->busy_end = r->t_done;
@@ -101,7 +132,7 @@ int launch(semr_server* s, Request* r) {
     if (cudaMallocAsync(reinterpret_cast<void**>(&r->dev), r->bytes, st) != cudaSuccess) return SEMR_ENOMEM;
     semr_outputs o;
     o.payload = r->dev;
-    o.payload_cap = r->sz.payload_worst;
+    o.payload_cap = r->payload_cap;
     o.elem_report = reinterpret_cast<double*>(r->dev + r->off_elem);
     o.summary = reinterpret_cast<semr_summary*>(r->dev + r->off_summary);
     o.scratch = r->dev + r->off_scratch;
@@ -120,6 +151,33 @@ void dispatch_loop(semr_server* s) {
     std::unique_lock<std::mutex> lk(s->mu);
     while (!s->stop) {
         bool progressed = false;
+        while (!s->reruns.empty()) {  // re-runs at the exact size, on the same slot, first
+            Request* r = s->reqs[s->reruns.front()];
+            const uint64_t need = std::max<uint64_t>(r->summary.payload_bytes, r->sz.code_base);
+            const uint64_t old_bytes = r->bytes;
+            uint8_t* old_dev = r->dev;
+            Request grown = *r;
+            layout(&grown, need);
+            if (s->budget && s->held - old_bytes + grown.bytes > s->budget) break;  // wait for memory
+            s->reruns.pop_front();
+            layout(r, need);
+            r->rerun = true;
+            r->state = 1;
+            s->held = s->held - old_bytes + r->bytes;
+            lk.unlock();
+            cudaFreeAsync(old_dev, s->streams[r->slot]);  // the first run is complete
+            const int rc = launch(s, r);
+            lk.lock();
+            if (rc) {
+                r->status = rc;
+                r->state = 3;
+                s->slot_req[r->slot] = -1;
+                s->held -= r->bytes;
+                r->dev = nullptr;
+                s->done_cv.notify_all();
+            }
+            progressed = true;
+        }
         while (!s->queue.empty()) {
             Request* r = s->reqs[s->queue.front()];
             int slot = -1;
@@ -207,10 +265,14 @@ extern "C" int semr_server_submit(semr_server* s, const semr_fieldset* fs, const
     }
     r->fs = *fs;
     r->mesh = *mesh;
-    r->off_scratch = align256(r->sz.payload_worst);
-    r->off_summary = align256(r->off_scratch + r->sz.scratch_bytes);
-    r->off_elem = align256(r->off_summary + sizeof(semr_summary));
-    r->bytes = align256(r->off_elem + r->sz.elem_report_bytes);
+    r->modes = uint64_t(fs->n_fields) * uint64_t(mesh->n_elem) * uint64_t(mesh->lx) * mesh->lx * mesh->lx;
+    double fill;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        fill = s->fill_seen ? s->fill : 1.0 / 32.0;
+    }
+    const double est = std::min(1.0, 2.0 * fill) * double(r->modes) + 4096.0;
+    layout(r, std::min<uint64_t>(r->sz.payload_worst, r->sz.code_base + r->sz.code_width * uint64_t(est)));
     if (s->budget && r->bytes > s->budget) {
         delete r;
         return SEMR_EBUDGET;  // could never be admitted
@@ -234,8 +296,8 @@ extern "C" int semr_server_wait(semr_server* s, uint64_t id, int wait, semr_requ
     auto it = s->reqs.find(id);
     if (it == s->reqs.end()) return SEMR_EINVAL;
     Request* r = it->second;
-    if (wait) s->done_cv.wait(lk, [&] { return r->state >= 2; });
-    if (r->state < 2) return SEMR_EAGAIN;
+    if (wait) s->done_cv.wait(lk, [&] { return r->state == 2 || r->state == 3; });
+    if (r->state != 2 && r->state != 3) return SEMR_EAGAIN;  // running, queued or being re-run
     if (info) {
         info->t_submit = r->t_submit;
         info->t_admit = r->t_admit;
@@ -261,7 +323,7 @@ extern "C" int semr_server_release(semr_server* s, uint64_t id, void* payload, u
         auto it = s->reqs.find(id);
         if (it == s->reqs.end()) return SEMR_EINVAL;
         r = it->second;
-        s->done_cv.wait(lk, [&] { return r->state >= 2; });
+        s->done_cv.wait(lk, [&] { return r->state == 2 || r->state == 3; });
         s->reqs.erase(it);
     }
     // no lock held below: CUDA calls only

@@ -64,8 +64,16 @@ def test_each_result_same_alone_and_in_the_mix(precision):
 
 def test_budget_queues_and_rejects():
     reqs = _requests()
-    sz = [semr.semr_sizes_for(r[2], r[1].numel(), len(r[0]), r[3]) for r in reqs]
-    sizes = [s.payload_worst + s.scratch_bytes for s in sz]  # what the server reserves per request
+    # what the server reserves per request (payload estimate or exact re-run size, scratch, reports)
+    probe = semr.Server(slots=1)
+    sizes = []
+    for r in reqs:
+        rid = probe.submit(*r)
+        rc, info = probe.wait(rid)
+        assert rc == semr.SEMR_OK
+        sizes.append(int(info.device_bytes))
+        probe.release(rid)
+    probe.close()
     budget = int(max(sizes) * 1.3)  # only about one request fits at a time
     srv = semr.Server(slots=4, mem_budget_bytes=budget)
     ids = [srv.submit(*r) for r in reqs]
@@ -82,6 +90,35 @@ def test_budget_queues_and_rejects():
         tiny.submit(*reqs[0])
     assert e.value.code == semr.SEMR_EBUDGET
     tiny.close()
+
+
+def test_codes_beyond_the_estimate_rerun_exactly():
+    """A white-noise snapshot keeps about half its modes, far beyond the
+    server's first payload estimate (1/16 of the modes plus 4096 codes): its
+    request is re-run on its slot at the exact size the first run reports,
+    and the result equals the same reduction alone; requests after it are
+    sized from that fill and run once."""
+    import torch
+    E = 400
+    g = torch.Generator().manual_seed(91)
+    f = torch.randn(1, E, 512, dtype=torch.float64, generator=g).cuda().contiguous()
+    j = (0.5 + 1.5 * torch.rand(E, dtype=torch.float64, generator=g)).cuda().contiguous()
+    req = ([f[0]], j, 8, 1e-3)
+    alone = _alone(req, semr.SEMR_FP64)
+    sz = semr.semr_sizes_for(8, E, 1, 1e-3)
+    kept = (alone.size - int(sz.code_base)) // 2
+    assert kept > (E * 512) // 16 + 4096  # beyond the first estimate
+    srv = semr.Server(slots=2)
+    for _ in range(2):
+        rid = srv.submit(*req, precision=semr.SEMR_FP64)
+        rc, info = srv.wait(rid)
+        assert rc == semr.SEMR_OK and info.summary.status == 0
+        assert info.device_bytes >= info.summary.payload_bytes
+        buf = np.zeros(int(info.summary.payload_bytes), dtype=np.uint8)
+        rc, _ = srv.release(rid, buf)
+        assert rc == semr.SEMR_OK and np.array_equal(buf, alone)
+    assert srv.stats()["held_bytes"] == 0
+    srv.close()
 
 
 def test_served_results_equal_the_oracle():
