@@ -359,7 +359,9 @@ int semr_selftest_waits(uint32_t* status_out);
 /* ------------------------------------------------------ batched launches */
 
 /* One snapshot of a batch: as for semr_reduce_async; out.scratch is ignored
- * (the batch owns the scratch).  Precision SEMR_FP64 or SEMR_FP32. */
+ * (the batch owns the scratch).  Precision SEMR_FP64 or SEMR_FP32 (FP64 mode
+ * not lossless); SEMR_CUMULATIVE at lx = 6, 8 and 10 with int16 codes (the
+ * orders the warp-level kernels serve), SEMR_EUNSUPPORTED otherwise. */
 typedef struct {
     semr_fieldset fs;
     semr_mesh mesh;
@@ -374,7 +376,7 @@ typedef struct semr_batch semr_batch;
  * semr_batch_create: plan the reduction of n_items snapshots of any sizes and
  * orders in one launch sequence (many uneven snapshots per launch, the
  * batched form of the in-situ reduction).  Snapshots are grouped by (lx,
- * precision); each group runs one persistent kernel over a single work queue
+ * precision, truncation); each group runs one persistent kernel over a single work queue
  * of all its snapshots' tiles, then one finalize kernel.  With
  * SEMR_BATCH_AUTOTUNE the elements per CTA of each group are chosen by timing
  * every compiled variant on the group's largest snapshot (this runs kernels

@@ -396,17 +396,20 @@ class Batch:
     """A planned batch of snapshot reductions (semr_batch_* entry points).
 
     ``snapshots``: list of (fields: list of CUDA FP64 tensors, jac, lx, tau,
-    precision).  Output buffers are allocated here (torch) and kept alive."""
+    precision[, cumulative]).  Output buffers are allocated here (torch) and
+    kept alive."""
 
     def __init__(self, snapshots, autotune: bool = True, stream=None):
         import torch
         self.snapshots = snapshots
         self.bufs = []
         items = (semr_batch_item * len(snapshots))()
-        for i, (fields, jac, lx, tau, prec) in enumerate(snapshots):
+        for i, snap in enumerate(snapshots):
+            fields, jac, lx, tau, prec = snap[:5]
+            cumulative = bool(snap[5]) if len(snap) > 5 else False
             b = alloc_buffers(lx, jac.numel(), len(fields), tau, fields[0].device)
             self.bufs.append(b)
-            items[i].fs = make_fieldset(fields, tau, prec)
+            items[i].fs = make_fieldset(fields, tau, prec, cumulative=cumulative)
             items[i].mesh = make_mesh(lx, jac)
             items[i].out = b.outputs
         self._items = items

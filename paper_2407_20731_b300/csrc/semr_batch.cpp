@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <vector>
 
 #include "semr_internal.h"
@@ -25,6 +26,7 @@ namespace {
 // group_tile(lx) is the warp-group kernel; every other tile is the CTA kernel.
 struct Group {
     int lx = 0, precision = 0, tile = 0;
+    bool cum = false;             // cumulative-energy truncation (warp-level kernels only)
     std::vector<int> items;       // indices into the caller's item array
     float tuned_ms[4] = {0, 0, 0, 0};
     int variants[4] = {0, 0, 0, 0};
@@ -53,7 +55,6 @@ int fill_params(const semr_batch_item& it, int tile, LaunchParams& p) {
     if (rc) return rc;
     if (fs.precision != SEMR_FP64 && fs.precision != SEMR_FP32) return SEMR_EUNSUPPORTED;
     if (fs.precision == SEMR_FP64 && fs.tau == 0.0) return SEMR_EUNSUPPORTED;  // lossless FP64: single launches
-    if (fs.flags & SEMR_CUMULATIVE) return SEMR_EUNSUPPORTED;  // cumulative variant: single launches
     if (!m.jac || !it.out.payload || !it.out.summary) return SEMR_EINVAL;
     if (it.out.payload_cap < sz.code_base) return SEMR_EINVAL;
     const uintptr_t amask = (m.lx % 2 == 0) ? 15u : 7u;
@@ -81,6 +82,7 @@ int fill_params(const semr_batch_item& it, int tile, LaunchParams& p) {
     p.code_base = sz.code_base;
     p.lx = m.lx;
     p.tile = tile;
+    p.cumulative = (fs.flags & SEMR_CUMULATIVE) && fs.tau != 0.0 ? 1 : 0;
     return SEMR_OK;
 }
 
@@ -213,10 +215,11 @@ int launch_all(semr_batch* b, cudaStream_t st) {
         if (cudaMemsetAsync(b->ws + G.off_zero, 0, G.zero_bytes, st) != cudaSuccess) return SEMR_ECUDA;
         const BatchQueue q = queue_of(b, G);
         if (G.warp()) {
-            if (launch_reduce_warp_batch(q, G.precision, G.stage_ctas, st) != cudaSuccess) return SEMR_ECUDA;
+            if (launch_reduce_warp_batch(q, G.precision, G.cum, G.stage_ctas, st) != cudaSuccess) return SEMR_ECUDA;
             if (launch_finalize_warp_batch(q, G.total_fields, st) != cudaSuccess) return SEMR_ECUDA;
         } else if (G.grp()) {
-            if (launch_reduce_group_batch(q, G.lx, G.precision, G.stage_ctas, st) != cudaSuccess) return SEMR_ECUDA;
+            if (launch_reduce_group_batch(q, G.lx, G.precision, G.cum, G.stage_ctas, st) != cudaSuccess)
+                return SEMR_ECUDA;
             if (launch_finalize_group_batch(q, G.lx, G.total_fields, st) != cudaSuccess) return SEMR_ECUDA;
         } else {
             if (launch_reduce_fast_batch(q, G.lx, G.precision, G.tile, st) != cudaSuccess) return SEMR_ECUDA;
@@ -228,7 +231,8 @@ int launch_all(semr_batch* b, cudaStream_t st) {
 
 // Time the warp-level kernel of the snapshot's lx on it as a one-item batch (one
 // warm-up, three timed launches); ms < 0 when it cannot run.
-int probe_warp(const semr_batch_item& it, int precision, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+int probe_warp(const semr_batch_item& it, int precision, bool cum, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1,
+               float* ms) {
     *ms = -1.0f;
     const int lx = it.mesh.lx, tile = wl_tile(lx);
     LaunchParams p;
@@ -270,8 +274,8 @@ int probe_warp(const semr_batch_item& it, int precision, cudaStream_t st, cudaEv
     for (int rep = 0; rep < 4 && ok; ++rep) {
         cudaMemsetAsync(w + o_zero, 0, zero, st);
         cudaEventRecord(e0, st);
-        ok = (lx == 8 ? launch_reduce_warp_batch(q, precision, stage_ctas, st)
-                      : launch_reduce_group_batch(q, lx, precision, stage_ctas, st)) == cudaSuccess;
+        ok = (lx == 8 ? launch_reduce_warp_batch(q, precision, cum, stage_ctas, st)
+                      : launch_reduce_group_batch(q, lx, precision, cum, stage_ctas, st)) == cudaSuccess;
         cudaEventRecord(e1, st);
         if (ok) ok = cudaEventSynchronize(e1) == cudaSuccess;
         float m = 0.0f;
@@ -308,7 +312,7 @@ int autotune(semr_batch* b, Group& G, cudaStream_t st) {
     for (int v = 0; v < G.n_variants; ++v) {
         if (G.variants[v] == wl_tile(G.lx)) {
             float ms = -1.0f;
-            const int rc = probe_warp(it, G.precision, st, e0, e1, &ms);
+            const int rc = probe_warp(it, G.precision, G.cum, st, e0, e1, &ms);
             if (rc) {
                 cudaEventDestroy(e0);
                 cudaEventDestroy(e1);
@@ -381,7 +385,7 @@ extern "C" int semr_batch_create(semr_batch** out, const semr_batch_item* items,
     if (!b) return SEMR_ENOMEM;
     cudaGetDevice(&b->device);
     b->items.assign(items, items + n_items);
-    std::map<std::pair<int, int>, int> gid;
+    std::map<std::tuple<int, int, bool>, int> gid;
     for (int i = 0; i < n_items; ++i) {
         LaunchParams p;
         const int rc = fill_params(items[i], tile_elems(items[i].mesh.lx), p);
@@ -389,12 +393,13 @@ extern "C" int semr_batch_create(semr_batch** out, const semr_batch_item* items,
             delete b;
             return rc;
         }
-        const auto key = std::make_pair(items[i].mesh.lx, items[i].fs.precision);
+        const auto key = std::make_tuple(items[i].mesh.lx, items[i].fs.precision, p.cumulative != 0);
         auto f = gid.find(key);
         if (f == gid.end()) {
             Group G;
-            G.lx = key.first;
-            G.precision = key.second;
+            G.lx = std::get<0>(key);
+            G.precision = std::get<1>(key);
+            G.cum = std::get<2>(key);
             G.n_variants = tile_variants(G.lx, G.variants, 4);
             G.tile = G.variants[0];
             gid[key] = (int)b->groups.size();
@@ -418,6 +423,15 @@ extern "C" int semr_batch_create(semr_batch** out, const semr_batch_item* items,
             ++G.n_variants;
             G.tile = wt;
         }
+    }
+    for (Group& G : b->groups) {  // cumulative truncation: the warp-level kernels alone have a batched form
+        if (!G.cum) continue;
+        if (!G.warp_ok) {
+            delete b;
+            return SEMR_EUNSUPPORTED;
+        }
+        G.variants[0] = G.tile = wl_tile(G.lx);
+        G.n_variants = 1;
     }
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (flags & SEMR_BATCH_AUTOTUNE) {

@@ -1590,10 +1590,20 @@ int launch_reduce_group(const LaunchParams& p, void* stream) {
     }
 }
 
-int launch_reduce_group_batch(const BatchQueue& q, int lx, int precision, uint64_t stage_ctas, void* stream) {
+int launch_reduce_group_batch(const BatchQueue& q, int lx, int precision, bool cumulative, uint64_t stage_ctas,
+                              void* stream) {
     const bool df = precision != SEMR_FP32;
     LaunchParams p;
     std::memset(&p, 0, sizeof(p));
+    if (cumulative) {
+        switch (lx) {
+            case 6: return df ? launch_group_mode<6, 1, true, true>(p, q, stage_ctas, stream)
+                              : launch_group_mode<6, 0, true, true>(p, q, stage_ctas, stream);
+            case 10: return df ? launch_group_mode<10, 1, true, true>(p, q, stage_ctas, stream)
+                               : launch_group_mode<10, 0, true, true>(p, q, stage_ctas, stream);
+            default: return (int)cudaErrorInvalidValue;
+        }
+    }
     switch (lx) {
         case 6: return df ? launch_group_mode<6, 1, true>(p, q, stage_ctas, stream) : launch_group_mode<6, 0, true>(p, q, stage_ctas, stream);
         case 10: return df ? launch_group_mode<10, 1, true>(p, q, stage_ctas, stream) : launch_group_mode<10, 0, true>(p, q, stage_ctas, stream);

@@ -177,23 +177,25 @@ int launch_finalize_batch(const BatchQueue& q, uint32_t total_fields, void* stre
 // split by split_scratch_warp, p.tile = kWarpTile).
 bool warp_applicable(const LaunchParams& p);
 int launch_reduce_warp(const LaunchParams& p, void* stream);
-// Batched form: items of one precision, each laid out as split_scratch_warp does
-// except that they share one code staging (stage_ctas CTAs).  warp_encode_maps
-// writes an item's n_fields tensor maps (128 bytes each) to host memory.
+// Batched form: items of one precision and truncation (cumulative or not), each laid
+// out as split_scratch_warp does except that they share one code staging (stage_ctas
+// CTAs).  warp_encode_maps writes an item's n_fields tensor maps (128 bytes each) to
+// host memory.
 constexpr uint64_t kTensorMapBytes = 128;
 int warp_encode_maps(const LaunchParams& p, void* maps);
-int launch_reduce_warp_batch(const BatchQueue& q, int precision, uint64_t stage_ctas, void* stream);
+int launch_reduce_warp_batch(const BatchQueue& q, int precision, bool cumulative, uint64_t stage_ctas, void* stream);
 int launch_finalize_warp_batch(const BatchQueue& q, uint32_t total_fields, void* stream);
 
-// Warp-group kernel (semr_group.cu): lx = 6 and 10 threshold truncation in
+// Warp-group kernel (semr_group.cu): lx = 6 and 10, threshold or cumulative truncation in
 // SEMR_FP64 / SEMR_FP32 with int16 codes, one element per group of one (lx = 6)
 // or two (lx = 10) warps; the warp kernel's scratch layout with tiles of
 // group_tile(lx) elements (0 for an lx it does not serve).
 int group_tile(int lx);
 bool group_applicable(const LaunchParams& p);
 int launch_reduce_group(const LaunchParams& p, void* stream);
-// Batched form: items of one (lx, precision), laid out as for the warp kernel (no tensor maps).
-int launch_reduce_group_batch(const BatchQueue& q, int lx, int precision, uint64_t stage_ctas, void* stream);
+// Batched form: items of one (lx, precision, truncation), laid out as for the warp kernel (no tensor maps).
+int launch_reduce_group_batch(const BatchQueue& q, int lx, int precision, bool cumulative, uint64_t stage_ctas,
+                              void* stream);
 int launch_finalize_group_batch(const BatchQueue& q, int lx, uint32_t total_fields, void* stream);
 
 // Kernel launchers (semr_kernels.cu).  Return a cudaError_t value.

@@ -1657,10 +1657,13 @@ int warp_encode_maps(const LaunchParams& p, void* maps) {
     return 0;
 }
 
-int launch_reduce_warp_batch(const BatchQueue& q, int precision, uint64_t stage_ctas, void* stream) {
+int launch_reduce_warp_batch(const BatchQueue& q, int precision, bool cumulative, uint64_t stage_ctas, void* stream) {
     WArgs a;
     std::memset(&a, 0, sizeof(a));
     a.tab = make_wtables();
+    if (cumulative)
+        return precision == SEMR_FP32 ? launch_mode<0, true, true>(a, q, q.total_tiles, stage_ctas, stream)
+                                      : launch_mode<1, true, true>(a, q, q.total_tiles, stage_ctas, stream);
     return precision == SEMR_FP32 ? launch_mode<0, true>(a, q, q.total_tiles, stage_ctas, stream)
                                   : launch_mode<1, true>(a, q, q.total_tiles, stage_ctas, stream);
 }

@@ -60,3 +60,36 @@ def test_batch_matches_single_launches_and_graph_replay(precision):
                               fragile_cap=100000)
             compare_payloads(payload, o.payload, o.fragile)
     b.close()
+
+
+@pytest.mark.parametrize("precision", [semr.SEMR_FP64, semr.SEMR_FP32])
+def test_batch_cumulative_truncation(precision):
+    """Cumulative-energy truncation in a batch, next to threshold snapshots of the
+    same orders (their own groups): each result byte-identical to its single
+    launch, and in FP64 mode to the oracle's cumulative variant outside its
+    fragile list; a cumulative snapshot of an order without a warp-level kernel
+    is refused (single launches only)."""
+    shapes = [(700, 6, 2, 1e-3, True), (1500, 8, 1, 1e-3, True), (300, 10, 2, 1e-4, True), (900, 8, 2, 1e-3, False),
+              (400, 6, 1, 1e-2, False), (2500, 8, 1, 1e-5, True)]
+    snaps = []
+    for i, (ne, lx, nf, tau, cum) in enumerate(shapes):
+        f, j = make_case(ne, lx, nf, seed=130 + i)
+        snaps.append(([f[k] for k in range(nf)], j, lx, tau, precision, cum, f))
+    b = semr.Batch([s[:6] for s in snaps], autotune=True)
+    assert len(b.schedule()) == 5  # (lx, truncation) groups: 6 cum, 8 cum, 10 cum, 8 thr, 6 thr
+    b.capture()
+    b.replay()
+    for (payload, sm), (fields, jac, lx, tau, prec, cum, f) in zip(b.results(), snaps):
+        assert sm.status == 0
+        assert bool(oracle.parse_header(payload)["flags"] & semr.SEMR_PAYLOAD_CUMULATIVE) == cum
+        ref = semr.reduce(fields, jac, lx, tau, precision=prec, cumulative=cum)
+        assert np.array_equal(payload, ref.payload)
+        if precision == semr.SEMR_FP64:
+            o = oracle.reduce(f.cpu().numpy(), jac.cpu().numpy(), tau, want_recon=False, want_coeffs=False,
+                              fragile_cap=100000, cumulative=cum)
+            compare_payloads(payload, o.payload, o.fragile)
+    b.close()
+    f, j = make_case(50, 7, 1, seed=140)
+    with pytest.raises(semr.SemrError) as e:
+        semr.Batch([([f[0]], j, 7, 1e-3, precision, True)])
+    assert e.value.code == semr.SEMR_EUNSUPPORTED
