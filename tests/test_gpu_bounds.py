@@ -115,14 +115,15 @@ def _reduce_case(semr, lx, E, F, tau, precision, recon=False, cumulative=False, 
 
 def _batch_case(semr):
     from parity import make_case
-    specs = [(6, 700, 2, 1e-3, semr.SEMR_FP64, 11), (8, 900, 1, 1e-3, semr.SEMR_FP64, 12),
-             (10, 300, 2, 1e-4, semr.SEMR_FP64, 13), (8, 500, 2, 1e-3, semr.SEMR_FP32, 14)]
+    specs = [(6, 700, 2, 1e-3, semr.SEMR_FP64, 11, False), (8, 900, 1, 1e-3, semr.SEMR_FP64, 12, False),
+             (10, 300, 2, 1e-4, semr.SEMR_FP64, 13, False), (8, 500, 2, 1e-3, semr.SEMR_FP32, 14, False),
+             (8, 600, 1, 1e-4, semr.SEMR_FP64, 15, True), (10, 200, 1, 1e-3, semr.SEMR_FP32, 16, True)]
     items = (semr.semr_batch_item * len(specs))()
     keep = []
-    for i, (lx, E, F, tau, prec, seed) in enumerate(specs):
+    for i, (lx, E, F, tau, prec, seed, cum) in enumerate(specs):
         f, j = make_case(E, lx, F, seed=seed)
         bufs, o = _outputs(semr, lx, E, F, tau)
-        items[i].fs = semr.make_fieldset([f[k] for k in range(F)], tau, prec)
+        items[i].fs = semr.make_fieldset([f[k] for k in range(F)], tau, prec, cumulative=cum)
         items[i].mesh = semr.make_mesh(lx, j)
         items[i].out = o
         keep.append((f, j, bufs, F, E))
