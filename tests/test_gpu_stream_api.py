@@ -220,3 +220,42 @@ def test_close_with_tickets_outstanding():
         assert _fetch(h, t, f)[0] == semr.SEMR_OK
     finally:
         semr.semr_close(h)
+
+
+def test_concurrent_submit_query_fetch():
+    """Four producer threads share one stream handle, each submitting, polling
+    and fetching its own tickets while the others do the same (the calls are
+    documented thread-safe with respect to each other): every result equals
+    the same reduction through semr_reduce_async, byte for byte."""
+    import threading
+    cases = [make_case(300 + 150 * i, 8 if i % 2 == 0 else 6, 1 + i % 3, seed=200 + i) for i in range(8)]
+    lxs = [8 if i % 2 == 0 else 6 for i in range(8)]
+    direct = [semr.reduce([f[k] for k in range(f.shape[0])], j, lx, 1e-3).payload for (f, j), lx in zip(cases, lxs)]
+    torch.cuda.synchronize()
+    h = semr.semr_open(0, 0, 0)
+    errors = []
+
+    def producer(idx):
+        try:
+            for _ in range(3):
+                for i in idx:
+                    f, j = cases[i]
+                    rc, t = _submit(h, f, j, lxs[i], 1e-3)
+                    assert rc == semr.SEMR_OK
+                    while semr.semr_query(h, t) == semr.SEMR_EAGAIN:
+                        pass
+                    rc, payload, reps, elem = _fetch(h, t, f)
+                    assert rc == semr.SEMR_OK
+                    assert np.array_equal(payload, direct[i]), i
+        except Exception as e:  # noqa: BLE001 -- reported by the main thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=producer, args=([k, k + 4],)) for k in range(4)]
+    try:
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+    finally:
+        semr.semr_close(h)
+    assert not errors, errors
