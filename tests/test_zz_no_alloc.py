@@ -26,24 +26,24 @@ from parity import make_case
 pytestmark = pytest.mark.gpu
 
 
-def _reference(fields, jac, lx, tau):
+def _reference(fields, jac, lx, tau, cumulative=False):
     F, E = fields.shape[0], fields.shape[1]
     bufs = semr.alloc_buffers(lx, E, F, tau)
-    semr.reduce_async([fields[i] for i in range(F)], jac, lx, tau, bufs)
+    semr.reduce_async([fields[i] for i in range(F)], jac, lx, tau, bufs, cumulative=cumulative)
     torch.cuda.synchronize()
     sm = semr.summary_from(bufs)
     return (bufs.payload[: sm.payload_bytes].cpu().numpy(), bytes(bufs.summary.cpu().numpy()),
             bufs.elem_report.cpu().numpy())
 
 
-def _noalloc(fields, jac, lx, tau):
+def _noalloc(fields, jac, lx, tau, cumulative=False):
     F, E = fields.shape[0], fields.shape[1]
     sz = semr.semr_sizes_for(lx, E, F, tau)
     # outputs allocated by the caller beforehand; filled with junk to show they are overwritten
     payload = torch.full((int(sz.payload_worst),), 0xA5, dtype=torch.uint8, device="cuda")
     summary = torch.full((ctypes.sizeof(semr.semr_summary),), 0x5A, dtype=torch.uint8, device="cuda")
     elem = torch.full((F * E * 3,), -1.0, dtype=torch.float64, device="cuda")
-    fs = semr.make_fieldset([fields[i] for i in range(F)], tau)
+    fs = semr.make_fieldset([fields[i] for i in range(F)], tau, cumulative=cumulative)
     mesh = semr.make_mesh(lx, jac)
     rc = semr.semr_reduce_async_noalloc(fs, mesh, payload.data_ptr(), payload.numel(), elem.data_ptr(),
                                         summary.data_ptr(), torch.cuda.current_stream().cuda_stream)
@@ -55,11 +55,13 @@ def _noalloc(fields, jac, lx, tau):
 
 
 def test_noalloc_matches_reduce_async_on_two_calls_in_a_row():
-    cases = [(3001, 8, 3, 1e-3, 21), (1500, 6, 2, 1e-2, 22)]
-    for n_elem, lx, nf, tau, seed in cases:
+    # the warp kernel, the warp-group kernel (lx = 6 and 10) and the cumulative truncation
+    cases = [(3001, 8, 3, 1e-3, 21, False), (1500, 6, 2, 1e-2, 22, False), (900, 10, 2, 1e-3, 23, False),
+             (2000, 8, 2, 1e-3, 24, True), (700, 10, 1, 1e-4, 25, True)]
+    for n_elem, lx, nf, tau, seed, cum in cases:
         fields, jac = make_case(n_elem, lx, nf, seed=seed)
-        ref_p, ref_s, ref_e = _reference(fields, jac, lx, tau)
-        got_p, got_s, got_e = _noalloc(fields, jac, lx, tau)
+        ref_p, ref_s, ref_e = _reference(fields, jac, lx, tau, cum)
+        got_p, got_s, got_e = _noalloc(fields, jac, lx, tau, cum)
         assert got_p.size == ref_p.size and np.array_equal(got_p, ref_p)
         assert _meaningful(got_s, nf) == _meaningful(ref_s, nf)
         assert np.array_equal(got_e, ref_e)
