@@ -481,8 +481,8 @@ class Server:
         self.handle = h.value
         self._keep = {}
 
-    def submit(self, fields, jac, lx: int, tau: float, precision: int = SEMR_FP32) -> int:
-        fs = make_fieldset(fields, tau, precision)
+    def submit(self, fields, jac, lx: int, tau: float, precision: int = SEMR_FP32, cumulative: bool = False) -> int:
+        fs = make_fieldset(fields, tau, precision, cumulative=cumulative)
         mesh = make_mesh(lx, jac)
         rid = ctypes.c_uint64(0)
         _check(_lib.semr_server_submit(self.handle, ctypes.byref(fs), ctypes.byref(mesh), ctypes.byref(rid)),

@@ -143,3 +143,33 @@ def test_served_results_equal_the_oracle():
             # the 1e-12 max|u| reconstruction tolerance allows ~1e-8 relative on L2_rel at tau = 1e-7
             np.testing.assert_allclose(info.summary.field[f].l2_rel, o.field_report[f, 1], rtol=1e-6)
     srv.close()
+
+
+def test_cumulative_requests_in_the_mix():
+    """Cumulative-energy truncation through the server, mixed with threshold
+    requests on the same slots (lx 6, 8 and 10, FP64 mode): every served
+    payload equals its single launch byte for byte, and the cumulative ones
+    equal the oracle's cumulative variant outside its fragile list.  The
+    cumulative budget keeps more codes than the threshold, so these requests
+    also exercise the payload estimate and its exact re-run."""
+    reqs = _requests()[:6]
+    cum = [True, False, True, False, True, True]
+    alone = [semr.reduce(f, j, lx, tau, precision=semr.SEMR_FP64, cumulative=c).payload
+             for (f, j, lx, tau), c in zip(reqs, cum)]
+    srv = semr.Server(slots=3)
+    ids = [srv.submit(*r, precision=semr.SEMR_FP64, cumulative=c) for r, c in zip(reqs, cum)]
+    for k, rid in enumerate(ids):
+        rc, info = srv.wait(rid)
+        assert rc == semr.SEMR_OK
+        buf = np.zeros(int(info.summary.payload_bytes), dtype=np.uint8)
+        rc, _ = srv.release(rid, buf)
+        assert rc == semr.SEMR_OK
+        assert np.array_equal(buf, alone[k])
+        if cum[k]:
+            fields, jac, lx, tau = reqs[k]
+            f_np = np.stack([f.cpu().numpy() for f in fields])
+            o = oracle.reduce(f_np, jac.cpu().numpy(), tau, fragile_cap=100000, cumulative=True)
+            compare_payloads(buf, o.payload, o.fragile)
+    assert srv.stats()["held_bytes"] == 0
+    srv.close()
+

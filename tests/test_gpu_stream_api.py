@@ -44,8 +44,8 @@ def _oracle_check(fields, jac, tau, payload, reps, elem):
         np.testing.assert_allclose(reps[f].l2_rel, o.field_report[f, 1], rtol=1e-9)
 
 
-def _submit(h, fields, jac, lx, tau, precision=semr.SEMR_FP64):
-    fs = semr.make_fieldset([fields[i] for i in range(fields.shape[0])], tau, precision)
+def _submit(h, fields, jac, lx, tau, precision=semr.SEMR_FP64, cumulative=False):
+    fs = semr.make_fieldset([fields[i] for i in range(fields.shape[0])], tau, precision, cumulative=cumulative)
     rc, t = semr.semr_submit(h, fs, semr.make_mesh(lx, jac))
     return rc, t
 
@@ -88,6 +88,38 @@ def test_three_tickets_equal_the_oracle():
             # a fetched ticket is gone
             assert semr.semr_query(h, tickets[k]) == semr.SEMR_EINVAL
             assert _fetch(h, tickets[k], f)[0] == semr.SEMR_EINVAL
+    finally:
+        semr.semr_close(h)
+
+
+@pytest.mark.parametrize("lx", [6, 8, 10])
+def test_cumulative_ticket_equals_the_oracle(lx):
+    """A cumulative-truncation ticket (FP64 mode) next to a threshold one on
+    the same stream: the fetched payload equals the oracle's cumulative
+    variant outside its fragile list and the single launch byte for byte,
+    and its field reports match the oracle."""
+    f, j = make_case(900, lx, 2, seed=74 + lx)
+    g, k = make_case(500, lx, 1, seed=75 + lx)
+    h = semr.semr_open(0, 0, 0)
+    try:
+        rc, t_cum = _submit(h, f, j, lx, 1e-3, cumulative=True)
+        assert rc == semr.SEMR_OK
+        rc, t_thr = _submit(h, g, k, lx, 1e-3)
+        assert rc == semr.SEMR_OK
+        rc, payload, reps, elem = _fetch(h, t_cum, f)
+        assert rc == semr.SEMR_OK
+        alone = semr.reduce([f[i] for i in range(2)], j, lx, 1e-3, precision=semr.SEMR_FP64, cumulative=True)
+        assert np.array_equal(payload, alone.payload)
+        o = oracle.reduce(f.cpu().numpy(), j.cpu().numpy(), 1e-3, fragile_cap=100000, cumulative=True)
+        compare_payloads(payload, o.payload, o.fragile)
+        for fi in range(2):
+            assert reps[fi].umax == o.field_report[fi, 6]
+            assert reps[fi].kept == int(o.field_report[fi, 7])
+            np.testing.assert_allclose(reps[fi].sum_energy, o.field_report[fi, 5], rtol=1e-12)
+            np.testing.assert_allclose(reps[fi].l2_rel, o.field_report[fi, 1], rtol=1e-9)
+        rc, payload2, _, _ = _fetch(h, t_thr, g)
+        assert rc == semr.SEMR_OK
+        assert np.array_equal(payload2, semr.reduce([g[0]], k, lx, 1e-3, precision=semr.SEMR_FP64).payload)
     finally:
         semr.semr_close(h)
 
