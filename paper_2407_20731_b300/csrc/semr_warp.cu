@@ -1450,74 +1450,17 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
     }
 }
 
-// Finalize of field f: tree over its tile partials, then the exact maximum of
-// |u|.  The kernel records each element's largest high word of |u| (sign
-// cleared, exponent and top 20 mantissa bits), which orders the elements like
-// their maxima, so the elements whose high word is the field's hold the exact
-// maximum: those few blocks are reread.  A field whose every high word is 0
-// (zeros and subnormals only) reports 0 without a reread.  256 threads.
-__device__ void finalize_warp_field(const LaunchParams& p, int f) {
-    __shared__ double red[4][256];
-    __shared__ int s_list[64];
-    __shared__ int s_cnt;
-    __shared__ unsigned long long s_umax;
-    const int tid = threadIdx.x;
-    finalize_tree(p.tile_part, f, static_cast<uint64_t>(p.tiles_per_field), red);
-    const double M = red[3][0];
-    if (tid == 0) {
-        s_cnt = 0;
-        s_umax = 0ull;
+// One warp per (item, field) of a batched launch, eight per block: the fixed-order finalize of a
+// single launch's last CTA, so a batched snapshot's reports equal its single launch's bit for bit.
+__global__ void __launch_bounds__(256) finalize_warp_batch_kernel(const BatchQueue q, uint32_t total_fields) {
+    const uint32_t gf = blockIdx.x * 8u + (threadIdx.x >> 5);
+    if (gf >= total_fields) return;  // uniform over the warp
+    int lo = 0, hi = q.n_items - 1;  // last item with field_base <= gf
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (q.field_base[mid] <= gf) lo = mid; else hi = mid - 1;
     }
-    __syncthreads();
-    const uint64_t E = static_cast<uint64_t>(p.n_elem);
-    const uint32_t* um = p.hmax_elem + static_cast<uint64_t>(f) * E;
-    const double* src = p.fields[f];
-    for (uint64_t t = tid; M > 0.0 && t < static_cast<uint64_t>(p.tiles_per_field); t += 256) {
-        if (p.tile_part[4 * (static_cast<uint64_t>(f) * p.tiles_per_field + t) + 3] != M) continue;
-        const uint64_t ee = min(E, (t + 1) * kWarpTile);
-        for (uint64_t e = t * kWarpTile; e < ee; ++e) {
-            if (static_cast<double>(um[e]) != M) continue;
-            const int k = atomicAdd(&s_cnt, 1);
-            if (k < 64) {
-                s_list[k] = static_cast<int>(e);
-            } else {  // many ties (e.g. constant fields): this thread scans the block itself
-                unsigned long long m = 0ull;
-                for (int i = 0; i < WN3; ++i)
-                    m = max(m, static_cast<unsigned long long>(__double_as_longlong(src[e * WN3 + i])) &
-                                   0x7fffffffffffffffull);
-                atomicMax(&s_umax, m);
-            }
-        }
-    }
-    __syncthreads();
-    const int nl = min(s_cnt, 64);
-    unsigned long long m = 0ull;
-    for (int l = 0; l < nl; ++l) {
-        const double* blk = src + static_cast<uint64_t>(s_list[l]) * WN3;
-        for (int i = tid; i < WN3; i += 256)
-            m = max(m, static_cast<unsigned long long>(__double_as_longlong(blk[i])) & 0x7fffffffffffffffull);
-    }
-    atomicMax(&s_umax, m);
-    __syncthreads();
-    if (tid == 0)
-        finalize_report(p, f, WLX, red[0][0], red[1][0], red[2][0], __longlong_as_double(static_cast<long long>(s_umax)));
-}
-
-
-// One block per (item, field) of a batched launch.
-__global__ void __launch_bounds__(256) finalize_warp_batch_kernel(const BatchQueue q) {
-    __shared__ int s_item;
-    if (threadIdx.x == 0) {
-        int lo = 0, hi = q.n_items - 1;  // last item with field_base <= blockIdx.x
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) / 2;
-            if (q.field_base[mid] <= blockIdx.x) lo = mid; else hi = mid - 1;
-        }
-        s_item = lo;
-    }
-    __syncthreads();
-    const LaunchParams& p = q.items[s_item];
-    finalize_warp_field(p, static_cast<int>(blockIdx.x - q.field_base[s_item]));
+    finalize_field_warp(q.items[lo], static_cast<int>(gf - q.field_base[lo]), WLX, kWarpTile);
 }
 
 // ------------------------------------------------------------ host side
@@ -1669,7 +1612,7 @@ int launch_reduce_warp_batch(const BatchQueue& q, int precision, bool cumulative
 }
 
 int launch_finalize_warp_batch(const BatchQueue& q, uint32_t total_fields, void* stream) {
-    finalize_warp_batch_kernel<<<total_fields, 256, 0, static_cast<cudaStream_t>(stream)>>>(q);
+    finalize_warp_batch_kernel<<<(total_fields + 7) / 8, 256, 0, static_cast<cudaStream_t>(stream)>>>(q, total_fields);
     return (int)cudaGetLastError();
 }
 

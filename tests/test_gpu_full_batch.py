@@ -1,0 +1,153 @@
+"""Parity of the batched form at its full size: the 64 uneven snapshots of the
+batched workload (element counts log-uniform in [4096, 200000], lx from
+{6, 8, 10}, 1-4 FP64 fields, spectral slopes in [-3, -5/3]; 33.3 GB of input),
+FP64 mode, tau = 1e-3, in the launch configuration bench.py times: one plan
+with autotuned tiles, captured into a CUDA graph and replayed.
+
+Every order runs its warp-level kernel, and every snapshot's payload, summary
+and element report written by the replay equal its single launch byte for byte.  Each element-field depends only on its
+own block, J_e and tau (Sec. IV-B: the compression works element by element),
+so sampled element-fields of every snapshot are compared with an oracle run on
+just those blocks (bit-exact outside the oracle's fragile list), and
+properties that hold at any size cover every element-field: the counts are
+the masks' popcounts, the code section holds exactly their sum, every code is
+a nonzero integer with |c| <= 2/sqrt(tau), and each field report is the sum
+and maximum of its element reports.
+"""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2407_20731_b300 as semr
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TAU = 1e-3
+
+
+def _summary_bytes(sm):
+    """The summary's bytes up to and including its n_fields field reports."""
+    n = semr.semr_summary.field.offset + sm.n_fields * ctypes.sizeof(semr.semr_field_report)
+    return bytes(ctypes.string_at(ctypes.addressof(sm), n))
+
+
+@pytest.fixture(scope="module")
+def batch_run():
+    cases = synth.batched_cases()
+    snaps = []
+    for c in cases:
+        f, j = synth.snapshot(c["n_elem"], c["lx"], c["seeds"], slope=c["slope"], device="cuda")
+        f = f.reshape(len(c["seeds"]), c["n_elem"], c["lx"] ** 3)
+        snaps.append(([f[k] for k in range(f.shape[0])], j.contiguous(), c["lx"], TAU, semr.SEMR_FP64))
+    b = semr.Batch(snaps, autotune=True)
+    # at these sizes every order runs its warp-level kernel (tiles of 64 or 128 elements), as a
+    # single launch does; the CTA kernels' tiles hold at most 32
+    assert all(g[2] >= 64 for g in b.schedule()), b.schedule()
+    b.capture()
+    for buf in b.bufs:  # what the replay writes, and nothing left from the autotuner
+        buf.payload.zero_()
+        buf.summary.zero_()
+        buf.elem_report.fill_(float("nan"))
+    b.replay()
+    res = b.results()
+    yield cases, snaps, b, res
+    del b, snaps
+    torch.cuda.empty_cache()
+
+
+def _sections(payload, lx, F, E):
+    """Mask bytes [F, E, ceil(lx^3 / 8)], steps, counts and the int16 codes."""
+    h = oracle.parse_header(payload)
+    assert (h["lx"], h["n_fields"], h["n_elem"]) == (lx, F, E)
+    mb = (lx ** 3 + 7) // 8
+    fixed = oracle.field_fixed_bytes(lx, E)
+    pad = lambda v: (v + 15) & ~15  # noqa: E731
+    masks = np.empty((F, E, mb), np.uint8)
+    steps = np.empty((F, E), np.int16)
+    counts = np.empty((F, E), np.uint16)
+    for f in range(F):
+        base = h["header_bytes"] + f * fixed
+        masks[f] = payload[base:base + mb * E].reshape(E, mb)
+        sb = base + pad(mb * E)
+        steps[f] = payload[sb:sb + 2 * E].view("<i2")
+        cb = sb + pad(2 * E)
+        counts[f] = payload[cb:cb + 2 * E].view("<u2")
+    codes = payload[h["code_base"]:h["code_base"] + 2 * h["code_total"]].view("<i2")
+    return h, masks, steps, counts, codes
+
+
+def test_replay_equals_single_launches(batch_run):
+    cases, snaps, b, res = batch_run
+    for i, (s, (payload, sm)) in enumerate(zip(snaps, res)):
+        fields, jac, lx, tau, prec = s
+        bufs = semr.alloc_buffers(lx, jac.numel(), len(fields), tau, "cuda")
+        semr.reduce_async(fields, jac, lx, tau, bufs, prec)
+        torch.cuda.synchronize()
+        one = semr.summary_from(bufs)
+        assert sm.status == 0 and one.status == 0, i
+        assert np.array_equal(payload, bufs.payload[: one.payload_bytes].cpu().numpy()), i
+        assert _summary_bytes(sm) == _summary_bytes(one), i
+        assert torch.equal(b.bufs[i].elem_report, bufs.elem_report), i
+        del bufs
+
+
+def test_sampled_elements_equal_the_oracle(batch_run):
+    cases, snaps, b, res = batch_run
+    rng = np.random.default_rng(11)
+    n_frag = n_cmp = 0
+    for i, (c, s, (payload, sm)) in enumerate(zip(cases, snaps, res)):
+        fields, jac, lx, tau, _ = s
+        F, E = len(fields), jac.numel()
+        h, masks, steps, counts, codes = _sections(payload, lx, F, E)
+        # any size: counts, code total, code range, field sums and maxima
+        pc = np.bitwise_count(masks).sum(axis=2, dtype=np.int64)
+        assert np.array_equal(pc, counts.astype(np.int64)), i
+        total = int(counts.astype(np.int64).sum())
+        assert h["code_total"] == total == sm.code_total and sm.payload_bytes == h["code_base"] + 2 * total
+        assert codes.size == total and np.all(codes != 0)
+        assert np.abs(codes.astype(np.int32)).max() <= 2.0 / math.sqrt(TAU)
+        er = b.bufs[i].elem_report.view(F, E, 3).cpu().numpy()
+        for f in range(F):
+            fr = sm.field[f]
+            assert fr.kept == int(counts[f].astype(np.int64).sum())
+            assert fr.umax == float(fields[f].abs().max())
+            assert fr.linf_abs == er[f, :, 2].max()
+            np.testing.assert_allclose(fr.sum_energy, er[f, :, 1].sum(), rtol=1e-12)
+            np.testing.assert_allclose(fr.sum_err2, er[f, :, 0].sum(), rtol=1e-12)
+        # sampled element-fields (random, the ends and tile boundaries) against the oracle
+        edges = [0, 1, 63, 64, 127, 128, 129, E // 2, E - 65, E - 64, E - 2, E - 1]
+        idx = np.unique(np.concatenate([rng.choice(E, 40, replace=False), edges]))
+        ti = torch.as_tensor(idx, device="cuda")
+        f_np = torch.stack([fd[ti] for fd in fields]).cpu().numpy()
+        j_np = jac[ti].cpu().numpy()
+        o = oracle.reduce(f_np, j_np, TAU, want_recon=False, want_coeffs=False, fragile_cap=100000)
+        osec = oracle.sections(o.payload)
+        om = np.packbits(osec["masks"], axis=2, bitorder="little")
+        fragile = {(int(f), int(k)) for f, k, _, _ in o.fragile}
+        offs = np.concatenate([[0], np.cumsum(counts.astype(np.int64).reshape(-1))])
+        o_offs = np.concatenate([[0], np.cumsum(osec["counts"].astype(np.int64).reshape(-1))])
+        S = idx.size
+        for f in range(F):
+            for k, e in enumerate(idx):
+                g0, o0 = f * E + e, f * S + k
+                same = (np.array_equal(masks[f, e], om[f, k]) and steps[f, e] == osec["steps"][f, k]
+                        and counts[f, e] == osec["counts"][f, k]
+                        and np.array_equal(codes[offs[g0]:offs[g0 + 1]], osec["codes"][o_offs[o0]:o_offs[o0 + 1]]))
+                n_cmp += 1
+                if not same:
+                    n_frag += 1
+                    assert (f, k) in fragile, f"snapshot {i}: element-field ({f}, {e}) differs outside the fragile list"
+        d = (1e-12 * np.array([float(fd.abs().max()) for fd in fields]))[:, None]
+        ge, oe = er[:, idx], o.elem_report
+        J = j_np[None, :]
+        bound = 2 * d * np.sqrt(8 * J * oe[:, :, 0]) + 8 * J * d * d + 1e-12 * oe[:, :, 0]
+        assert np.all(np.abs(ge[:, :, 0] - oe[:, :, 0]) <= bound), i
+        np.testing.assert_allclose(ge[:, :, 1], oe[:, :, 1], rtol=1e-12, atol=0)
+        assert np.all(np.abs(ge[:, :, 2] - oe[:, :, 2]) <= d), i
+    # the fragile exemption stays rare
+    assert n_frag <= max(2, n_cmp // 1000), (n_frag, n_cmp)
