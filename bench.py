@@ -43,9 +43,10 @@ _CSRC = "paper_2407_20731_b300/csrc/"
 KERNEL_SOURCES = [_CSRC + "semr_warp.cu", _CSRC + "semr_warp_common.cuh", _CSRC + "semr_device.cuh",
                   _CSRC + "semr_internal.h"]
 CUMULATIVE_SOURCES = KERNEL_SOURCES
-# ... and the warp-group kernel (lx = 6 and 10)
+# ... the warp-group kernel (lx = 6 and 10) and the slice kernels
 GROUP_SOURCES = [_CSRC + "semr_group.cu", _CSRC + "semr_warp_common.cuh", _CSRC + "semr_device.cuh",
                  _CSRC + "semr_internal.h"]
+SLICE_SOURCES = [_CSRC + "semr_slice.cu", _CSRC + "semr_internal.h"]
 # FP64 pipe of B300, nominal (the FP32 pipes run ~50x faster; FP64 mode runs on them)
 FP64_PIPE_TFLOPS_NOMINAL = 1.25
 
@@ -73,9 +74,13 @@ def parse_args():
     return ap.parse_args()
 
 
-def kernel_source_hash(cumulative: bool = False, group: bool = False) -> str:
+def kernel_source_hash(cumulative: bool = False, kernel: str = "warp") -> str:
+    """Short hash of the sources of one kernel family ("warp", "group" or "slice"); a profile
+    summary records it, so a summary whose kernel has changed since its capture can be told."""
+    srcs = {"warp": CUMULATIVE_SOURCES if cumulative else KERNEL_SOURCES, "group": GROUP_SOURCES,
+            "slice": SLICE_SOURCES}[kernel]
     h = hashlib.sha256()
-    for rel in (GROUP_SOURCES if group else CUMULATIVE_SOURCES if cumulative else KERNEL_SOURCES):
+    for rel in srcs:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
