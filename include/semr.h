@@ -244,7 +244,8 @@ int semr_reduce_async_timed(const semr_fieldset* fs, const semr_mesh* mesh, cons
  * modes before the first completes), plus 4096 codes, at most every mode.  A
  * ticket whose codes do not fit is re-run once, at the exact size its first
  * run reports, when its completion is next observed (semr_query or
- * semr_fetch); the field and Jacobian buffers must therefore stay valid
+ * semr_fetch), unless that run also reported SEMR_STATUS_TIMEOUT, _STAGE or
+ * _BOUNDS (the input flags _TINY and _NONFINITE recur in the re-run); the field and Jacobian buffers must therefore stay valid
  * until semr_query returns SEMR_OK or semr_fetch succeeds.  The stream's
  * calls are thread-safe with respect to each other, except semr_close,
  * which must not overlap any other call on the stream.  No call holds the
@@ -420,8 +421,9 @@ void semr_batch_destroy(semr_batch* b);
  * modes kept by the requests completed so far (1/16 of all modes before the
  * first), plus 4096 codes, at most every mode kept.  A request whose codes do
  * not fit is re-run once on its slot at the exact size its first run reports
- * (when that fits the budget), so its completion comes later but its result is
- * the same.  Admitted requests run concurrently and overlap on the GPU;
+ * (when that fits the budget, and unless that run also reported
+ * SEMR_STATUS_TIMEOUT, _STAGE or _BOUNDS), so its completion comes later but
+ * its result is the same.  Admitted requests run concurrently and overlap on the GPU;
  * results stay on the device until released.  The input buffers must stay
  * valid until the request completes.
  */

@@ -290,7 +290,9 @@ int ticket_state(semr_stream* s, Ticket& t) {
         }
         return SEMR_OK;
     }
-    if (t.rerun || (sm.status & ~uint32_t(SEMR_STATUS_OVERFLOW))) return SEMR_OK;  // reported as it stands
+    // re-run once at the exact size unless the kernel also reported a device-side problem (TINY and
+    // NONFINITE describe the input: they recur unchanged in the re-run)
+    if (t.rerun || (sm.status & (SEMR_STATUS_TIMEOUT | SEMR_STATUS_STAGE | SEMR_STATUS_BOUNDS))) return SEMR_OK;
     semr_sizes sz;
     if (semr_sizes_for(t.mesh.lx, t.mesh.n_elem, t.fs.n_fields, t.fs.tau, &sz) != SEMR_OK) return SEMR_EINVAL;
     const uint64_t need = std::max<uint64_t>(sm.payload_bytes, sz.code_base);

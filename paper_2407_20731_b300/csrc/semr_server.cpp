@@ -100,9 +100,12 @@ void CUDART_CB on_done(void* arg) {
     {
         std::lock_guard<std::mutex> lk(s->mu);
         std::memcpy(&r->summary, s->slot_summary[r->slot], sizeof(semr_summary));
-        if (r->summary.status == SEMR_STATUS_OVERFLOW && !r->rerun) {
+        const uint32_t st = r->summary.status;
+        if ((st & SEMR_STATUS_OVERFLOW) && !(st & (SEMR_STATUS_TIMEOUT | SEMR_STATUS_STAGE | SEMR_STATUS_BOUNDS)) &&
+            !r->rerun) {
             // the codes outgrew the estimate: the dispatcher re-runs the request on its slot (which
-            // stays taken) at the exact size; no CUDA call may run in this callback
+            // stays taken) at the exact size (TINY and NONFINITE describe the input and recur
+            // unchanged); no CUDA call may run in this callback
             r->state = 4;
             s->reruns.push_back(r->id);
             s->cv.notify_all();

@@ -121,6 +121,37 @@ def test_codes_beyond_the_estimate_rerun_exactly():
     srv.close()
 
 
+@pytest.mark.parametrize("flagged", ["subnormal", "nan"])
+def test_rerun_with_input_flags(flagged):
+    """A request beyond the first payload estimate whose input also raises an
+    input flag (an element of subnormal values only: SEMR_STATUS_TINY,
+    informational; a NaN: SEMR_STATUS_NONFINITE) is still re-run at the exact
+    size: the released payload is complete and equals the reduction alone."""
+    import torch
+    E = 400
+    g = torch.Generator().manual_seed(92)
+    f = torch.randn(1, E, 512, dtype=torch.float64, generator=g)
+    if flagged == "subnormal":
+        f[0, 33] = torch.randn(512, dtype=torch.float64, generator=g) * 1e-310
+    else:
+        f[0, 33, 7] = float("nan")
+    f = f.cuda().contiguous()
+    j = (0.5 + 1.5 * torch.rand(E, dtype=torch.float64, generator=g)).cuda().contiguous()
+    req = ([f[0]], j, 8, 1e-3)
+    alone = semr.reduce(*req, precision=semr.SEMR_FP64)
+    flag = semr.SEMR_STATUS_TINY if flagged == "subnormal" else semr.SEMR_STATUS_NONFINITE
+    assert alone.summary.status == flag
+    srv = semr.Server(slots=2)
+    rid = srv.submit(*req, precision=semr.SEMR_FP64)
+    rc, info = srv.wait(rid)
+    assert rc == (semr.SEMR_OK if flagged == "subnormal" else semr.SEMR_ENONFINITE)
+    assert info.summary.status == flag
+    buf = np.zeros(int(info.summary.payload_bytes), dtype=np.uint8)
+    rc, _ = srv.release(rid, buf)
+    assert rc == semr.SEMR_OK and np.array_equal(buf, alone.payload)
+    srv.close()
+
+
 def test_served_results_equal_the_oracle():
     """FP64 mode through the server, all eight requests in flight together on
     four slots: every served payload equals the FP64 oracle's outside its

@@ -225,6 +225,39 @@ def test_codes_beyond_the_estimate_rerun_exactly():
         semr.semr_close(h)
 
 
+@pytest.mark.parametrize("flagged", ["subnormal", "nan"])
+def test_rerun_with_input_flags(flagged):
+    """A ticket whose codes outgrow the first payload estimate and whose input
+    also raises an input flag -- an element of subnormal values only
+    (SEMR_STATUS_TINY, informational) or one holding a NaN
+    (SEMR_STATUS_NONFINITE) -- is still re-run at the exact size: the fetch
+    delivers the complete payload, equal to a direct semr_reduce_async, with
+    SEMR_OK or SEMR_ENONFINITE respectively."""
+    E = 400
+    g = torch.Generator().manual_seed(79)
+    f = torch.randn(1, E, 512, dtype=torch.float64, generator=g)
+    if flagged == "subnormal":
+        f[0, 17] = torch.randn(512, dtype=torch.float64, generator=g) * 1e-310
+    else:
+        f[0, 17, 100] = float("nan")
+    f = f.cuda().contiguous()
+    j = (0.5 + 1.5 * torch.rand(E, dtype=torch.float64, generator=g)).cuda().contiguous()
+    direct = semr.reduce([f[0]], j, 8, 1e-3)
+    flag = semr.SEMR_STATUS_TINY if flagged == "subnormal" else semr.SEMR_STATUS_NONFINITE
+    assert direct.summary.status == flag
+    assert direct.summary.code_total > (E * 512) // 16 + 4096  # beyond the first estimate
+    h = semr.semr_open(0, 0, 0)
+    try:
+        rc, t = _submit(h, f, j, 8, 1e-3)
+        assert rc == semr.SEMR_OK
+        rc, payload, reps, elem = _fetch(h, t, f)
+        assert rc == (semr.SEMR_OK if flagged == "subnormal" else semr.SEMR_ENONFINITE)
+        assert np.array_equal(payload, direct.payload)
+        assert np.array_equal(elem, direct.elem_report, equal_nan=True)
+    finally:
+        semr.semr_close(h)
+
+
 def test_bad_tickets_and_arguments():
     f, j = make_case(64, 8, 1, seed=78)
     h = semr.semr_open(0, 0, 0)
