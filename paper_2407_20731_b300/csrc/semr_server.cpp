@@ -132,7 +132,11 @@ void CUDART_CB on_done(void* arg) {
 // pending callbacks, so no CUDA call may run while the lock is held.
 int launch(semr_server* s, Request* r) {
     cudaStream_t st = s->streams[r->slot];
-    if (cudaMallocAsync(reinterpret_cast<void**>(&r->dev), r->bytes, st) != cudaSuccess) return SEMR_ENOMEM;
+    r->dev = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&r->dev), r->bytes, st) != cudaSuccess) {
+        r->dev = nullptr;
+        return SEMR_ENOMEM;
+    }
     semr_outputs o;
     o.payload = r->dev;
     o.payload_cap = r->payload_cap;
@@ -147,6 +151,24 @@ int launch(semr_server* s, Request* r) {
         return SEMR_ECUDA;
     if (cudaLaunchHostFunc(st, on_done, r) != cudaSuccess) return SEMR_ECUDA;
     return SEMR_OK;
+}
+
+// A request that could not be started (lock held on entry and exit): report it, free its slot and
+// its memory (stream-ordered on the slot's stream, behind anything of it already enqueued there).
+void fail_start(semr_server* s, Request* r, int rc, std::unique_lock<std::mutex>& lk) {
+    uint8_t* dev = r->dev;
+    cudaStream_t st = s->streams[r->slot];
+    r->dev = nullptr;
+    r->status = rc;
+    r->state = 3;
+    s->slot_req[r->slot] = -1;
+    s->held -= r->bytes;
+    s->done_cv.notify_all();  // r may be released (and deleted) once the lock is dropped
+    if (dev) {
+        lk.unlock();
+        cudaFreeAsync(dev, st);
+        lk.lock();
+    }
 }
 
 void dispatch_loop(semr_server* s) {
@@ -171,14 +193,7 @@ void dispatch_loop(semr_server* s) {
             cudaFreeAsync(old_dev, s->streams[r->slot]);  // the first run is complete
             const int rc = launch(s, r);
             lk.lock();
-            if (rc) {
-                r->status = rc;
-                r->state = 3;
-                s->slot_req[r->slot] = -1;
-                s->held -= r->bytes;
-                r->dev = nullptr;
-                s->done_cv.notify_all();
-            }
+            if (rc) fail_start(s, r, rc, lk);
             progressed = true;
         }
         while (!s->queue.empty()) {
@@ -202,13 +217,7 @@ void dispatch_loop(semr_server* s) {
             lk.unlock();
             const int rc = launch(s, r);
             lk.lock();
-            if (rc) {  // failed to start: report and free the slot and memory
-                r->status = rc;
-                r->state = 3;
-                s->slot_req[slot] = -1;
-                s->held -= r->bytes;
-                s->done_cv.notify_all();
-            }
+            if (rc) fail_start(s, r, rc, lk);
             progressed = true;
         }
         if (!progressed) s->cv.wait_for(lk, std::chrono::milliseconds(2));
