@@ -207,7 +207,7 @@ struct semr_stream {
     uint64_t budget = 0;
     uint64_t in_flight = 0;
     uint64_t next_ticket = 1;
-    double fill = 1.0 / 16;  // largest share of modes kept so far (payload estimate)
+    double fill = 1.0 / 32;  // largest share of modes kept so far (the estimate is twice it: 1/16 at first)
     bool fill_seen = false;
     std::unordered_map<uint64_t, Ticket> tickets;
     std::vector<semr_summary*> pinned_free;

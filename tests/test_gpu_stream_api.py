@@ -147,9 +147,9 @@ def test_eagain_until_complete():
         semr.semr_close(h)
 
 
-def _ticket_bytes(lx, E, F, tau, fill=1.0 / 16):
+def _ticket_bytes(lx, E, F, tau, fill=1.0 / 32):
     """Device bytes of a fresh stream's first ticket: the payload estimate
-    (twice 1/16 of all modes, plus 4096 codes), scratch, summary, report
+    (1/16 of all modes, plus 4096 codes), scratch, summary, report
     (the layout semr_submit documents, with its alignment slack)."""
     sz = semr.semr_sizes_for(lx, E, F, tau)
     modes = F * E * lx ** 3
@@ -211,7 +211,7 @@ def test_codes_beyond_the_estimate_rerun_exactly():
     f[0] = torch.randn(E, 512, dtype=torch.float64, generator=g).cuda()
     direct = semr.reduce([f[0]], j, 8, 1e-3)
     kept = direct.summary.code_total
-    assert kept > 2 * (E * 512) // 16 + 4096  # beyond the first estimate
+    assert kept > (E * 512) // 16 + 4096  # beyond the first estimate
     h = semr.semr_open(0, 0, 0)
     try:
         for _ in range(2):
