@@ -417,10 +417,11 @@ extern "C" int semr_batch_create(semr_batch** out, const semr_batch_item* items,
             G.warp_ok = G.warp_ok && fill_params(items[idx], wt, p) == SEMR_OK &&
                         (G.lx == 8 ? warp_applicable(p) : group_applicable(p));
         }
-        if (G.warp_ok && G.n_variants < 4) {
-            for (int v = G.n_variants; v > 0; --v) G.variants[v] = G.variants[v - 1];
+        if (G.warp_ok) {  // first, ahead of the CTA kernel's tiles (the last of four gives way)
+            const int n = std::min(G.n_variants, 3);
+            for (int v = n; v > 0; --v) G.variants[v] = G.variants[v - 1];
             G.variants[0] = wt;
-            ++G.n_variants;
+            G.n_variants = n + 1;
             G.tile = wt;
         }
     }
@@ -474,8 +475,12 @@ extern "C" int semr_batch_capture(semr_batch* b, void* cuda_stream) {
         if (rc == SEMR_OK) {
             if (b->exec) cudaGraphExecDestroy(b->exec);
             if (b->graph) cudaGraphDestroy(b->graph);
+            b->exec = nullptr;
             b->graph = g;
-            if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) rc = SEMR_ECUDA;
+            if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+                b->exec = nullptr;  // replay refuses (SEMR_EINVAL) until a capture succeeds
+                rc = SEMR_ECUDA;
+            }
         } else if (g) {
             cudaGraphDestroy(g);
         }
