@@ -5,10 +5,11 @@ FP64 mode, tau = 1e-3, in the launch configuration bench.py times: one plan
 with autotuned tiles, captured into a CUDA graph and replayed.
 
 Every order runs its warp-level kernel, and every snapshot's payload, summary
-and element report written by the replay equal its single launch byte for byte.  Each element-field depends only on its
-own block, J_e and tau (Sec. IV-B: the compression works element by element),
-so sampled element-fields of every snapshot are compared with an oracle run on
-just those blocks (bit-exact outside the oracle's fragile list), and
+and element report written by the replay equal its single launch byte for
+byte.  Each element-field depends only on its own block, J_e and tau
+(Sec. IV-B: the compression works element by element), so sampled
+element-fields of every snapshot are compared with an oracle run on just
+those blocks (bit-exact outside the oracle's fragile list), and
 properties that hold at any size cover every element-field: the counts are
 the masks' popcounts, the code section holds exactly their sum, every code is
 a nonzero integer with |c| <= 2/sqrt(tau), and each field report is the sum
