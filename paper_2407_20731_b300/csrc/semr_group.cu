@@ -1102,15 +1102,40 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
             vl[i] = make_float2(0.0f, 0.0f);
         }
         if (n_e <= static_cast<uint32_t>(KL)) {
-            for (uint32_t tk = 0; tk < n_e; ++tk) {
-                const int2 kv = skl[tk];
-                const int m = kv.x, pp = m % LX, qq = (m / LX) % LX, rr = m / NP;
-                const float cs = __int_as_float(kv.y) * qu;  // c 2^s', exact
-                if constexpr (DF) {
-                    // B = c 2^s' phi_q(x_j) phi_r(x_k) per pencil (pairs), then B phi_p(x_i) at each point
+            // u~(i) = sum over kept modes of B phi_p(x_i), B = c 2^s' phi_q(x_j) phi_r(x_k) per pencil
+            if constexpr (DF) {
+                // Two passes over the kept list: the modes with p = 0 (phi_0 is constant along the
+                // pencil; most kept modes have p = 0) give one pair per pencil that starts every
+                // point, and each other mode adds B phi_p(x_i) at the LX points
+                auto bcoef = [&](int2 kv) -> p2 {  // B of both pencils as pairs
+                    const int qq = (kv.x / LX) % LX, rr = kv.x / NP;
+                    const float cs = __int_as_float(kv.y) * qu;  // c 2^s', exact
                     const f2 b0 = df_mulf(df_mul({sPh[j0 * LX + qq], sPl[j0 * LX + qq]}, {sPh[k0 * LX + rr], sPl[k0 * LX + rr]}), cs);
                     const f2 b1 = df_mulf(df_mul({sPh[j1 * LX + qq], sPl[j1 * LX + qq]}, {sPh[k1 * LX + rr], sPl[k1 * LX + rr]}), cs);
-                    const p2 B = {make_float2(b0.h, b1.h), make_float2(b0.l, b1.l)};
+                    return {make_float2(b0.h, b1.h), make_float2(b0.l, b1.l)};
+                };
+                p2 c0 = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};  // sum of B over the p = 0 modes
+                for (uint32_t tk = 0; tk < n_e; ++tk) {
+                    const int2 kv = skl[tk];
+                    if (kv.x % LX != 0) continue;
+                    const p2 B = bcoef(kv);
+                    const p2 sm = two_sum2(c0.h, B.h);
+                    c0 = fast_two_sum2(sm.h, f2add(sm.l, f2add(c0.l, B.l)));
+                }
+                {  // times phi_0, the same at every point
+                    p2 v0 = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+                    df_fma_acc2(v0, c0, {f2dup(sPTh[0]), f2dup(sPTl[0])});
+#pragma unroll
+                    for (int i = 0; i < LX; ++i) {
+                        vh[i] = v0.h;
+                        vl[i] = v0.l;
+                    }
+                }
+                for (uint32_t tk = 0; tk < n_e; ++tk) {
+                    const int2 kv = skl[tk];
+                    const int pp = kv.x % LX;
+                    if (pp == 0) continue;
+                    const p2 B = bcoef(kv);
 #pragma unroll
                     for (int i = 0; i < LX; ++i) {
                         p2 acc = {vh[i], vl[i]};
@@ -1118,19 +1143,22 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
                         vh[i] = acc.h;
                         vl[i] = acc.l;
                     }
-                } else {
-                    const float2 B = make_float2(cs * sPh[j0 * LX + qq] * sPh[k0 * LX + rr],
-                                                 cs * sPh[j1 * LX + qq] * sPh[k1 * LX + rr]);
-#pragma unroll
-                    for (int i = 0; i < LX; ++i) vh[i] = f2fma(B, f2dup(sPTh[pp * LX + i]), vh[i]);
                 }
-            }
-            if constexpr (DF) {
 #pragma unroll
                 for (int i = 0; i < LX; ++i) {
                     const p2 nn = df_norm2({vh[i], vl[i]});
                     vh[i] = nn.h;
                     vl[i] = nn.l;
+                }
+            } else {  // one pass: the FP32 form is faster without the p = 0 split
+                for (uint32_t tk = 0; tk < n_e; ++tk) {
+                    const int2 kv = skl[tk];
+                    const int m = kv.x, pp = m % LX, qq = (m / LX) % LX, rr = m / NP;
+                    const float cs = __int_as_float(kv.y) * qu;  // c 2^s', exact
+                    const float2 B = make_float2(cs * sPh[j0 * LX + qq] * sPh[k0 * LX + rr],
+                                                 cs * sPh[j1 * LX + qq] * sPh[k1 * LX + rr]);
+#pragma unroll
+                    for (int i = 0; i < LX; ++i) vh[i] = f2fma(B, f2dup(sPTh[pp * LX + i]), vh[i]);
                 }
             }
         } else {
