@@ -1107,12 +1107,17 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
                 // Two passes over the kept list: the modes with p = 0 (phi_0 is constant along the
                 // pencil; most kept modes have p = 0) give one pair per pencil that starts every
                 // point, and each other mode adds B phi_p(x_i) at the LX points
-                auto bcoef = [&](int2 kv) -> p2 {  // B of both pencils as pairs
+                auto bcoef = [&](int2 kv) -> p2 {  // B of both pencils as packed pairs
                     const int qq = (kv.x / LX) % LX, rr = kv.x / NP;
-                    const float cs = __int_as_float(kv.y) * qu;  // c 2^s', exact
-                    const f2 b0 = df_mulf(df_mul({sPh[j0 * LX + qq], sPl[j0 * LX + qq]}, {sPh[k0 * LX + rr], sPl[k0 * LX + rr]}), cs);
-                    const f2 b1 = df_mulf(df_mul({sPh[j1 * LX + qq], sPl[j1 * LX + qq]}, {sPh[k1 * LX + rr], sPl[k1 * LX + rr]}), cs);
-                    return {make_float2(b0.h, b1.h), make_float2(b0.l, b1.l)};
+                    const float2 cs = f2dup(__int_as_float(kv.y) * qu);  // c 2^s', exact
+                    const float2 fjh = make_float2(sPh[j0 * LX + qq], sPh[j1 * LX + qq]);
+                    const float2 fjl = make_float2(sPl[j0 * LX + qq], sPl[j1 * LX + qq]);
+                    const float2 fkh = make_float2(sPh[k0 * LX + rr], sPh[k1 * LX + rr]);
+                    const float2 fkl = make_float2(sPl[k0 * LX + rr], sPl[k1 * LX + rr]);
+                    const float2 ph = f2mul(fjh, fkh);
+                    const float2 pl = f2add(f2fma(fjh, fkh, f2neg(ph)), f2fma(fjh, fkl, f2mul(fjl, fkh)));
+                    const float2 bh = f2mul(ph, cs);
+                    return {bh, f2fma(pl, cs, f2fma(ph, cs, f2neg(bh)))};
                 };
                 p2 c0 = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};  // sum of B over the p = 0 modes
                 for (uint32_t tk = 0; tk < n_e; ++tk) {
