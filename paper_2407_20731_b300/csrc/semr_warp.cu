@@ -1120,22 +1120,25 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
         if (staged) atop += n_e;
         __syncwarp();
 
-        // ---- reconstruction u~ of the lane's nodal pencils (both packed; pairs in FP64 mode)
+        // ---- reconstruction of the lane's nodal pencils (both packed).  FP64 mode accumulates
+        // d = u - u~ in pairs: the accumulators start at u and every kept mode is subtracted, so the
+        // errors read d directly (a requested u~ is written as u - d in FP64 below); the FP32 form
+        // accumulates u~
         float2 vh[8], vl[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            vh[i] = make_float2(0.0f, 0.0f);
-            vl[i] = make_float2(0.0f, 0.0f);
+            vh[i] = DF ? uh[i] : make_float2(0.0f, 0.0f);
+            vl[i] = DF ? ul[i] : make_float2(0.0f, 0.0f);
         }
         if (n_e <= static_cast<uint32_t>(wsparse<DF>())) {
             if constexpr (DF) {
-                // u~(i) = sum over kept modes of B phi_p(x_i), B = c 2^s phi_q(x_j) phi_r(x_k) per pencil,
-                // both pencils packed.  Two passes over the kept list: the modes with p = 0 (phi_0 is
-                // constant along the pencil) give one pair per pencil that starts every point; each
-                // other mode adds B phi_p(x_i) at the eight points
+                // d(i) = u(i) + sum over kept modes of B phi_p(x_i), B = -c 2^s phi_q(x_j) phi_r(x_k) per
+                // pencil, both pencils packed.  Two passes over the kept list: the modes with p = 0
+                // (phi_0 is constant along the pencil) give one pair per pencil added to every point;
+                // each other mode adds B phi_p(x_i) at the eight points
                 auto coef = [&](int2 kv) -> p2 {  // B of both pencils (k0, k0 + 4) as packed pairs
                     const int qq = (kv.x >> 3) & 7, rr = kv.x >> 6;
-                    const float2 cs = f2dup(__int_as_float(kv.y) * qu);  // c 2^s, exact
+                    const float2 cs = f2dup(-(__int_as_float(kv.y) * qu));  // -c 2^s, exact
                     const float2 fjh = f2dup(sPTh[qq * 8 + j]), fjl = f2dup(sPTl[qq * 8 + j]);
                     const float2 frh = make_float2(sPTh[rr * 8 + k0], sPTh[rr * 8 + k0 + 4]);
                     const float2 frl = make_float2(sPTl[rr * 8 + k0], sPTl[rr * 8 + k0 + 4]);
@@ -1158,8 +1161,9 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
                     df_fma_acc2(v0, c0, ph0);
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        vh[i] = v0.h;
-                        vl[i] = v0.l;
+                        const p2 sm = two_sum2(vh[i], v0.h);
+                        vh[i] = sm.h;
+                        vl[i] = f2add(vl[i], f2add(sm.l, v0.l));
                     }
                 }
                 for (uint32_t tk = 0; tk < n_e; ++tk) {
@@ -1214,8 +1218,9 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const float2 v0 = tb2[lane * 9 + i], v1 = tb2[(lane + 32) * 9 + i];
-                vh[i] = make_float2(v0.x, v1.x);
-                vl[i] = make_float2(v0.y, v1.y);
+                const p2 d = df_sub2({vh[i], vl[i]}, {make_float2(v0.x, v1.x), make_float2(v0.y, v1.y)});
+                vh[i] = d.h;
+                vl[i] = d.l;
             }
             __syncwarp();
         } else {
@@ -1231,14 +1236,14 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
             __syncwarp();
         }
 
-        // ---- errors of the lane's points: e2 = sum w (u - u~)^2, Linf = max |u - u~|
+        // ---- errors of the lane's points: e2 = sum w d^2, Linf = max |d|, d = u - u~
         f2 e2;
         float lh = 0.0f, ll = 0.0f;  // Linf as a pair (|dh| first, then the signed low word)
         if constexpr (DF) {
             p2 ep = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                const p2 d = df_sub2({uh[i], ul[i]}, {vh[i], vl[i]});
+                const p2 d = {vh[i], vl[i]};
                 const float4 w = sWq4[i * 32 + lane];
                 const float2 ph = f2mul(d.h, d.h);
                 const float2 pl = f2fma(d.h, f2add(d.l, d.l), f2fma(d.h, d.h, f2neg(ph)));
@@ -1254,7 +1259,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
             if (lh == LH) {
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                    const p2 d = df_sub2({uh[i], ul[i]}, {vh[i], vl[i]});
+                    const p2 d = {vh[i], vl[i]};
                     if (fabsf(d.h.x) == LH)
                         ll = fmaxf(ll, __uint_as_float(__float_as_uint(d.l.x) ^ (__float_as_uint(d.h.x) & 0x80000000u)));
                     if (fabsf(d.h.y) == LH)
@@ -1279,17 +1284,24 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? 4 : 6)
             e2 = {warp_sum_f(fmaf(ep.x, wjk.x, ep.y * wjk.y)), 0.0f};
             lh = warp_max_nonneg(dm);
         }
-        if (p.write_recon && p.recon[f] && eok) {  // u~ = u~' 2^ke (exact)
-            const double sc = pow2d(s_res[il].ke);
+        if (p.write_recon && p.recon[f] && eok) {  // FP64 mode: u~ = u - d' 2^ke, u reread from global
+            const double sc = pow2d(s_res[il].ke);     // memory; the FP32 form: u~ = u~' 2^ke (exact)
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
-                double2* dst = reinterpret_cast<double2*>(p.recon[f] + static_cast<uint64_t>(e) * WN3 + (lane + 32 * s) * 8);
+                const uint64_t o = static_cast<uint64_t>(e) * WN3 + (lane + 32 * s) * 8;
+                double2* dst = reinterpret_cast<double2*>(p.recon[f] + o);
 #pragma unroll
                 for (int i = 0; i < 8; i += 2) {
                     const float h0 = s ? vh[i].y : vh[i].x, l0 = s ? vl[i].y : vl[i].x;
                     const float h1 = s ? vh[i + 1].y : vh[i + 1].x, l1 = s ? vl[i + 1].y : vl[i + 1].x;
-                    dst[i / 2] = make_double2((static_cast<double>(h0) + static_cast<double>(l0)) * sc,
-                                              (static_cast<double>(h1) + static_cast<double>(l1)) * sc);
+                    const double2 v = make_double2((static_cast<double>(h0) + static_cast<double>(l0)) * sc,
+                                                   (static_cast<double>(h1) + static_cast<double>(l1)) * sc);
+                    if constexpr (DF) {
+                        const double2 u = reinterpret_cast<const double2*>(p.fields[f] + o)[i / 2];
+                        dst[i / 2] = make_double2(u.x - v.x, u.y - v.y);
+                    } else {
+                        dst[i / 2] = v;
+                    }
                 }
             }
         }
