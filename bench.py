@@ -47,6 +47,7 @@ CUMULATIVE_SOURCES = KERNEL_SOURCES
 GROUP_SOURCES = [_CSRC + "semr_group.cu", _CSRC + "semr_warp_common.cuh", _CSRC + "semr_device.cuh",
                  _CSRC + "semr_internal.h"]
 SLICE_SOURCES = [_CSRC + "semr_slice.cu", _CSRC + "semr_internal.h"]
+NATIVE_SOURCES = [_CSRC + "semr_kernels.cu", _CSRC + "semr_device.cuh", _CSRC + "semr_internal.h"]
 # FP64 pipe of B300, nominal (the FP32 pipes run ~50x faster; FP64 mode runs on them)
 FP64_PIPE_TFLOPS_NOMINAL = 1.25
 
@@ -58,7 +59,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["semr", "reference"], default="semr")
     ap.add_argument("--tau", type=float, default=1e-3)
-    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "fp64-native"], default="fp64",
+                    help="fp64-native: the hardware-FP64 cross-check kernel (profiling it)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-extras", action="store_true", help="skip the per-tau and precision-form extras")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
@@ -75,10 +77,10 @@ def parse_args():
 
 
 def kernel_source_hash(cumulative: bool = False, kernel: str = "warp") -> str:
-    """Short hash of the sources of one kernel family ("warp", "group" or "slice"); a profile
+    """Short hash of the sources of one kernel family ("warp", "group", "slice" or "native"); a profile
     summary records it, so a summary whose kernel has changed since its capture can be told."""
     srcs = {"warp": CUMULATIVE_SOURCES if cumulative else KERNEL_SOURCES, "group": GROUP_SOURCES,
-            "slice": SLICE_SOURCES}[kernel]
+            "slice": SLICE_SOURCES, "native": NATIVE_SOURCES}[kernel]
     h = hashlib.sha256()
     for rel in srcs:
         with open(os.path.join(ROOT, rel), "rb") as f:
@@ -308,7 +310,7 @@ def run_semr(args):
 
     world, rank, local = dist_setup(args)
     dev = torch.device("cuda", local if world > 1 else 0)
-    prec = semr.SEMR_FP64 if args.precision == "fp64" else semr.SEMR_FP32
+    prec = {"fp64": semr.SEMR_FP64, "fp32": semr.SEMR_FP32, "fp64-native": semr.SEMR_FP64_NATIVE}[args.precision]
     fields, jac = make_snapshot(rank, dev)
     E = N_SIDE ** 3
     flist = [fields[i] for i in range(N_FIELDS)]
@@ -351,10 +353,11 @@ def run_semr(args):
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "peak_source": f"{peaks['source']} (MEASURED_PEAKS hbm_gbs, copy)",
-                "kernel": ("reduce_warp_kernel<" if LX == 8 else
-                           f"reduce_group_kernel<{LX}, " if LX in (6, 10) else f"reduce_fast_kernel<{LX}, ")
-                          + ('FP64 mode' if prec == semr.SEMR_FP64 else 'FP32')
-                          + (", cumulative" if args.cumulative else "") + ">",
+                "kernel": (f"reduce_kernel<{LX}, double>" if prec == semr.SEMR_FP64_NATIVE else
+                           ("reduce_warp_kernel<" if LX == 8 else
+                            f"reduce_group_kernel<{LX}, " if LX in (6, 10) else f"reduce_fast_kernel<{LX}, ")
+                           + ('FP64 mode' if prec == semr.SEMR_FP64 else 'FP32')
+                           + (", cumulative" if args.cumulative else "") + ">"),
                 "kernel_ms": round(kernel_ms, 4), "algorithmic_bytes_per_launch": algo}
     flops = algorithmic_flops(E, N_FIELDS)
     roofline["alu"] = {"algorithmic_flops_per_launch": flops,
@@ -810,12 +813,13 @@ def emit(args, rank, world, value, ms_step, prec, roofline, cpu, e2e, clk, sm, e
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64" if prec == semr.SEMR_FP64 else "f32",
+                "vs_baseline": None, "dtype": "f32" if prec == semr.SEMR_FP32 else "f64",
                 "data": "synthetic (seeded 16-mode |k|^-5/3 spectra + N(0,1e-6) noise, J~U[0.5,2])",
                 "config": workload_config(args, world), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 # one fused kernel per step at lx = 6, 8 and 10 (the warp-level kernels finalize in
-                # their last CTA, both truncations); other lx run the CTA kernel and its finalize
-                "gpu_launches": (1 if LX in (6, 8, 10) else 2) * args.steps, "clocks": clk,
+                # their last CTA, both truncations); other lx, and the hardware-FP64 cross-check
+                # kernel, run a CTA kernel and its finalize
+                "gpu_launches": (1 if LX in (6, 8, 10) and prec != semr.SEMR_FP64_NATIVE else 2) * args.steps, "clocks": clk,
                 "result": {"cr": round(sm.cr, 5), "payload_bytes": int(sm.payload_bytes),
                            "l2_rel": [round(sm.field[i].l2_rel, 6) for i in range(N_FIELDS)],
                            "linf_rel": [round(sm.field[i].linf_rel, 6) for i in range(N_FIELDS)]},
@@ -869,7 +873,7 @@ def main():
     if args.batched_only:
         import torch
         torch.cuda.set_device(0)
-        prec = 0 if args.precision == "fp64" else 1
+        prec = {"fp64": 0, "fp32": 1, "fp64-native": 2}[args.precision]
         print(json.dumps({"batched": run_batched(torch.device("cuda", 0), prec)}), flush=True)
         return
     if args.slice_only:
