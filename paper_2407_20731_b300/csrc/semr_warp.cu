@@ -462,11 +462,11 @@ __device__ __noinline__ void dense_inverse_pairs(float2* buf, const float* Ph, c
 // BATCH = false: one reduction, parameters and tensor maps in A.  BATCH = true: the
 // work queue q of several lx = 8 reductions (each with its own descriptor, payload
 // and scratch; their tensor maps in global memory at q.tmaps, field_base order).
-// CTAs per SM the register budget aims at: FP64 mode 3 (168 registers, no spills) with threshold
-// truncation, 4 (128) with the cumulative variant, whose larger code runs better with more warps;
-// the FP32 form 6 (80).
+// CTAs per SM the register budget aims at (measured): FP64 mode 3 (168 registers, no spills) with
+// threshold truncation and 4 (128) with the cumulative variant, whose larger code runs better with
+// more warps; the FP32 form 6 (80) and 5 (96, no spills) with the cumulative variant.
 template <int MODE, bool BATCH, bool CUM = false>
-__global__ void __launch_bounds__(WPB * 32, MODE ? (CUM ? 4 : 3) : 6)
+__global__ void __launch_bounds__(WPB * 32, MODE ? (CUM ? 4 : 3) : (CUM ? 5 : 6))
     reduce_warp_kernel(const __grid_constant__ WArgs A, const BatchQueue q) {
     constexpr bool DF = MODE != 0;
     using SM = WSmem<DF>;
