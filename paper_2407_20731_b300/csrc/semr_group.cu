@@ -438,16 +438,16 @@ __device__ __noinline__ uint32_t g_cum_general(float* M, const float* am, uint32
     return kb;
 }
 
-template <int LX, int MODE>
-struct GOcc {  // CTAs per SM the register budget aims at
-    static constexpr int value = LX <= 6 ? (MODE ? 3 : 5) : 3;
+template <int LX, int MODE, bool CUM>
+struct GOcc {  // CTAs per SM the register budget aims at (measured)
+    static constexpr int value = LX <= 6 ? (MODE ? (CUM ? 4 : 3) : 5) : 3;
 };
 
 // BATCH = false: one reduction, parameters in A.p.  BATCH = true: the work queue q of
 // several reductions of this lx (each with its own descriptor, payload and scratch; they
 // share one code staging).
 template <int LX, int MODE, bool BATCH, bool CUM = false>
-__global__ void __launch_bounds__(GCTA, GOcc<LX, MODE>::value)
+__global__ void __launch_bounds__(GCTA, GOcc<LX, MODE, CUM>::value)
     reduce_group_kernel(const __grid_constant__ GArgs<LX> A, const BatchQueue q) {
     using C = GCfg<LX>;
     constexpr bool DF = MODE != 0;
