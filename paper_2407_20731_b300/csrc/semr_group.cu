@@ -979,11 +979,7 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE, CUM>::value)
                     kb = g_resolve<LX>(M, w0, amb, kb, p.fields[f] + static_cast<uint64_t>(e) * N3, A.tab.A64,
                                        pow2d(-ke), t, qd, qu, recomputed);
                 }
-            } else {
-#pragma unroll
-                for (int kk = 0; kk < WPW; ++kk)
-                    if (fabsf(am[kk]) >= gth) kb |= 1u << kk;
-            }
+            }  // the FP32 form ballots its threshold test directly below
         }
 
         // ---- mask words of this warp (ballots), the group's count and this warp's rank base
@@ -991,7 +987,8 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE, CUM>::value)
 #pragma unroll
         for (int kk = 0; kk < WPW; ++kk) {
             if (w0 + kk < MW) {
-                const uint32_t wv = __ballot_sync(FULL, (kb >> kk) & 1u);
+                const bool keep = (DF || CUM) ? ((kb >> kk) & 1u) != 0u : (emode == 1 && fabsf(am[kk]) >= gth);
+                const uint32_t wv = __ballot_sync(FULL, keep);
                 if (lane == 0) bm[w0 + kk] = wv;
                 cw += __popc(wv);
                 nzw |= (wv != 0u ? 1u : 0u) << kk;
