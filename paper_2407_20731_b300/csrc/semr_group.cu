@@ -99,7 +99,8 @@ struct GSmem {
     static constexpr size_t o_kl = o_bm + 4ull * ((C::MW + 3) / 4 * 4);   // kept list (mode, code)
     static constexpr size_t o_x = o_kl + 8ull * gsparse<DF>();            // exchange slots
     static constexpr size_t o_bar = o_x + 4ull * 32;
-    static constexpr size_t gbytes = (o_bar + 8 + 127) / 128 * 128;
+    static constexpr size_t o_ul = (o_bar + 8 + 15) / 16 * 16;            // FP64 mode: parked low words [LX][GT]
+    static constexpr size_t gbytes = ((DF ? o_ul + 8ull * LX * C::GT : o_bar + 8) + 127) / 128 * 128;
     // per CTA
     static constexpr size_t off_tab = C::GPC * gbytes;                    // Phi [i][p] and [p][i], hi and lo
     static constexpr size_t off_res = off_tab + 16ull * C::NP;            // GStash[TILE]
@@ -714,6 +715,26 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE, CUM>::value)
             }
         }
 
+        // FP64 mode at lx = 10 and with cumulative truncation (measured): the thread's energy partial
+        // now, and the pencils' low words parked in the group's slots until the errors need them
+        // (their registers are free in between)
+        constexpr bool PARK = DF && (LX > 6 || CUM);
+        f2 sp_e = {0.0f, 0.0f};
+        if constexpr (PARK) {
+            p2 acc = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+#pragma unroll
+            for (int i = 0; i < LX; ++i) {
+                const float2 ph = f2mul(uh[i], uh[i]);
+                const float2 pl = f2fma(uh[i], f2add(ul[i], ul[i]), f2fma(uh[i], uh[i], f2neg(ph)));
+                df_fma_acc2(acc, {A.tab.wh2[i], A.tab.wl2[i]}, {ph, pl});
+            }
+            acc = df_norm2(acc);
+            sp_e = df_add(df_mul({acc.h.x, acc.l.x}, wjk0), df_mul({acc.h.y, acc.l.y}, wjk1));
+            float2* sul = reinterpret_cast<float2*>(gsm + SM::o_ul);
+#pragma unroll
+            for (int i = 0; i < LX; ++i) sul[i * GT + g] = ul[i];
+        }
+
         // ---- forward transform: i in registers, j and k through the group's transposes
         float2 a2[LX];  // coefficient r of the modal pencils (q, p) = P0, P1
         {
@@ -754,7 +775,9 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE, CUM>::value)
         f2 S;
         {
             f2 sp = {0.0f, 0.0f};
-            if constexpr (DF) {
+            if constexpr (PARK) {
+                sp = warp_sum_pair(sp_e);
+            } else if constexpr (DF) {
                 p2 acc = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
 #pragma unroll
                 for (int i = 0; i < LX; ++i) {
@@ -1251,6 +1274,11 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE, CUM>::value)
         f2 e2;
         float lh = 0.0f, ll = 0.0f;
         if constexpr (DF) {
+            if constexpr (PARK) {
+                const float2* sul = reinterpret_cast<const float2*>(gsm + SM::o_ul);
+#pragma unroll
+                for (int ii = 0; ii < LX; ++ii) ul[ii] = sul[ii * GT + g];
+            }
             p2 acc = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
             float dm = 0.0f;
 #pragma unroll
