@@ -105,7 +105,8 @@ struct WSmem {
     static constexpr size_t o_mask = o_tb + tb_bytes;     // 16 mask words
     static constexpr size_t o_kl = o_mask + 64;           // kept list (mode, code)
     static constexpr size_t o_bar = o_kl + 8 * wsparse<DF>();
-    static constexpr size_t wbytes = o_bar + 16;
+    static constexpr size_t o_ul = (o_bar + 16 + 15) / 16 * 16;  // FP64 mode: parked low words [8][32] float2
+    static constexpr size_t wbytes = DF ? o_ul + 8 * 8 * 32 : o_bar + 16;
     static constexpr size_t bytes = off_warp + WPB * wbytes + 512;  // + alignment slack
 };
 static_assert(8 * 8 * TSK2 >= 4 * 8 * TSK, "pair buffer holds the FP32 one");
@@ -462,11 +463,11 @@ __device__ __noinline__ void dense_inverse_pairs(float2* buf, const float* Ph, c
 // BATCH = false: one reduction, parameters and tensor maps in A.  BATCH = true: the
 // work queue q of several lx = 8 reductions (each with its own descriptor, payload
 // and scratch; their tensor maps in global memory at q.tmaps, field_base order).
-// CTAs per SM the register budget aims at (measured): FP64 mode 3 (168 registers, no spills) with
-// threshold truncation and 4 (128) with the cumulative variant, whose larger code runs better with
-// more warps; the FP32 form 6 (80) and 5 (96, no spills) with the cumulative variant.
+// CTAs per SM the register budget aims at (measured): FP64 mode 4 (128 registers; the low words
+// of u parked in shared memory keep it nearly free of spills), the FP32 form 6 (80) and 5 (96, no
+// spills) with the cumulative variant.
 template <int MODE, bool BATCH, bool CUM = false>
-__global__ void __launch_bounds__(WPB * 32, MODE ? (CUM ? 4 : 3) : (CUM ? 5 : 6))
+__global__ void __launch_bounds__(WPB * 32, MODE ? 4 : (CUM ? 5 : 6))
     reduce_warp_kernel(const __grid_constant__ WArgs A, const BatchQueue q) {
     constexpr bool DF = MODE != 0;
     using SM = WSmem<DF>;
@@ -505,6 +506,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? (CUM ? 4 : 3) : (CUM ? 5 : 6)
     uint32_t* smask = reinterpret_cast<uint32_t*>(wb + SM::o_mask);
     int2* skl = reinterpret_cast<int2*>(wb + SM::o_kl);
     uint64_t* bar = reinterpret_cast<uint64_t*>(wb + SM::o_bar);
+    float2* sul = reinterpret_cast<float2*>(wb + SM::o_ul);  // FP64 mode only
     if (lane == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
@@ -710,6 +712,24 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? (CUM ? 4 : 3) : (CUM ? 5 : 6)
                 }
             }
         }
+        // ---- element energy S, FP64 mode: sum w u^2 at the nodes in pairs (Parseval's identity in
+        // nodal form), right after the split; the low words then wait in the warp's slots until the
+        // reconstruction starts from u (their registers are free in between)
+        f2 S = {0.0f, 0.0f};
+        if constexpr (DF) {
+            p2 sp = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float4 w = sWq4[i * 32 + lane];
+                const float2 ph = f2mul(uh[i], uh[i]);
+                const float2 pl = f2fma(uh[i], f2add(ul[i], ul[i]), f2fma(uh[i], uh[i], f2neg(ph)));
+                df_fma_acc2(sp, {make_float2(w.x, w.y), make_float2(w.z, w.w)}, {ph, pl});
+            }
+            sp = df_norm2(sp);
+            S = warp_sum_pair(df_add({sp.h.x, sp.l.x}, {sp.h.y, sp.l.y}));
+#pragma unroll
+            for (int i = 0; i < 8; ++i) sul[i * 32 + lane] = ul[i];
+        }
         // once every lane has consumed its loads, the stage may be refilled with this warp's
         // next element (an exact recomputation below rereads the block from global memory)
         __syncwarp();
@@ -751,21 +771,8 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? (CUM ? 4 : 3) : (CUM ? 5 : 6)
             w_fwd2(A.tab.A2, x, a2);
         }
 
-        // ---- element energy S: FP64 mode sum w u^2 at the nodes in pairs (Parseval's
-        // identity in nodal form), FP32 form sum a^2 of the coefficients
-        f2 S;
-        if constexpr (DF) {
-            p2 sp = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float4 w = sWq4[i * 32 + lane];
-                const float2 ph = f2mul(uh[i], uh[i]);
-                const float2 pl = f2fma(uh[i], f2add(ul[i], ul[i]), f2fma(uh[i], uh[i], f2neg(ph)));
-                df_fma_acc2(sp, {make_float2(w.x, w.y), make_float2(w.z, w.w)}, {ph, pl});
-            }
-            sp = df_norm2(sp);
-            S = warp_sum_pair(df_add({sp.h.x, sp.l.x}, {sp.h.y, sp.l.y}));
-        } else {
+        // ---- element energy S, FP32 form: sum a^2 of the coefficients (FP64 mode formed it above)
+        if constexpr (!DF) {
             float2 sp = make_float2(0.0f, 0.0f);
 #pragma unroll
             for (int r = 0; r < 8; ++r) sp = f2fma(a2[r], a2[r], sp);
@@ -1131,7 +1138,7 @@ __global__ void __launch_bounds__(WPB * 32, MODE ? (CUM ? 4 : 3) : (CUM ? 5 : 6)
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             vh[i] = DF ? uh[i] : make_float2(0.0f, 0.0f);
-            vl[i] = DF ? ul[i] : make_float2(0.0f, 0.0f);
+            vl[i] = DF ? sul[i * 32 + lane] : make_float2(0.0f, 0.0f);
         }
         if (n_e <= static_cast<uint32_t>(wsparse<DF>())) {
             if constexpr (DF) {
