@@ -99,8 +99,8 @@ struct GSmem {
     static constexpr size_t o_kl = o_bm + 4ull * ((C::MW + 3) / 4 * 4);   // kept list (mode, code)
     static constexpr size_t o_x = o_kl + 8ull * gsparse<DF>();            // exchange slots
     static constexpr size_t o_bar = o_x + 4ull * 32;
-    static constexpr size_t o_ul = (o_bar + 8 + 15) / 16 * 16;            // FP64 mode: parked low words [LX][GT]
-    static constexpr size_t gbytes = ((DF ? o_ul + 8ull * LX * C::GT : o_bar + 8) + 127) / 128 * 128;
+    static constexpr size_t o_ul = (o_bar + 8 + 15) / 16 * 16;            // parked words of u [LX][GT] float2
+    static constexpr size_t gbytes = (o_ul + 8ull * LX * C::GT + 127) / 128 * 128;
     // per CTA
     static constexpr size_t off_tab = C::GPC * gbytes;                    // Phi [i][p] and [p][i], hi and lo
     static constexpr size_t off_res = off_tab + 16ull * C::NP;            // GStash[TILE]
@@ -740,6 +740,11 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE, CUM>::value)
         {
             float2 y[LX];
             g_fwd2<LX>(A.tab.A2, uh, y);
+            if constexpr (!DF) {  // the FP32 form parks u until the errors
+                float2* sul = reinterpret_cast<float2*>(gsm + SM::o_ul);
+#pragma unroll
+                for (int i = 0; i < LX; ++i) sul[i * GT + g] = uh[i];
+            }
 #pragma unroll
             for (int pp = 0; pp < LX; ++pp) {
                 T[k0 * PL + j0 * LP + pp] = y[pp].x;
@@ -1310,6 +1315,11 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE, CUM>::value)
             lh = LH;
             ll = (LH == 0.0f) ? 0.0f : __uint_as_float((kmax >> 31) ? (kmax ^ 0x80000000u) : ~kmax);
         } else {
+            {
+                const float2* sul = reinterpret_cast<const float2*>(gsm + SM::o_ul);
+#pragma unroll
+                for (int ii = 0; ii < LX; ++ii) uh[ii] = sul[ii * GT + g];
+            }
             float2 acc = make_float2(0.0f, 0.0f);
             float dm = 0.0f;
 #pragma unroll
