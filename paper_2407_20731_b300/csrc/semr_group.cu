@@ -89,7 +89,7 @@ struct GStash {    // one element's results, kept until the end of its tile
 };
 static_assert(sizeof(GStash) == 32, "stash entry");
 
-template <int LX, bool DF>
+template <int LX, bool DF, bool CUM = false>
 struct GSmem {
     using C = GCfg<LX>;
     // per group
@@ -100,7 +100,9 @@ struct GSmem {
     static constexpr size_t o_x = o_kl + 8ull * gsparse<DF>();            // exchange slots
     static constexpr size_t o_bar = o_x + 4ull * 32;
     static constexpr size_t o_ul = (o_bar + 8 + 15) / 16 * 16;            // parked words of u [LX][GT] float2
-    static constexpr size_t gbytes = (o_ul + 8ull * LX * C::GT + 127) / 128 * 128;
+    static constexpr size_t o_uh = o_ul + 8ull * LX * C::GT;               // FP64 mode at lx = 10 with threshold
+    static constexpr size_t gbytes =                                       // truncation: parked high words
+        (o_uh + (DF && LX > 6 && !CUM ? 8ull * LX * C::GT : 0) + 127) / 128 * 128;
     // per CTA
     static constexpr size_t off_tab = C::GPC * gbytes;                    // Phi [i][p] and [p][i], hi and lo
     static constexpr size_t off_res = off_tab + 16ull * C::NP;            // GStash[TILE]
@@ -452,7 +454,7 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE, CUM>::value)
     reduce_group_kernel(const __grid_constant__ GArgs<LX> A, const BatchQueue q) {
     using C = GCfg<LX>;
     constexpr bool DF = MODE != 0;
-    using SM = GSmem<LX, DF>;
+    using SM = GSmem<LX, DF, CUM>;
     constexpr int N3 = C::N3, NP = C::NP, GT = C::GT, GPC = C::GPC, WPE = C::WPE, TILE = C::TILE;
     constexpr int MW = C::MW, WPW = C::WPW, MB = C::MB, LP = C::LP, PL = C::PL, TB = C::TB;
     constexpr int KL = gsparse<DF>();
@@ -719,6 +721,7 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE, CUM>::value)
         // now, and the pencils' low words parked in the group's slots until the errors need them
         // (their registers are free in between)
         constexpr bool PARK = DF && (LX > 6 || CUM);
+        constexpr bool PARKH = DF && LX > 6 && !CUM;  // and the high words (after the first contraction)
         f2 sp_e = {0.0f, 0.0f};
         if constexpr (PARK) {
             p2 acc = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
@@ -744,6 +747,10 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE, CUM>::value)
                 float2* sul = reinterpret_cast<float2*>(gsm + SM::o_ul);
 #pragma unroll
                 for (int i = 0; i < LX; ++i) sul[i * GT + g] = uh[i];
+            } else if constexpr (PARKH) {  // FP64 mode at lx = 10, threshold truncation: the high words too
+                float2* suh = reinterpret_cast<float2*>(gsm + SM::o_uh);
+#pragma unroll
+                for (int i = 0; i < LX; ++i) suh[i * GT + g] = uh[i];
             }
 #pragma unroll
             for (int pp = 0; pp < LX; ++pp) {
@@ -1284,6 +1291,11 @@ __global__ void __launch_bounds__(GCTA, GOcc<LX, MODE, CUM>::value)
 #pragma unroll
                 for (int ii = 0; ii < LX; ++ii) ul[ii] = sul[ii * GT + g];
             }
+            if constexpr (PARKH) {
+                const float2* suh = reinterpret_cast<const float2*>(gsm + SM::o_uh);
+#pragma unroll
+                for (int ii = 0; ii < LX; ++ii) uh[ii] = suh[ii * GT + g];
+            }
             p2 acc = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
             float dm = 0.0f;
 #pragma unroll
@@ -1537,7 +1549,7 @@ GTables<LX> make_gtables() {
 // Launch of one reduction (q empty) or of a batch queue (BATCH; p unused but for stage_ctas).
 template <int LX, int MODE, bool BATCH, bool CUM = false>
 int launch_group_mode(const LaunchParams& p, const BatchQueue& q, uint64_t stage_ctas, void* stream) {
-    using SM = GSmem<LX, MODE != 0>;
+    using SM = GSmem<LX, MODE != 0, CUM>;
     GArgs<LX> a;
     std::memset(&a, 0, sizeof(a));
     a.tab = make_gtables<LX>();
